@@ -1,0 +1,257 @@
+"""Plain FP64 CPU oracle of the preconditioned time-domain FWI gradient.
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package. The
+product path (``paper_1406_1864_gb300``) never imports it and shares no code
+with it; both receive their inputs from the seeded generators in
+``paper_1406_1864_gb300.workloads``, which hold none of the method's arithmetic.
+
+The wave propagation, adjoint imaging and Born operator are plain C loops in
+``fwi_oracle.c`` (double precision, OpenMP over shots). This module holds the
+parts that are clearest in numpy, each following the paper:
+
+* OLS misfit J = 1/2 sum_s sum_r sum_t (u - d)^2 and its adjoint source, the
+  residual (Sec. 2, first misfit);
+* the time-integral misfit J = 1/2 || int_0^t (u - d) dtau ||^2 (Eq. 2), with
+  the integral read as the inclusive rectangle rule dt * sum_{k<=n}, and its
+  adjoint source C^T C r (reverse cumulative sum);
+* the gradient preconditioning of Sec. 3 / Fig. 5: g / (P + eps max P) with P the
+  shot illumination (Eq. 1) or the offset-Hessian diagonal summed over offsets.
+
+Parity pins: none of these functions is trusted on its own; tests/test_oracle_*
+check them against closed forms (2-D Green's function), adjoint dot products,
+central finite differences, the cumulative-source identity of Sec. 2 and brute
+force sums over dumped wavefields. The relation of Eq. 3 (the integral-misfit
+gradient as -sum int u v dt) holds only in the continuum and is checked loosely:
+parity unpinned for that form.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fwi_oracle.c")
+_LIB = os.path.join(_HERE, "libfwi_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP) into oracle/libfwi_oracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i, d, p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        grid = [i, i, i, i, i, d, d, i, d, d]
+        lib.oracle_forward.argtypes = grid + [p, i, p, p, i, p, p, p, i, i, p, p, i, i]
+        lib.oracle_gradient.argtypes = grid + [p, i, p, p, i, p, p, p, p, p, i]
+        lib.oracle_born.argtypes = grid + [p, p, i, p, p, i, p, p, i]
+        lib.oracle_eta.argtypes = [i, i, i, i, i, d, d, d, p]
+        for f in (lib.oracle_forward, lib.oracle_gradient, lib.oracle_born, lib.oracle_eta):
+            f.restype = i
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Grid:
+    """Discretisation of one model: physical nz x ny x nx (ny=1 in 2-D)."""
+    ndim: int
+    nz: int
+    ny: int
+    nx: int
+    dx: float
+    dt: float
+    nt: int
+    sponge: int = 20
+    vref: float = 3000.0
+    refl: float = 0.05
+
+    @classmethod
+    def of(cls, prob) -> "Grid":
+        return cls(prob.ndim, prob.nz, prob.ny, prob.nx, prob.dx, prob.dt, prob.nt,
+                   prob.sponge, prob.vref, prob.refl)
+
+    def args(self):
+        return (self.ndim, self.nz, self.ny, self.nx, self.sponge, float(self.dx),
+                float(self.dt), self.nt, float(self.vref), float(self.refl))
+
+    @property
+    def padded_shape(self):
+        P = self.sponge
+        nyp = self.ny + 2 * P if self.ndim == 3 else 1
+        return (self.nz + 2 * P, nyp, self.nx + 2 * P)
+
+
+def _geom(src, rec, wav, nt):
+    src = np.ascontiguousarray(src, dtype=np.int32).reshape(-1, 3)
+    ns = src.shape[0]
+    rec = np.ascontiguousarray(rec, dtype=np.int32).reshape(ns, -1, 3)
+    wav = np.ascontiguousarray(wav, dtype=np.float64).reshape(ns, nt)
+    return src, rec, wav, ns, rec.shape[1]
+
+
+def _check(rc, name):
+    if rc != 0:
+        raise ValueError(f"{name}: invalid arguments (code {rc})")
+
+
+def forward(grid: Grid, v, src, rec, wav, *, illum=False, illum_utt=False, hmax=None,
+            dump_shot=None, nthreads=0):
+    """Forward modelling of every shot.
+
+    Returns a dict with ``seis`` [ns, nt, nrec] and, on request, ``illum``
+    [nz, ny, nx] (Eq. 1 as sum_s sum_n u^2 dt, or u_tt^2 dt), ``offh``
+    [hmax+1, nz, ny, nx] (offset-Hessian diagonal, Sec. 3) and ``dump``
+    [nt, nzp, nyp, nxp] (every time level of one shot, padded grid).
+    """
+    lib = _load()
+    src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    seis = np.zeros((ns, grid.nt, nrec))
+    out = {"seis": seis}
+    il = np.zeros((grid.nz, grid.ny, grid.nx)) if illum else None
+    oh = np.zeros((hmax + 1, grid.nz, grid.ny, grid.nx)) if hmax is not None else None
+    dump = np.zeros((grid.nt,) + grid.padded_shape) if dump_shot is not None else None
+    rc = lib.oracle_forward(*grid.args(), _ptr(v), ns, _ptr(src), _ptr(wav), nrec, _ptr(rec),
+                            _ptr(seis), _ptr(il), int(illum_utt), int(hmax or 0), _ptr(oh),
+                            _ptr(dump), int(dump_shot or 0), int(nthreads))
+    _check(rc, "oracle_forward")
+    if il is not None:
+        out["illum"] = il
+    if oh is not None:
+        out["offh"] = oh
+    if dump is not None:
+        out["dump"] = dump
+    return out
+
+
+def gradient_for_adjoint_source(grid: Grid, v, src, rec, wav, adj, *, want_pad=False,
+                                want_psi_src=False, nthreads=0):
+    """Gradient w.r.t. the physical velocity of sum a^n(r) d^n(r) for a given
+    adjoint source ``adj`` [ns, nt, nrec] (Sec. 2 zero-lag cross-correlation,
+    as the exact derivative of the discrete scheme). Returns a dict with
+    ``grad`` [nz, ny, nx], and optionally ``grad_pad`` (padded, before the
+    fold) and ``psi_src`` [ns, nt] (adjoint of the source-to-trace map)."""
+    lib = _load()
+    src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    adj = np.ascontiguousarray(adj, dtype=np.float64).reshape(ns, grid.nt, nrec)
+    grad = np.zeros((grid.nz, grid.ny, grid.nx))
+    gpad = np.zeros(grid.padded_shape) if want_pad else None
+    psi = np.zeros((ns, grid.nt)) if want_psi_src else None
+    rc = lib.oracle_gradient(*grid.args(), _ptr(v), ns, _ptr(src), _ptr(wav), nrec, _ptr(rec),
+                             _ptr(adj), _ptr(grad), _ptr(gpad), _ptr(psi), int(nthreads))
+    _check(rc, "oracle_gradient")
+    out = {"grad": grad}
+    if gpad is not None:
+        out["grad_pad"] = gpad
+    if psi is not None:
+        out["psi_src"] = psi
+    return out
+
+
+def born(grid: Grid, v, dv, src, rec, wav, nthreads=0):
+    """Born modelling, Eq. 4: traces' derivative along the velocity change dv."""
+    lib = _load()
+    src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    dv = np.ascontiguousarray(dv, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    dseis = np.zeros((ns, grid.nt, nrec))
+    rc = lib.oracle_born(*grid.args(), _ptr(v), _ptr(dv), ns, _ptr(src), _ptr(wav), nrec,
+                         _ptr(rec), _ptr(dseis), int(nthreads))
+    _check(rc, "oracle_born")
+    return dseis
+
+
+def eta(grid: Grid):
+    """Sponge damping profile on the padded grid."""
+    lib = _load()
+    out = np.zeros(grid.padded_shape)
+    rc = lib.oracle_eta(grid.ndim, grid.nz, grid.ny, grid.nx, grid.sponge, float(grid.dx),
+                        float(grid.vref), float(grid.refl), _ptr(out))
+    _check(rc, "oracle_eta")
+    return out
+
+
+# ---------------------------------------------------------------- misfits (Sec. 2)
+
+def misfit_ols(seis, d_obs):
+    """OLS misfit with W_d = I (Sec. 2): J = 1/2 sum r^2, r = u - d.
+    Returns (J, adjoint source dJ/du = r)."""
+    r = np.asarray(seis, dtype=np.float64) - np.asarray(d_obs, dtype=np.float64)
+    return 0.5 * float(np.sum(r * r)), r
+
+
+def time_integral(r, dt):
+    """(C r)^n = dt * sum_{k<=n} r^k along the time axis (axis 1) -- the
+    data weighting W_d u = int_0^t u dtau of Eq. 2, inclusive rectangle rule."""
+    return dt * np.cumsum(r, axis=1)
+
+
+def time_integral_adjoint(y, dt):
+    """(C^T y)^n = dt * sum_{k>=n} y^k: the transpose of time_integral."""
+    return dt * np.cumsum(y[:, ::-1, :], axis=1)[:, ::-1, :]
+
+
+def misfit_time_integral(seis, d_obs, dt):
+    """Time-integral residual misfit, Eq. 2: J = 1/2 || C (u - d) ||^2.
+    Returns (J, adjoint source C^T C (u - d))."""
+    r = np.asarray(seis, dtype=np.float64) - np.asarray(d_obs, dtype=np.float64)
+    y = time_integral(r, dt)
+    return 0.5 * float(np.sum(y * y)), time_integral_adjoint(y, dt)
+
+
+# ------------------------------------------------------- preconditioning (Sec. 3)
+
+def offset_scale(offh):
+    """Per-point scale from the offset-Hessian diagonal H(x, h), h = 0..hmax:
+    sum over |h| <= hmax of |H(x, h)| (H is even in h)."""
+    offh = np.asarray(offh, dtype=np.float64)
+    return np.abs(offh[0]) + 2.0 * np.sum(np.abs(offh[1:]), axis=0)
+
+
+def precondition(grad, P, eps=1e-3):
+    """Diagonal scaling of the gradient: g / (P + eps * max P)."""
+    P = np.asarray(P, dtype=np.float64)
+    return np.asarray(grad, dtype=np.float64) / (P + eps * P.max())
+
+
+def fwi_gradient(grid: Grid, v, src, rec, wav, d_obs, *, misfit="ols", hmax=None,
+                 illum_utt=False, eps=1e-3, nthreads=0):
+    """The whole preconditioned gradient of one model: forward modelling,
+    misfit, adjoint source, adjoint imaging, illumination / offset-Hessian
+    preconditioners. Returns a dict of float64 arrays and the misfit J."""
+    fw = forward(grid, v, src, rec, wav, illum=True, illum_utt=illum_utt, hmax=hmax,
+                 nthreads=nthreads)
+    if misfit == "ols":
+        J, adj = misfit_ols(fw["seis"], d_obs)
+    elif misfit == "integral":
+        J, adj = misfit_time_integral(fw["seis"], d_obs, grid.dt)
+    else:
+        raise ValueError(misfit)
+    g = gradient_for_adjoint_source(grid, v, src, rec, wav, adj, nthreads=nthreads)["grad"]
+    out = {"seis": fw["seis"], "J": J, "grad": g, "illum": fw["illum"],
+           "grad_pre_illum": precondition(g, fw["illum"], eps)}
+    if hmax is not None:
+        out["offh"] = fw["offh"]
+        out["grad_pre_offset"] = precondition(g, offset_scale(fw["offh"]), eps)
+    return out

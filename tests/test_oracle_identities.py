@@ -1,0 +1,109 @@
+"""Pins of the oracle's accumulations and of Sec. 2's time-integral wavefield.
+
+* U(x,t) = int_0^t u dtau satisfies the same wave equation with the integrated
+  source H(t) * f(t) (Sec. 2). For the discrete, linear, time-invariant scheme
+  this is exact: modelling with dt*cumsum(f) gives dt*cumsum of the traces.
+* The pseudo-diagonal Hessian of Eq. 1 in its time-domain form, the summed
+  squared forward wavefield, equals a brute-force sum over dumped wavefields;
+  the omega^4-weighted form equals the same sum over the second time
+  difference (Parseval).
+* The offset-Hessian diagonal (Sec. 3) equals a brute-force sum of shifted
+  products, reduces to the illumination at h = 0, and obeys Cauchy-Schwarz.
+* The time-integral misfit's gradient is a low-passed version of the OLS
+  gradient (Sec. 2, after Eq. 3): its wavenumber centroid is lower.
+"""
+import numpy as np
+
+from paper_1406_1864_gb300 import workloads as W
+
+
+def test_cumulative_source_identity(oracle_mod):
+    p = W.dipping(nz=30, nx=40, dx=10.0, dt=1e-3, nt=300, ns=2, nrec=20, rec_step=2, f0=15.0,
+                  sponge=8, seed=1)
+    g = oracle_mod.Grid.of(p)
+    w = p.wavelet.astype(np.float64)
+    s = oracle_mod.forward(g, p.v_true, p.src, p.rec, w)["seis"]
+    S = oracle_mod.forward(g, p.v_true, p.src, p.rec, p.dt * np.cumsum(w, axis=1))["seis"]
+    ref = p.dt * np.cumsum(s, axis=1)
+    assert np.linalg.norm(S - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def _single_shot(nt=220, nz=26, nx=36, sponge=6):
+    return W.dipping(nz=nz, nx=nx, dx=10.0, dt=1e-3, nt=nt, ns=1, nrec=10, rec_step=3, f0=15.0,
+                     sponge=sponge, seed=4)
+
+
+def test_illumination_brute_force(oracle_mod):
+    p = _single_shot()
+    g = oracle_mod.Grid.of(p)
+    P = p.sponge
+    out = oracle_mod.forward(g, p.v_init, p.src, p.rec, p.wavelet, illum=True, hmax=5, dump_shot=0)
+    u = out["dump"][:, :, 0, :]                     # [nt, nzp, nxp]
+    phys = u[:, P:P + p.nz, P:P + p.nx]
+    I = np.sum(phys ** 2, axis=0) * p.dt
+    assert np.allclose(out["illum"][:, 0, :], I, rtol=1e-12, atol=0)
+    # offset-Hessian diagonal by explicit shifts (zero outside the padded grid)
+    for h in range(6):
+        up = np.zeros_like(u)
+        um = np.zeros_like(u)
+        up[:, :, :u.shape[2] - h] = u[:, :, h:]            # u(x + h)
+        um[:, :, h:] = u[:, :, :u.shape[2] - h]            # u(x - h)
+        H = np.sum(up * um, axis=0)[P:P + p.nz, P:P + p.nx] * p.dt
+        assert np.allclose(out["offh"][h, :, 0, :], H, rtol=1e-12, atol=1e-30)
+    # h = 0 is Eq. 1's pseudo-diagonal Hessian
+    assert np.array_equal(out["offh"][0], out["illum"])
+    # Cauchy-Schwarz: |H(x,h)| <= sqrt(I(x+h) I(x-h)), I on the padded grid
+    Ipad = np.sum(u ** 2, axis=0) * p.dt
+    for h in range(1, 6):
+        Ip = np.zeros_like(Ipad)
+        Im = np.zeros_like(Ipad)
+        Ip[:, :Ipad.shape[1] - h] = Ipad[:, h:]
+        Im[:, h:] = Ipad[:, :Ipad.shape[1] - h]
+        bound = np.sqrt(Ip * Im)[P:P + p.nz, P:P + p.nx]
+        assert np.all(np.abs(out["offh"][h, :, 0, :]) <= bound * (1 + 1e-12) + 1e-300)
+
+
+def test_illumination_utt_form(oracle_mod):
+    p = _single_shot()
+    g = oracle_mod.Grid.of(p)
+    P = p.sponge
+    out = oracle_mod.forward(g, p.v_init, p.src, p.rec, p.wavelet, illum=True, illum_utt=True,
+                             dump_shot=0)
+    u = out["dump"][:, P:P + p.nz, 0, P:P + p.nx]
+    um1 = np.concatenate([np.zeros_like(u[:1]), u[:-1]])
+    utt = (u[1:] - 2 * u[:-1] + um1[:-1]) / p.dt ** 2
+    ref = np.sum(utt ** 2, axis=0) * p.dt
+    assert np.allclose(out["illum"][:, 0, :], ref, rtol=1e-12, atol=0)
+
+
+def test_offset_hessian_symmetry_homogeneous(oracle_mod):
+    """One shot in a homogeneous medium, source on the centre column: the
+    illumination and every offset slice are mirror-symmetric about it."""
+    n = 41
+    p = W.homogeneous(n, n, v=2000.0, nt=200, src=[[5, 0, n // 2]], rec=[[0, 0, 0]], sponge=8,
+                      f0=15.0)
+    g = oracle_mod.Grid.of(p)
+    out = oracle_mod.forward(g, p.v_init, p.src, p.rec, p.wavelet, illum=True, hmax=4)
+    H = out["offh"][:, :, 0, :]
+    assert np.allclose(H, H[:, :, ::-1], rtol=1e-10, atol=1e-12 * np.abs(H).max())
+
+
+def _centroid(img):
+    F = np.abs(np.fft.rfft2(img - img.mean())) ** 2
+    kz = np.fft.fftfreq(img.shape[0])[:, None]
+    kx = np.fft.rfftfreq(img.shape[1])[None, :]
+    k = np.sqrt(kz ** 2 + kx ** 2)
+    return float(np.sum(k * F) / np.sum(F))
+
+
+def test_time_integral_gradient_is_low_passed(oracle_mod):
+    p = W.two_layer(nz=60, nx=80, nt=700, ns=2, nrec=80, sponge=12)
+    g = oracle_mod.Grid.of(p)
+    w = p.wavelet.astype(np.float64)
+    d_obs = oracle_mod.forward(g, p.v_true, p.src, p.rec, w)["seis"]
+    go = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w, d_obs, misfit="ols")["grad"][:, 0, :]
+    gi = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w, d_obs, misfit="integral")["grad"][:, 0, :]
+    # below the source row, away from the source/receiver imprint: the
+    # integral misfit's gradient carries lower wavenumbers (measured ~0.85x)
+    assert _centroid(gi[6:, :]) < 0.95 * _centroid(go[6:, :])
+    assert _centroid(gi[10:50, :]) < 0.95 * _centroid(go[10:50, :])
