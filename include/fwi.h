@@ -1,0 +1,203 @@
+/*
+ * fwi.h -- C ABI of the GB300 (sm_103a) library for the preconditioned
+ * time-domain full-waveform-inversion gradient of Huang, Wang & Ren, "Two New
+ * Gradient Precondition Schemes for Full Waveform Inversion" (arXiv:1406.1864).
+ *
+ * The library computes, for every shot of one velocity model:
+ *   forward modelling of the constant-density acoustic wave equation
+ *     1/v^2 u_tt - lap u = delta(x - x_s) f_s(t)                  [Sec. 2]
+ *   traces d_s(x_r, t_n) = u_s(x_r, t_n) at the receivers         [Sec. 2]
+ *   the OLS misfit J = 1/2 sum_s sum_r sum_n (d - d_obs)^2         [Sec. 2]
+ *   or the time-integral misfit J = 1/2 || int_0^t (d - d_obs) ||^2 [Eq. 2]
+ *   the adjoint (back-propagated residual) wavefield and the zero-lag
+ *   cross-correlation gradient g = 2/v^3 sum_s int u_tt v_s dt      [Sec. 2]
+ *   the shot illumination / pseudo-diagonal Hessian sum_s sum_n u^2 dt [Eq. 1]
+ *   the diagonal of the localized subsurface-offset Hessian,
+ *     H(x,h) = sum_s sum_n u(x + h e_x) u(x - h e_x) dt, h = 0..hmax [Sec. 3]
+ *   and the preconditioned gradient g / (P + eps max P)             [Sec. 3.1]
+ *
+ * Discretisation (the paper names only "time domain finite difference"):
+ * 8th-order centred Laplacian, second-order leapfrog in time, and an absorbing
+ * sponge u_tt + 2 eta u_t of `sponge` cells added outside the model on every
+ * side, the velocity there replicating the nearest model cell. The gradient is
+ * the exact derivative of the discrete misfit; the part that falls on sponge
+ * cells is added to the model edge cell they replicate.
+ *
+ * Conventions for every entry point:
+ *   - Arrays are caller-owned, contiguous, C order. "DEVICE" arrays live in
+ *     CUDA device memory of the current device; "HOST" arrays in host memory.
+ *   - Physical-grid shapes only: [nz][nx] in 2-D. Padding is internal.
+ *   - float is IEEE binary32 (the stencil arithmetic), double is binary64
+ *     (misfit reductions only).
+ *   - `ws` is a DEVICE workspace of at least the size reported by
+ *     fwi_workspace_bytes() for the same operation and arguments; the library
+ *     allocates no device memory of its own and keeps no state between calls,
+ *     except the forward checkpoints that fwi_forward(save=1) leaves in `ws`
+ *     for a following fwi_adjoint_apply().
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
+ *     queued on it; the call returns after queueing, except that argument
+ *     errors are found before anything is queued and a status flag written by
+ *     the kernels (timeouts, non-finite wavefields) is read back at the end of
+ *     the call, which synchronises `stream` once.
+ *   - Return value: FWI_OK or an error code; fwi_last_error() then gives a
+ *     message (per host thread). On error the outputs are unspecified.
+ *   - Only ndim = 2 is supported by this version; ndim = 3 returns
+ *     FWI_ERR_INVALID_ARG.
+ */
+#ifndef FWI_H
+#define FWI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FWI_OK = 0,
+    FWI_ERR_INVALID_ARG = 1, /* bad size, index, pointer or option           */
+    FWI_ERR_CFL = 2,         /* v dt / dx above the stability limit           */
+    FWI_ERR_NOMEM = 3,       /* workspace smaller than fwi_workspace_bytes()  */
+    FWI_ERR_CUDA = 4,        /* a CUDA runtime call failed                    */
+    FWI_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                 */
+    FWI_ERR_UNSTABLE = 6     /* a wavefield became non-finite                 */
+} fwi_status;
+
+enum { FWI_MISFIT_OLS = 0, FWI_MISFIT_TIME_INTEGRAL = 1 };
+enum { FWI_ILLUM_U2 = 0, FWI_ILLUM_UTT2 = 1 };
+enum { FWI_PRECOND_NONE = 0, FWI_PRECOND_ILLUM = 1, FWI_PRECOND_OFFSET = 2 };
+enum {
+    FWI_OP_FORWARD = 0,        /* fwi_forward(save = 0)                     */
+    FWI_OP_FORWARD_SAVE = 1,   /* fwi_forward(save = 1) + fwi_adjoint_apply */
+    FWI_OP_GRADIENT = 2,       /* fwi_adjoint_gradient                      */
+    FWI_OP_ILLUMINATION = 3,   /* fwi_illumination                          */
+    FWI_OP_OFFSET_HESSIAN = 4, /* fwi_offset_hessian_diag                   */
+    FWI_OP_PRECONDITION = 5    /* fwi_precondition                          */
+};
+
+#define FWI_HMAX_LIMIT 12 /* largest offset (cells) of the offset Hessian */
+
+/* Grid and time axis. */
+typedef struct {
+    int ndim;     /* 2                                                        */
+    int nz;       /* model rows (depth)                                       */
+    int ny;       /* 1 in 2-D                                                 */
+    int nx;       /* model columns                                            */
+    float dx;     /* grid spacing (m), the same on every axis                 */
+    float dt;     /* time step (s)                                            */
+    int nt;       /* number of time levels t_n = n dt, n = 0..nt-1 (>= 2)     */
+    int sponge;   /* sponge width P (cells), 1..64                            */
+    float vref;   /* speed (m/s) that sets the damping; independent of v      */
+    float refl;   /* sponge strength R in (0,1): eta_max = 3 vref ln(1/R)/(2 P dx) */
+} fwi_grid;
+
+/* Acquisition: one point source and nrec receivers per shot. */
+typedef struct {
+    int nshots;          /* >= 1                                                */
+    int nrec;            /* receivers per shot, >= 0                             */
+    const int *src;      /* HOST [nshots][3]: (z, y, x) model cell of the source; y = 0 in 2-D */
+    const int *rec;      /* HOST [nshots][nrec][3]: (z, y, x) of each receiver   */
+    const float *wavelet;/* DEVICE [nshots][nt]: source time function f_s(t_n)  */
+} fwi_geometry;
+
+/* What to compute besides the plain gradient. */
+typedef struct {
+    int misfit;     /* FWI_MISFIT_OLS or FWI_MISFIT_TIME_INTEGRAL              */
+    int illum_mode; /* FWI_ILLUM_U2: sum u^2 dt; FWI_ILLUM_UTT2: sum u_tt^2 dt
+                       (the omega^4 weighting of Eq. 1, by Parseval)           */
+    int hmax;       /* offsets 0..hmax of the offset Hessian, 0..FWI_HMAX_LIMIT;
+                       -1: not computed                                        */
+    int precond;    /* FWI_PRECOND_*: preconditioner applied for grad_pre      */
+    float eps;      /* water level of the division, > 0 (e.g. 1e-3)           */
+} fwi_options;
+
+/* Per-phase device times of the last call on this host thread, when enabled
+   with fwi_profile_enable(1); CUDA events recorded on the call's stream. */
+typedef struct {
+    float forward_ms;    /* forward time loop (all shots)                      */
+    float adjoint_ms;    /* backward time loop: adjoint, reconstruction, imaging */
+    float other_ms;      /* set-up, misfit, fold, preconditioning              */
+    int forward_launches;/* kernel launches in the forward time loop          */
+    int adjoint_launches;/* kernel launches in the backward time loop         */
+    int other_launches;  /* all other kernel launches of the call             */
+} fwi_phase_times;
+
+/* Workspace size (bytes) of operation `op` (FWI_OP_*) for these arguments.
+   The returned size covers the padded wavefields, the sponge checkpoints of
+   the adjoint pass (largest part: nshots * nt * sponge cells * 4 bytes) and
+   the traces. opts may be NULL for FWI_OP_FORWARD. */
+fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom,
+                               const fwi_options *opts, int op, size_t *bytes);
+
+/* Forward modelling of every shot [Sec. 2].
+   v     DEVICE [nz][nx] velocity (m/s)
+   seis  DEVICE [nshots][nt][nrec] output traces d_s^n(r) = u_s^n(x_r)
+   save  1: leave the checkpoints for fwi_adjoint_apply() in ws (workspace of
+         FWI_OP_FORWARD_SAVE); 0: do not (FWI_OP_FORWARD). */
+fwi_status fwi_forward(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                       const float *v, float *seis, int save, void *ws, size_t ws_bytes,
+                       void *stream);
+
+/* Gradient, with respect to v, of sum_s sum_n sum_r adj_src[s][n][r] * d_s^n(r):
+   the adjoint of the Jacobian applied to adj_src [Sec. 2, zero-lag
+   cross-correlation of forward and back-propagated wavefields]. Needs the
+   checkpoints of a preceding fwi_forward(save = 1) with the same grid,
+   geometry, v and ws, and nothing else on ws in between.
+   adj_src DEVICE [nshots][nt][nrec]; grad DEVICE [nz][nx] output. */
+fwi_status fwi_adjoint_apply(const fwi_grid *grid, const fwi_geometry *geom,
+                             const fwi_options *opts, const float *v, const float *adj_src,
+                             float *grad, void *ws, size_t ws_bytes, void *stream);
+
+/* The whole preconditioned gradient of one model [Sec. 2, Eq. 1-2, Sec. 3]:
+   forward modelling, misfit (opts->misfit), adjoint source, back-propagation,
+   imaging, illumination (always) and offset Hessian (opts->hmax >= 0).
+   v        DEVICE [nz][nx] velocity
+   d_obs    DEVICE [nshots][nt][nrec] observed traces
+   grad     DEVICE [nz][nx] gradient dJ/dv
+   grad_pre DEVICE [nz][nx] preconditioned gradient (opts->precond), or NULL
+   misfit   DEVICE double, the misfit J, or NULL
+   illum    DEVICE [nz][nx] illumination (opts->illum_mode), or NULL
+   offh     DEVICE [hmax+1][nz][nx] offset-Hessian diagonal, or NULL */
+fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom,
+                                const fwi_options *opts, const float *v, const float *d_obs,
+                                float *grad, float *grad_pre, double *misfit, float *illum,
+                                float *offh, void *ws, size_t ws_bytes, void *stream);
+
+/* Shot illumination, the pseudo-diagonal Hessian of Eq. 1:
+   illum DEVICE [nz][nx] = sum_s sum_n u_s^n(x)^2 dt (FWI_ILLUM_U2) or
+   sum_s sum_n (u_tt)_s^n(x)^2 dt (FWI_ILLUM_UTT2), from a forward modelling. */
+fwi_status fwi_illumination(const fwi_grid *grid, const fwi_geometry *geom,
+                            const fwi_options *opts, const float *v, float *illum, void *ws,
+                            size_t ws_bytes, void *stream);
+
+/* Diagonal of the localized subsurface-offset Hessian [Sec. 3], source side,
+   horizontal offsets h = 0..opts->hmax (opts->hmax >= 0):
+   offh DEVICE [hmax+1][nz][nx] = sum_s sum_n u_s^n(x + h e_x) u_s^n(x - h e_x) dt,
+   u = 0 outside the padded grid. offh[0] equals the illumination. */
+fwi_status fwi_offset_hessian_diag(const fwi_grid *grid, const fwi_geometry *geom,
+                                   const fwi_options *opts, const float *v, float *offh,
+                                   void *ws, size_t ws_bytes, void *stream);
+
+/* Diagonal preconditioning [Sec. 3.1, Fig. 5]: out = grad / (P + eps max P),
+   P = scale[0] (kind FWI_PRECOND_ILLUM: scale is an illumination [nz][nx]) or
+   P = |scale[0]| + 2 sum_{h=1..hmax} |scale[h]| (FWI_PRECOND_OFFSET: scale is an
+   offset Hessian [hmax+1][nz][nx]). All DEVICE; ws of FWI_OP_PRECONDITION. */
+fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float *scale, int kind,
+                            int hmax, float eps, float *out, void *ws, size_t ws_bytes,
+                            void *stream);
+
+/* Per-call phase timing with CUDA events (off by default). */
+fwi_status fwi_profile_enable(int on);
+fwi_status fwi_profile_last(fwi_phase_times *out);
+
+/* Message of the last error on this host thread ("" if none). */
+const char *fwi_last_error(void);
+
+/* Library version, 100 * major + minor. */
+int fwi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FWI_H */

@@ -1,0 +1,679 @@
+// fwi_api.cu -- the C ABI of libfwi (include/fwi.h): argument checks,
+// workspace plan, and the order of kernels for each entry point.
+//
+// Order of one gradient (fwi_adjoint_gradient), after [Sec. 2] and [Sec. 3]:
+//   c2 = (v dt/dx)^2 on the padded grid (+ velocity / stability checks)
+//   forward time loop n = 0..nt-1 over all shots: u^{n+1}, traces d^n,
+//     illumination, offset Hessian, sponge checkpoints        (fwi_step2d.cu)
+//   residual r = d - d_obs and misfit; for Eq. 2 the adjoint source C^T C r
+//   backward time loop m = nt-1..1: psi^m, u^{m-2}, imaging   (fwi_step2d.cu)
+//   fold + 2/(v dx^2), illumination / offset-Hessian outputs, preconditioning
+// Everything between the call's start and its final status read stays on the
+// device and is queued on the caller's stream.
+#include "fwi.h"
+#include "fwi_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace fwi {
+int fwd_tile_height(bool with_offh);
+int bwd_tile_height();
+} // namespace fwi
+
+using namespace fwi;
+
+namespace {
+
+thread_local std::string t_err;
+thread_local bool t_prof = false;
+thread_local fwi_phase_times t_times{};
+thread_local cudaEvent_t t_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+thread_local bool t_ev_recorded = false;
+thread_local int t_launch[3] = {0, 0, 0};
+
+fwi_status fail(fwi_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+fwi_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(FWI_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Stability limit of v dt / dx for the 8th-order / leapfrog pair in 2-D:
+// (v dt/dx)^2 * 2 * max|symbol| <= 4, max|symbol| = 205/72 + 2(8/5 + 1/5 + 8/315 + 1/560).
+constexpr float CFL_2D = 0.5546f;
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x, size_t a = ALIGN) { return (x + a - 1) / a * a; }
+
+struct Part {
+    size_t off = 0, bytes = 0;
+};
+
+int sm_count()
+{
+    static int n = -1;
+    if (n < 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else {
+            cudaGetLastError();
+            n = 152;
+        }
+    }
+    return n;
+}
+
+// resident CTAs per SM assumed when sizing the shot groups
+constexpr int RES_FWD = 4, RES_FWD_H = 3, RES_BWD = 3;
+
+struct Plan {
+    Lay2D L{};
+    int ns = 0, nt = 0, nrec = 0, hmax = -1, op = 0;
+    bool with_offh = false; // forward kernel accumulates the offset Hessian
+    bool need_bwd = false;  // adjoint pass (gradient / forward_save)
+    bool need_seis_tab = false;
+    Tiling tf{}, tb{};
+    Part scal, c2, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab;
+    size_t tab_src = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0;
+    size_t total = 0;
+};
+
+fwi_status check_grid(const fwi_grid *g)
+{
+    if (!g) return fail(FWI_ERR_INVALID_ARG, "grid is NULL");
+    if (g->ndim != 2) return fail(FWI_ERR_INVALID_ARG, "ndim=%d: only 2-D grids are supported", g->ndim);
+    if (g->ny != 1) return fail(FWI_ERR_INVALID_ARG, "ny must be 1 in 2-D (got %d)", g->ny);
+    if (g->nz < 1 || g->nx < 1) return fail(FWI_ERR_INVALID_ARG, "nz=%d nx=%d must be >= 1", g->nz, g->nx);
+    if (g->nt < 2) return fail(FWI_ERR_INVALID_ARG, "nt=%d must be >= 2", g->nt);
+    if (g->sponge < 1 || g->sponge > 64) return fail(FWI_ERR_INVALID_ARG, "sponge=%d outside 1..64", g->sponge);
+    if (!(g->dx > 0.f) || !std::isfinite(g->dx)) return fail(FWI_ERR_INVALID_ARG, "dx must be > 0");
+    if (!(g->dt > 0.f) || !std::isfinite(g->dt)) return fail(FWI_ERR_INVALID_ARG, "dt must be > 0");
+    if (!(g->vref > 0.f) || !std::isfinite(g->vref)) return fail(FWI_ERR_INVALID_ARG, "vref must be > 0");
+    if (!(g->refl > 0.f && g->refl < 1.f)) return fail(FWI_ERR_INVALID_ARG, "refl must be in (0,1)");
+    const long long nzp = g->nz + 2LL * g->sponge, nxp = g->nx + 2LL * g->sponge;
+    if (nzp * (nxp + GXL + GXR + 32) >= (1LL << 31)) return fail(FWI_ERR_INVALID_ARG, "grid too large");
+    return FWI_OK;
+}
+
+fwi_status check_geom(const fwi_grid *g, const fwi_geometry *ge, bool coords)
+{
+    if (!ge) return fail(FWI_ERR_INVALID_ARG, "geometry is NULL");
+    if (ge->nshots < 1) return fail(FWI_ERR_INVALID_ARG, "nshots=%d must be >= 1", ge->nshots);
+    if (ge->nrec < 0) return fail(FWI_ERR_INVALID_ARG, "nrec=%d must be >= 0", ge->nrec);
+    if ((long long)ge->nshots * ge->nrec >= (1LL << 31)) return fail(FWI_ERR_INVALID_ARG, "too many receivers");
+    if (!coords) return FWI_OK;
+    if (!ge->src) return fail(FWI_ERR_INVALID_ARG, "geometry.src is NULL");
+    if (ge->nrec > 0 && !ge->rec) return fail(FWI_ERR_INVALID_ARG, "geometry.rec is NULL");
+    if (!ge->wavelet) return fail(FWI_ERR_INVALID_ARG, "geometry.wavelet is NULL");
+    for (int s = 0; s < ge->nshots; ++s) {
+        const int *c = ge->src + 3 * s;
+        if (c[0] < 0 || c[0] >= g->nz || c[1] != 0 || c[2] < 0 || c[2] >= g->nx)
+            return fail(FWI_ERR_INVALID_ARG, "source of shot %d at (%d,%d,%d) outside the model", s, c[0], c[1], c[2]);
+        for (int r = 0; r < ge->nrec; ++r) {
+            const int *q = ge->rec + 3 * ((long long)s * ge->nrec + r);
+            if (q[0] < 0 || q[0] >= g->nz || q[1] != 0 || q[2] < 0 || q[2] >= g->nx)
+                return fail(FWI_ERR_INVALID_ARG, "receiver %d of shot %d at (%d,%d,%d) outside the model", r, s, q[0], q[1], q[2]);
+        }
+    }
+    return FWI_OK;
+}
+
+fwi_status check_opts(const fwi_options *o, int op)
+{
+    if (!o) {
+        if (op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_PRECONDITION) return FWI_OK;
+        return fail(FWI_ERR_INVALID_ARG, "options are NULL");
+    }
+    if (o->misfit != FWI_MISFIT_OLS && o->misfit != FWI_MISFIT_TIME_INTEGRAL)
+        return fail(FWI_ERR_INVALID_ARG, "misfit=%d unknown", o->misfit);
+    if (o->illum_mode != FWI_ILLUM_U2 && o->illum_mode != FWI_ILLUM_UTT2)
+        return fail(FWI_ERR_INVALID_ARG, "illum_mode=%d unknown", o->illum_mode);
+    if (o->hmax < -1 || o->hmax > FWI_HMAX_LIMIT)
+        return fail(FWI_ERR_INVALID_ARG, "hmax=%d outside -1..%d", o->hmax, FWI_HMAX_LIMIT);
+    if (o->precond < FWI_PRECOND_NONE || o->precond > FWI_PRECOND_OFFSET)
+        return fail(FWI_ERR_INVALID_ARG, "precond=%d unknown", o->precond);
+    if (o->precond == FWI_PRECOND_OFFSET && o->hmax < 0)
+        return fail(FWI_ERR_INVALID_ARG, "precond=OFFSET needs hmax >= 0");
+    if (!(o->eps > 0.f) || !std::isfinite(o->eps)) return fail(FWI_ERR_INVALID_ARG, "eps must be > 0");
+    return FWI_OK;
+}
+
+Lay2D make_layout(const fwi_grid *g)
+{
+    Lay2D L{};
+    L.nz = g->nz;
+    L.nx = g->nx;
+    L.P = g->sponge;
+    L.nzp = g->nz + 2 * g->sponge;
+    L.nxp = g->nx + 2 * g->sponge;
+    L.pitch = (int)align_up((size_t)(GXL + L.nxp + GXR), 32);
+    L.rows = L.nzp + 2 * GZ;
+    L.fstride = (long long)align_up((size_t)L.rows * L.pitch, 64);
+    L.nband = 2 * L.P * L.nxp + 2 * L.P * L.nz;
+    L.dt = g->dt;
+    L.dx = g->dx;
+    const double etamax = 3.0 * g->vref * std::log(1.0 / g->refl) / (2.0 * g->sponge * g->dx);
+    L.etamax_dt = (float)(etamax * g->dt);
+    L.inv_p2 = (float)(1.0 / ((double)g->sponge * g->sponge));
+    return L;
+}
+
+fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_options *o, int op,
+                     bool coords, Plan &pl)
+{
+    fwi_status st;
+    if ((st = check_grid(g)) != FWI_OK) return st;
+    if (op != FWI_OP_PRECONDITION && (st = check_geom(g, ge, coords)) != FWI_OK) return st;
+    if ((st = check_opts(o, op)) != FWI_OK) return st;
+    pl.L = make_layout(g);
+    pl.op = op;
+    pl.nt = g->nt;
+    const Lay2D &L = pl.L;
+    size_t off = 0;
+    auto take = [&](Part &p, size_t bytes) {
+        p.off = off;
+        p.bytes = bytes;
+        off = align_up(off + bytes);
+    };
+    take(pl.scal, 256);
+    if (op == FWI_OP_PRECONDITION) {
+        pl.total = off;
+        return FWI_OK;
+    }
+    pl.ns = ge->nshots;
+    pl.nrec = ge->nrec;
+    pl.hmax = o ? o->hmax : -1;
+    pl.with_offh = (op == FWI_OP_GRADIENT || op == FWI_OP_OFFSET_HESSIAN) && pl.hmax >= 0;
+    if (op == FWI_OP_OFFSET_HESSIAN && pl.hmax < 0)
+        return fail(FWI_ERR_INVALID_ARG, "offset Hessian needs hmax >= 0");
+    pl.need_bwd = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE);
+    pl.need_seis_tab = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE);
+    const int smc = sm_count();
+    pl.tf = make_tiling(L, pl.ns, fwd_tile_height(pl.with_offh), smc * (pl.with_offh ? RES_FWD_H : RES_FWD));
+    pl.tb = make_tiling(L, pl.ns, bwd_tile_height(), smc * RES_BWD);
+    const size_t fbytes = (size_t)L.fstride * sizeof(float);
+    const size_t nphys = (size_t)L.nz * L.nx;
+    take(pl.c2, fbytes);
+    take(pl.u[0], fbytes * pl.ns);
+    take(pl.u[1], fbytes * pl.ns);
+    if (pl.need_bwd) {
+        take(pl.p[0], fbytes * pl.ns);
+        take(pl.p[1], fbytes * pl.ns);
+        take(pl.band, (size_t)pl.ns * pl.nt * L.nband * sizeof(float));
+        take(pl.acc_g, (size_t)pl.tb.groups * L.nzp * L.nxp * sizeof(float));
+    }
+    if (op == FWI_OP_GRADIENT) take(pl.syn, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
+    if (op == FWI_OP_GRADIENT || op == FWI_OP_ILLUMINATION)
+        take(pl.acc_i, (size_t)pl.tf.groups * nphys * sizeof(float));
+    if (pl.with_offh) take(pl.acc_h, (size_t)pl.tf.groups * (pl.hmax + 1) * nphys * sizeof(float));
+    // tables: src offsets, receiver CSR of the forward and backward tilings
+    size_t t = 0;
+    auto tk = [&](size_t &o2, size_t bytes) {
+        o2 = t;
+        t = align_up(t + bytes, 16);
+    };
+    tk(pl.tab_src, (size_t)pl.ns * sizeof(int));
+    const size_t nent = (size_t)pl.ns * pl.nrec;
+    tk(pl.tab_fptr, ((size_t)pl.tf.ntx * pl.tf.ntz * pl.ns + 1) * sizeof(int));
+    tk(pl.tab_fent, std::max<size_t>(nent, 1) * sizeof(int2));
+    if (pl.need_bwd) {
+        tk(pl.tab_bptr, ((size_t)pl.tb.ntx * pl.tb.ntz * pl.ns + 1) * sizeof(int));
+        tk(pl.tab_bent, std::max<size_t>(nent, 1) * sizeof(int2));
+    }
+    take(pl.tab, t);
+    pl.total = off;
+    return FWI_OK;
+}
+
+template <class T> T *at(void *ws, const Part &p) { return reinterpret_cast<T *>(static_cast<char *>(ws) + p.off); }
+template <class T> T *at(void *ws, const Part &p, size_t extra)
+{
+    return reinterpret_cast<T *>(static_cast<char *>(ws) + p.off + extra);
+}
+
+void build_csr(const Plan &pl, const Tiling &t, const int *rec, std::vector<char> &buf, size_t ptr_off,
+               size_t ent_off)
+{
+    const Lay2D &L = pl.L;
+    const int ntiles = t.ntx * t.ntz;
+    int *ptr = reinterpret_cast<int *>(buf.data() + ptr_off);
+    int2 *ent = reinterpret_cast<int2 *>(buf.data() + ent_off);
+    std::vector<int> cnt((size_t)ntiles * pl.ns + 1, 0);
+    auto tile_of = [&](int s, int r, int &local) {
+        const int *q = rec + 3 * ((long long)s * pl.nrec + r);
+        const int i = q[0] + L.P, j = q[2] + L.P;
+        const int tz = i / t.tz, tx = j / TX;
+        local = (i - tz * t.tz) * TX + (j - tx * TX);
+        return tz * t.ntx + tx;
+    };
+    for (int s = 0; s < pl.ns; ++s)
+        for (int r = 0; r < pl.nrec; ++r) {
+            int loc;
+            const int tl = tile_of(s, r, loc);
+            cnt[(size_t)tl * pl.ns + s + 1]++;
+        }
+    for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+    std::memcpy(ptr, cnt.data(), cnt.size() * sizeof(int));
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int s = 0; s < pl.ns; ++s)
+        for (int r = 0; r < pl.nrec; ++r) {
+            int loc;
+            const int tl = tile_of(s, r, loc);
+            ent[fill[(size_t)tl * pl.ns + s]++] = make_int2(loc, r);
+        }
+}
+
+fwi_status upload_tables(const Plan &pl, const fwi_geometry *ge, void *ws, cudaStream_t st)
+{
+    std::vector<char> buf(pl.tab.bytes, 0);
+    int *src = reinterpret_cast<int *>(buf.data() + pl.tab_src);
+    for (int s = 0; s < pl.ns; ++s) {
+        const int *c = ge->src + 3 * s;
+        src[s] = (int)fidx(pl.L, c[0] + pl.L.P, c[2] + pl.L.P);
+    }
+    if (pl.nrec > 0) {
+        build_csr(pl, pl.tf, ge->rec, buf, pl.tab_fptr, pl.tab_fent);
+        if (pl.need_bwd) build_csr(pl, pl.tb, ge->rec, buf, pl.tab_bptr, pl.tab_bent);
+    }
+    cudaError_t e = cudaMemcpyAsync(at<char>(ws, pl.tab), buf.data(), buf.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload of geometry tables");
+    return FWI_OK;
+}
+
+fwi_status check_ws(const Plan &pl, void *ws, size_t ws_bytes)
+{
+    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
+        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
+    if (ws_bytes < pl.total)
+        return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, pl.total);
+    return FWI_OK;
+}
+
+void prof_record(int k, cudaStream_t st)
+{
+    if (!t_prof) return;
+    if (!t_ev[0])
+        for (int i = 0; i < 4; ++i) cudaEventCreate(&t_ev[i]);
+    cudaEventRecord(t_ev[k], st);
+    if (k == 3) t_ev_recorded = true;
+}
+
+StepCommon make_common(const Plan &pl, const fwi_geometry *ge, void *ws, const Tiling &t)
+{
+    StepCommon c{};
+    c.L = pl.L;
+    c.c2 = at<float>(ws, pl.c2);
+    c.src_off = at<int>(ws, pl.tab, pl.tab_src);
+    c.wav = ge->wavelet;
+    c.src_scale = 1.0f; // dx^(2-ndim) in 2-D
+    c.ns = pl.ns;
+    c.nt = pl.nt;
+    c.nrec = pl.nrec;
+    c.ntx = t.ntx;
+    c.ntz = t.ntz;
+    c.spg = t.spg;
+    c.status = at<int>(ws, pl.scal, 8);
+    return c;
+}
+
+// set-up shared by every propagation: status, tables, c2, zero fields
+fwi_status setup(const Plan &pl, const fwi_geometry *ge, const float *v, void *ws, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.scal), 0, pl.scal.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    fwi_status s = upload_tables(pl, ge, ws, st);
+    if (s != FWI_OK) return s;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.c2), 0, pl.c2.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_prep_c2(pl.L, v, at<float>(ws, pl.c2), CFL_2D, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
+        return cuda_fail(e, "prep kernel");
+    t_launch[2]++;
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaMemsetAsync(at<char>(ws, pl.u[b]), 0, pl.u[b].bytes, st)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+    return FWI_OK;
+}
+
+// forward time loop n = 0..nt-1
+fwi_status run_forward(const Plan &pl, const fwi_geometry *ge, void *ws, float *seis, bool save,
+                       float *acc_i, float *acc_h, int illum_utt, cudaStream_t st)
+{
+    cudaError_t e;
+    if (acc_i && (e = cudaMemsetAsync(acc_i, 0, pl.acc_i.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if (acc_h && (e = cudaMemsetAsync(acc_h, 0, pl.acc_h.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    FwdArgs a{};
+    a.c = make_common(pl, ge, ws, pl.tf);
+    a.band = save ? at<float>(ws, pl.band) : nullptr;
+    a.seis = (seis && pl.nrec > 0) ? seis : nullptr;
+    a.acc_illum = acc_i;
+    a.acc_offh = acc_h;
+    a.rt.ptr = at<int>(ws, pl.tab, pl.tab_fptr);
+    a.rt.ent = at<int2>(ws, pl.tab, pl.tab_fent);
+    a.illum_utt = illum_utt;
+    a.hmax = pl.hmax;
+    float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
+    for (int n = 0; n < pl.nt; ++n) {
+        a.n = n;
+        a.last = (n == pl.nt - 1);
+        a.ucur = U[n & 1];
+        a.uprev = U[(n + 1) & 1];
+        if ((e = launch_fwd_step(a, pl.tf, pl.with_offh && acc_h, st)) != cudaSuccess)
+            return cuda_fail(e, "forward step");
+        t_launch[0]++;
+    }
+    for (int b = 0; b < 2; ++b)
+        if ((e = launch_check_finite(U[b], (long long)pl.ns * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
+            return cuda_fail(e, "finite check");
+    t_launch[2] += 2;
+    return FWI_OK;
+}
+
+// backward time loop m = nt-1..1, adjoint source adj [ns][nt][nrec]
+fwi_status run_backward(const Plan &pl, const fwi_geometry *ge, void *ws, const float *adj,
+                        cudaStream_t st)
+{
+    cudaError_t e;
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaMemsetAsync(at<char>(ws, pl.p[b]), 0, pl.p[b].bytes, st)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.acc_g), 0, pl.acc_g.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    BwdArgs a{};
+    a.c = make_common(pl, ge, ws, pl.tb);
+    a.band = at<float>(ws, pl.band);
+    a.adj = adj;
+    a.acc_grad = at<float>(ws, pl.acc_g);
+    a.rt.ptr = at<int>(ws, pl.tab, pl.tab_bptr);
+    a.rt.ent = at<int2>(ws, pl.tab, pl.tab_bent);
+    a.adj_scale = pl.L.dx * pl.L.dx;
+    float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
+    float *Pp[2] = {at<float>(ws, pl.p[0]), at<float>(ws, pl.p[1])};
+    if (pl.nrec == 0) {
+        // no receivers: adjoint source is empty; tables hold no entries
+        a.adj = nullptr;
+    }
+    for (int m = pl.nt - 1; m >= 1; --m) {
+        a.m = m;
+        a.ua = U[m & 1];
+        a.ub = U[(m - 1) & 1];
+        a.pa = Pp[(m + 1) & 1];
+        a.pb = Pp[m & 1];
+        if ((e = launch_bwd_step(a, pl.tb, st)) != cudaSuccess) return cuda_fail(e, "backward step");
+        t_launch[1]++;
+    }
+    if ((e = launch_check_finite(Pp[0], (long long)pl.ns * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
+        return cuda_fail(e, "finite check");
+    t_launch[2]++;
+    return FWI_OK;
+}
+
+fwi_status finish(const Plan &pl, void *ws, cudaStream_t st)
+{
+    int status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, at<int>(ws, pl.scal, 8), sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "status read-back");
+    if (t_ev_recorded && t_prof) {
+        float ms[3] = {0, 0, 0}, tot = 0;
+        cudaEventElapsedTime(&ms[0], t_ev[0], t_ev[1]);
+        cudaEventElapsedTime(&ms[1], t_ev[1], t_ev[2]);
+        cudaEventElapsedTime(&tot, t_ev[0], t_ev[3]);
+        t_times.forward_ms = ms[0];
+        t_times.adjoint_ms = ms[1];
+        t_times.other_ms = tot - ms[0] - ms[1];
+        t_times.forward_launches = t_launch[0];
+        t_times.adjoint_launches = t_launch[1];
+        t_times.other_launches = t_launch[2];
+    }
+    if (status & ST_BAD_VELOCITY) return fail(FWI_ERR_INVALID_ARG, "velocity not finite and positive");
+    if (status & ST_CFL) return fail(FWI_ERR_CFL, "v dt/dx above the stability limit %g", CFL_2D);
+    if (status & ST_TIMEOUT) return fail(FWI_ERR_TIMEOUT, "a device wait timed out");
+    if (status & ST_NONFINITE) return fail(FWI_ERR_UNSTABLE, "non-finite wavefield");
+    t_err.clear();
+    return FWI_OK;
+}
+
+void begin_call(cudaStream_t st)
+{
+    t_launch[0] = t_launch[1] = t_launch[2] = 0;
+    t_ev_recorded = false;
+    prof_record(0, st);
+}
+
+// events 1 and 2 bracket the backward loop; for calls without one they
+// coincide, and for calls without a forward loop event 1 is the start.
+} // namespace
+
+extern "C" {
+
+int fwi_version(void) { return 100; }
+
+const char *fwi_last_error(void) { return t_err.c_str(); }
+
+fwi_status fwi_profile_enable(int on)
+{
+    t_prof = on != 0;
+    return FWI_OK;
+}
+
+fwi_status fwi_profile_last(fwi_phase_times *out)
+{
+    if (!out) return fail(FWI_ERR_INVALID_ARG, "out is NULL");
+    *out = t_times;
+    return FWI_OK;
+}
+
+fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                               int op, size_t *bytes)
+{
+    if (!bytes) return fail(FWI_ERR_INVALID_ARG, "bytes is NULL");
+    if (op < FWI_OP_FORWARD || op > FWI_OP_PRECONDITION) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, op, false, pl);
+    if (s != FWI_OK) return s;
+    *bytes = pl.total;
+    t_err.clear();
+    return FWI_OK;
+}
+
+fwi_status fwi_forward(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                       const float *v, float *seis, int save, void *ws, size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, save ? FWI_OP_FORWARD_SAVE : FWI_OP_FORWARD, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || (!seis && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v or seis is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    if ((s = run_forward(pl, geom, ws, seis, save != 0, nullptr, nullptr, 0, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    prof_record(2, st);
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_adjoint_apply(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                             const float *v, const float *adj_src, float *grad, void *ws, size_t ws_bytes,
+                             void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_FORWARD_SAVE, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || !grad || (!adj_src && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v, adj_src or grad is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    prof_record(1, st);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.scal), 0, pl.scal.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((s = upload_tables(pl, geom, ws, st)) != FWI_OK) return s;
+    if ((s = run_backward(pl, geom, ws, adj_src, st)) != FWI_OK) return s;
+    prof_record(2, st);
+    if ((e = launch_fold_grad(pl.L, at<float>(ws, pl.acc_g), pl.tb.groups, v, grad, st)) != cudaSuccess)
+        return cuda_fail(e, "fold kernel");
+    t_launch[2]++;
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                                const float *v, const float *d_obs, float *grad, float *grad_pre, double *misfit,
+                                float *illum, float *offh, void *ws, size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_GRADIENT, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || !grad || (!d_obs && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v, d_obs or grad is NULL");
+    if (offh && opts->hmax < 0) return fail(FWI_ERR_INVALID_ARG, "offh requested with hmax < 0");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    begin_call(st);
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    float *acc_i = at<float>(ws, pl.acc_i);
+    float *acc_h = pl.with_offh ? at<float>(ws, pl.acc_h) : nullptr;
+    float *syn = at<float>(ws, pl.syn);
+    if ((s = run_forward(pl, geom, ws, syn, true, acc_i, acc_h, opts->illum_mode, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    double *J = at<double>(ws, pl.scal, 0);
+    const long long nsamp = (long long)pl.ns * pl.nt * pl.nrec;
+    if (nsamp > 0) {
+        if ((e = launch_residual_ols(syn, d_obs, nsamp, opts->misfit == FWI_MISFIT_OLS ? J : nullptr, st)) != cudaSuccess)
+            return cuda_fail(e, "residual kernel");
+        t_launch[2]++;
+        if (opts->misfit == FWI_MISFIT_TIME_INTEGRAL) {
+            if ((e = launch_time_integral(syn, pl.ns, pl.nt, pl.nrec, pl.L.dt, J, st)) != cudaSuccess)
+                return cuda_fail(e, "time-integral kernel");
+            t_launch[2]++;
+        }
+    }
+    if ((s = run_backward(pl, geom, ws, syn, st)) != FWI_OK) return s;
+    prof_record(2, st);
+    if ((e = launch_fold_grad(pl.L, at<float>(ws, pl.acc_g), pl.tb.groups, v, grad, st)) != cudaSuccess)
+        return cuda_fail(e, "fold kernel");
+    t_launch[2]++;
+    // illumination: dt sum u^2, or (1/dt^3) sum (second difference)^2
+    const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
+    float *ill_out = illum ? illum : acc_i; // in place into group 0 when not requested
+    if ((e = launch_finish_accum(pl.L, acc_i, pl.tf.groups, 1, iscale, ill_out, st)) != cudaSuccess)
+        return cuda_fail(e, "illumination output");
+    t_launch[2]++;
+    float *off_out = nullptr;
+    if (acc_h) {
+        off_out = offh ? offh : acc_h;
+        if ((e = launch_finish_accum(pl.L, acc_h, pl.tf.groups, pl.hmax + 1, pl.L.dt, off_out, st)) != cudaSuccess)
+            return cuda_fail(e, "offset-Hessian output");
+        t_launch[2]++;
+    }
+    if (grad_pre) {
+        if (opts->precond == FWI_PRECOND_NONE) {
+            if ((e = cudaMemcpyAsync(grad_pre, grad, (size_t)pl.L.nz * pl.L.nx * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "copy");
+        } else {
+            const bool ill = opts->precond == FWI_PRECOND_ILLUM;
+            if ((e = launch_precond(pl.L, grad, ill ? ill_out : off_out, ill ? 1 : 2, pl.hmax, opts->eps, grad_pre,
+                                    at<unsigned>(ws, pl.scal, 12), st)) != cudaSuccess)
+                return cuda_fail(e, "precondition kernel");
+            t_launch[2] += 2;
+        }
+    }
+    if (misfit && (e = cudaMemcpyAsync(misfit, J, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_illumination(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                            const float *v, float *illum, void *ws, size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_ILLUMINATION, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || !illum) return fail(FWI_ERR_INVALID_ARG, "v or illum is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    float *acc_i = at<float>(ws, pl.acc_i);
+    if ((s = run_forward(pl, geom, ws, nullptr, false, acc_i, nullptr, opts->illum_mode, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    prof_record(2, st);
+    const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
+    cudaError_t e;
+    if ((e = launch_finish_accum(pl.L, acc_i, pl.tf.groups, 1, iscale, illum, st)) != cudaSuccess)
+        return cuda_fail(e, "illumination output");
+    t_launch[2]++;
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_offset_hessian_diag(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                                   const float *v, float *offh, void *ws, size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_OFFSET_HESSIAN, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || !offh) return fail(FWI_ERR_INVALID_ARG, "v or offh is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    float *acc_h = at<float>(ws, pl.acc_h);
+    if ((s = run_forward(pl, geom, ws, nullptr, false, nullptr, acc_h, 0, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    prof_record(2, st);
+    cudaError_t e;
+    if ((e = launch_finish_accum(pl.L, acc_h, pl.tf.groups, pl.hmax + 1, pl.L.dt, offh, st)) != cudaSuccess)
+        return cuda_fail(e, "offset-Hessian output");
+    t_launch[2]++;
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float *scale, int kind, int hmax,
+                            float eps, float *out, void *ws, size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, nullptr, nullptr, FWI_OP_PRECONDITION, false, pl);
+    if (s != FWI_OK) return s;
+    if (!grad || !scale || !out) return fail(FWI_ERR_INVALID_ARG, "grad, scale or out is NULL");
+    if (kind != FWI_PRECOND_ILLUM && kind != FWI_PRECOND_OFFSET) return fail(FWI_ERR_INVALID_ARG, "kind=%d", kind);
+    if (kind == FWI_PRECOND_OFFSET && (hmax < 0 || hmax > FWI_HMAX_LIMIT))
+        return fail(FWI_ERR_INVALID_ARG, "hmax=%d outside 0..%d", hmax, FWI_HMAX_LIMIT);
+    if (!(eps > 0.f)) return fail(FWI_ERR_INVALID_ARG, "eps must be > 0");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    prof_record(1, st);
+    prof_record(2, st);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.scal), 0, pl.scal.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_precond(pl.L, grad, scale, kind, hmax, eps, out, at<unsigned>(ws, pl.scal, 12), st)) != cudaSuccess)
+        return cuda_fail(e, "precondition kernel");
+    t_launch[2] += 2;
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+} // extern "C"

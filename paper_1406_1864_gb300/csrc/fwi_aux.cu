@@ -1,0 +1,254 @@
+// fwi_aux.cu -- the small kernels around the time loops (sm_103a):
+// model preparation, misfits and adjoint sources (OLS of Sec. 2 and the
+// time-integral misfit of Eq. 2), folding of the padded-grid gradient,
+// illumination / offset-Hessian outputs (Eq. 1, Sec. 3) and the diagonal
+// preconditioning g / (P + eps max P) of Sec. 3.1.
+#include "fwi_internal.h"
+
+#include <cfloat>
+
+namespace fwi {
+
+namespace {
+
+constexpr int NT1 = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum of v over the block, added atomically to *out (FP64)
+__device__ __forceinline__ void block_sum_add(double v, double *out)
+{
+    __shared__ double part[NT1 / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) part[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < NT1 / 32 ? part[lane] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) atomicAdd(out, v);
+    }
+}
+
+__device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
+
+// c2 = (v dt / dx)^2 on the padded grid, the sponge replicating the nearest
+// model cell; checks v > 0, finite, and the stability limit.
+__global__ void k_prep_c2(const Lay2D L, const float *__restrict__ v, float *__restrict__ c2,
+                          float cfl_limit, int *status)
+{
+    const long long n = (long long)L.nzp * L.nxp;
+    int bad = 0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / L.nxp), j = (int)(e - (long long)i * L.nxp);
+        const int iz = clampi(i - L.P, 0, L.nz - 1), ix = clampi(j - L.P, 0, L.nx - 1);
+        const float vv = v[(long long)iz * L.nx + ix];
+        const float r = vv * L.dt / L.dx;
+        if (!(vv > 0.f) || !isfinite(vv)) bad |= ST_BAD_VELOCITY;
+        else if (r > cfl_limit) bad |= ST_CFL;
+        c2[fidx(L, i, j)] = r * r;
+    }
+    if (bad) atomicOr(status, bad);
+}
+
+// r = syn - obs (in place in syn), misfit += 1/2 sum r^2 (misfit may be NULL)
+__global__ void k_residual_ols(float *__restrict__ syn, const float *__restrict__ obs, long long n,
+                               double *misfit)
+{
+    double acc = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const float r = syn[e] - obs[e];
+        syn[e] = r;
+        acc += (double)r * (double)r;
+    }
+    if (misfit != nullptr) block_sum_add(0.5 * acc, misfit); // uniform over the grid
+}
+
+// Time-integral misfit of Eq. 2 on residual traces r[s][n][rec] (in place):
+// y^n = dt sum_{k<=n} r^k (inclusive rectangle rule), misfit += 1/2 sum y^2,
+// then the adjoint source a^n = dt sum_{k>=n} y^k = (C^T C r)^n overwrites r.
+// One thread per trace; compensated (Kahan) FP32 sums along time.
+__global__ void k_time_integral(float *__restrict__ r, int ns, int nt, int nrec, float dt,
+                                double *misfit)
+{
+    const long long tr = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (tr < (long long)ns * nrec) {
+        const int s = (int)(tr / nrec), q = (int)(tr - (long long)s * nrec);
+        float *base = r + (long long)s * nt * nrec + q;
+        float sum = 0.f, cmp = 0.f;
+        for (int n = 0; n < nt; ++n) {
+            const float x = base[(long long)n * nrec];
+            const float y = x - cmp;
+            const float t = sum + y;
+            cmp = (t - sum) - y;
+            sum = t;
+            const float yi = dt * sum;
+            base[(long long)n * nrec] = yi;
+            acc += (double)yi * (double)yi;
+        }
+        sum = 0.f;
+        cmp = 0.f;
+        for (int n = nt - 1; n >= 0; --n) {
+            const float x = base[(long long)n * nrec];
+            const float y = x - cmp;
+            const float t = sum + y;
+            cmp = (t - sum) - y;
+            sum = t;
+            base[(long long)n * nrec] = dt * sum;
+        }
+    }
+    block_sum_add(0.5 * acc, misfit);
+}
+
+// grad(iz, ix) = 2 / (v dx^2) * sum over groups and over the padded cells
+// that replicate model cell (iz, ix) of the imaging sum G.
+__global__ void k_fold_grad(const Lay2D L, const float *__restrict__ acc, int groups,
+                            const float *__restrict__ v, float *__restrict__ grad)
+{
+    const long long n = (long long)L.nz * L.nx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int iz = (int)(e / L.nx), ix = (int)(e - (long long)iz * L.nx);
+        const int ia = iz == 0 ? 0 : iz + L.P;
+        const int ib = iz == L.nz - 1 ? L.nzp - 1 : iz + L.P;
+        const int ja = ix == 0 ? 0 : ix + L.P;
+        const int jb = ix == L.nx - 1 ? L.nxp - 1 : ix + L.P;
+        float sum = 0.f;
+        for (int g = 0; g < groups; ++g) {
+            const float *ag = acc + (long long)g * L.nzp * L.nxp;
+            for (int i = ia; i <= ib; ++i)
+                for (int j = ja; j <= jb; ++j) sum += ag[(long long)i * L.nxp + j];
+        }
+        grad[e] = sum * (2.0f / (v[e] * L.dx * L.dx));
+    }
+}
+
+// out[plane][iz][ix] = scale * sum_g acc[g][plane][iz][ix]
+__global__ void k_finish_accum(long long nphys, const float *__restrict__ acc, int groups,
+                               int planes, float scale, float *__restrict__ out)
+{
+    const long long n = nphys * planes;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        float sum = 0.f;
+        for (int g = 0; g < groups; ++g) sum += acc[(long long)g * n + e];
+        out[e] = sum * scale;
+    }
+}
+
+__device__ __forceinline__ float precond_scale(const float *__restrict__ sc, long long e,
+                                               long long nphys, int kind, int hmax)
+{
+    if (kind == 1) return sc[e];
+    float p = fabsf(sc[e]);
+    for (int h = 1; h <= hmax; ++h) p += 2.0f * fabsf(sc[h * nphys + e]);
+    return p;
+}
+
+// max over the model of the preconditioner (non-negative: float bits order
+// like unsigned integers)
+__global__ void k_precond_max(long long nphys, const float *__restrict__ sc, int kind, int hmax,
+                              unsigned *pmax)
+{
+    float mx = 0.f;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nphys;
+         e += (long long)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, precond_scale(sc, e, nphys, kind, hmax));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(pmax, __float_as_uint(mx));
+}
+
+__global__ void k_precond_apply(long long nphys, const float *__restrict__ g,
+                                const float *__restrict__ sc, int kind, int hmax, float eps,
+                                const unsigned *pmax, float *__restrict__ out)
+{
+    const float w = eps * __uint_as_float(*pmax);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nphys;
+         e += (long long)gridDim.x * blockDim.x)
+        out[e] = g[e] / (precond_scale(sc, e, nphys, kind, hmax) + w);
+}
+
+__global__ void k_check_finite(const float *__restrict__ x, long long n, int *status)
+{
+    int bad = 0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(x[e])) bad = 1;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+}
+
+int grid_for(long long n)
+{
+    long long b = (n + NT1 - 1) / NT1;
+    if (b < 1) b = 1;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)b;
+}
+
+} // namespace
+
+cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float cfl_limit,
+                           int *status, cudaStream_t st)
+{
+    k_prep_c2<<<grid_for((long long)L.nzp * L.nxp), NT1, 0, st>>>(L, v, c2, cfl_limit, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_ols(float *syn, const float *obs, long long n, double *misfit,
+                                cudaStream_t st)
+{
+    k_residual_ols<<<grid_for(n / 4 + 1), NT1, 0, st>>>(syn, obs, n, misfit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_time_integral(float *r, int ns, int nt, int nrec, float dt, double *misfit,
+                                 cudaStream_t st)
+{
+    const long long ntr = (long long)ns * nrec;
+    const int blocks = (int)((ntr + NT1 - 1) / NT1);
+    if (blocks > 0) k_time_integral<<<blocks, NT1, 0, st>>>(r, ns, nt, nrec, dt, misfit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_grad(const Lay2D &L, const float *acc, int groups, const float *v,
+                             float *grad, cudaStream_t st)
+{
+    k_fold_grad<<<grid_for((long long)L.nz * L.nx), NT1, 0, st>>>(L, acc, groups, v, grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_accum(const Lay2D &L, const float *acc, int groups, int planes,
+                                float scale, float *out, cudaStream_t st)
+{
+    const long long nphys = (long long)L.nz * L.nx;
+    k_finish_accum<<<grid_for(nphys * planes), NT1, 0, st>>>(nphys, acc, groups, planes, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precond(const Lay2D &L, const float *grad, const float *scale, int kind,
+                           int hmax, float eps, float *out, unsigned *pmax, cudaStream_t st)
+{
+    const long long nphys = (long long)L.nz * L.nx;
+    cudaError_t e = cudaMemsetAsync(pmax, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    k_precond_max<<<grid_for(nphys), NT1, 0, st>>>(nphys, scale, kind, hmax, pmax);
+    k_precond_apply<<<grid_for(nphys), NT1, 0, st>>>(nphys, grad, scale, kind, hmax, eps, pmax, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const float *x, long long n, int *status, cudaStream_t st)
+{
+    k_check_finite<<<grid_for(n), NT1, 0, st>>>(x, n, status);
+    return cudaGetLastError();
+}
+
+} // namespace fwi

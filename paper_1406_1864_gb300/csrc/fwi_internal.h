@@ -1,0 +1,150 @@
+// fwi_internal.h -- layouts, kernel arguments and launchers shared by the
+// translation units of libfwi (CUDA, sm_103a). Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fwi {
+
+// ---------------------------------------------------------------- layout
+// A padded 2-D field (model + sponge, nzp x nxp) is stored row-major with a
+// zero ghost frame so that stencil and offset reads never leave the buffer:
+// GZ rows above and below, GXL columns on the left (128-byte aligned start of
+// the padded row) and at least GXR columns on the right. Ghost cells are set
+// to zero once per call and never written.
+constexpr int GZ = 4;
+constexpr int GXL = 32;
+constexpr int GXR = 16;
+constexpr int RADIUS = 4;          // half-width of the 8th-order stencil
+constexpr int HMAX_LIMIT = 12;     // largest offset of the offset Hessian
+
+// Tile of the 2-D step kernels: TX columns (16 threads x float4) by
+// TZ = 8 * RZ rows (8 thread rows x RZ rows each), 128 threads.
+constexpr int TX = 64;
+constexpr int TPB = 128;
+
+struct Lay2D {
+    int nz, nx, P;        // model and sponge
+    int nzp, nxp;         // padded grid
+    int pitch;            // floats per stored row
+    int rows;             // stored rows = nzp + 2 GZ
+    long long fstride;    // floats per stored field (rows * pitch), 64-float aligned
+    int nband;            // sponge cells of one field (checkpointed each step)
+    float dt, dx;
+    float etamax_dt;      // eta_max * dt
+    float inv_p2;         // 1 / P^2
+};
+
+__host__ __device__ inline long long fidx(const Lay2D &L, int i, int j)
+{
+    return (long long)(i + GZ) * L.pitch + (j + GXL);
+}
+
+// cells into the sponge along one axis (0 inside the model)
+__host__ __device__ inline int sponge_depth(int i, int P, int n)
+{
+    return i < P ? P - i : (i >= P + n ? i - (P + n - 1) : 0);
+}
+
+// index of sponge cell (i, j) in the per-step checkpoint of one field;
+// -1 for model cells. Order: top P rows, then (left P, right P) per model row,
+// then bottom P rows.
+__host__ __device__ inline int band_index(const Lay2D &L, int i, int j)
+{
+    const int P = L.P;
+    if (i < P) return i * L.nxp + j;
+    if (i >= P + L.nz) return P * L.nxp + 2 * P * L.nz + (i - P - L.nz) * L.nxp + j;
+    if (j < P) return P * L.nxp + (i - P) * 2 * P + j;
+    if (j >= P + L.nx) return P * L.nxp + (i - P) * 2 * P + P + (j - P - L.nx);
+    return -1;
+}
+
+// ------------------------------------------------------- receiver tables
+// Receivers of each (tile, shot), for a tiling of TX x TZ: entries
+// [ptr[t*ns+s], ptr[t*ns+s+1]) of ent, each {local = zl*TX + xl, r}.
+struct RecTable {
+    const int *ptr;
+    const int2 *ent;
+};
+
+// ------------------------------------------------------------ kernel args
+struct StepCommon {
+    Lay2D L;
+    const float *c2;       // (v dt / dx)^2, field layout
+    const int *src_off;    // [ns] field offset of each source cell
+    const float *wav;      // [ns][nt]
+    float src_scale;       // dx^(2 - ndim)
+    int ns, nt, nrec;
+    int ntx, ntz;          // tiles of this launch's tiling
+    int spg;               // shots per group (blockIdx.z)
+    int *status;           // device status flags
+};
+
+struct FwdArgs {
+    StepCommon c;
+    const float *ucur;     // u^n  (shot s at + s*fstride)
+    float *uprev;          // u^{n-1} in, u^{n+1} out
+    float *band;           // [ns][nt][nband] checkpoints (u^{n+1} stored) or null
+    float *seis;           // [ns][nt][nrec] traces or null
+    float *acc_illum;      // [G][nz][nx] or null
+    float *acc_offh;       // [G][hmax+1][nz][nx] or null
+    RecTable rt;
+    int n;                 // time level of ucur
+    int last;              // n == nt-1: extract and accumulate only
+    int illum_utt;         // accumulate (u^{n+1}-2u^n+u^{n-1})^2 instead of u^2
+    int hmax;
+};
+
+struct BwdArgs {
+    StepCommon c;
+    float *ua;             // u^m in, u^{m-2} out
+    const float *ub;       // u^{m-1}
+    const float *pa;       // psi^{m+1}
+    float *pb;             // psi^{m+2} in, psi^m out
+    const float *band;     // [ns][nt][nband] checkpoints
+    const float *adj;      // [ns][nt][nrec] adjoint source
+    float *acc_grad;       // [G][nzp][nxp] sum psi^m * (L u^{m-1} + s^{m-1}) * dx^2
+    RecTable rt;
+    float adj_scale;       // dx^2
+    int m;
+};
+
+// status bits written by kernels
+enum : int {
+    ST_NONFINITE = 1,
+    ST_BAD_VELOCITY = 2,
+    ST_CFL = 4,
+    ST_TIMEOUT = 8
+};
+
+// ------------------------------------------------------------- launchers
+// Tiling of the step kernels: rz rows per thread (tile height 8*rz).
+struct Tiling {
+    int tz;       // tile height
+    int ntx, ntz; // tiles
+    int groups;   // shot groups (grid.z)
+    int spg;      // shots per group
+};
+Tiling make_tiling(const Lay2D &L, int ns, int tz, int target_ctas);
+
+cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st);
+cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st);
+
+// auxiliary kernels (fwi_aux.cu)
+cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float cfl_limit,
+                           int *status, cudaStream_t st);
+cudaError_t launch_residual_ols(float *syn, const float *obs, long long n, double *misfit,
+                                cudaStream_t st);
+cudaError_t launch_time_integral(float *r, int ns, int nt, int nrec, float dt, double *misfit,
+                                 cudaStream_t st);
+cudaError_t launch_fold_grad(const Lay2D &L, const float *acc, int groups, const float *v,
+                             float *grad, cudaStream_t st);
+cudaError_t launch_finish_accum(const Lay2D &L, const float *acc, int groups, int planes,
+                                float scale, float *out, cudaStream_t st);
+cudaError_t launch_precond(const Lay2D &L, const float *grad, const float *scale, int kind,
+                           int hmax, float eps, float *out, unsigned *pmax, cudaStream_t st);
+cudaError_t launch_check_finite(const float *x, long long n, int *status, cudaStream_t st);
+
+} // namespace fwi

@@ -1,0 +1,258 @@
+"""Python binding of the C ABI (include/fwi.h): argument marshalling only.
+
+Every step of the path runs in libfwi's CUDA kernels. PyTorch supplies device
+memory (the workspace and outputs are torch CUDA tensors) and the stream; the
+functions below fill the C structs, pass raw pointers and raise FwiError on a
+non-OK status.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import FwiError  # noqa: F401  (re-export)
+
+OPS = {"forward": L.FWI_OP_FORWARD, "forward_save": L.FWI_OP_FORWARD_SAVE,
+       "gradient": L.FWI_OP_GRADIENT, "illumination": L.FWI_OP_ILLUMINATION,
+       "offset_hessian": L.FWI_OP_OFFSET_HESSIAN, "precondition": L.FWI_OP_PRECONDITION}
+
+
+@dataclass
+class Grid:
+    """fwi_grid: physical nz x nx model, spacing dx (m), step dt (s), nt levels."""
+    nz: int
+    nx: int
+    dx: float
+    dt: float
+    nt: int
+    sponge: int = 20
+    vref: float = 3000.0
+    refl: float = 0.05
+
+    def c(self) -> L.FwiGrid:
+        return L.FwiGrid(2, self.nz, 1, self.nx, self.dx, self.dt, self.nt, self.sponge, self.vref,
+                         self.refl)
+
+    @property
+    def shape(self):
+        return (self.nz, self.nx)
+
+
+class Geometry:
+    """fwi_geometry: src [ns,3] and rec [ns,nrec,3] int32 host arrays of
+    (z, y, x) model cells, wavelet [ns, nt] float32 CUDA tensor."""
+
+    def __init__(self, src, rec, wavelet: torch.Tensor):
+        self.src = np.ascontiguousarray(src, dtype=np.int32).reshape(-1, 3)
+        ns = self.src.shape[0]
+        self.rec = np.ascontiguousarray(rec, dtype=np.int32).reshape(ns, -1, 3)
+        if not (isinstance(wavelet, torch.Tensor) and wavelet.is_cuda and wavelet.dtype == torch.float32):
+            raise TypeError("wavelet must be a float32 CUDA tensor")
+        self.wavelet = wavelet.contiguous()
+
+    @property
+    def nshots(self) -> int:
+        return self.src.shape[0]
+
+    @property
+    def nrec(self) -> int:
+        return self.rec.shape[1]
+
+    def c(self) -> L.FwiGeometry:
+        return L.FwiGeometry(self.nshots, self.nrec, self.src.ctypes.data, self.rec.ctypes.data,
+                             self.wavelet.data_ptr())
+
+
+@dataclass
+class Options:
+    """fwi_options: misfit 'ols' | 'integral', illum 'u2' | 'utt2', hmax
+    (-1 = no offset Hessian), precond 'none' | 'illum' | 'offset', eps."""
+    misfit: str = "ols"
+    illum: str = "u2"
+    hmax: int = -1
+    precond: str = "illum"
+    eps: float = 1e-3
+
+    def c(self) -> L.FwiOptions:
+        m = {"ols": L.FWI_MISFIT_OLS, "integral": L.FWI_MISFIT_TIME_INTEGRAL}[self.misfit]
+        i = {"u2": L.FWI_ILLUM_U2, "utt2": L.FWI_ILLUM_UTT2}[self.illum]
+        p = {"none": L.FWI_PRECOND_NONE, "illum": L.FWI_PRECOND_ILLUM,
+             "offset": L.FWI_PRECOND_OFFSET}[self.precond]
+        return L.FwiOptions(m, i, int(self.hmax), p, float(self.eps))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, shape=None, dtype=torch.float32):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def workspace_bytes(grid: Grid, geom: Geometry, opts: Options | None, op: str) -> int:
+    n = ctypes.c_size_t(0)
+    g, ge = grid.c(), geom.c()
+    o = opts.c() if opts is not None else None
+    L.check(L.load().fwi_workspace_bytes(ctypes.byref(g), ctypes.byref(ge),
+                                         ctypes.byref(o) if o is not None else None,
+                                         OPS[op], ctypes.byref(n)), "fwi_workspace_bytes")
+    return int(n.value)
+
+
+class Workspace:
+    """A reusable device workspace (grows on demand)."""
+
+    def __init__(self, device=None):
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = None
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def _ws(ws, nbytes):
+    if ws is None:
+        ws = Workspace()
+    buf = ws.get(nbytes) if isinstance(ws, Workspace) else ws
+    return buf, buf.numel()
+
+
+def forward(grid: Grid, geom: Geometry, v: torch.Tensor, *, save=False, out=None, ws=None,
+            opts: Options | None = None, stream=None) -> torch.Tensor:
+    """fwi_forward: traces [ns, nt, nrec] of every shot."""
+    _dev(v, "v", grid.shape)
+    seis = out if out is not None else torch.empty((geom.nshots, grid.nt, geom.nrec),
+                                                   dtype=torch.float32, device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "forward_save" if save else "forward"))
+    g, ge = grid.c(), geom.c()
+    o = opts.c() if opts is not None else None
+    L.check(L.load().fwi_forward(ctypes.byref(g), ctypes.byref(ge),
+                                 ctypes.byref(o) if o is not None else None, _ptr(v), _ptr(seis),
+                                 int(bool(save)), _ptr(buf), nb, _stream(stream)), "fwi_forward")
+    return seis
+
+
+def adjoint_apply(grid: Grid, geom: Geometry, v: torch.Tensor, adj_src: torch.Tensor, ws, *,
+                  out=None, opts: Options | None = None, stream=None) -> torch.Tensor:
+    """fwi_adjoint_apply: gradient of <adj_src, traces> w.r.t. v, after
+    forward(save=True) on the same workspace."""
+    _dev(v, "v", grid.shape)
+    _dev(adj_src, "adj_src", (geom.nshots, grid.nt, geom.nrec))
+    grad = out if out is not None else torch.empty(grid.shape, dtype=torch.float32, device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "forward_save"))
+    g, ge = grid.c(), geom.c()
+    o = opts.c() if opts is not None else None
+    L.check(L.load().fwi_adjoint_apply(ctypes.byref(g), ctypes.byref(ge),
+                                       ctypes.byref(o) if o is not None else None, _ptr(v),
+                                       _ptr(adj_src), _ptr(grad), _ptr(buf), nb, _stream(stream)),
+            "fwi_adjoint_apply")
+    return grad
+
+
+def adjoint_gradient(grid: Grid, geom: Geometry, v: torch.Tensor, d_obs: torch.Tensor,
+                     opts: Options | None = None, *, want_pre=True, want_illum=True,
+                     want_offh=None, ws=None, out=None, stream=None) -> dict:
+    """fwi_adjoint_gradient: the whole preconditioned gradient.
+    Returns dict(grad, grad_pre?, misfit (0-d float64 CUDA tensor), illum?, offh?)."""
+    opts = opts or Options()
+    _dev(v, "v", grid.shape)
+    _dev(d_obs, "d_obs", (geom.nshots, grid.nt, geom.nrec))
+    dev = v.device
+    want_offh = opts.hmax >= 0 if want_offh is None else want_offh
+    o = out or {}
+    res = {"grad": o.get("grad", torch.empty(grid.shape, dtype=torch.float32, device=dev)),
+           "misfit": o.get("misfit", torch.zeros((), dtype=torch.float64, device=dev))}
+    if want_pre:
+        res["grad_pre"] = o.get("grad_pre", torch.empty(grid.shape, dtype=torch.float32, device=dev))
+    if want_illum:
+        res["illum"] = o.get("illum", torch.empty(grid.shape, dtype=torch.float32, device=dev))
+    if want_offh:
+        res["offh"] = o.get("offh", torch.empty((opts.hmax + 1,) + grid.shape, dtype=torch.float32,
+                                                device=dev))
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "gradient"))
+    g, ge, oc = grid.c(), geom.c(), opts.c()
+    L.check(L.load().fwi_adjoint_gradient(
+        ctypes.byref(g), ctypes.byref(ge), ctypes.byref(oc), _ptr(v), _ptr(d_obs), _ptr(res["grad"]),
+        _ptr(res.get("grad_pre")), _ptr(res["misfit"]), _ptr(res.get("illum")), _ptr(res.get("offh")),
+        _ptr(buf), nb, _stream(stream)), "fwi_adjoint_gradient")
+    return res
+
+
+def illumination(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options | None = None, *,
+                 ws=None, stream=None) -> torch.Tensor:
+    """fwi_illumination: sum_s sum_n u^2 dt (or u_tt^2 dt), [nz, nx]."""
+    opts = opts or Options()
+    _dev(v, "v", grid.shape)
+    out = torch.empty(grid.shape, dtype=torch.float32, device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "illumination"))
+    g, ge, oc = grid.c(), geom.c(), opts.c()
+    L.check(L.load().fwi_illumination(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(oc), _ptr(v),
+                                      _ptr(out), _ptr(buf), nb, _stream(stream)), "fwi_illumination")
+    return out
+
+
+def offset_hessian_diag(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options, *, ws=None,
+                        stream=None) -> torch.Tensor:
+    """fwi_offset_hessian_diag: [hmax+1, nz, nx] source-side offset-Hessian diagonal."""
+    _dev(v, "v", grid.shape)
+    out = torch.empty((opts.hmax + 1,) + grid.shape, dtype=torch.float32, device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "offset_hessian"))
+    g, ge, oc = grid.c(), geom.c(), opts.c()
+    L.check(L.load().fwi_offset_hessian_diag(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(oc),
+                                             _ptr(v), _ptr(out), _ptr(buf), nb, _stream(stream)),
+            "fwi_offset_hessian_diag")
+    return out
+
+
+def precondition(grid: Grid, grad: torch.Tensor, scale: torch.Tensor, kind: str, eps=1e-3, *,
+                 ws=None, stream=None) -> torch.Tensor:
+    """fwi_precondition: grad / (P + eps max P), kind 'illum' or 'offset'."""
+    _dev(grad, "grad", grid.shape)
+    k = {"illum": L.FWI_PRECOND_ILLUM, "offset": L.FWI_PRECOND_OFFSET}[kind]
+    hmax = scale.shape[0] - 1 if kind == "offset" else 0
+    _dev(scale, "scale", grid.shape if kind == "illum" else (hmax + 1,) + grid.shape)
+    out = torch.empty_like(grad)
+    g = grid.c()
+    nbytes = ctypes.c_size_t(0)
+    L.check(L.load().fwi_workspace_bytes(ctypes.byref(g), None, None, L.FWI_OP_PRECONDITION,
+                                         ctypes.byref(nbytes)), "fwi_workspace_bytes")
+    buf, nb = _ws(ws, int(nbytes.value))
+    L.check(L.load().fwi_precondition(ctypes.byref(g), _ptr(grad), _ptr(scale), k, hmax, float(eps),
+                                      _ptr(out), _ptr(buf), nb, _stream(stream)), "fwi_precondition")
+    return out
+
+
+def profile(on: bool = True):
+    L.check(L.load().fwi_profile_enable(int(on)), "fwi_profile_enable")
+
+
+def last_phase_times() -> dict:
+    t = L.FwiPhaseTimes()
+    L.check(L.load().fwi_profile_last(ctypes.byref(t)), "fwi_profile_last")
+    return {k: getattr(t, k) for k, _ in L.FwiPhaseTimes._fields_}
+
+
+# ------------------------------------------------------------------ conveniences
+
+def from_problem(prob, device="cuda"):
+    """(Grid, Geometry) of a workloads.Problem, the wavelet uploaded to the GPU."""
+    grid = Grid(prob.nz, prob.nx, float(prob.dx), float(prob.dt), int(prob.nt), int(prob.sponge),
+                float(prob.vref), float(prob.refl))
+    wav = torch.as_tensor(np.ascontiguousarray(prob.wavelet, dtype=np.float32), device=device)
+    return grid, Geometry(prob.src, prob.rec, wav)

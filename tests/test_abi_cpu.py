@@ -1,0 +1,151 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+entry point declared in include/*.h, and rejects bad arguments on the host
+(no compute calls are made here)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(fwi_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1406_1864_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["fwi_forward", "fwi_adjoint_gradient", "fwi_illumination", "fwi_offset_hessian_diag",
+                 "fwi_adjoint_apply", "fwi_workspace_bytes", "fwi_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert lib.fwi_version() >= 100
+
+
+def test_library_is_sm103a_only():
+    from paper_1406_1864_gb300 import build as b
+    assert "arch=compute_103a,code=sm_103a" in " ".join(b.ARCH)
+
+
+def _structs(nz=30, nx=40, nt=100, ns=2, nrec=5):
+    from paper_1406_1864_gb300 import _lib as L
+    g = L.FwiGrid(2, nz, 1, nx, 10.0, 1e-3, nt, 10, 3000.0, 0.05)
+    src = np.zeros((ns, 3), np.int32)
+    src[:, 2] = [5, 30][:ns] if ns <= 2 else np.arange(ns) % nx
+    rec = np.zeros((ns, nrec, 3), np.int32)
+    rec[:, :, 2] = np.arange(nrec)
+    ge = L.FwiGeometry(ns, nrec, src.ctypes.data, rec.ctypes.data, 1)
+    o = L.FwiOptions(0, 0, 3, 1, 1e-3)
+    return g, ge, o, (src, rec)
+
+
+def ws_bytes(lib, g, ge, o, op):
+    n = ctypes.c_size_t(0)
+    st = lib.fwi_workspace_bytes(ctypes.byref(g), ctypes.byref(ge) if ge is not None else None,
+                                 ctypes.byref(o) if o is not None else None, op, ctypes.byref(n))
+    return st, n.value
+
+
+def test_workspace_sizes(lib):
+    from paper_1406_1864_gb300 import _lib as L
+    g, ge, o, keep = _structs()
+    sizes = {}
+    for op in range(6):
+        st, n = ws_bytes(lib, g, ge, o, op)
+        assert st == L.FWI_OK, lib.fwi_last_error()
+        sizes[op] = n
+    # the gradient holds the per-step sponge checkpoints: >= ns * nt * sponge cells * 4 B
+    P, nz, nx, nt, ns = 10, 30, 40, 100, 2
+    nband = 2 * P * (nx + 2 * P) + 2 * P * nz
+    assert sizes[L.FWI_OP_GRADIENT] >= ns * nt * nband * 4
+    assert sizes[L.FWI_OP_FORWARD] < sizes[L.FWI_OP_FORWARD_SAVE] <= sizes[L.FWI_OP_GRADIENT]
+    # more shots, more workspace
+    g2, ge2, o2, keep2 = _structs(ns=2, nt=200)
+    assert ws_bytes(lib, g2, ge2, o2, L.FWI_OP_GRADIENT)[1] > sizes[L.FWI_OP_GRADIENT]
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("ndim", 3, 1), ("ny", 2, 1), ("nz", 0, 1), ("nt", 1, 1), ("sponge", 0, 1), ("dx", 0.0, 1),
+    ("dt", -1.0, 1), ("refl", 1.0, 1), ("vref", 0.0, 1)])
+def test_bad_grid_rejected(lib, field, value, code):
+    g, ge, o, keep = _structs()
+    setattr(g, field, value)
+    st, _ = ws_bytes(lib, g, ge, o, 2)
+    assert st == code
+    assert len(lib.fwi_last_error()) > 0
+
+
+@pytest.mark.parametrize("field,value", [("misfit", 7), ("illum_mode", 3), ("hmax", 13),
+                                         ("hmax", -2), ("precond", 5), ("eps", 0.0)])
+def test_bad_options_rejected(lib, field, value):
+    from paper_1406_1864_gb300 import _lib as L
+    g, ge, o, keep = _structs()
+    setattr(o, field, value)
+    st, _ = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
+    assert st == L.FWI_ERR_INVALID_ARG
+
+
+def test_offset_precond_needs_hmax(lib):
+    from paper_1406_1864_gb300 import _lib as L
+    g, ge, o, keep = _structs()
+    o.hmax, o.precond = -1, L.FWI_PRECOND_OFFSET
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[0] == L.FWI_ERR_INVALID_ARG
+    o.precond = L.FWI_PRECOND_ILLUM
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_OFFSET_HESSIAN)[0] == L.FWI_ERR_INVALID_ARG
+
+
+def test_call_argument_errors_before_any_device_work(lib):
+    """Entry points reject bad coordinates / NULL pointers / small workspaces
+    before they queue anything (these return without touching a GPU)."""
+    from paper_1406_1864_gb300 import _lib as L
+    g, ge, o, (src, rec) = _structs()
+    src[0, 0] = 30  # row out of range
+    st = lib.fwi_forward(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1),
+                         ctypes.c_void_p(1), 0, ctypes.c_void_p(256), 1 << 40, None)
+    assert st == L.FWI_ERR_INVALID_ARG and b"outside" in lib.fwi_last_error()
+    src[0, 0] = 0
+    st = lib.fwi_forward(ctypes.byref(g), ctypes.byref(ge), None, None, ctypes.c_void_p(1), 0,
+                         ctypes.c_void_p(256), 1 << 40, None)
+    assert st == L.FWI_ERR_INVALID_ARG
+    st = lib.fwi_forward(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1),
+                         ctypes.c_void_p(1), 0, ctypes.c_void_p(256), 16, None)
+    assert st == L.FWI_ERR_NOMEM
+    st = lib.fwi_forward(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1),
+                         ctypes.c_void_p(1), 0, ctypes.c_void_p(8), 1 << 40, None)
+    assert st == L.FWI_ERR_INVALID_ARG  # misaligned workspace
+    ge.src = None
+    st = lib.fwi_forward(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1),
+                         ctypes.c_void_p(1), 0, ctypes.c_void_p(256), 1 << 40, None)
+    assert st == L.FWI_ERR_INVALID_ARG
+
+
+def test_product_path_does_not_import_the_oracle():
+    import subprocess
+    import sys
+    code = ("import sys; import paper_1406_1864_gb300.fwi, paper_1406_1864_gb300.workloads; "
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
+    out = subprocess.check_output([sys.executable, "-c", code], cwd=ROOT).decode().strip()
+    assert out == "False"
+    for f in glob.glob(os.path.join(ROOT, "paper_1406_1864_gb300", "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".h", ".cuh")):
+            txt = open(f).read()
+            assert "import oracle" not in txt and "from oracle" not in txt, f
