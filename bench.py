@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
+    ap.add_argument("--shots", type=int, default=0, help="use only the first N shots (profiling)")
+    ap.add_argument("--nt", type=int, default=0, help="use only the first N time levels (profiling)")
     return ap.parse_args()
 
 
@@ -65,6 +67,16 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def load_workload(args):
+    from paper_1406_1864_gb300 import workloads as W
+    prob = W.workload(args.workload)
+    if args.shots:
+        prob = prob.subset(list(range(min(args.shots, prob.nshots))))
+    if args.nt:
+        prob = prob.with_nt(args.nt)
+    return prob
 
 
 def options_for(variant):
@@ -108,8 +120,7 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
-    from paper_1406_1864_gb300 import workloads as W
-    prob = W.workload(args.workload)
+    prob = load_workload(args)
     cores = os.cpu_count() or 1
     per = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
@@ -232,7 +243,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     from paper_1406_1864_gb300 import fwi, workloads as W
-    prob = W.workload(args.workload)
+    prob = load_workload(args)
     grid, geom = fwi.from_problem(prob)
     opts = options_for(args.variant)
     dev = torch.device("cuda", local)
@@ -339,7 +350,9 @@ def run_ours(args):
             "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "variant": args.variant,
+            "config": {"workload": args.workload + (f" (first {prob.nshots} shots, nt {prob.nt})"
+                                                    if (args.shots or args.nt) else ""),
+                       "variant": args.variant,
                        "grid": [prob.nz, prob.nx], "dx_m": prob.dx, "dt_s": prob.dt, "nt": prob.nt,
                        "shots": prob.nshots, "receivers": prob.nrec, "sponge": prob.sponge,
                        "misfit": opts.misfit, "offset_hessian_hmax": opts.hmax,

@@ -21,11 +21,6 @@
 #include <string>
 #include <vector>
 
-namespace fwi {
-int fwd_tile_height(bool with_offh);
-int bwd_tile_height();
-} // namespace fwi
-
 using namespace fwi;
 
 namespace {
@@ -64,25 +59,6 @@ struct Part {
     size_t off = 0, bytes = 0;
 };
 
-int sm_count()
-{
-    static int n = -1;
-    if (n < 0) {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-            n = v;
-        else {
-            cudaGetLastError();
-            n = 152;
-        }
-    }
-    return n;
-}
-
-// resident CTAs per SM assumed when sizing the shot groups
-constexpr int RES_FWD = 4, RES_FWD_H = 3, RES_BWD = 3;
-
 struct Plan {
     Lay2D L{};
     int ns = 0, nt = 0, nrec = 0, hmax = -1, op = 0;
@@ -91,7 +67,7 @@ struct Plan {
     bool need_seis_tab = false;
     Tiling tf{}, tb{};
     Part scal, c2, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab;
-    size_t tab_src = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0;
+    size_t tab_src = 0, tab_srcij = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0;
     size_t total = 0;
 };
 
@@ -167,6 +143,7 @@ Lay2D make_layout(const fwi_grid *g)
     L.rows = L.nzp + 2 * GZ;
     L.fstride = (long long)align_up((size_t)L.rows * L.pitch, 64);
     L.nband = 2 * L.P * L.nxp + 2 * L.P * L.nz;
+    L.nbandp = (L.nband + 3) / 4 * 4;
     L.dt = g->dt;
     L.dx = g->dx;
     const double etamax = 3.0 * g->vref * std::log(1.0 / g->refl) / (2.0 * g->sponge * g->dx);
@@ -205,9 +182,8 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         return fail(FWI_ERR_INVALID_ARG, "offset Hessian needs hmax >= 0");
     pl.need_bwd = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE);
     pl.need_seis_tab = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE);
-    const int smc = sm_count();
-    pl.tf = make_tiling(L, pl.ns, fwd_tile_height(pl.with_offh), smc * (pl.with_offh ? RES_FWD_H : RES_FWD));
-    pl.tb = make_tiling(L, pl.ns, bwd_tile_height(), smc * RES_BWD);
+    pl.tf = make_tiling(L, pl.ns, pl.with_offh ? STEP_FWD_OFFH : STEP_FWD);
+    pl.tb = make_tiling(L, pl.ns, STEP_BWD);
     const size_t fbytes = (size_t)L.fstride * sizeof(float);
     const size_t nphys = (size_t)L.nz * L.nx;
     take(pl.c2, fbytes);
@@ -216,13 +192,13 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
     if (pl.need_bwd) {
         take(pl.p[0], fbytes * pl.ns);
         take(pl.p[1], fbytes * pl.ns);
-        take(pl.band, (size_t)pl.ns * pl.nt * L.nband * sizeof(float));
-        take(pl.acc_g, (size_t)pl.tb.groups * L.nzp * L.nxp * sizeof(float));
+        take(pl.band, (size_t)pl.ns * pl.nt * L.nbandp * sizeof(float));
+        take(pl.acc_g, (size_t)L.nzp * L.nxp * sizeof(float));
     }
     if (op == FWI_OP_GRADIENT) take(pl.syn, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
     if (op == FWI_OP_GRADIENT || op == FWI_OP_ILLUMINATION)
-        take(pl.acc_i, (size_t)pl.tf.groups * nphys * sizeof(float));
-    if (pl.with_offh) take(pl.acc_h, (size_t)pl.tf.groups * (pl.hmax + 1) * nphys * sizeof(float));
+        take(pl.acc_i, nphys * sizeof(float));
+    if (pl.with_offh) take(pl.acc_h, (size_t)(pl.hmax + 1) * nphys * sizeof(float));
     // tables: src offsets, receiver CSR of the forward and backward tilings
     size_t t = 0;
     auto tk = [&](size_t &o2, size_t bytes) {
@@ -230,6 +206,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         t = align_up(t + bytes, 16);
     };
     tk(pl.tab_src, (size_t)pl.ns * sizeof(int));
+    tk(pl.tab_srcij, (size_t)pl.ns * sizeof(int2));
     const size_t nent = (size_t)pl.ns * pl.nrec;
     tk(pl.tab_fptr, ((size_t)pl.tf.ntx * pl.tf.ntz * pl.ns + 1) * sizeof(int));
     tk(pl.tab_fent, std::max<size_t>(nent, 1) * sizeof(int2));
@@ -284,9 +261,11 @@ fwi_status upload_tables(const Plan &pl, const fwi_geometry *ge, void *ws, cudaS
 {
     std::vector<char> buf(pl.tab.bytes, 0);
     int *src = reinterpret_cast<int *>(buf.data() + pl.tab_src);
+    int2 *srcij = reinterpret_cast<int2 *>(buf.data() + pl.tab_srcij);
     for (int s = 0; s < pl.ns; ++s) {
         const int *c = ge->src + 3 * s;
         src[s] = (int)fidx(pl.L, c[0] + pl.L.P, c[2] + pl.L.P);
+        srcij[s] = make_int2(c[0] + pl.L.P, c[2] + pl.L.P);
     }
     if (pl.nrec > 0) {
         build_csr(pl, pl.tf, ge->rec, buf, pl.tab_fptr, pl.tab_fent);
@@ -322,6 +301,7 @@ StepCommon make_common(const Plan &pl, const fwi_geometry *ge, void *ws, const T
     c.L = pl.L;
     c.c2 = at<float>(ws, pl.c2);
     c.src_off = at<int>(ws, pl.tab, pl.tab_src);
+    c.src_ij = at<int2>(ws, pl.tab, pl.tab_srcij);
     c.wav = ge->wavelet;
     c.src_scale = 1.0f; // dx^(2-ndim) in 2-D
     c.ns = pl.ns;
@@ -329,7 +309,6 @@ StepCommon make_common(const Plan &pl, const fwi_geometry *ge, void *ws, const T
     c.nrec = pl.nrec;
     c.ntx = t.ntx;
     c.ntz = t.ntz;
-    c.spg = t.spg;
     c.status = at<int>(ws, pl.scal, 8);
     return c;
 }
@@ -370,12 +349,20 @@ fwi_status run_forward(const Plan &pl, const fwi_geometry *ge, void *ws, float *
     a.illum_utt = illum_utt;
     a.hmax = pl.hmax;
     float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
+    const bool offh = pl.with_offh && acc_h;
+    int hx, hy, px, py;
+    step_boxes(offh ? STEP_FWD_OFFH : STEP_FWD, hx, hy, px, py);
+    CUtensorMap mh[2], mp[2];
+    for (int b = 0; b < 2; ++b)
+        if (!encode_field_map(&mh[b], U[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&mp[b], U[b], pl.L, pl.ns, px, py))
+            return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
     for (int n = 0; n < pl.nt; ++n) {
         a.n = n;
         a.last = (n == pl.nt - 1);
-        a.ucur = U[n & 1];
+        a.tm_cur = mh[n & 1];
+        a.tm_prev = mp[(n + 1) & 1];
         a.uprev = U[(n + 1) & 1];
-        if ((e = launch_fwd_step(a, pl.tf, pl.with_offh && acc_h, st)) != cudaSuccess)
+        if ((e = launch_fwd_step(a, pl.tf, offh, st)) != cudaSuccess)
             return cuda_fail(e, "forward step");
         t_launch[0]++;
     }
@@ -410,11 +397,20 @@ fwi_status run_backward(const Plan &pl, const fwi_geometry *ge, void *ws, const 
         // no receivers: adjoint source is empty; tables hold no entries
         a.adj = nullptr;
     }
+    int hx, hy, px, py;
+    step_boxes(STEP_BWD, hx, hy, px, py);
+    CUtensorMap uh[2], up[2], ph[2], pp[2];
+    for (int b = 0; b < 2; ++b)
+        if (!encode_field_map(&uh[b], U[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&up[b], U[b], pl.L, pl.ns, px, py) ||
+            !encode_field_map(&ph[b], Pp[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&pp[b], Pp[b], pl.L, pl.ns, px, py))
+            return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
     for (int m = pl.nt - 1; m >= 1; --m) {
         a.m = m;
+        a.tm_ub = uh[(m - 1) & 1];
+        a.tm_pa = ph[(m + 1) & 1];
+        a.tm_ua = up[m & 1];
+        a.tm_pb = pp[m & 1];
         a.ua = U[m & 1];
-        a.ub = U[(m - 1) & 1];
-        a.pa = Pp[(m + 1) & 1];
         a.pb = Pp[m & 1];
         if ((e = launch_bwd_step(a, pl.tb, st)) != cudaSuccess) return cuda_fail(e, "backward step");
         t_launch[1]++;
@@ -529,7 +525,7 @@ fwi_status fwi_adjoint_apply(const fwi_grid *grid, const fwi_geometry *geom, con
     if ((s = upload_tables(pl, geom, ws, st)) != FWI_OK) return s;
     if ((s = run_backward(pl, geom, ws, adj_src, st)) != FWI_OK) return s;
     prof_record(2, st);
-    if ((e = launch_fold_grad(pl.L, at<float>(ws, pl.acc_g), pl.tb.groups, v, grad, st)) != cudaSuccess)
+    if ((e = launch_fold_grad(pl.L, at<float>(ws, pl.acc_g), 1, v, grad, st)) != cudaSuccess)
         return cuda_fail(e, "fold kernel");
     t_launch[2]++;
     prof_record(3, st);
@@ -569,19 +565,19 @@ fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom, 
     }
     if ((s = run_backward(pl, geom, ws, syn, st)) != FWI_OK) return s;
     prof_record(2, st);
-    if ((e = launch_fold_grad(pl.L, at<float>(ws, pl.acc_g), pl.tb.groups, v, grad, st)) != cudaSuccess)
+    if ((e = launch_fold_grad(pl.L, at<float>(ws, pl.acc_g), 1, v, grad, st)) != cudaSuccess)
         return cuda_fail(e, "fold kernel");
     t_launch[2]++;
     // illumination: dt sum u^2, or (1/dt^3) sum (second difference)^2
     const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
     float *ill_out = illum ? illum : acc_i; // in place into group 0 when not requested
-    if ((e = launch_finish_accum(pl.L, acc_i, pl.tf.groups, 1, iscale, ill_out, st)) != cudaSuccess)
+    if ((e = launch_finish_accum(pl.L, acc_i, 1, 1, iscale, ill_out, st)) != cudaSuccess)
         return cuda_fail(e, "illumination output");
     t_launch[2]++;
     float *off_out = nullptr;
     if (acc_h) {
         off_out = offh ? offh : acc_h;
-        if ((e = launch_finish_accum(pl.L, acc_h, pl.tf.groups, pl.hmax + 1, pl.L.dt, off_out, st)) != cudaSuccess)
+        if ((e = launch_finish_accum(pl.L, acc_h, 1, pl.hmax + 1, pl.L.dt, off_out, st)) != cudaSuccess)
             return cuda_fail(e, "offset-Hessian output");
         t_launch[2]++;
     }
@@ -621,7 +617,7 @@ fwi_status fwi_illumination(const fwi_grid *grid, const fwi_geometry *geom, cons
     prof_record(2, st);
     const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
     cudaError_t e;
-    if ((e = launch_finish_accum(pl.L, acc_i, pl.tf.groups, 1, iscale, illum, st)) != cudaSuccess)
+    if ((e = launch_finish_accum(pl.L, acc_i, 1, 1, iscale, illum, st)) != cudaSuccess)
         return cuda_fail(e, "illumination output");
     t_launch[2]++;
     prof_record(3, st);
@@ -644,7 +640,7 @@ fwi_status fwi_offset_hessian_diag(const fwi_grid *grid, const fwi_geometry *geo
     prof_record(1, st);
     prof_record(2, st);
     cudaError_t e;
-    if ((e = launch_finish_accum(pl.L, acc_h, pl.tf.groups, pl.hmax + 1, pl.L.dt, offh, st)) != cudaSuccess)
+    if ((e = launch_finish_accum(pl.L, acc_h, 1, pl.hmax + 1, pl.L.dt, offh, st)) != cudaSuccess)
         return cuda_fail(e, "offset-Hessian output");
     t_launch[2]++;
     prof_record(3, st);

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace fwi {
@@ -32,6 +33,7 @@ struct Lay2D {
     int rows;             // stored rows = nzp + 2 GZ
     long long fstride;    // floats per stored field (rows * pitch), 64-float aligned
     int nband;            // sponge cells of one field (checkpointed each step)
+    int nbandp;           // per-step checkpoint stride: nband rounded up to 4 floats
     float dt, dx;
     float etamax_dt;      // eta_max * dt
     float inv_p2;         // 1 / P^2
@@ -74,38 +76,45 @@ struct StepCommon {
     Lay2D L;
     const float *c2;       // (v dt / dx)^2, field layout
     const int *src_off;    // [ns] field offset of each source cell
+    const int2 *src_ij;    // [ns] padded (row, column) of each source cell
     const float *wav;      // [ns][nt]
     float src_scale;       // dx^(2 - ndim)
     int ns, nt, nrec;
     int ntx, ntz;          // tiles of this launch's tiling
-    int spg;               // shots per group (blockIdx.z)
     int *status;           // device status flags
 };
 
+// Time-loop kernels read their tiles with TMA: 3-D tensor maps over the
+// [ns][rows][pitch] wavefield buffers, one "halo" box (tile + stencil halo)
+// and one "point" box (tile only) per buffer. CUtensorMap carries its own
+// alignment and is read from the kernel's parameter space (__grid_constant__).
 struct FwdArgs {
+    CUtensorMap tm_cur;    // u^n, halo box
+    CUtensorMap tm_prev;   // u^{n-1}, point box
     StepCommon c;
-    const float *ucur;     // u^n  (shot s at + s*fstride)
-    float *uprev;          // u^{n-1} in, u^{n+1} out
-    float *band;           // [ns][nt][nband] checkpoints (u^{n+1} stored) or null
+    float *uprev;          // u^{n-1} buffer: u^{n+1} is written here
+    float *band;           // [ns][nt][nbandp] checkpoints (u^{n+1} stored) or null
     float *seis;           // [ns][nt][nrec] traces or null
-    float *acc_illum;      // [G][nz][nx] or null
-    float *acc_offh;       // [G][hmax+1][nz][nx] or null
+    float *acc_illum;      // [nz][nx] or null (red.add)
+    float *acc_offh;       // [hmax+1][nz][nx] or null (red.add)
     RecTable rt;
-    int n;                 // time level of ucur
+    int n;                 // time level of u^n
     int last;              // n == nt-1: extract and accumulate only
     int illum_utt;         // accumulate (u^{n+1}-2u^n+u^{n-1})^2 instead of u^2
     int hmax;
 };
 
 struct BwdArgs {
+    CUtensorMap tm_ub;     // u^{m-1}, halo box
+    CUtensorMap tm_pa;     // psi^{m+1}, halo box
+    CUtensorMap tm_ua;     // u^m, point box
+    CUtensorMap tm_pb;     // psi^{m+2}, point box
     StepCommon c;
-    float *ua;             // u^m in, u^{m-2} out
-    const float *ub;       // u^{m-1}
-    const float *pa;       // psi^{m+1}
-    float *pb;             // psi^{m+2} in, psi^m out
-    const float *band;     // [ns][nt][nband] checkpoints
+    float *ua;             // u^m buffer: u^{m-2} is written here
+    float *pb;             // psi^{m+2} buffer: psi^m is written here
+    const float *band;     // [ns][nt][nbandp] checkpoints
     const float *adj;      // [ns][nt][nrec] adjoint source
-    float *acc_grad;       // [G][nzp][nxp] sum psi^m * (L u^{m-1} + s^{m-1}) * dx^2
+    float *acc_grad;       // [nzp][nxp] sum psi^m * (Lhat u^{m-1} + f delta_s) (red.add)
     RecTable rt;
     float adj_scale;       // dx^2
     int m;
@@ -120,15 +129,19 @@ enum : int {
 };
 
 // ------------------------------------------------------------- launchers
-// Tiling of the step kernels: rz rows per thread (tile height 8*rz).
+// Step kernels: grid (tiles, groups); CTA (t, g) owns tile t and shots
+// g, g + groups, ...
 struct Tiling {
-    int tz;       // tile height
-    int ntx, ntz; // tiles
-    int groups;   // shot groups (grid.z)
-    int spg;      // shots per group
+    int tz;        // tile height
+    int ntx, ntz;  // tiles
+    int groups;    // shot groups (as many as fill the resident CTA slots)
 };
-Tiling make_tiling(const Lay2D &L, int ns, int tz, int target_ctas);
+enum StepKind { STEP_FWD = 0, STEP_FWD_OFFH = 1, STEP_BWD = 2 };
+Tiling make_tiling(const Lay2D &L, int ns, StepKind kind);
+// box sizes (x, y) of the halo and point tiles of a step kernel
+void step_boxes(StepKind kind, int &hx, int &hy, int &px, int &py);
 
+bool encode_field_map(CUtensorMap *map, const float *base, const Lay2D &L, int nfields, int bx, int by);
 cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st);
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st);
 
