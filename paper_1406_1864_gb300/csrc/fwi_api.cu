@@ -67,7 +67,8 @@ struct Plan {
     bool need_seis_tab = false;
     Tiling tf{}, tb{};
     Part scal, c2, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab;
-    size_t tab_src = 0, tab_srcij = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0;
+    size_t tab_src = 0, tab_srcij = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0, tab_bshot = 0;
+    Part adj_t; // adjoint source in backward-table order [nt][ns*nrec]
     size_t total = 0;
 };
 
@@ -196,6 +197,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         take(pl.acc_g, (size_t)L.nzp * L.nxp * sizeof(float));
     }
     if (op == FWI_OP_GRADIENT) take(pl.syn, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
+    if (pl.need_bwd) take(pl.adj_t, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
     if (op == FWI_OP_GRADIENT || op == FWI_OP_ILLUMINATION)
         take(pl.acc_i, nphys * sizeof(float));
     if (pl.with_offh) take(pl.acc_h, (size_t)(pl.hmax + 1) * nphys * sizeof(float));
@@ -213,6 +215,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
     if (pl.need_bwd) {
         tk(pl.tab_bptr, ((size_t)pl.tb.ntx * pl.tb.ntz * pl.ns + 1) * sizeof(int));
         tk(pl.tab_bent, std::max<size_t>(nent, 1) * sizeof(int2));
+        tk(pl.tab_bshot, std::max<size_t>(nent, 1) * sizeof(int));
     }
     take(pl.tab, t);
     pl.total = off;
@@ -226,7 +229,7 @@ template <class T> T *at(void *ws, const Part &p, size_t extra)
 }
 
 void build_csr(const Plan &pl, const Tiling &t, const int *rec, std::vector<char> &buf, size_t ptr_off,
-               size_t ent_off)
+               size_t ent_off, size_t shot_off = (size_t)-1)
 {
     const Lay2D &L = pl.L;
     const int ntiles = t.ntx * t.ntz;
@@ -253,7 +256,9 @@ void build_csr(const Plan &pl, const Tiling &t, const int *rec, std::vector<char
         for (int r = 0; r < pl.nrec; ++r) {
             int loc;
             const int tl = tile_of(s, r, loc);
-            ent[fill[(size_t)tl * pl.ns + s]++] = make_int2(loc, r);
+            const int e = fill[(size_t)tl * pl.ns + s]++;
+            ent[e] = make_int2(loc, r);
+            if (shot_off != (size_t)-1) reinterpret_cast<int *>(buf.data() + shot_off)[e] = s;
         }
 }
 
@@ -269,7 +274,7 @@ fwi_status upload_tables(const Plan &pl, const fwi_geometry *ge, void *ws, cudaS
     }
     if (pl.nrec > 0) {
         build_csr(pl, pl.tf, ge->rec, buf, pl.tab_fptr, pl.tab_fent);
-        if (pl.need_bwd) build_csr(pl, pl.tb, ge->rec, buf, pl.tab_bptr, pl.tab_bent);
+        if (pl.need_bwd) build_csr(pl, pl.tb, ge->rec, buf, pl.tab_bptr, pl.tab_bent, pl.tab_bshot);
     }
     cudaError_t e = cudaMemcpyAsync(at<char>(ws, pl.tab), buf.data(), buf.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "upload of geometry tables");
@@ -386,17 +391,23 @@ fwi_status run_backward(const Plan &pl, const fwi_geometry *ge, void *ws, const 
     BwdArgs a{};
     a.c = make_common(pl, ge, ws, pl.tb);
     a.band = at<float>(ws, pl.band);
-    a.adj = adj;
+    a.adj = nullptr;
+    if (pl.nrec > 0) {
+        // adjoint source in the order of the backward receiver table: each
+        // (tile, shot) reads one contiguous run per time level
+        if ((e = launch_permute_adj(adj, at<int2>(ws, pl.tab, pl.tab_bent), at<int>(ws, pl.tab, pl.tab_bshot),
+                                    pl.ns * pl.nrec, pl.nt, pl.nrec, at<float>(ws, pl.adj_t), st)) != cudaSuccess)
+            return cuda_fail(e, "adjoint-source permutation");
+        t_launch[2]++;
+        a.adj = at<float>(ws, pl.adj_t);
+    }
+    a.nent = pl.ns * pl.nrec;
     a.acc_grad = at<float>(ws, pl.acc_g);
     a.rt.ptr = at<int>(ws, pl.tab, pl.tab_bptr);
     a.rt.ent = at<int2>(ws, pl.tab, pl.tab_bent);
     a.adj_scale = pl.L.dx * pl.L.dx;
     float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
     float *Pp[2] = {at<float>(ws, pl.p[0]), at<float>(ws, pl.p[1])};
-    if (pl.nrec == 0) {
-        // no receivers: adjoint source is empty; tables hold no entries
-        a.adj = nullptr;
-    }
     int hx, hy, px, py;
     step_boxes(STEP_BWD, hx, hy, px, py);
     CUtensorMap uh[2], up[2], ph[2], pp[2];

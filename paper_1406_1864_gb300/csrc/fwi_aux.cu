@@ -186,6 +186,20 @@ __global__ void k_check_finite(const float *__restrict__ x, long long n, int *st
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
 }
 
+// adj_t[m][e] = adj[shot(e)][m][rec(e)]: the adjoint source in the order of
+// the backward receiver table
+__global__ void k_permute_adj(const float *__restrict__ adj, const int2 *__restrict__ ent,
+                              const int *__restrict__ eshot, int nent, int nt, int nrec,
+                              float *__restrict__ adj_t)
+{
+    const long long n = (long long)nent * nt;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(q / nent), e = (int)(q - (long long)m * nent);
+        adj_t[q] = adj[((long long)eshot[e] * nt + m) * nrec + ent[e].y];
+    }
+}
+
 int grid_for(long long n)
 {
     long long b = (n + NT1 - 1) / NT1;
@@ -242,6 +256,13 @@ cudaError_t launch_precond(const Lay2D &L, const float *grad, const float *scale
     if (e != cudaSuccess) return e;
     k_precond_max<<<grid_for(nphys), NT1, 0, st>>>(nphys, scale, kind, hmax, pmax);
     k_precond_apply<<<grid_for(nphys), NT1, 0, st>>>(nphys, grad, scale, kind, hmax, eps, pmax, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_adj(const float *adj, const int2 *ent, const int *eshot, int nent, int nt, int nrec,
+                               float *adj_t, cudaStream_t st)
+{
+    k_permute_adj<<<grid_for((long long)nent * nt / 4 + 1), NT1, 0, st>>>(adj, ent, eshot, nent, nt, nrec, adj_t);
     return cudaGetLastError();
 }
 

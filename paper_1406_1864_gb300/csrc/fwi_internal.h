@@ -113,7 +113,8 @@ struct BwdArgs {
     float *ua;             // u^m buffer: u^{m-2} is written here
     float *pb;             // psi^{m+2} buffer: psi^m is written here
     const float *band;     // [ns][nt][nbandp] checkpoints
-    const float *adj;      // [ns][nt][nrec] adjoint source
+    const float *adj;      // [nt][nent] adjoint source in receiver-table order, or null
+    int nent;              // ns * nrec
     float *acc_grad;       // [nzp][nxp] sum psi^m * (Lhat u^{m-1} + f delta_s) (red.add)
     RecTable rt;
     float adj_scale;       // dx^2
@@ -159,5 +160,7 @@ cudaError_t launch_finish_accum(const Lay2D &L, const float *acc, int groups, in
 cudaError_t launch_precond(const Lay2D &L, const float *grad, const float *scale, int kind,
                            int hmax, float eps, float *out, unsigned *pmax, cudaStream_t st);
 cudaError_t launch_check_finite(const float *x, long long n, int *status, cudaStream_t st);
+cudaError_t launch_permute_adj(const float *adj, const int2 *ent, const int *eshot, int nent, int nt, int nrec,
+                               float *adj_t, cudaStream_t st);
 
 } // namespace fwi

@@ -50,20 +50,53 @@ constexpr float W2 = -1.0f / 5.0f;
 constexpr float W3 = 8.0f / 315.0f;
 constexpr float W4 = -1.0f / 560.0f;
 
-// Lhat u at one point in second-difference form: q = sum_k W_k ((x_{-k} +
-// x_{+k} - 2c) + (z_{-k} + z_{+k} - 2c)), smallest weights first. The
-// differences vanish exactly for a constant field and keep the rounding of q
-// relative to the field's curvature rather than to its value. The forward and
-// backward kernels both call this, so q is bitwise the same in both passes.
-__device__ __forceinline__ float lap8(float c, float x1, float z1, float x2, float z2, float x3,
-                                     float z3, float x4, float z4)
+// Lhat u in second-difference form: q = sum_k W_k ((x_{-k} + x_{+k} - 2c) +
+// (z_{-k} + z_{+k} - 2c)), smallest weights first. The differences vanish
+// exactly for a constant field and keep the rounding of q relative to the
+// field's curvature rather than to its value. The forward and backward
+// kernels both evaluate it with lap8x2 below, so q is bitwise the same in
+// both passes.
+
+// ---- paired FP32 (two lanes per instruction; each lane rounds exactly like
+// the scalar operation, so paired and scalar code give identical bits)
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, one rounding
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 half2of(const float4 &v, int h) { return h == 0 ? lo2(v) : hi2(v); }
+
+// Lhat for two adjacent points: xs[k-1], zs[k-1] are the neighbour pair sums
+// at distance k along x and z.
+__device__ __forceinline__ float2 lap8x2(float2 c, const float2 (&xs)[4], const float2 (&zs)[4])
 {
-    const float c2x = 2.0f * c;
-    float q = W4 * ((x4 - c2x) + (z4 - c2x));
-    q = fmaf(W3, (x3 - c2x) + (z3 - c2x), q);
-    q = fmaf(W2, (x2 - c2x) + (z2 - c2x), q);
-    q = fmaf(W1, (x1 - c2x) + (z1 - c2x), q);
+    const float2 m2 = make_float2(-2.f, -2.f);
+    float2 q = mul2(make_float2(W4, W4), add2(fma2(c, m2, xs[3]), fma2(c, m2, zs[3])));
+    q = fma2(make_float2(W3, W3), add2(fma2(c, m2, xs[2]), fma2(c, m2, zs[2])), q);
+    q = fma2(make_float2(W2, W2), add2(fma2(c, m2, xs[1]), fma2(c, m2, zs[1])), q);
+    q = fma2(make_float2(W1, W1), add2(fma2(c, m2, xs[0]), fma2(c, m2, zs[0])), q);
     return q;
+}
+
+// Lhat of the 4 points of one thread row r: x-window w (the row, w[WL] the
+// first point) and the column window zc (rows r .. r+8 of the stage tile).
+template <int WL, int NZ>
+__device__ __forceinline__ void lap4(float2 (&q)[2], const float *w, const float4 (&zc)[NZ], int r)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int p = 2 * h;
+        float2 xs[4], zs[4];
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) {
+            xs[k - 1] = add2(f2(w[WL + p - k], w[WL + p + 1 - k]), f2(w[WL + p + k], w[WL + p + 1 + k]));
+            zs[k - 1] = add2(half2of(zc[r + 4 - k], h), half2of(zc[r + 4 + k], h));
+        }
+        q[h] = lap8x2(f2(w[WL + p], w[WL + p + 1]), xs, zs);
+    }
 }
 
 // One damped leapfrog step in increment form:
@@ -73,11 +106,8 @@ __device__ __forceinline__ float lap8(float c, float x1, float z1, float x2, flo
 // in the kernels as u + fma(c2 ia, q, ((1 - e) ia)(u - u_prev)), e = eta dt,
 // ia = 1/(1 + e), which is exactly u + fma(c2, q, u - u_prev) where e = 0.
 
-// Reverse step in the model (eta = 0): u^{n-1} from u^n, u^{n+1} and q^n.
-__device__ __forceinline__ float leap_back(float u, float up, float c2v, float q)
-{
-    return u - fmaf(-c2v, q, up - u);
-}
+// The reverse step in the model (eta = 0), u^{n-1} = u^n - ((u^{n+1} - u^n)
+// - c2 q^n), is written out on lane pairs in the backward kernel.
 
 __device__ __forceinline__ float comp(const float4 &v, int p)
 {
@@ -321,17 +351,6 @@ __device__ __forceinline__ void load_c2_tile(float *dst, const float *c2, const 
     }
 }
 
-// Lhat u of 4 consecutive points from an x-window w[-WL..WL+3] (offset WL)
-// and the column values zm[k], zp[k] = rows -k, +k (k = 1..4) of each point.
-#define FWI_LAP4(Q, W, WL, ZC, R)                                                                        \
-    _Pragma("unroll") for (int p = 0; p < 4; ++p)                                                       \
-    {                                                                                                   \
-        Q[p] = lap8(W[WL + p], W[WL + p - 1] + W[WL + p + 1], comp(ZC[R + 3], p) + comp(ZC[R + 5], p),   \
-                    W[WL + p - 2] + W[WL + p + 2], comp(ZC[R + 2], p) + comp(ZC[R + 6], p),             \
-                    W[WL + p - 3] + W[WL + p + 3], comp(ZC[R + 1], p) + comp(ZC[R + 7], p),             \
-                    W[WL + p - 4] + W[WL + p + 4], comp(ZC[R + 0], p) + comp(ZC[R + 8], p));            \
-    }
-
 // ------------------------------------------------------------ forward step
 template <int RZ, int HX, bool WITH_H, int STAGES>
 using FwdRing = Ring<8 * RZ, HX, 1, 1, STAGES, 8 * RZ * TX * 4>;
@@ -393,23 +412,36 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     if (threadIdx.x == 0)
         for (int k = 0; k < STAGES - 1 && k < count; ++k) issue(k);
 
-    float acc_i[RZ][4];
+    float2 acc_i[RZ][2];
     float acc_h[NH][4];
 #pragma unroll
-    for (int r = 0; r < RZ; ++r)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) acc_i[r][p] = 0.f;
+    for (int r = 0; r < RZ; ++r) acc_i[r][0] = acc_i[r][1] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int h = 0; h < NH; ++h)
 #pragma unroll
         for (int p = 0; p < 4; ++p) acc_h[h][p] = 0.f;
 
-    ShotScalars nxt = fetch_scalars(c, a.rt, tile, g, a.n, !a.last, use_rec);
+    // receiver entry of this thread for an item (local index, receiver)
+    auto fetch_rec = [&](const ShotScalars &v, int2 &en) {
+        en = make_int2(-1, 0);
+        const int e = v.rb + (int)threadIdx.x;
+        if (e < v.re) en = a.rt.ent[e];
+    };
+    ShotScalars cur = fetch_scalars(c, a.rt, tile, g, a.n, !a.last, use_rec);
+    ShotScalars nxt = cur;
+    if (count > 1) nxt = fetch_scalars(c, a.rt, tile, g + G, a.n, !a.last, use_rec);
+    int2 rec_en;
+    fetch_rec(cur, rec_en);
     for (int k = 0; k < count; ++k) {
         if (threadIdx.x == 0 && k + STAGES - 1 < count) issue(k + STAGES - 1);
         const int s = g + k * G;
-        const ShotScalars cur = nxt;
-        if (k + 1 < count) nxt = fetch_scalars(c, a.rt, tile, s + G, a.n, !a.last, use_rec);
+        const ShotScalars now = cur;
+        const int2 now_en = rec_en;
+        cur = nxt;
+        if (k + 1 < count) {
+            fetch_rec(cur, rec_en);
+            if (k + 2 < count) nxt = fetch_scalars(c, a.rt, tile, s + 2 * G, a.n, !a.last, use_rec);
+        }
         const int st = k % STAGES;
         if (stage_ready<STAGES>(bars, k, &s_abort)) {
             const float *sm = R::halo(smem, st, 0);
@@ -417,12 +449,17 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
             float *up = a.uprev + (long long)s * L.fstride;
 
             // receiver extraction d^n = R u^n
-            for (int e = cur.rb + (int)threadIdx.x; e < cur.re; e += TPB) {
+            float *seis_s = a.seis + ((long long)s * c.nt + a.n) * c.nrec;
+            if (now_en.x >= 0) {
+                const int zl = now_en.x / TX, xl = now_en.x - zl * TX;
+                seis_s[now_en.y] = sm[(zl + RADIUS) * TXS + HX + xl];
+            }
+            for (int e = now.rb + TPB + (int)threadIdx.x; e < now.re; e += TPB) {
                 const int2 en = a.rt.ent[e];
                 const int zl = en.x / TX, xl = en.x - zl * TX;
-                a.seis[((long long)s * c.nt + a.n) * c.nrec + en.y] = sm[(zl + RADIUS) * TXS + HX + xl];
+                seis_s[en.y] = sm[(zl + RADIUS) * TXS + HX + xl];
             }
-            const int sslot = source_slot<RZ>(cur, i0, j0);
+            const int sslot = source_slot<RZ>(now, i0, j0);
 
             float4 zc[RZ + 2 * RADIUS];
 #pragma unroll
@@ -437,56 +474,58 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                     const float4 t = lds4(row - WL + 4 * kk);
                     w[4 * kk] = t.x; w[4 * kk + 1] = t.y; w[4 * kk + 2] = t.z; w[4 * kk + 3] = t.w;
                 }
+                const float2 u0[2] = {f2(w[WL], w[WL + 1]), f2(w[WL + 2], w[WL + 3])};
                 if (!a.last) {
-                    float q[4];
-                    FWI_LAP4(q, w, WL, zc, r)
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-                        if (sslot == r * 4 + p) q[p] += cur.amp;
+                    float2 q[2];
+                    lap4<WL>(q, w, zc, r);
+                    if (sslot == r * 4 + 0) q[0].x += now.amp;
+                    if (sslot == r * 4 + 1) q[0].y += now.amp;
+                    if (sslot == r * 4 + 2) q[1].x += now.amp;
+                    if (sslot == r * 4 + 3) q[1].y += now.amp;
                     const float4 um4 = lds4(&pm[(ty * RZ + r) * TX + 4 * tx]);
                     const float4 c24 = lds4(&c2s[(ty * RZ + r) * TX + 4 * tx]);
-                    float out[4];
+                    float2 out[2];
                     if (!tile_sponge) {
 #pragma unroll
-                        for (int p = 0; p < 4; ++p) {
-                            const float u0 = w[WL + p];
-                            out[p] = u0 + fmaf(comp(c24, p), q[p], u0 - comp(um4, p));
-                        }
+                        for (int h = 0; h < 2; ++h)
+                            out[h] = add2(u0[h], fma2(half2of(c24, h), q[h], sub2(u0[h], half2of(um4, h))));
                         *reinterpret_cast<float4 *>(up + fidx(L, i0 + r, j0)) =
-                            make_float4(out[0], out[1], out[2], out[3]);
+                            make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
                     } else {
                         // damped update; identical to the plain one where eta = 0
                         const int i = i0 + r;
 #pragma unroll
-                        for (int p = 0; p < 4; ++p) {
-                            const float e = sg.ez[r] + sg.ex[p];
-                            const float ia = __frcp_rn(1.0f + e);
-                            const float u0 = w[WL + p];
-                            out[p] = u0 + fmaf(comp(c24, p) * ia, q[p], ((1.0f - e) * ia) * (u0 - comp(um4, p)));
+                        for (int h = 0; h < 2; ++h) {
+                            const float2 e2 = add2(make_float2(sg.ez[r], sg.ez[r]), f2(sg.ex[2 * h], sg.ex[2 * h + 1]));
+                            const float2 ia2 = f2(__frcp_rn(1.0f + e2.x), __frcp_rn(1.0f + e2.y));
+                            const float2 kb = mul2(sub2(make_float2(1.f, 1.f), e2), ia2);
+                            out[h] = add2(u0[h], fma2(mul2(half2of(c24, h), ia2), q[h],
+                                                      mul2(kb, sub2(u0[h], half2of(um4, h)))));
                         }
-                        if (colok && i < L.nzp) store4(up + fidx(L, i, j0), j0, L.nxp, out);
+                        const float o[4] = {out[0].x, out[0].y, out[1].x, out[1].y};
+                        if (colok && i < L.nzp) store4(up + fidx(L, i, j0), j0, L.nxp, o);
                         if (a.band != nullptr && sg.brow[r] != -1) {
                             float *bb = a.band + ((long long)s * c.nt + a.n + 1) * L.nbandp;
                             if (sg.brow[r] >= 0) {
-                                *reinterpret_cast<float4 *>(bb + sg.brow[r]) = make_float4(out[0], out[1], out[2], out[3]);
+                                *reinterpret_cast<float4 *>(bb + sg.brow[r]) = make_float4(o[0], o[1], o[2], o[3]);
                             } else {
 #pragma unroll
                                 for (int p = 0; p < 4; ++p)
-                                    if (in_band(L, i, j0 + p)) bb[band_index(L, i, j0 + p)] = out[p];
+                                    if (in_band(L, i, j0 + p)) bb[band_index(L, i, j0 + p)] = o[p];
                             }
                         }
                     }
                     if (a.illum_utt) {
 #pragma unroll
-                        for (int p = 0; p < 4; ++p) {
-                            const float d2 = (out[p] - 2.0f * w[WL + p]) + comp(um4, p);
-                            acc_i[r][p] = fmaf(d2, d2, acc_i[r][p]);
+                        for (int h = 0; h < 2; ++h) {
+                            const float2 d2 = add2(fma2(u0[h], make_float2(-2.f, -2.f), out[h]), half2of(um4, h));
+                            acc_i[r][h] = fma2(d2, d2, acc_i[r][h]);
                         }
                     }
                 }
                 if (!a.illum_utt) {
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) acc_i[r][p] = fmaf(w[WL + p], w[WL + p], acc_i[r][p]);
+                    acc_i[r][0] = fma2(u0[0], u0[0], acc_i[r][0]);
+                    acc_i[r][1] = fma2(u0[1], u0[1], acc_i[r][1]);
                 }
                 if (WITH_H) {
 #pragma unroll
@@ -514,7 +553,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
             const int ix = j0 + p - L.P;
             if (iz < 0 || iz >= L.nz || ix < 0 || ix >= L.nx) continue;
             const long long o = (long long)iz * L.nx + ix;
-            if (a.acc_illum != nullptr) atomicAdd(a.acc_illum + o, acc_i[r][p]);
+            if (a.acc_illum != nullptr)
+                atomicAdd(a.acc_illum + o, p < 2 ? (p == 0 ? acc_i[r][0].x : acc_i[r][0].y)
+                                                 : (p == 2 ? acc_i[r][1].x : acc_i[r][1].y));
             if (WITH_H) {
 #pragma unroll
                 for (int h = 0; h < NH; ++h)
@@ -583,22 +624,40 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     if (threadIdx.x == 0)
         for (int k = 0; k < STAGES - 1 && k < count; ++k) issue(k);
 
-    float acc_g[RZ][4];
+    float2 acc_g[RZ][2];
 #pragma unroll
-    for (int r = 0; r < RZ; ++r)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) acc_g[r][p] = 0.f;
+    for (int r = 0; r < RZ; ++r) acc_g[r][0] = acc_g[r][1] = make_float2(0.f, 0.f);
 
     // adjoint-source entry of this thread for the next item (one entry per
     // thread is prefetched; further entries of a crowded tile are read late)
-    auto fetch_adj = [&](const ShotScalars &v, int s, int &loc, float &val) {
+    auto fetch_adj = [&](const ShotScalars &v, int &loc, float &val) {
         loc = -1;
         val = 0.f;
         const int e = v.rb + (int)threadIdx.x;
         if (e < v.re) {
-            const int2 en = a.rt.ent[e];
-            loc = en.x;
-            val = a.adj[((long long)s * c.nt + m) * c.nrec + en.y] * a.adj_scale;
+            loc = a.rt.ent[e].x;
+            val = a.adj[(long long)m * a.nent + e] * a.adj_scale;
+        }
+    };
+
+    // checkpointed sponge values of u^{m-2} of one item (sponge tiles only)
+    auto fetch_band = [&](int s, float4 (&bv)[RZ]) {
+#pragma unroll
+        for (int r = 0; r < RZ; ++r) {
+            bv[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (need_band && sg.brow[r] != -1) {
+                const float *bb = a.band + ((long long)s * c.nt + (m - 2)) * L.nbandp;
+                if (sg.brow[r] >= 0) {
+                    bv[r] = __ldcs(reinterpret_cast<const float4 *>(bb + sg.brow[r]));
+                } else {
+                    const int i = i0 + r;
+                    float t[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+                        if (in_band(L, i, j0 + p)) t[p] = __ldcs(bb + band_index(L, i, j0 + p));
+                    bv[r] = make_float4(t[0], t[1], t[2], t[3]);
+                }
+            }
         }
     };
 
@@ -607,44 +666,28 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     if (count > 1) nxt = fetch_scalars(c, a.rt, tile, g + G, m - 1, true, use_rec);
     int adj_loc;
     float adj_val;
-    fetch_adj(cur, g, adj_loc, adj_val);
+    fetch_adj(cur, adj_loc, adj_val);
+    float4 bval[RZ];
+    if (tile_sponge) fetch_band(g, bval);
     for (int k = 0; k < count; ++k) {
         if (threadIdx.x == 0 && k + STAGES - 1 < count) issue(k + STAGES - 1);
         const int s = g + k * G;
-        // checkpointed sponge values of u^{m-2}, requested before the stage wait
-        float4 bval[RZ];
-        if (tile_sponge) {
+        float4 bnow[RZ];
 #pragma unroll
-            for (int r = 0; r < RZ; ++r) {
-                bval[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (need_band && sg.brow[r] != -1) {
-                    const float *bb = a.band + ((long long)s * c.nt + (m - 2)) * L.nbandp;
-                    if (sg.brow[r] >= 0) {
-                        bval[r] = __ldcs(reinterpret_cast<const float4 *>(bb + sg.brow[r]));
-                    } else {
-                        const int i = i0 + r;
-                        float t[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int p = 0; p < 4; ++p)
-                            if (in_band(L, i, j0 + p)) t[p] = __ldcs(bb + band_index(L, i, j0 + p));
-                        bval[r] = make_float4(t[0], t[1], t[2], t[3]);
-                    }
-                }
-            }
-        }
+        for (int r = 0; r < RZ; ++r) bnow[r] = bval[r];
         const bool has_rec = cur.rb < cur.re; // uniform over the CTA
+        const int my_loc = adj_loc;
         if (has_rec) {
             if (adj_loc >= 0) atomicAdd(&sinj[adj_loc], adj_val);
-            for (int e = cur.rb + TPB + (int)threadIdx.x; e < cur.re; e += TPB) {
-                const int2 en = a.rt.ent[e];
-                atomicAdd(&sinj[en.x], a.adj[((long long)s * c.nt + m) * c.nrec + en.y] * a.adj_scale);
-            }
+            for (int e = cur.rb + TPB + (int)threadIdx.x; e < cur.re; e += TPB)
+                atomicAdd(&sinj[a.rt.ent[e].x], a.adj[(long long)m * a.nent + e] * a.adj_scale);
         }
-        // prefetch the next item's scalars (two ahead) and adjoint entry
+        // prefetch: scalars two items ahead, adjoint entry and checkpoint one ahead
         const ShotScalars now = cur;
         cur = nxt;
         if (k + 1 < count) {
-            fetch_adj(cur, s + G, adj_loc, adj_val);
+            fetch_adj(cur, adj_loc, adj_val);
+            if (tile_sponge) fetch_band(s + G, bval);
             if (k + 2 < count) nxt = fetch_scalars(c, a.rt, tile, s + 2 * G, m - 1, true, use_rec);
         }
         if (has_rec) __syncthreads();
@@ -657,70 +700,84 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             const long long so = (long long)s * L.fstride;
             const int sslot = source_slot<RZ>(now, i0, j0);
 
-            float4 zu[RZ + 2 * RADIUS], zp[RZ + 2 * RADIUS];
+            // q^{m-1} = Lhat u^{m-1} + f(t_{m-1}) delta_s (as in the forward
+            // step m-1), then Lhat psi^{m+1}; one column window live at a time
+            float2 qu[RZ][2], qp[RZ][2];
 #pragma unroll
-            for (int kk = 0; kk < RZ + 2 * RADIUS; ++kk) {
-                zu[kk] = lds4(&su[(ty * RZ + kk) * TXS + HX + 4 * tx]);
-                zp[kk] = lds4(&sp[(ty * RZ + kk) * TXS + HX + 4 * tx]);
+            for (int fld = 0; fld < 2; ++fld) {
+                const float *sf = fld == 0 ? su : sp;
+                float4 zc[RZ + 2 * RADIUS];
+#pragma unroll
+                for (int kk = 0; kk < RZ + 2 * RADIUS; ++kk) zc[kk] = lds4(&sf[(ty * RZ + kk) * TXS + HX + 4 * tx]);
+#pragma unroll
+                for (int r = 0; r < RZ; ++r) {
+                    const float *rw = &sf[(ty * RZ + r + RADIUS) * TXS + HX + 4 * tx];
+                    const float4 a0 = lds4(rw - 4), a2 = lds4(rw + 4);
+                    const float4 a1 = zc[r + RADIUS];
+                    const float w[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+                    if (fld == 0)
+                        lap4<4>(qu[r], w, zc, r);
+                    else
+                        lap4<4>(qp[r], w, zc, r);
+                }
             }
 #pragma unroll
             for (int r = 0; r < RZ; ++r) {
-                const int sr = ty * RZ + r + RADIUS;
-                float wu[12], wp[12];
-                {
-                    const float *ru = &su[sr * TXS + HX + 4 * tx];
-                    const float *rp = &sp[sr * TXS + HX + 4 * tx];
-                    const float4 a0 = lds4(ru - 4), a1 = lds4(ru), a2 = lds4(ru + 4);
-                    const float4 b0 = lds4(rp - 4), b1 = lds4(rp), b2 = lds4(rp + 4);
-                    wu[0] = a0.x; wu[1] = a0.y; wu[2] = a0.z; wu[3] = a0.w;
-                    wu[4] = a1.x; wu[5] = a1.y; wu[6] = a1.z; wu[7] = a1.w;
-                    wu[8] = a2.x; wu[9] = a2.y; wu[10] = a2.z; wu[11] = a2.w;
-                    wp[0] = b0.x; wp[1] = b0.y; wp[2] = b0.z; wp[3] = b0.w;
-                    wp[4] = b1.x; wp[5] = b1.y; wp[6] = b1.z; wp[7] = b1.w;
-                    wp[8] = b2.x; wp[9] = b2.y; wp[10] = b2.z; wp[11] = b2.w;
-                }
-                // q^{m-1} = Lhat u^{m-1} + f(t_{m-1}) delta_s (as in the forward step m-1)
-                float qu[4], qp[4];
-                FWI_LAP4(qu, wu, 4, zu, r)
-                FWI_LAP4(qp, wp, 4, zp, r)
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-                    if (sslot == r * 4 + p) qu[p] += now.amp;
+                if (sslot == r * 4 + 0) qu[r][0].x += now.amp;
+                if (sslot == r * 4 + 1) qu[r][0].y += now.amp;
+                if (sslot == r * 4 + 2) qu[r][1].x += now.amp;
+                if (sslot == r * 4 + 3) qu[r][1].y += now.amp;
                 if (has_rec) {
                     const float4 inj = lds4(&sinj[(ty * RZ + r) * TX + 4 * tx]);
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) qp[p] += comp(inj, p);
+                    qp[r][0] = add2(qp[r][0], lo2(inj));
+                    qp[r][1] = add2(qp[r][1], hi2(inj));
                 }
+                const int sr = ty * RZ + r + RADIUS;
+                const float4 uc = lds4(&su[sr * TXS + HX + 4 * tx]);
+                const float4 pc = lds4(&sp[sr * TXS + HX + 4 * tx]);
+                const float2 p1[2] = {lo2(pc), hi2(pc)};
+                const float2 u1[2] = {lo2(uc), hi2(uc)};
                 const float4 ua4 = lds4(&pua[(ty * RZ + r) * TX + 4 * tx]);
                 const float4 pb4 = lds4(&ppb[(ty * RZ + r) * TX + 4 * tx]);
                 const float4 c24 = lds4(&c2s[(ty * RZ + r) * TX + 4 * tx]);
-                float unew[4], pnew[4];
                 if (!tile_sponge) {
+                    float2 pn[2], un[2];
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const float p1 = wp[4 + p], u1 = wu[4 + p], c2v = comp(c24, p);
-                        pnew[p] = p1 + fmaf(c2v, qp[p], p1 - comp(pb4, p));
-                        acc_g[r][p] = fmaf(pnew[p], qu[p], acc_g[r][p]);
-                        unew[p] = leap_back(u1, comp(ua4, p), c2v, qu[p]);
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 c2v = half2of(c24, h);
+                        pn[h] = add2(p1[h], fma2(c2v, qp[r][h], sub2(p1[h], half2of(pb4, h))));
+                        acc_g[r][h] = fma2(pn[h], qu[r][h], acc_g[r][h]);
+                        // leap_back on two lanes: u1 - (-(c2 q) + (u^m - u1))
+                        un[h] = sub2(u1[h], fma2(make_float2(-c2v.x, -c2v.y), qu[r][h], sub2(half2of(ua4, h), u1[h])));
                     }
                     *reinterpret_cast<float4 *>(a.pb + so + fidx(L, i0 + r, j0)) =
-                        make_float4(pnew[0], pnew[1], pnew[2], pnew[3]);
+                        make_float4(pn[0].x, pn[0].y, pn[1].x, pn[1].y);
                     if (m >= 2)
                         *reinterpret_cast<float4 *>(a.ua + so + fidx(L, i0 + r, j0)) =
-                            make_float4(unew[0], unew[1], unew[2], unew[3]);
+                            make_float4(un[0].x, un[0].y, un[1].x, un[1].y);
                 } else {
+                    // damped adjoint update (identical to the plain one where
+                    // eta = 0); sponge values of u^{m-2} from the checkpoint
                     const int i = i0 + r;
+                    float2 pn[2], un[2];
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const int j = j0 + p;
-                        const float e = sg.ez[r] + sg.ex[p];
-                        const float ia = __frcp_rn(1.0f + e);
-                        const float p1 = wp[4 + p], u1 = wu[4 + p], c2v = comp(c24, p);
-                        const bool valid = i < L.nzp && j < L.nxp;
-                        pnew[p] = p1 + fmaf(c2v * ia, qp[p], ((1.0f - e) * ia) * (p1 - comp(pb4, p)));
-                        if (valid) acc_g[r][p] = fmaf(pnew[p], qu[p], acc_g[r][p]);
-                        unew[p] = (valid && band_index(L, i, j) >= 0) ? comp(bval[r], p)
-                                                                       : leap_back(u1, comp(ua4, p), c2v, qu[p]);
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 e2 = add2(make_float2(sg.ez[r], sg.ez[r]), f2(sg.ex[2 * h], sg.ex[2 * h + 1]));
+                        const float2 ia2 = f2(__frcp_rn(1.0f + e2.x), __frcp_rn(1.0f + e2.y));
+                        const float2 c2v = half2of(c24, h);
+                        const float2 kb = mul2(sub2(make_float2(1.f, 1.f), e2), ia2);
+                        pn[h] = add2(p1[h], fma2(mul2(c2v, ia2), qp[r][h], mul2(kb, sub2(p1[h], half2of(pb4, h)))));
+                        acc_g[r][h] = fma2(pn[h], qu[r][h], acc_g[r][h]);
+                        un[h] = sub2(u1[h], fma2(make_float2(-c2v.x, -c2v.y), qu[r][h], sub2(half2of(ua4, h), u1[h])));
+                    }
+                    float pnew[4] = {pn[0].x, pn[0].y, pn[1].x, pn[1].y};
+                    float unew[4] = {un[0].x, un[0].y, un[1].x, un[1].y};
+                    if (sg.brow[r] >= 0) {
+                        unew[0] = bnow[r].x; unew[1] = bnow[r].y; unew[2] = bnow[r].z; unew[3] = bnow[r].w;
+                    } else if (sg.brow[r] == -2) {
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+                            if (in_band(L, i, j0 + p)) unew[p] = comp(bnow[r], p);
                     }
                     if (colok && i < L.nzp) {
                         store4(a.pb + so + fidx(L, i, j0), j0, L.nxp, pnew);
@@ -735,7 +792,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             return;
         }
         if (has_rec) {
-            for (int e = now.rb + (int)threadIdx.x; e < now.re; e += TPB) sinj[a.rt.ent[e].x] = 0.f;
+            if (my_loc >= 0) sinj[my_loc] = 0.f;
+            for (int e = now.rb + TPB + (int)threadIdx.x; e < now.re; e += TPB) sinj[a.rt.ent[e].x] = 0.f;
             __syncthreads();
         }
     }
@@ -747,7 +805,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const int j = j0 + p;
-            if (i < L.nzp && j < L.nxp) atomicAdd(a.acc_grad + (long long)i * L.nxp + j, acc_g[r][p]);
+            const float v = p < 2 ? (p == 0 ? acc_g[r][0].x : acc_g[r][0].y) : (p == 2 ? acc_g[r][1].x : acc_g[r][1].y);
+            if (i < L.nzp && j < L.nxp) atomicAdd(a.acc_grad + (long long)i * L.nxp + j, v);
         }
     }
 }
