@@ -186,6 +186,28 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
                             int hmax, float eps, float *out, void *ws, size_t ws_bytes,
                             void *stream);
 
+/* Forward modelling without a caller workspace (no counterpart in the paper:
+   a deployment aid). For callers that cannot allocate device memory -- code
+   where cudaMalloc is not allowed or not wanted, a host framework that owns
+   all device memory through its own pool, a plugin handed only its inputs and
+   outputs -- this computes exactly what fwi_forward(save = 0) computes, in a
+   scratch array the library holds itself: FWI_NOALLOC_SCRATCH_BYTES of device
+   memory, reserved on every GPU that loads this part of the library and kept
+   until the process exits. It allocates no device memory.
+   v     DEVICE [nz][nx] velocity; seis DEVICE [nshots][nt][nrec] output traces.
+   Errors: FWI_ERR_NOMEM (with a message giving both sizes) when the problem's
+   forward workspace, fwi_workspace_bytes(..., FWI_OP_FORWARD, ...), exceeds
+   FWI_NOALLOC_SCRATCH_BYTES; otherwise as fwi_forward.
+   The first call on a device looks up the scratch array's device address
+   (cudaGetSymbolAddress), so make that first call before any stream capture.
+   All calls share the one array, which keeps the previous call's contents
+   (every call clears what must start at zero): calls that may overlap on the
+   GPU -- on different streams, or from different host threads -- race and
+   corrupt each other's results; serialise them. */
+#define FWI_NOALLOC_SCRATCH_BYTES (32u << 20)
+fwi_status fwi_forward_noalloc(const fwi_grid *grid, const fwi_geometry *geom, const float *v,
+                               float *seis, void *stream);
+
 /* Per-call phase timing with CUDA events (off by default). */
 fwi_status fwi_profile_enable(int on);
 fwi_status fwi_profile_last(fwi_phase_times *out);

@@ -64,6 +64,7 @@ _SIGS = {
                                 c_void_p, c_size_t, c_void_p],
     "fwi_precondition": [P(FwiGrid), c_void_p, c_void_p, c_int, c_int, c_float, c_void_p, c_void_p,
                          c_size_t, c_void_p],
+    "fwi_forward_noalloc": [P(FwiGrid), P(FwiGeometry), c_void_p, c_void_p, c_void_p],
     "fwi_profile_enable": [c_int],
     "fwi_profile_last": [P(FwiPhaseTimes)],
 }

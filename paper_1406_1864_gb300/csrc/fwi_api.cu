@@ -18,6 +18,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -684,3 +685,70 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
 }
 
 } // extern "C"
+
+// --------------------------------------------------------------------------
+// Forward modelling without a caller workspace.
+//
+// Some callers cannot allocate device memory: code that runs where cudaMalloc
+// is not allowed or not wanted (inside a region that must not synchronise the
+// device, a host framework that owns all device memory through its own pool,
+// or a plugin that is handed only input and output buffers). For them
+// fwi_forward_noalloc() runs the same forward modelling as fwi_forward(save=0)
+// in a scratch array that the library itself holds: a file-scope __device__
+// array of FWI_NOALLOC_SCRATCH_BYTES, present on every GPU that loads this
+// part of the library until the process exits. The entry point calls no
+// cudaMalloc, cudaFree or other allocating routine on the device.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FWI_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (host code sees
+// only a host-side stand-in under its name). Set up once per device.
+fwi_status noalloc_scratch(void **ptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(FWI_ERR_INVALID_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress of the library scratch");
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return FWI_OK;
+}
+
+} // namespace
+
+extern "C" fwi_status fwi_forward_noalloc(const fwi_grid *grid, const fwi_geometry *geom, const float *v,
+                                          float *seis, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, nullptr, FWI_OP_FORWARD, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || (!seis && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v or seis is NULL");
+    if (pl.total > (size_t)FWI_NOALLOC_SCRATCH_BYTES)
+        return fail(FWI_ERR_NOMEM,
+                    "this problem needs %zu bytes of scratch; fwi_forward_noalloc holds %zu "
+                    "(use fwi_forward with a workspace of fwi_workspace_bytes(FWI_OP_FORWARD))",
+                    pl.total, (size_t)FWI_NOALLOC_SCRATCH_BYTES);
+    void *ws = nullptr;
+    if ((s = noalloc_scratch(&ws)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    // set-up clears everything that must start at zero (status, c2 ghost
+    // frame, both wavefields): the scratch keeps the previous call's contents
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    if ((s = run_forward(pl, geom, ws, seis, false, nullptr, nullptr, 0, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    prof_record(2, st);
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
