@@ -67,7 +67,7 @@ struct Plan {
     bool need_bwd = false;  // adjoint pass (gradient / forward_save)
     bool need_seis_tab = false;
     Tiling tf{}, tb{};
-    Part scal, c2, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab;
+    Part scal, c2, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab, sched;
     size_t tab_src = 0, tab_srcij = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0, tab_bshot = 0;
     Part adj_t; // adjoint source in backward-table order [nt][ns*nrec]
     size_t total = 0;
@@ -172,6 +172,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         off = align_up(off + bytes);
     };
     take(pl.scal, 256);
+    if (op != FWI_OP_PRECONDITION) take(pl.sched, (size_t)2 * g->nt * sizeof(int));
     if (op == FWI_OP_PRECONDITION) {
         pl.total = off;
         return FWI_OK;
@@ -316,6 +317,8 @@ StepCommon make_common(const Plan &pl, const fwi_geometry *ge, void *ws, const T
     c.ntx = t.ntx;
     c.ntz = t.ntz;
     c.status = at<int>(ws, pl.scal, 8);
+    c.sched = at<int>(ws, pl.sched);
+    c.chunk = t.chunk;
     return c;
 }
 
@@ -324,6 +327,8 @@ fwi_status setup(const Plan &pl, const fwi_geometry *ge, const float *v, void *w
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(at<char>(ws, pl.scal), 0, pl.scal.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.sched), 0, pl.sched.bytes, st)) != cudaSuccess)
         return cuda_fail(e, "memset");
     fwi_status s = upload_tables(pl, ge, ws, st);
     if (s != FWI_OK) return s;
@@ -367,6 +372,7 @@ fwi_status run_forward(const Plan &pl, const fwi_geometry *ge, void *ws, float *
         a.last = (n == pl.nt - 1);
         a.tm_cur = mh[n & 1];
         a.tm_prev = mp[(n + 1) & 1];
+        a.c.sched = at<int>(ws, pl.sched) + n;
         a.uprev = U[(n + 1) & 1];
         if ((e = launch_fwd_step(a, pl.tf, offh, st)) != cudaSuccess)
             return cuda_fail(e, "forward step");
@@ -418,6 +424,7 @@ fwi_status run_backward(const Plan &pl, const fwi_geometry *ge, void *ws, const 
             return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
     for (int m = pl.nt - 1; m >= 1; --m) {
         a.m = m;
+        a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
         a.tm_ub = uh[(m - 1) & 1];
         a.tm_pa = ph[(m + 1) & 1];
         a.tm_ua = up[m & 1];
@@ -534,6 +541,7 @@ fwi_status fwi_adjoint_apply(const fwi_grid *grid, const fwi_geometry *geom, con
     prof_record(1, st);
     cudaError_t e;
     if ((e = cudaMemsetAsync(at<char>(ws, pl.scal), 0, pl.scal.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.sched), 0, pl.sched.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
     if ((s = upload_tables(pl, geom, ws, st)) != FWI_OK) return s;
     if ((s = run_backward(pl, geom, ws, adj_src, st)) != FWI_OK) return s;
     prof_record(2, st);

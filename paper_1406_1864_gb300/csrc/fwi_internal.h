@@ -82,6 +82,8 @@ struct StepCommon {
     int ns, nt, nrec;
     int ntx, ntz;          // tiles of this launch's tiling
     int *status;           // device status flags
+    int *sched;            // this launch's chunk counter (zero at launch)
+    int chunk;             // shots per chunk of the work schedule
 };
 
 // Time-loop kernels read their tiles with TMA: 3-D tensor maps over the
@@ -130,12 +132,13 @@ enum : int {
 };
 
 // ------------------------------------------------------------- launchers
-// Step kernels: grid (tiles, groups); CTA (t, g) owns tile t and shots
-// g, g + groups, ...
+// Step kernels: `ctas` CTAs (one per resident slot) take chunks of `chunk`
+// shots of one tile from an atomic counter.
 struct Tiling {
     int tz;        // tile height
     int ntx, ntz;  // tiles
-    int groups;    // shot groups (as many as fill the resident CTA slots)
+    int ctas;      // CTAs of one launch
+    int chunk;     // shots per chunk
 };
 enum StepKind { STEP_FWD = 0, STEP_FWD_OFFH = 1, STEP_BWD = 2 };
 Tiling make_tiling(const Lay2D &L, int ns, StepKind kind);

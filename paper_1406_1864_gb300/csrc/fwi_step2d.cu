@@ -21,17 +21,19 @@
 //     which is dx^2 (L u + s); the factor 2 / (v dx^2) is applied once at the
 //     end (fwi_aux.cu).
 //
-// Work decomposition: a CTA of 128 threads owns one 64 x (8 RZ) tile of the
-// padded grid and one group of shots (g, g+G, g+2G, ...); all CTAs walk their
-// shots in the same order, so a shot's neighbouring tiles read each other's
-// halos at about the same time and those re-reads hit L2. For each shot the
-// tile (plus the stencil halo) and the point tiles the update needs are
-// brought into a multi-stage shared-memory ring by TMA (cp.async.bulk.tensor)
-// on mbarriers, STAGES-1 shots ahead of the compute, so HBM streams while the
-// stencil runs. The tile's c2 sits in shared memory for the whole launch and
-// its accumulators (illumination, offset Hessian, gradient) in registers
-// across the shots; they are added to global memory (red.add) once at the
-// end. Threads whose 4 x RZ points are all inside the model take a branch-free
+// Work decomposition: the (tile, shot) pairs of one time level, cut into
+// chunks of a few shots of one 64 x (8 RZ) tile, are handed out in order by
+// an atomic counter to one CTA (128 threads) per resident slot: the load is
+// balanced whatever a tile costs (sponge and receiver tiles do more), and at
+// any moment all CTAs work on neighbouring tiles of the same shots, whose
+// halo re-reads then hit L2. Thread 0 stages item descriptors a few items
+// ahead; for each item the tile (plus the stencil halo) and the point tiles
+// the update needs are brought into a multi-stage shared-memory ring by TMA
+// (cp.async.bulk.tensor) on mbarriers, STAGES-1 items ahead of the compute,
+// so HBM streams while the stencil runs. The tile's c2 sits in shared memory
+// and its accumulators (illumination, offset Hessian, gradient) in registers
+// for the chunk; they are added to global memory (red.add) at each tile
+// change. Threads whose 4 x RZ points are all inside the model take a branch-free
 // path (no damping, no checkpoint, no masking). Every mbarrier wait is bounded
 // (~2 s of %globaltimer), after which the kernel sets ST_TIMEOUT and returns.
 #include "fwi_internal.h"
@@ -231,17 +233,7 @@ __device__ __forceinline__ bool stage_ready(uint64_t *bars, int k, int *s_abort)
     return false;
 }
 
-// After a timeout (seen by the whole CTA after a barrier): record it and wait,
-// bounded, for the copies of pairs k+1.. still in flight, so that no TMA write
-// lands in shared memory after the CTA has left.
-template <int STAGES>
-__device__ void abort_drain(uint64_t *bars, int k, int count, int *status)
-{
-    if (threadIdx.x != 0) return;
-    atomicOr(status, ST_TIMEOUT);
-    for (int j = k + 1; j < count && j < k + STAGES; ++j)
-        mbar_wait(smem_u32(&bars[j % STAGES]), (j / STAGES) & 1, DRAIN_NS);
-}
+constexpr int DESC_RING = 8; // item descriptors staged ahead (ring size)
 
 __device__ __forceinline__ unsigned char *align_smem(unsigned char *p)
 {
@@ -257,29 +249,107 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 
 } // namespace
 
-// Per-shot scalars of one work item, fetched ahead so that their
-// global-memory latency overlaps the previous item's stencil.
-struct ShotScalars {
-    int si, sj;    // padded cell of the source
-    float amp;     // source amplitude of this time level (0 if none)
+// ------------------------------------------------------------- scheduling
+// The work of one launch is the (tile, shot) pairs. They are cut into chunks
+// of S shots of one tile; chunk q covers tile q % ntiles and shots
+// [(q / ntiles) S, (q / ntiles) S + S). One CTA per resident slot takes chunks
+// in order from an atomic counter, so the load is balanced whatever a tile
+// costs, and at any moment all CTAs work on nearby chunks: neighbouring tiles
+// of the same shots, whose halo re-reads then hit L2.
+struct ItemDesc {
+    int tile, s;   // tile and shot of the item; tile < 0: no more work
     int rb, re;    // receiver-table range of (tile, shot)
+    int si, sj;    // padded cell of the shot's source
+    float amp;     // source amplitude at this time level
+    int pad;
 };
 
-__device__ __forceinline__ ShotScalars fetch_scalars(const StepCommon &c, const RecTable &rt, int tile, int s,
-                                                     int n_src, bool use_src, bool use_rec)
+// Thread-0 state that walks the CTA's chunks.
+struct Cursor {
+    int tile, s, s_end; // current chunk
+    int q_next;         // next chunk, taken one chunk ahead (-1: none)
+    bool done;
+};
+
+__device__ __forceinline__ int grab_chunk(int *counter, int nchunks)
 {
-    ShotScalars v;
-    const int2 ij = c.src_ij[s];
-    v.si = ij.x;
-    v.sj = ij.y;
-    v.amp = use_src ? c.wav[(long long)s * c.nt + n_src] * c.src_scale : 0.f;
-    v.rb = 0;
-    v.re = 0;
-    if (use_rec) {
-        v.rb = rt.ptr[tile * c.ns + s];
-        v.re = rt.ptr[tile * c.ns + s + 1];
+    const int q = atomicAdd(counter, 1);
+    return q < nchunks ? q : -1;
+}
+
+__device__ __forceinline__ void cursor_set(Cursor &cu, int q, int ntiles, int S, int ns)
+{
+    const int blk = q / ntiles;
+    cu.tile = q - blk * ntiles;
+    cu.s = blk * S;
+    cu.s_end = min(ns, cu.s + S);
+}
+
+__device__ __forceinline__ void cursor_init(Cursor &cu, int *counter, int nchunks, int ntiles, int S, int ns)
+{
+    const int q = grab_chunk(counter, nchunks);
+    cu.done = q < 0;
+    cu.q_next = -1;
+    cu.tile = cu.s = cu.s_end = 0;
+    if (!cu.done) {
+        cursor_set(cu, q, ntiles, S, ns);
+        cu.q_next = grab_chunk(counter, nchunks);
     }
-    return v;
+}
+
+// next (tile, shot) of this CTA; false when the launch's work is exhausted
+__device__ __forceinline__ bool cursor_next(Cursor &cu, int *counter, int nchunks, int ntiles, int S, int ns,
+                                            int &tile, int &s)
+{
+    if (cu.done) return false;
+    if (cu.s >= cu.s_end) {
+        if (cu.q_next < 0) {
+            cu.done = true;
+            return false;
+        }
+        cursor_set(cu, cu.q_next, ntiles, S, ns);
+        cu.q_next = grab_chunk(counter, nchunks);
+    }
+    tile = cu.tile;
+    s = cu.s++;
+    return true;
+}
+
+// descriptor of item (tile, s) with its per-shot scalars (global loads)
+__device__ __forceinline__ ItemDesc make_desc(const StepCommon &c, const RecTable &rt, int tile, int s,
+                                              int n_src, bool use_src, bool use_rec)
+{
+    ItemDesc d;
+    d.tile = tile;
+    d.s = s;
+    d.pad = 0;
+    if (tile < 0) {
+        d.rb = d.re = d.si = d.sj = 0;
+        d.amp = 0.f;
+        return d;
+    }
+    const int2 ij = c.src_ij[s];
+    d.si = ij.x;
+    d.sj = ij.y;
+    d.amp = use_src ? c.wav[(long long)s * c.nt + n_src] * c.src_scale : 0.f;
+    d.rb = d.re = 0;
+    if (use_rec) {
+        d.rb = rt.ptr[tile * c.ns + s];
+        d.re = rt.ptr[tile * c.ns + s + 1];
+    }
+    return d;
+}
+
+// After a timeout (seen by the whole CTA after a barrier): record it and wait,
+// bounded, for the copies of the items after k that were issued, so that no
+// TMA write lands in shared memory after the CTA has left.
+template <int STAGES>
+__device__ void abort_drain_ring(uint64_t *bars, const ItemDesc *desc, int k, int *status)
+{
+    if (threadIdx.x != 0) return;
+    atomicOr(status, ST_TIMEOUT);
+    for (int j = k + 1; j < k + STAGES; ++j)
+        if (desc[j % DESC_RING].tile >= 0) mbar_wait(smem_u32(&bars[j % STAGES]), (j / STAGES) & 1, DRAIN_NS);
 }
 
 // Damping of the thread's rows / columns (eta dt is separable: rows + columns)
@@ -332,7 +402,7 @@ __device__ __forceinline__ bool in_band(const Lay2D &L, int i, int j)
 
 // index (row * 4 + column) of the thread's point that holds the source, or -1
 template <int RZ>
-__device__ __forceinline__ int source_slot(const ShotScalars &v, int i0, int j0)
+__device__ __forceinline__ int source_slot(const ItemDesc &v, int i0, int j0)
 {
     const int dr = v.si - i0, dc = v.sj - j0;
     return (dr >= 0 && dr < RZ && dc >= 0 && dc < 4) ? dr * 4 + dc : -1;
@@ -355,9 +425,6 @@ __device__ __forceinline__ void load_c2_tile(float *dst, const float *c2, const 
 template <int RZ, int HX, bool WITH_H, int STAGES>
 using FwdRing = Ring<8 * RZ, HX, 1, 1, STAGES, 8 * RZ * TX * 4>;
 
-// grid = (tiles, groups): CTA (t, g) owns tile t and the shots g, g+G, ...;
-// all CTAs walk their shots in the same order, so neighbouring tiles read
-// each other's halos of the same shot at about the same time (L2 hits).
 template <int RZ, int HX, bool WITH_H, int STAGES, int MINB>
 __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ FwdArgs a)
 {
@@ -367,9 +434,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     constexpr int NH = WITH_H ? HMAX_LIMIT + 1 : 1;
     constexpr int WL = WITH_H ? HMAX_LIMIT : RADIUS; // x-window left extent
     constexpr int NW = (2 * WL + 4) / 4;             // float4s in the x-window
+    constexpr int D = STAGES - 1;                    // items in flight ahead of the compute
     static_assert(!WITH_H || (RZ == 1 && HX == 12), "offset Hessian uses RZ=1, HX=12");
+    // item k+1's descriptor is read in iteration k and written in iteration
+    // k+1-D: it must be written at least one barrier earlier, so D >= 2
+    static_assert(D >= 2 && D + 2 <= DESC_RING, "needs 3 <= STAGES <= 7");
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_abort;
+    __shared__ ItemDesc s_desc[DESC_RING];
     unsigned char *smem = align_smem(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *c2s = reinterpret_cast<float *>(R::extra(smem));
@@ -377,70 +449,118 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     const StepCommon &c = a.c;
     const Lay2D &L = c.L;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int tile = blockIdx.x, G = gridDim.y, g = blockIdx.y;
-    const int count = (c.ns - g + G - 1) / G;
-    if (count <= 0) return;
-    const int bz = tile / c.ntx, bx = tile - bz * c.ntx;
-    const int bi = bz * TZ, bj = bx * TX;
-    const int i0 = bi + ty * RZ, j0 = bj + 4 * tx;
-    // tiles with a point outside the model take the damped path in all their
-    // threads (uniform per CTA); tiles inside the model the plain update
-    const bool tile_sponge = bi < L.P || bi + TZ > L.P + L.nz || bj < L.P || bj + TX > L.P + L.nx;
-    const bool colok = j0 < L.nxp;
     const long long nphys = (long long)L.nz * L.nx;
     const bool use_rec = a.seis != nullptr;
-    SpongeInfo<RZ> sg;
-    if (tile_sponge) sg.init(L, i0, j0);
+    const int ntiles = c.ntx * c.ntz;
+    const int nchunks = ntiles * ((c.ns + c.chunk - 1) / c.chunk);
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < STAGES; ++k) mbar_init(smem_u32(&bars[k]), 1);
         fence_mbar_init();
         s_abort = 0;
     }
-    load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
     __syncthreads();
 
-    auto issue = [&](int k) {
-        const int s = g + k * G;
+    // thread 0 walks the chunks, stages descriptors D items ahead and loads
+    // the per-shot scalars of the item after that one iteration early
+    Cursor cu;
+    ItemDesc pend;
+    auto next_desc = [&]() {
+        int t = -1, sh = 0;
+        if (!cursor_next(cu, c.sched, nchunks, ntiles, c.chunk, c.ns, t, sh)) t = -1;
+        return make_desc(c, a.rt, t, sh, a.n, !a.last, use_rec);
+    };
+    auto issue = [&](const ItemDesc &d, int k) {
+        const int bz = d.tile / c.ntx, bx = d.tile - bz * c.ntx;
         const int st = k % STAGES;
         const uint32_t bar = smem_u32(&bars[st]);
         fence_proxy_async_smem();
         mbar_expect_tx(bar, (R::HALO + (a.last ? 0 : R::PT)) * 4);
-        tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_cur, GXL + bj - HX, bi, s, bar);
-        if (!a.last) tma_load_3d(smem_u32(R::point(smem, st, 0)), &a.tm_prev, GXL + bj, bi + GZ, s, bar);
+        tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_cur, GXL + bx * TX - HX, bz * TZ, d.s, bar);
+        if (!a.last) tma_load_3d(smem_u32(R::point(smem, st, 0)), &a.tm_prev, GXL + bx * TX, bz * TZ + GZ, d.s, bar);
     };
-    if (threadIdx.x == 0)
-        for (int k = 0; k < STAGES - 1 && k < count; ++k) issue(k);
+    if (threadIdx.x == 0) {
+        cursor_init(cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
+        for (int k = 0; k < D; ++k) {
+            const ItemDesc d = next_desc();
+            s_desc[k] = d;
+            if (d.tile >= 0) issue(d, k);
+        }
+        pend = next_desc();
+    }
+    __syncthreads();
 
     float2 acc_i[RZ][2];
     float acc_h[NH][4];
+    int cur_tile = -1, bi = 0, bj = 0, i0 = 0, j0 = 0;
+    bool tile_sponge = false, colok = false;
+    SpongeInfo<RZ> sg;
+
+    auto flush = [&]() {
 #pragma unroll
-    for (int r = 0; r < RZ; ++r) acc_i[r][0] = acc_i[r][1] = make_float2(0.f, 0.f);
+        for (int r = 0; r < RZ; ++r) {
+            const int iz = i0 + r - L.P;
 #pragma unroll
-    for (int h = 0; h < NH; ++h)
+            for (int p = 0; p < 4; ++p) {
+                const int ix = j0 + p - L.P;
+                if (iz < 0 || iz >= L.nz || ix < 0 || ix >= L.nx) continue;
+                const long long o = (long long)iz * L.nx + ix;
+                if (a.acc_illum != nullptr)
+                    atomicAdd(a.acc_illum + o, p < 2 ? (p == 0 ? acc_i[r][0].x : acc_i[r][0].y)
+                                                     : (p == 2 ? acc_i[r][1].x : acc_i[r][1].y));
+                if (WITH_H) {
 #pragma unroll
-        for (int p = 0; p < 4; ++p) acc_h[h][p] = 0.f;
+                    for (int h = 0; h < NH; ++h)
+                        if (h <= a.hmax) atomicAdd(a.acc_offh + h * nphys + o, acc_h[h][p]);
+                }
+            }
+        }
+    };
 
     // receiver entry of this thread for an item (local index, receiver)
-    auto fetch_rec = [&](const ShotScalars &v, int2 &en) {
+    auto fetch_rec = [&](const ItemDesc &v, int2 &en) {
         en = make_int2(-1, 0);
         const int e = v.rb + (int)threadIdx.x;
-        if (e < v.re) en = a.rt.ent[e];
+        if (v.tile >= 0 && e < v.re) en = a.rt.ent[e];
     };
-    ShotScalars cur = fetch_scalars(c, a.rt, tile, g, a.n, !a.last, use_rec);
-    ShotScalars nxt = cur;
-    if (count > 1) nxt = fetch_scalars(c, a.rt, tile, g + G, a.n, !a.last, use_rec);
     int2 rec_en;
-    fetch_rec(cur, rec_en);
-    for (int k = 0; k < count; ++k) {
-        if (threadIdx.x == 0 && k + STAGES - 1 < count) issue(k + STAGES - 1);
-        const int s = g + k * G;
-        const ShotScalars now = cur;
+    fetch_rec(s_desc[0], rec_en);
+
+    int k = 0;
+    for (;; ++k) {
+        if (threadIdx.x == 0) {
+            const ItemDesc d = pend;
+            s_desc[(k + D) % DESC_RING] = d;
+            if (d.tile >= 0) issue(d, k + D);
+            pend = next_desc();
+        }
+        const ItemDesc now = s_desc[k % DESC_RING];
+        if (now.tile < 0) break;
+        const ItemDesc nx = s_desc[(k + 1) % DESC_RING];
+        const int s = now.s;
         const int2 now_en = rec_en;
-        cur = nxt;
-        if (k + 1 < count) {
-            fetch_rec(cur, rec_en);
-            if (k + 2 < count) nxt = fetch_scalars(c, a.rt, tile, s + 2 * G, a.n, !a.last, use_rec);
+        fetch_rec(nx, rec_en);
+        if (now.tile != cur_tile) {
+            if (cur_tile >= 0) flush();
+            cur_tile = now.tile;
+            const int bz = cur_tile / c.ntx, bx = cur_tile - bz * c.ntx;
+            bi = bz * TZ;
+            bj = bx * TX;
+            i0 = bi + ty * RZ;
+            j0 = bj + 4 * tx;
+            // tiles with a point outside the model take the damped path in
+            // all their threads (uniform per CTA); inside the model the plain update
+            tile_sponge = bi < L.P || bi + TZ > L.P + L.nz || bj < L.P || bj + TX > L.P + L.nx;
+            colok = j0 < L.nxp;
+            if (tile_sponge) sg.init(L, i0, j0);
+#pragma unroll
+            for (int r = 0; r < RZ; ++r) acc_i[r][0] = acc_i[r][1] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int h = 0; h < NH; ++h)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc_h[h][p] = 0.f;
+            load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
+            __syncthreads();
         }
         const int st = k % STAGES;
         if (stage_ready<STAGES>(bars, k, &s_abort)) {
@@ -539,30 +659,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
         }
         __syncthreads();
         if (s_abort) {
-            abort_drain<STAGES>(bars, k, count, c.status);
+            abort_drain_ring<STAGES>(bars, s_desc, k, c.status);
             return;
         }
     }
-
-    // add this CTA's sums over its shots (model cells only)
-#pragma unroll
-    for (int r = 0; r < RZ; ++r) {
-        const int iz = i0 + r - L.P;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int ix = j0 + p - L.P;
-            if (iz < 0 || iz >= L.nz || ix < 0 || ix >= L.nx) continue;
-            const long long o = (long long)iz * L.nx + ix;
-            if (a.acc_illum != nullptr)
-                atomicAdd(a.acc_illum + o, p < 2 ? (p == 0 ? acc_i[r][0].x : acc_i[r][0].y)
-                                                 : (p == 2 ? acc_i[r][1].x : acc_i[r][1].y));
-            if (WITH_H) {
-#pragma unroll
-                for (int h = 0; h < NH; ++h)
-                    if (h <= a.hmax) atomicAdd(a.acc_offh + h * nphys + o, acc_h[h][p]);
-            }
-        }
-    }
+    if (cur_tile >= 0) flush();
 }
 
 // ----------------------------------------------------------- backward step
@@ -576,8 +677,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     constexpr int TZ = 8 * RZ;
     constexpr int HX = RADIUS;
     constexpr int TXS = R::TXS;
+    constexpr int D = STAGES - 1;
+    // item k+1's descriptor is read in iteration k and written in iteration
+    // k+1-D: it must be written at least one barrier earlier, so D >= 2
+    static_assert(D >= 2 && D + 2 <= DESC_RING, "needs 3 <= STAGES <= 7");
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_abort;
+    __shared__ ItemDesc s_desc[DESC_RING];
     unsigned char *smem = align_smem(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *c2s = reinterpret_cast<float *>(R::extra(smem));
@@ -586,61 +692,82 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     const StepCommon &c = a.c;
     const Lay2D &L = c.L;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int tile = blockIdx.x, G = gridDim.y, g = blockIdx.y;
-    const int count = (c.ns - g + G - 1) / G;
-    if (count <= 0) return;
-    const int bz = tile / c.ntx, bx = tile - bz * c.ntx;
-    const int bi = bz * TZ, bj = bx * TX;
-    const int i0 = bi + ty * RZ, j0 = bj + 4 * tx;
-    const bool tile_sponge = bi < L.P || bi + TZ > L.P + L.nz || bj < L.P || bj + TX > L.P + L.nx;
-    const bool colok = j0 < L.nxp;
     const int m = a.m;
     const bool use_rec = a.adj != nullptr;
     const bool need_band = m >= 3; // u^{m-2} in the sponge comes from checkpoint m-2 >= 1
-    SpongeInfo<RZ> sg;
-    if (tile_sponge) sg.init(L, i0, j0);
+    const int ntiles = c.ntx * c.ntz;
+    const int nchunks = ntiles * ((c.ns + c.chunk - 1) / c.chunk);
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < STAGES; ++k) mbar_init(smem_u32(&bars[k]), 1);
         fence_mbar_init();
         s_abort = 0;
     }
-    load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
     for (int e = threadIdx.x; e < TZ * TX; e += TPB) sinj[e] = 0.f;
     __syncthreads();
 
-    auto issue = [&](int k) {
-        const int s = g + k * G;
+    Cursor cu;
+    ItemDesc pend;
+    auto next_desc = [&]() {
+        int t = -1, sh = 0;
+        if (!cursor_next(cu, c.sched, nchunks, ntiles, c.chunk, c.ns, t, sh)) t = -1;
+        return make_desc(c, a.rt, t, sh, m - 1, true, use_rec);
+    };
+    auto issue = [&](const ItemDesc &d, int k) {
+        const int bz = d.tile / c.ntx, bx = d.tile - bz * c.ntx;
+        const int bi = bz * TZ, bj = bx * TX;
         const int st = k % STAGES;
         const uint32_t bar = smem_u32(&bars[st]);
         const bool need_ua = m >= 2;
         fence_proxy_async_smem();
         mbar_expect_tx(bar, (2 * R::HALO + (need_ua ? 2 : 1) * R::PT) * 4);
-        tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_ub, GXL + bj - HX, bi, s, bar);
-        tma_load_3d(smem_u32(R::halo(smem, st, 1)), &a.tm_pa, GXL + bj - HX, bi, s, bar);
-        tma_load_3d(smem_u32(R::point(smem, st, 1)), &a.tm_pb, GXL + bj, bi + GZ, s, bar);
-        if (need_ua) tma_load_3d(smem_u32(R::point(smem, st, 0)), &a.tm_ua, GXL + bj, bi + GZ, s, bar);
+        tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_ub, GXL + bj - HX, bi, d.s, bar);
+        tma_load_3d(smem_u32(R::halo(smem, st, 1)), &a.tm_pa, GXL + bj - HX, bi, d.s, bar);
+        tma_load_3d(smem_u32(R::point(smem, st, 1)), &a.tm_pb, GXL + bj, bi + GZ, d.s, bar);
+        if (need_ua) tma_load_3d(smem_u32(R::point(smem, st, 0)), &a.tm_ua, GXL + bj, bi + GZ, d.s, bar);
     };
-    if (threadIdx.x == 0)
-        for (int k = 0; k < STAGES - 1 && k < count; ++k) issue(k);
+    if (threadIdx.x == 0) {
+        cursor_init(cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
+        for (int k = 0; k < D; ++k) {
+            const ItemDesc d = next_desc();
+            s_desc[k] = d;
+            if (d.tile >= 0) issue(d, k);
+        }
+        pend = next_desc();
+    }
+    __syncthreads();
 
     float2 acc_g[RZ][2];
-#pragma unroll
-    for (int r = 0; r < RZ; ++r) acc_g[r][0] = acc_g[r][1] = make_float2(0.f, 0.f);
+    int cur_tile = -1, bi = 0, bj = 0, i0 = 0, j0 = 0;
+    bool tile_sponge = false, colok = false;
+    SpongeInfo<RZ> sg;
 
-    // adjoint-source entry of this thread for the next item (one entry per
-    // thread is prefetched; further entries of a crowded tile are read late)
-    auto fetch_adj = [&](const ShotScalars &v, int &loc, float &val) {
+    auto flush = [&]() {
+#pragma unroll
+        for (int r = 0; r < RZ; ++r) {
+            const int i = i0 + r;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int j = j0 + p;
+                const float v = p < 2 ? (p == 0 ? acc_g[r][0].x : acc_g[r][0].y) : (p == 2 ? acc_g[r][1].x : acc_g[r][1].y);
+                if (i < L.nzp && j < L.nxp) atomicAdd(a.acc_grad + (long long)i * L.nxp + j, v);
+            }
+        }
+    };
+
+    // adjoint-source entry of this thread for an item (one entry per thread
+    // is prefetched; further entries of a crowded tile are read late)
+    auto fetch_adj = [&](const ItemDesc &v, int &loc, float &val) {
         loc = -1;
         val = 0.f;
         const int e = v.rb + (int)threadIdx.x;
-        if (e < v.re) {
+        if (v.tile >= 0 && e < v.re) {
             loc = a.rt.ent[e].x;
             val = a.adj[(long long)m * a.nent + e] * a.adj_scale;
         }
     };
 
-    // checkpointed sponge values of u^{m-2} of one item (sponge tiles only)
+    // checkpointed sponge values of u^{m-2} of one item of the current tile
     auto fetch_band = [&](int s, float4 (&bv)[RZ]) {
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
@@ -661,35 +788,58 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         }
     };
 
-    ShotScalars cur = fetch_scalars(c, a.rt, tile, g, m - 1, true, use_rec);
-    ShotScalars nxt = cur;
-    if (count > 1) nxt = fetch_scalars(c, a.rt, tile, g + G, m - 1, true, use_rec);
     int adj_loc;
     float adj_val;
-    fetch_adj(cur, adj_loc, adj_val);
+    fetch_adj(s_desc[0], adj_loc, adj_val);
     float4 bval[RZ];
-    if (tile_sponge) fetch_band(g, bval);
-    for (int k = 0; k < count; ++k) {
-        if (threadIdx.x == 0 && k + STAGES - 1 < count) issue(k + STAGES - 1);
-        const int s = g + k * G;
-        float4 bnow[RZ];
+    bool bval_ok = false; // bval holds the current item's checkpoint values
+    int k = 0;
+    for (;; ++k) {
+        if (threadIdx.x == 0) {
+            const ItemDesc d = pend;
+            s_desc[(k + D) % DESC_RING] = d;
+            if (d.tile >= 0) issue(d, k + D);
+            pend = next_desc();
+        }
+        const ItemDesc now = s_desc[k % DESC_RING];
+        if (now.tile < 0) break;
+        const ItemDesc nx = s_desc[(k + 1) % DESC_RING];
+        const int s = now.s;
+        if (now.tile != cur_tile) {
+            if (cur_tile >= 0) flush();
+            cur_tile = now.tile;
+            const int bz = cur_tile / c.ntx, bx = cur_tile - bz * c.ntx;
+            bi = bz * TZ;
+            bj = bx * TX;
+            i0 = bi + ty * RZ;
+            j0 = bj + 4 * tx;
+            tile_sponge = bi < L.P || bi + TZ > L.P + L.nz || bj < L.P || bj + TX > L.P + L.nx;
+            colok = j0 < L.nxp;
+            if (tile_sponge) sg.init(L, i0, j0);
 #pragma unroll
-        for (int r = 0; r < RZ; ++r) bnow[r] = bval[r];
-        const bool has_rec = cur.rb < cur.re; // uniform over the CTA
+            for (int r = 0; r < RZ; ++r) acc_g[r][0] = acc_g[r][1] = make_float2(0.f, 0.f);
+            load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
+            bval_ok = false;
+            __syncthreads();
+        }
+        float4 bnow[RZ];
+        if (tile_sponge) {
+            if (!bval_ok) fetch_band(s, bval);
+#pragma unroll
+            for (int r = 0; r < RZ; ++r) bnow[r] = bval[r];
+        }
+        const bool has_rec = now.rb < now.re; // uniform over the CTA
         const int my_loc = adj_loc;
         if (has_rec) {
             if (adj_loc >= 0) atomicAdd(&sinj[adj_loc], adj_val);
-            for (int e = cur.rb + TPB + (int)threadIdx.x; e < cur.re; e += TPB)
+            for (int e = now.rb + TPB + (int)threadIdx.x; e < now.re; e += TPB)
                 atomicAdd(&sinj[a.rt.ent[e].x], a.adj[(long long)m * a.nent + e] * a.adj_scale);
         }
-        // prefetch: scalars two items ahead, adjoint entry and checkpoint one ahead
-        const ShotScalars now = cur;
-        cur = nxt;
-        if (k + 1 < count) {
-            fetch_adj(cur, adj_loc, adj_val);
-            if (tile_sponge) fetch_band(s + G, bval);
-            if (k + 2 < count) nxt = fetch_scalars(c, a.rt, tile, s + 2 * G, m - 1, true, use_rec);
-        }
+        // prefetch for the next item: adjoint entry, and its checkpoint values
+        // when it is on the same tile
+        fetch_adj(nx, adj_loc, adj_val);
+        bval_ok = tile_sponge && nx.tile == cur_tile;
+        if (bval_ok) fetch_band(nx.s, bval);
         if (has_rec) __syncthreads();
         const int st = k % STAGES;
         if (stage_ready<STAGES>(bars, k, &s_abort)) {
@@ -788,7 +938,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         }
         __syncthreads();
         if (s_abort) {
-            abort_drain<STAGES>(bars, k, count, c.status);
+            abort_drain_ring<STAGES>(bars, s_desc, k, c.status);
             return;
         }
         if (has_rec) {
@@ -797,18 +947,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             __syncthreads();
         }
     }
-
-    // add this CTA's sum over its shots (padded grid)
-#pragma unroll
-    for (int r = 0; r < RZ; ++r) {
-        const int i = i0 + r;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int j = j0 + p;
-            const float v = p < 2 ? (p == 0 ? acc_g[r][0].x : acc_g[r][0].y) : (p == 2 ? acc_g[r][1].x : acc_g[r][1].y);
-            if (i < L.nzp && j < L.nxp) atomicAdd(a.acc_grad + (long long)i * L.nxp + j, v);
-        }
-    }
+    if (cur_tile >= 0) flush();
 }
 
 // ---------------------------------------------------------------- launchers
@@ -822,6 +961,13 @@ namespace {
 #ifndef FWI_B_ST
 #define FWI_B_ST 3
 #endif
+#ifndef FWI_CHUNK
+#define FWI_CHUNK 8
+#endif
+#ifndef FWI_CHUNK_OFFH
+#define FWI_CHUNK_OFFH 16
+#endif
+constexpr int CHUNK = FWI_CHUNK, CHUNK_OFFH = FWI_CHUNK_OFFH;
 #ifndef FWI_F_MINB
 #define FWI_F_MINB 3
 #endif
@@ -903,26 +1049,26 @@ Tiling make_tiling(const Lay2D &L, int ns, StepKind kind)
     t.ntx = (L.nxp + TX - 1) / TX;
     t.ntz = (L.nzp + t.tz - 1) / t.tz;
     const int tiles = t.ntx * t.ntz;
-    const int slots = sm_count_dev() * g_occ[kind];
-    int groups = slots / tiles;
-    if (groups < 1) groups = 1;
-    if (groups > ns) groups = ns;
-    t.groups = groups;
+    t.chunk = kind == STEP_FWD_OFFH ? CHUNK_OFFH : CHUNK;
+    if (t.chunk > ns) t.chunk = ns;
+    const long long chunks = (long long)tiles * ((ns + t.chunk - 1) / t.chunk);
+    const long long slots = (long long)sm_count_dev() * g_occ[kind];
+    t.ctas = (int)(chunks < slots ? chunks : slots);
     return t;
 }
 
 cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st)
 {
     if (with_offh)
-        K_FWDH<<<dim3(t.ntx * t.ntz, t.groups), TPB, SMEM_FWDH, st>>>(a);
+        K_FWDH<<<t.ctas, TPB, SMEM_FWDH, st>>>(a);
     else
-        K_FWD<<<dim3(t.ntx * t.ntz, t.groups), TPB, SMEM_FWD, st>>>(a);
+        K_FWD<<<t.ctas, TPB, SMEM_FWD, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st)
 {
-    K_BWD<<<dim3(t.ntx * t.ntz, t.groups), TPB, SMEM_BWD, st>>>(a);
+    K_BWD<<<t.ctas, TPB, SMEM_BWD, st>>>(a);
     return cudaGetLastError();
 }
 
