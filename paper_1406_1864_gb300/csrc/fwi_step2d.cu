@@ -439,6 +439,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     // item k+1's descriptor is read in iteration k and written in iteration
     // k+1-D: it must be written at least one barrier earlier, so D >= 2
     static_assert(D >= 2 && D + 2 <= DESC_RING, "needs 3 <= STAGES <= 7");
+    // live descriptor slots in iteration k: k .. k+D+1 (read, issued, staged)
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_abort;
     __shared__ ItemDesc s_desc[DESC_RING];
@@ -479,19 +480,20 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
         tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_cur, GXL + bx * TX - HX, bz * TZ, d.s, bar);
         if (!a.last) tma_load_3d(smem_u32(R::point(smem, st, 0)), &a.tm_prev, GXL + bx * TX, bz * TZ + GZ, d.s, bar);
     };
-    if (threadIdx.x == 0) {
+    // lane 0 of warp 1 walks the chunks and stages descriptors; thread 0
+    // issues the copies of a descriptor staged one barrier earlier
+    if (threadIdx.x == 32) {
         cursor_init(cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
-        for (int k = 0; k < D; ++k) {
-            const ItemDesc d = next_desc();
-            s_desc[k] = d;
-            if (d.tile >= 0) issue(d, k);
-        }
+        for (int k = 0; k <= D; ++k) s_desc[k] = next_desc();
         pend = next_desc();
     }
     __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < D; ++k)
+            if (s_desc[k].tile >= 0) issue(s_desc[k], k);
 
     float2 acc_i[RZ][2];
-    float acc_h[NH][4];
+    float2 acc_h[NH][2];
     int cur_tile = -1, bi = 0, bj = 0, i0 = 0, j0 = 0;
     bool tile_sponge = false, colok = false;
     SpongeInfo<RZ> sg;
@@ -511,7 +513,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                 if (WITH_H) {
 #pragma unroll
                     for (int h = 0; h < NH; ++h)
-                        if (h <= a.hmax) atomicAdd(a.acc_offh + h * nphys + o, acc_h[h][p]);
+                        if (h <= a.hmax)
+                            atomicAdd(a.acc_offh + h * nphys + o, (p & 1) ? acc_h[h][p >> 1].y : acc_h[h][p >> 1].x);
                 }
             }
         }
@@ -529,9 +532,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     int k = 0;
     for (;; ++k) {
         if (threadIdx.x == 0) {
-            const ItemDesc d = pend;
-            s_desc[(k + D) % DESC_RING] = d;
+            const ItemDesc d = s_desc[(k + D) % DESC_RING];
             if (d.tile >= 0) issue(d, k + D);
+        } else if (threadIdx.x == 32) {
+            s_desc[(k + D + 1) % DESC_RING] = pend;
             pend = next_desc();
         }
         const ItemDesc now = s_desc[k % DESC_RING];
@@ -556,9 +560,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
 #pragma unroll
             for (int r = 0; r < RZ; ++r) acc_i[r][0] = acc_i[r][1] = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int h = 0; h < NH; ++h)
-#pragma unroll
-                for (int p = 0; p < 4; ++p) acc_h[h][p] = 0.f;
+            for (int h = 0; h < NH; ++h) acc_h[h][0] = acc_h[h][1] = make_float2(0.f, 0.f);
             load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
             __syncthreads();
         }
@@ -648,11 +650,22 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                     acc_i[r][1] = fma2(u0[1], u0[1], acc_i[r][1]);
                 }
                 if (WITH_H) {
+                    // u(x+h) u(x-h); even h on aligned lane pairs
 #pragma unroll
                     for (int h = 0; h < NH; ++h)
                         if (h <= a.hmax) {
+                            if ((h & 1) == 0) {
 #pragma unroll
-                            for (int p = 0; p < 4; ++p) acc_h[h][p] = fmaf(w[WL + p + h], w[WL + p - h], acc_h[h][p]);
+                                for (int q = 0; q < 2; ++q)
+                                    acc_h[h][q] = fma2(f2(w[WL + 2 * q + h], w[WL + 2 * q + 1 + h]),
+                                                       f2(w[WL + 2 * q - h], w[WL + 2 * q + 1 - h]), acc_h[h][q]);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 2; ++q) {
+                                    acc_h[h][q].x = fmaf(w[WL + 2 * q + h], w[WL + 2 * q - h], acc_h[h][q].x);
+                                    acc_h[h][q].y = fmaf(w[WL + 2 * q + 1 + h], w[WL + 2 * q + 1 - h], acc_h[h][q].y);
+                                }
+                            }
                         }
                 }
             }
@@ -681,6 +694,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     // item k+1's descriptor is read in iteration k and written in iteration
     // k+1-D: it must be written at least one barrier earlier, so D >= 2
     static_assert(D >= 2 && D + 2 <= DESC_RING, "needs 3 <= STAGES <= 7");
+    // live descriptor slots in iteration k: k .. k+D+1 (read, issued, staged)
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_abort;
     __shared__ ItemDesc s_desc[DESC_RING];
@@ -726,16 +740,17 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         tma_load_3d(smem_u32(R::point(smem, st, 1)), &a.tm_pb, GXL + bj, bi + GZ, d.s, bar);
         if (need_ua) tma_load_3d(smem_u32(R::point(smem, st, 0)), &a.tm_ua, GXL + bj, bi + GZ, d.s, bar);
     };
-    if (threadIdx.x == 0) {
+    // lane 0 of warp 1 walks the chunks and stages descriptors; thread 0
+    // issues the copies of a descriptor staged one barrier earlier
+    if (threadIdx.x == 32) {
         cursor_init(cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
-        for (int k = 0; k < D; ++k) {
-            const ItemDesc d = next_desc();
-            s_desc[k] = d;
-            if (d.tile >= 0) issue(d, k);
-        }
+        for (int k = 0; k <= D; ++k) s_desc[k] = next_desc();
         pend = next_desc();
     }
     __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < D; ++k)
+            if (s_desc[k].tile >= 0) issue(s_desc[k], k);
 
     float2 acc_g[RZ][2];
     int cur_tile = -1, bi = 0, bj = 0, i0 = 0, j0 = 0;
@@ -796,9 +811,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     int k = 0;
     for (;; ++k) {
         if (threadIdx.x == 0) {
-            const ItemDesc d = pend;
-            s_desc[(k + D) % DESC_RING] = d;
+            const ItemDesc d = s_desc[(k + D) % DESC_RING];
             if (d.tile >= 0) issue(d, k + D);
+        } else if (threadIdx.x == 32) {
+            s_desc[(k + D + 1) % DESC_RING] = pend;
             pend = next_desc();
         }
         const ItemDesc now = s_desc[k % DESC_RING];
