@@ -66,6 +66,8 @@ typedef enum {
 enum { FWI_MISFIT_OLS = 0, FWI_MISFIT_TIME_INTEGRAL = 1 };
 enum { FWI_ILLUM_U2 = 0, FWI_ILLUM_UTT2 = 1 };
 enum { FWI_PRECOND_NONE = 0, FWI_PRECOND_ILLUM = 1, FWI_PRECOND_OFFSET = 2 };
+enum { FWI_CKPT_SPONGE = 0, FWI_CKPT_SNAPSHOT = 1 };
+enum { FWI_SNAP_F32 = 0, FWI_SNAP_BF16 = 1, FWI_SNAP_F16S = 2 };
 enum {
     FWI_OP_FORWARD = 0,        /* fwi_forward(save = 0)                     */
     FWI_OP_FORWARD_SAVE = 1,   /* fwi_forward(save = 1) + fwi_adjoint_apply */
@@ -109,6 +111,17 @@ typedef struct {
                        -1: not computed                                        */
     int precond;    /* FWI_PRECOND_*: preconditioner applied for grad_pre      */
     float eps;      /* water level of the division, > 0 (e.g. 1e-3)           */
+    int ckpt;       /* forward state kept for the adjoint pass:
+                       FWI_CKPT_SPONGE: every time level's sponge cells (exact;
+                         the model part is rebuilt by reverse time stepping);
+                         nshots * nt * sponge cells * 4 bytes
+                       FWI_CKPT_SNAPSHOT: the whole field every snap_interval
+                         levels, each segment re-propagated from its snapshot
+                         during the adjoint pass (about sqrt(nt) snapshots) */
+    int snap_prec;  /* snapshot storage: FWI_SNAP_F32 (u^n, u^{n-1} exact),
+                       FWI_SNAP_BF16 / FWI_SNAP_F16S (u^n and u^n - u^{n-1},
+                       each scaled by its own max-abs, as bfloat16 / float16) */
+    int snap_interval; /* levels between snapshots; 0: ceil(sqrt(nt))       */
 } fwi_options;
 
 /* Per-phase device times of the last call on this host thread, when enabled
@@ -142,7 +155,9 @@ fwi_status fwi_forward(const fwi_grid *grid, const fwi_geometry *geom, const fwi
    the adjoint of the Jacobian applied to adj_src [Sec. 2, zero-lag
    cross-correlation of forward and back-propagated wavefields]. Needs the
    checkpoints of a preceding fwi_forward(save = 1) with the same grid,
-   geometry, v and ws, and nothing else on ws in between.
+   geometry, options (opts->ckpt, snap_prec, snap_interval), v and ws, and
+   nothing else on ws in between. The call overwrites the forward buffers of
+   ws: a second fwi_adjoint_apply needs a new fwi_forward(save = 1).
    adj_src DEVICE [nshots][nt][nrec]; grad DEVICE [nz][nx] output. */
 fwi_status fwi_adjoint_apply(const fwi_grid *grid, const fwi_geometry *geom,
                              const fwi_options *opts, const float *v, const float *adj_src,

@@ -21,6 +21,8 @@ STATUS_NAMES = ["FWI_OK", "FWI_ERR_INVALID_ARG", "FWI_ERR_CFL", "FWI_ERR_NOMEM",
 FWI_MISFIT_OLS, FWI_MISFIT_TIME_INTEGRAL = 0, 1
 FWI_ILLUM_U2, FWI_ILLUM_UTT2 = 0, 1
 FWI_PRECOND_NONE, FWI_PRECOND_ILLUM, FWI_PRECOND_OFFSET = 0, 1, 2
+FWI_CKPT_SPONGE, FWI_CKPT_SNAPSHOT = 0, 1
+FWI_SNAP_F32, FWI_SNAP_BF16, FWI_SNAP_F16S = 0, 1, 2
 (FWI_OP_FORWARD, FWI_OP_FORWARD_SAVE, FWI_OP_GRADIENT, FWI_OP_ILLUMINATION,
  FWI_OP_OFFSET_HESSIAN, FWI_OP_PRECONDITION) = range(6)
 FWI_HMAX_LIMIT = 12
@@ -39,7 +41,7 @@ class FwiGeometry(ctypes.Structure):
 
 class FwiOptions(ctypes.Structure):
     _fields_ = [("misfit", c_int), ("illum_mode", c_int), ("hmax", c_int), ("precond", c_int),
-                ("eps", c_float)]
+                ("eps", c_float), ("ckpt", c_int), ("snap_prec", c_int), ("snap_interval", c_int)]
 
 
 class FwiPhaseTimes(ctypes.Structure):

@@ -70,6 +70,12 @@ struct Plan {
     Part scal, c2, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab, sched;
     size_t tab_src = 0, tab_srcij = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0, tab_bshot = 0;
     Part adj_t; // adjoint source in backward-table order [nt][ns*nrec]
+    // snapshot checkpoints (FWI_CKPT_SNAPSHOT): snapshot j holds level j*K
+    bool snap = false;
+    int snap_prec = FWI_SNAP_F32, K = 0, nck = 0;
+    Tiling tr{};          // tiling of the segment re-propagation (plain forward)
+    Part snaps, snap_max; // [nck][2][ns][fstride] F32 / 16-bit, [nck][2][ns]
+    Part seg;             // segment levels beyond the two forward buffers
     size_t total = 0;
 };
 
@@ -130,6 +136,11 @@ fwi_status check_opts(const fwi_options *o, int op)
     if (o->precond == FWI_PRECOND_OFFSET && o->hmax < 0)
         return fail(FWI_ERR_INVALID_ARG, "precond=OFFSET needs hmax >= 0");
     if (!(o->eps > 0.f) || !std::isfinite(o->eps)) return fail(FWI_ERR_INVALID_ARG, "eps must be > 0");
+    if (o->ckpt != FWI_CKPT_SPONGE && o->ckpt != FWI_CKPT_SNAPSHOT)
+        return fail(FWI_ERR_INVALID_ARG, "ckpt=%d unknown", o->ckpt);
+    if (o->snap_prec < FWI_SNAP_F32 || o->snap_prec > FWI_SNAP_F16S)
+        return fail(FWI_ERR_INVALID_ARG, "snap_prec=%d unknown", o->snap_prec);
+    if (o->snap_interval < 0) return fail(FWI_ERR_INVALID_ARG, "snap_interval=%d must be >= 0", o->snap_interval);
     return FWI_OK;
 }
 
@@ -172,7 +183,10 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         off = align_up(off + bytes);
     };
     take(pl.scal, 256);
-    if (op != FWI_OP_PRECONDITION) take(pl.sched, (size_t)2 * g->nt * sizeof(int));
+    const bool need_bwd = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE);
+    pl.snap = need_bwd && o && o->ckpt == FWI_CKPT_SNAPSHOT;
+    // scheduler counters: forward, backward, and (snapshots) re-propagation
+    if (op != FWI_OP_PRECONDITION) take(pl.sched, (size_t)(pl.snap ? 3 : 2) * g->nt * sizeof(int));
     if (op == FWI_OP_PRECONDITION) {
         pl.total = off;
         return FWI_OK;
@@ -183,7 +197,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
     pl.with_offh = (op == FWI_OP_GRADIENT || op == FWI_OP_OFFSET_HESSIAN) && pl.hmax >= 0;
     if (op == FWI_OP_OFFSET_HESSIAN && pl.hmax < 0)
         return fail(FWI_ERR_INVALID_ARG, "offset Hessian needs hmax >= 0");
-    pl.need_bwd = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE);
+    pl.need_bwd = need_bwd;
     pl.need_seis_tab = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE);
     pl.tf = make_tiling(L, pl.ns, pl.with_offh ? STEP_FWD_OFFH : STEP_FWD);
     pl.tb = make_tiling(L, pl.ns, STEP_BWD);
@@ -195,7 +209,23 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
     if (pl.need_bwd) {
         take(pl.p[0], fbytes * pl.ns);
         take(pl.p[1], fbytes * pl.ns);
-        take(pl.band, (size_t)pl.ns * pl.nt * L.nbandp * sizeof(float));
+        if (!pl.snap) {
+            take(pl.band, (size_t)pl.ns * pl.nt * L.nbandp * sizeof(float));
+        } else {
+            // levels 0..nt-2 are needed; segment j re-propagates levels
+            // jK+1 .. min(jK+K-1, nt-2) from snapshot j (levels jK, jK-1)
+            pl.snap_prec = o->snap_prec;
+            pl.K = o->snap_interval > 0 ? o->snap_interval : (int)std::ceil(std::sqrt((double)pl.nt));
+            pl.K = std::max(1, std::min(pl.K, pl.nt - 1));
+            pl.nck = (pl.nt - 1 + pl.K - 1) / pl.K;
+            pl.tr = make_tiling(L, pl.ns, STEP_FWD);
+            const size_t esz = pl.snap_prec == FWI_SNAP_F32 ? 4 : 2;
+            take(pl.snaps, (size_t)pl.nck * 2 * pl.ns * L.fstride * esz);
+            if (pl.snap_prec != FWI_SNAP_F32) take(pl.snap_max, (size_t)pl.nck * 2 * pl.ns * sizeof(float));
+            // K + 1 slots (K levels and u^{jK-1}); the two forward buffers
+            // serve as slots 0 and 1
+            if (pl.K + 1 > 2) take(pl.seg, fbytes * pl.ns * (size_t)(pl.K - 1));
+        }
         take(pl.acc_g, (size_t)L.nzp * L.nxp * sizeof(float));
     }
     if (op == FWI_OP_GRADIENT) take(pl.syn, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
@@ -342,6 +372,48 @@ fwi_status setup(const Plan &pl, const fwi_geometry *ge, const float *v, void *w
     return FWI_OK;
 }
 
+// element count of one wavefield buffer (all shots)
+inline long long field_elems(const Plan &pl) { return (long long)pl.ns * pl.L.fstride; }
+
+fwi_status capture_snapshot(const Plan &pl, void *ws, int j, const float *u, const float *up, cudaStream_t st)
+{
+    const long long ne = field_elems(pl);
+    cudaError_t e;
+    if (pl.snap_prec == FWI_SNAP_F32) {
+        float *dst = at<float>(ws, pl.snaps) + (size_t)j * 2 * ne;
+        if ((e = cudaMemcpyAsync(dst, u, ne * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(dst + ne, up, ne * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "snapshot copy");
+        return FWI_OK;
+    }
+    float *mx = at<float>(ws, pl.snap_max) + (size_t)j * 2 * pl.ns;
+    void *dst = at<char>(ws, pl.snaps) + (size_t)j * 2 * ne * 2;
+    if ((e = launch_snap_absmax(u, up, pl.ns, pl.L.fstride, mx, st)) != cudaSuccess) return cuda_fail(e, "snapshot max");
+    if ((e = launch_snap_encode(u, up, pl.ns, pl.L.fstride, mx, pl.snap_prec, dst, st)) != cudaSuccess)
+        return cuda_fail(e, "snapshot encode");
+    t_launch[2] += 2;
+    return FWI_OK;
+}
+
+fwi_status restore_snapshot(const Plan &pl, void *ws, int j, float *u, float *up, cudaStream_t st)
+{
+    const long long ne = field_elems(pl);
+    cudaError_t e;
+    if (pl.snap_prec == FWI_SNAP_F32) {
+        const float *src = at<float>(ws, pl.snaps) + (size_t)j * 2 * ne;
+        if ((e = cudaMemcpyAsync(u, src, ne * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(up, src + ne, ne * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "snapshot copy");
+        return FWI_OK;
+    }
+    const float *mx = at<float>(ws, pl.snap_max) + (size_t)j * 2 * pl.ns;
+    const void *src = at<char>(ws, pl.snaps) + (size_t)j * 2 * ne * 2;
+    if ((e = launch_snap_decode(src, mx, pl.snap_prec, pl.ns, pl.L.fstride, u, up, st)) != cudaSuccess)
+        return cuda_fail(e, "snapshot decode");
+    t_launch[2]++;
+    return FWI_OK;
+}
+
 // forward time loop n = 0..nt-1
 fwi_status run_forward(const Plan &pl, const fwi_geometry *ge, void *ws, float *seis, bool save,
                        float *acc_i, float *acc_h, int illum_utt, cudaStream_t st)
@@ -351,7 +423,8 @@ fwi_status run_forward(const Plan &pl, const fwi_geometry *ge, void *ws, float *
     if (acc_h && (e = cudaMemsetAsync(acc_h, 0, pl.acc_h.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
     FwdArgs a{};
     a.c = make_common(pl, ge, ws, pl.tf);
-    a.band = save ? at<float>(ws, pl.band) : nullptr;
+    a.band = (save && !pl.snap) ? at<float>(ws, pl.band) : nullptr;
+    const bool capture = save && pl.snap;
     a.seis = (seis && pl.nrec > 0) ? seis : nullptr;
     a.acc_illum = acc_i;
     a.acc_offh = acc_h;
@@ -368,12 +441,17 @@ fwi_status run_forward(const Plan &pl, const fwi_geometry *ge, void *ws, float *
         if (!encode_field_map(&mh[b], U[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&mp[b], U[b], pl.L, pl.ns, px, py))
             return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
     for (int n = 0; n < pl.nt; ++n) {
+        if (capture && n % pl.K == 0 && n <= pl.nt - 2) {
+            // snapshot n / K of the state (u^n, u^{n-1}) before step n
+            fwi_status sc = capture_snapshot(pl, ws, n / pl.K, U[n & 1], U[(n + 1) & 1], st);
+            if (sc != FWI_OK) return sc;
+        }
         a.n = n;
         a.last = (n == pl.nt - 1);
         a.tm_cur = mh[n & 1];
         a.tm_prev = mp[(n + 1) & 1];
         a.c.sched = at<int>(ws, pl.sched) + n;
-        a.uprev = U[(n + 1) & 1];
+        a.uout = U[(n + 1) & 1];
         if ((e = launch_fwd_step(a, pl.tf, offh, st)) != cudaSuccess)
             return cuda_fail(e, "forward step");
         t_launch[0]++;
@@ -382,6 +460,73 @@ fwi_status run_forward(const Plan &pl, const fwi_geometry *ge, void *ws, float *
         if ((e = launch_check_finite(U[b], (long long)pl.ns * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
             return cuda_fail(e, "finite check");
     t_launch[2] += 2;
+    return FWI_OK;
+}
+
+// Backward loop with snapshot checkpoints. For segment j = nck-1..0 (levels
+// n_j = jK .. e_j = min(jK+K-1, nt-2)): restore (u^{n_j}, u^{n_j-1}) from
+// snapshot j, re-run forward steps n_j..e_j-1 into one slot per level, then
+// run adjoint steps m = e_j+1 .. n_j+1, each reading u^{m-1} from its slot.
+// The re-run is the same plain forward step as the forward loop (no traces,
+// no accumulators), so with F32 snapshots u^{m-1} is the forward's own value.
+fwi_status run_backward_segments(const Plan &pl, const fwi_geometry *ge, void *ws, BwdArgs &a, float *const U[2],
+                                 float *const Pp[2], const CUtensorMap ph[2], const CUtensorMap pp[2], cudaStream_t st)
+{
+    cudaError_t e;
+    const int K = pl.K;
+    // slot i < K holds level n_j + i; slot K holds u^{n_j - 1}
+    std::vector<float *> S(K + 1);
+    for (int i = 0; i <= K; ++i)
+        S[i] = i < 2 ? U[i] : at<float>(ws, pl.seg) + (size_t)(i - 2) * field_elems(pl);
+    // the re-run writes only the padded model: the ghost frame of every slot
+    // must read as zero
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaMemsetAsync(U[b], 0, pl.u[b].bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if (pl.seg.bytes && (e = cudaMemsetAsync(at<char>(ws, pl.seg), 0, pl.seg.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    int fhx, fhy, fpx, fpy, bhx, bhy, bpx, bpy;
+    step_boxes(STEP_FWD, fhx, fhy, fpx, fpy);
+    step_boxes(STEP_BWD, bhx, bhy, bpx, bpy);
+    std::vector<CUtensorMap> fh(K + 1), fp(K + 1), bh(K + 1);
+    for (int i = 0; i <= K; ++i)
+        if (!encode_field_map(&fh[i], S[i], pl.L, pl.ns, fhx, fhy) ||
+            !encode_field_map(&fp[i], S[i], pl.L, pl.ns, fpx, fpy) ||
+            !encode_field_map(&bh[i], S[i], pl.L, pl.ns, bhx, bhy))
+            return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the segment buffers");
+    FwdArgs f{};
+    f.c = make_common(pl, ge, ws, pl.tr);
+    f.hmax = -1;
+    for (int j = pl.nck - 1; j >= 0; --j) {
+        const int n0 = j * K, n1 = std::min(n0 + K - 1, pl.nt - 2);
+        fwi_status sr = restore_snapshot(pl, ws, j, S[0], S[K], st);
+        if (sr != FWI_OK) return sr;
+        for (int n = n0; n < n1; ++n) {
+            const int i = n - n0;
+            f.n = n;
+            f.last = 0;
+            f.tm_cur = fh[i];
+            f.tm_prev = fp[i == 0 ? K : i - 1];
+            f.uout = S[i + 1];
+            f.c.sched = at<int>(ws, pl.sched) + 2 * pl.nt + n;
+            if ((e = launch_fwd_step(f, pl.tr, false, st)) != cudaSuccess) return cuda_fail(e, "segment step");
+            t_launch[1]++;
+        }
+        for (int m = n1 + 1; m >= n0 + 1; --m) {
+            a.m = m;
+            a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
+            a.tm_ub = bh[m - 1 - n0];
+            a.tm_pa = ph[(m + 1) & 1];
+            a.tm_ua = pp[m & 1]; // not read without reconstruction
+            a.tm_pb = pp[m & 1];
+            a.ua = nullptr;
+            a.pb = Pp[m & 1];
+            if ((e = launch_bwd_step(a, pl.tb, st)) != cudaSuccess) return cuda_fail(e, "backward step");
+            t_launch[1]++;
+        }
+    }
+    if ((e = launch_check_finite(Pp[0], field_elems(pl), at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
+        return cuda_fail(e, "finite check");
+    t_launch[2]++;
     return FWI_OK;
 }
 
@@ -413,6 +558,7 @@ fwi_status run_backward(const Plan &pl, const fwi_geometry *ge, void *ws, const 
     a.rt.ptr = at<int>(ws, pl.tab, pl.tab_bptr);
     a.rt.ent = at<int2>(ws, pl.tab, pl.tab_bent);
     a.adj_scale = pl.L.dx * pl.L.dx;
+    a.recon = pl.snap ? 0 : 1;
     float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
     float *Pp[2] = {at<float>(ws, pl.p[0]), at<float>(ws, pl.p[1])};
     int hx, hy, px, py;
@@ -422,6 +568,7 @@ fwi_status run_backward(const Plan &pl, const fwi_geometry *ge, void *ws, const 
         if (!encode_field_map(&uh[b], U[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&up[b], U[b], pl.L, pl.ns, px, py) ||
             !encode_field_map(&ph[b], Pp[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&pp[b], Pp[b], pl.L, pl.ns, px, py))
             return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
+    if (pl.snap) return run_backward_segments(pl, ge, ws, a, U, Pp, ph, pp, st);
     for (int m = pl.nt - 1; m >= 1; --m) {
         a.m = m;
         a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;

@@ -6,6 +6,8 @@
 #include "fwi_internal.h"
 
 #include <cfloat>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace fwi {
 
@@ -200,6 +202,78 @@ __global__ void k_permute_adj(const float *__restrict__ adj, const int2 *__restr
     }
 }
 
+// ------------------------------------------------------------- snapshots
+// A snapshot of the state (u^n, u^{n-1}) in 16 bits keeps u^n and the
+// increment u^n - u^{n-1} separately, each scaled by its own max-abs so that
+// the largest value maps to SNAP_TARGET: the increment is small compared with
+// u, and rounding u^{n-1} on its own would swamp it.
+constexpr float SNAP_TARGET = 16384.0f;
+
+__device__ __forceinline__ float snap_scale(float mx) { return mx > 0.f ? SNAP_TARGET / mx : 1.0f; }
+
+// maxes[0][s] = max |u|, maxes[1][s] = max |u - up| over shot s's field
+__global__ void k_snap_absmax(const float *__restrict__ u, const float *__restrict__ up, long long fstride,
+                              float *maxes, int ns)
+{
+    const int s = blockIdx.y;
+    const float *us = u + (long long)s * fstride, *ps = up + (long long)s * fstride;
+    float mu = 0.f, md = 0.f;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < fstride;
+         e += (long long)gridDim.x * blockDim.x) {
+        const float a = us[e];
+        mu = fmaxf(mu, fabsf(a));
+        md = fmaxf(md, fabsf(a - ps[e]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned *>(maxes) + s, __float_as_uint(mu));
+        atomicMax(reinterpret_cast<unsigned *>(maxes) + ns + s, __float_as_uint(md));
+    }
+}
+
+template <typename H>
+__device__ __forceinline__ H to16(float x);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half to16<__half>(float x) { return __float2half_rn(x); }
+__device__ __forceinline__ float from16(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float from16(__half x) { return __half2float(x); }
+
+// dst [2][ns][fstride]: u * s_u, (u - up) * s_d
+template <typename H>
+__global__ void k_snap_encode(const float *__restrict__ u, const float *__restrict__ up, int ns, long long fstride,
+                              const float *__restrict__ maxes, H *__restrict__ dst)
+{
+    const long long n = (long long)ns * fstride;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(e / fstride);
+        const float a = u[e];
+        dst[e] = to16<H>(a * snap_scale(maxes[s]));
+        dst[n + e] = to16<H>((a - up[e]) * snap_scale(maxes[ns + s]));
+    }
+}
+
+// u = a / s_u, up = u - d / s_d
+template <typename H>
+__global__ void k_snap_decode(const H *__restrict__ src, const float *__restrict__ maxes, int ns, long long fstride,
+                              float *__restrict__ u, float *__restrict__ up)
+{
+    const long long n = (long long)ns * fstride;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(e / fstride);
+        const float a = from16(src[e]) / snap_scale(maxes[s]);
+        u[e] = a;
+        up[e] = a - from16(src[n + e]) / snap_scale(maxes[ns + s]);
+    }
+}
+
 int grid_for(long long n)
 {
     long long b = (n + NT1 - 1) / NT1;
@@ -256,6 +330,43 @@ cudaError_t launch_precond(const Lay2D &L, const float *grad, const float *scale
     if (e != cudaSuccess) return e;
     k_precond_max<<<grid_for(nphys), NT1, 0, st>>>(nphys, scale, kind, hmax, pmax);
     k_precond_apply<<<grid_for(nphys), NT1, 0, st>>>(nphys, grad, scale, kind, hmax, eps, pmax, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snap_absmax(const float *u, const float *up, int ns, long long fstride, float *maxes,
+                               cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(maxes, 0, 2 * (size_t)ns * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    int bx = (int)((fstride / 4 + NT1 - 1) / NT1);
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    k_snap_absmax<<<dim3(bx, ns), NT1, 0, st>>>(u, up, fstride, maxes, ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snap_encode(const float *u, const float *up, int ns, long long fstride, const float *maxes,
+                               int prec, void *dst, cudaStream_t st)
+{
+    const long long n = (long long)ns * fstride;
+    if (prec == 1)
+        k_snap_encode<__nv_bfloat16><<<grid_for(n / 4 + 1), NT1, 0, st>>>(u, up, ns, fstride, maxes,
+                                                                          static_cast<__nv_bfloat16 *>(dst));
+    else
+        k_snap_encode<__half><<<grid_for(n / 4 + 1), NT1, 0, st>>>(u, up, ns, fstride, maxes, static_cast<__half *>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snap_decode(const void *src, const float *maxes, int prec, int ns, long long fstride, float *u,
+                               float *up, cudaStream_t st)
+{
+    const long long n = (long long)ns * fstride;
+    if (prec == 1)
+        k_snap_decode<__nv_bfloat16><<<grid_for(n / 4 + 1), NT1, 0, st>>>(static_cast<const __nv_bfloat16 *>(src),
+                                                                          maxes, ns, fstride, u, up);
+    else
+        k_snap_decode<__half><<<grid_for(n / 4 + 1), NT1, 0, st>>>(static_cast<const __half *>(src), maxes, ns,
+                                                                   fstride, u, up);
     return cudaGetLastError();
 }
 

@@ -94,7 +94,8 @@ struct FwdArgs {
     CUtensorMap tm_cur;    // u^n, halo box
     CUtensorMap tm_prev;   // u^{n-1}, point box
     StepCommon c;
-    float *uprev;          // u^{n-1} buffer: u^{n+1} is written here
+    float *uout;           // u^{n+1} is written here (the u^{n-1} buffer, or a
+                           // segment slot when re-propagating from a snapshot)
     float *band;           // [ns][nt][nbandp] checkpoints (u^{n+1} stored) or null
     float *seis;           // [ns][nt][nrec] traces or null
     float *acc_illum;      // [nz][nx] or null (red.add)
@@ -121,6 +122,8 @@ struct BwdArgs {
     RecTable rt;
     float adj_scale;       // dx^2
     int m;
+    int recon;             // 1: rebuild u^{m-2} (model) / restore it (sponge);
+                           // 0: u^{m-1} comes from a re-propagated segment
 };
 
 // status bits written by kernels
@@ -163,6 +166,14 @@ cudaError_t launch_finish_accum(const Lay2D &L, const float *acc, int groups, in
 cudaError_t launch_precond(const Lay2D &L, const float *grad, const float *scale, int kind,
                            int hmax, float eps, float *out, unsigned *pmax, cudaStream_t st);
 cudaError_t launch_check_finite(const float *x, long long n, int *status, cudaStream_t st);
+// snapshots of (u^n, u^{n-1}) in 16 bits: u and u - u_prev, each scaled by
+// its own max-abs (prec 1: bfloat16, 2: float16)
+cudaError_t launch_snap_absmax(const float *u, const float *up, int ns, long long fstride, float *maxes,
+                               cudaStream_t st);
+cudaError_t launch_snap_encode(const float *u, const float *up, int ns, long long fstride, const float *maxes,
+                               int prec, void *dst, cudaStream_t st);
+cudaError_t launch_snap_decode(const void *src, const float *maxes, int prec, int ns, long long fstride, float *u,
+                               float *up, cudaStream_t st);
 cudaError_t launch_permute_adj(const float *adj, const int2 *ent, const int *eshot, int nent, int nt, int nrec,
                                float *adj_t, cudaStream_t st);
 

@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
         if (stage_ready<STAGES>(bars, k, &s_abort)) {
             const float *sm = R::halo(smem, st, 0);
             const float *pm = R::point(smem, st, 0);
-            float *up = a.uprev + (long long)s * L.fstride;
+            float *up = a.uout + (long long)s * L.fstride;
 
             // receiver extraction d^n = R u^n
             float *seis_s = a.seis + ((long long)s * c.nt + a.n) * c.nrec;
@@ -708,7 +708,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int m = a.m;
     const bool use_rec = a.adj != nullptr;
-    const bool need_band = m >= 3; // u^{m-2} in the sponge comes from checkpoint m-2 >= 1
+    const bool recon = a.recon != 0;
+    const bool need_band = recon && m >= 3; // u^{m-2} in the sponge comes from checkpoint m-2 >= 1
     const int ntiles = c.ntx * c.ntz;
     const int nchunks = ntiles * ((c.ns + c.chunk - 1) / c.chunk);
 
@@ -732,7 +733,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         const int bi = bz * TZ, bj = bx * TX;
         const int st = k % STAGES;
         const uint32_t bar = smem_u32(&bars[st]);
-        const bool need_ua = m >= 2;
+        const bool need_ua = recon && m >= 2;
         fence_proxy_async_smem();
         mbar_expect_tx(bar, (2 * R::HALO + (need_ua ? 2 : 1) * R::PT) * 4);
         tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_ub, GXL + bj - HX, bi, d.s, bar);
@@ -918,7 +919,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                     }
                     *reinterpret_cast<float4 *>(a.pb + so + fidx(L, i0 + r, j0)) =
                         make_float4(pn[0].x, pn[0].y, pn[1].x, pn[1].y);
-                    if (m >= 2)
+                    if (recon && m >= 2)
                         *reinterpret_cast<float4 *>(a.ua + so + fidx(L, i0 + r, j0)) =
                             make_float4(un[0].x, un[0].y, un[1].x, un[1].y);
                 } else {
@@ -947,7 +948,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                     }
                     if (colok && i < L.nzp) {
                         store4(a.pb + so + fidx(L, i, j0), j0, L.nxp, pnew);
-                        if (m >= 2) store4(a.ua + so + fidx(L, i, j0), j0, L.nxp, unew);
+                        if (recon && m >= 2) store4(a.ua + so + fidx(L, i, j0), j0, L.nxp, unew);
                     }
                 }
             }

@@ -70,19 +70,26 @@ class Geometry:
 @dataclass
 class Options:
     """fwi_options: misfit 'ols' | 'integral', illum 'u2' | 'utt2', hmax
-    (-1 = no offset Hessian), precond 'none' | 'illum' | 'offset', eps."""
+    (-1 = no offset Hessian), precond 'none' | 'illum' | 'offset', eps;
+    ckpt 'sponge' | 'snapshot', snap 'f32' | 'bf16' | 'f16s', snap_interval
+    (0 = ceil(sqrt(nt)))."""
     misfit: str = "ols"
     illum: str = "u2"
     hmax: int = -1
     precond: str = "illum"
     eps: float = 1e-3
+    ckpt: str = "sponge"
+    snap: str = "f32"
+    snap_interval: int = 0
 
     def c(self) -> L.FwiOptions:
         m = {"ols": L.FWI_MISFIT_OLS, "integral": L.FWI_MISFIT_TIME_INTEGRAL}[self.misfit]
         i = {"u2": L.FWI_ILLUM_U2, "utt2": L.FWI_ILLUM_UTT2}[self.illum]
         p = {"none": L.FWI_PRECOND_NONE, "illum": L.FWI_PRECOND_ILLUM,
              "offset": L.FWI_PRECOND_OFFSET}[self.precond]
-        return L.FwiOptions(m, i, int(self.hmax), p, float(self.eps))
+        k = {"sponge": L.FWI_CKPT_SPONGE, "snapshot": L.FWI_CKPT_SNAPSHOT}[self.ckpt]
+        sp = {"f32": L.FWI_SNAP_F32, "bf16": L.FWI_SNAP_BF16, "f16s": L.FWI_SNAP_F16S}[self.snap]
+        return L.FwiOptions(m, i, int(self.hmax), p, float(self.eps), k, sp, int(self.snap_interval))
 
 
 def _ptr(t):

@@ -95,13 +95,45 @@ def test_bad_grid_rejected(lib, field, value, code):
 
 
 @pytest.mark.parametrize("field,value", [("misfit", 7), ("illum_mode", 3), ("hmax", 13),
-                                         ("hmax", -2), ("precond", 5), ("eps", 0.0)])
+                                         ("hmax", -2), ("precond", 5), ("eps", 0.0), ("ckpt", 2),
+                                         ("snap_prec", 3), ("snap_interval", -1)])
 def test_bad_options_rejected(lib, field, value):
     from paper_1406_1864_gb300 import _lib as L
     g, ge, o, keep = _structs()
     setattr(o, field, value)
     st, _ = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
     assert st == L.FWI_ERR_INVALID_ARG
+
+
+def test_snapshot_workspace_sizes(lib):
+    """Snapshot checkpoints replace the per-level sponge band by about sqrt(nt)
+    whole fields: 2 fields per snapshot (F32) or 1 (16-bit), plus K - 1 segment
+    slots. Long runs need far less workspace than the sponge mode."""
+    from paper_1406_1864_gb300 import _lib as L
+    nt, ns = 4000, 2
+    g, ge, o, keep = _structs(nz=60, nx=80, nt=nt, ns=ns)
+    sponge = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[1]
+    o.ckpt = L.FWI_CKPT_SNAPSHOT
+    sizes = {}
+    for prec in (L.FWI_SNAP_F32, L.FWI_SNAP_BF16, L.FWI_SNAP_F16S):
+        o.snap_prec = prec
+        st, n = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
+        assert st == L.FWI_OK, lib.fwi_last_error()
+        sizes[prec] = n
+    assert sizes[L.FWI_SNAP_F32] < sponge / 4
+    assert sizes[L.FWI_SNAP_BF16] == sizes[L.FWI_SNAP_F16S] < sizes[L.FWI_SNAP_F32]
+    # K = ceil(sqrt(4000)) = 64 -> 63 snapshots of 2 fields; the F32 and 16-bit
+    # plans differ by the snapshots' bytes (less the 16-bit maxima)
+    nck = (nt - 1 + 63) // 64
+    diff = sizes[L.FWI_SNAP_F32] - sizes[L.FWI_SNAP_BF16]
+    field_all_shots = diff / (nck * 2 * 2)
+    assert field_all_shots > ns * 60 * 80 and field_all_shots < ns * 4 * (60 + 40) * (80 + 100)
+    # a longer interval keeps fewer snapshots but more segment slots
+    o.snap_prec = L.FWI_SNAP_F32
+    o.snap_interval = 8
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[1] > sizes[L.FWI_SNAP_F32]
+    # forward without save and the other forward-only calls keep nothing
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_FORWARD)[1] < sizes[L.FWI_SNAP_BF16]
 
 
 def test_offset_precond_needs_hmax(lib):
