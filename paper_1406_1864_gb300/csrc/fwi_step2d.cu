@@ -341,14 +341,14 @@ __device__ __forceinline__ ItemDesc make_desc(const StepCommon &c, const RecTabl
 }
 
 // After a timeout (seen by the whole CTA after a barrier): record it and wait,
-// bounded, for the copies of the items after k that were issued, so that no
-// TMA write lands in shared memory after the CTA has left.
+// bounded, for the copies of item k and of the items after it that were
+// issued, so that no TMA write lands in shared memory after the CTA has left.
 template <int STAGES>
 __device__ void abort_drain_ring(uint64_t *bars, const ItemDesc *desc, int k, int *status)
 {
     if (threadIdx.x != 0) return;
     atomicOr(status, ST_TIMEOUT);
-    for (int j = k + 1; j < k + STAGES; ++j)
+    for (int j = k; j < k + STAGES; ++j)
         if (desc[j % DESC_RING].tile >= 0) mbar_wait(smem_u32(&bars[j % STAGES]), (j / STAGES) & 1, DRAIN_NS);
 }
 
@@ -436,9 +436,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     constexpr int NW = (2 * WL + 4) / 4;             // float4s in the x-window
     constexpr int D = STAGES - 1;                    // items in flight ahead of the compute
     static_assert(!WITH_H || (RZ == 1 && HX == 12), "offset Hessian uses RZ=1, HX=12");
-    // item k+1's descriptor is read in iteration k and written in iteration
-    // k+1-D: it must be written at least one barrier earlier, so D >= 2
-    static_assert(D >= 2 && D + 2 <= DESC_RING, "needs 3 <= STAGES <= 7");
+    // item j's descriptor is staged (lane 0 of warp 1) in iteration j-D-1
+    // and read in iteration j-D (copy issue) and j-1 (prefetch) and j: always
+    // at least one barrier after it was written, for any D >= 1
+    static_assert(D >= 1 && D + 2 <= DESC_RING, "needs 2 <= STAGES <= 7");
     // live descriptor slots in iteration k: k .. k+D+1 (read, issued, staged)
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_abort;
@@ -691,9 +692,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     constexpr int HX = RADIUS;
     constexpr int TXS = R::TXS;
     constexpr int D = STAGES - 1;
-    // item k+1's descriptor is read in iteration k and written in iteration
-    // k+1-D: it must be written at least one barrier earlier, so D >= 2
-    static_assert(D >= 2 && D + 2 <= DESC_RING, "needs 3 <= STAGES <= 7");
+    // item j's descriptor is staged (lane 0 of warp 1) in iteration j-D-1
+    // and read in iteration j-D (copy issue) and j-1 (prefetch) and j: always
+    // at least one barrier after it was written, for any D >= 1
+    static_assert(D >= 1 && D + 2 <= DESC_RING, "needs 2 <= STAGES <= 7");
     // live descriptor slots in iteration k: k .. k+D+1 (read, issued, staged)
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_abort;
@@ -973,10 +975,10 @@ namespace {
 #define FWI_F_ST 3
 #endif
 #ifndef FWI_H_ST
-#define FWI_H_ST 4
+#define FWI_H_ST 3
 #endif
 #ifndef FWI_B_ST
-#define FWI_B_ST 3
+#define FWI_B_ST 2
 #endif
 #ifndef FWI_CHUNK
 #define FWI_CHUNK 8
@@ -986,17 +988,26 @@ namespace {
 #endif
 constexpr int CHUNK = FWI_CHUNK, CHUNK_OFFH = FWI_CHUNK_OFFH;
 #ifndef FWI_F_MINB
-#define FWI_F_MINB 3
+#define FWI_F_MINB 4
 #endif
 #ifndef FWI_B_MINB
-#define FWI_B_MINB 3
+#define FWI_B_MINB 4
 #endif
-// forward without the offset Hessian: 64 x 32 tiles
-constexpr int F_RZ = 4, F_ST = FWI_F_ST, F_MINB = FWI_F_MINB;
+#ifndef FWI_F_RZ
+#define FWI_F_RZ 2
+#endif
+#ifndef FWI_B_RZ
+#define FWI_B_RZ 2
+#endif
+// forward without the offset Hessian: 64 x 16 tiles
+constexpr int F_RZ = FWI_F_RZ, F_ST = FWI_F_ST, F_MINB = FWI_F_MINB;
+#ifndef FWI_H_MINB
+#define FWI_H_MINB 4
+#endif
 // forward with the offset Hessian: 64 x 8 tiles, halo 12
-constexpr int H_RZ = 1, H_ST = FWI_H_ST, H_MINB = 3;
+constexpr int H_RZ = 1, H_ST = FWI_H_ST, H_MINB = FWI_H_MINB;
 // backward: 64 x 16 tiles
-constexpr int B_RZ = 2, B_ST = FWI_B_ST, B_MINB = FWI_B_MINB;
+constexpr int B_RZ = FWI_B_RZ, B_ST = FWI_B_ST, B_MINB = FWI_B_MINB;
 
 #define K_FWD k_fwd_step<F_RZ, RADIUS, false, F_ST, F_MINB>
 #define K_FWDH k_fwd_step<H_RZ, HMAX_LIMIT, true, H_ST, H_MINB>
