@@ -67,7 +67,7 @@ struct Plan {
     bool need_bwd = false;  // adjoint pass (gradient / forward_save)
     bool need_seis_tab = false;
     Tiling tf{}, tb{};
-    Part scal, c2, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab, sched;
+    Part scal, c2, damp, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab, sched;
     size_t tab_src = 0, tab_srcij = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0, tab_bshot = 0;
     Part adj_t; // adjoint source in backward-table order [nt][ns*nrec]
     // snapshot checkpoints (FWI_CKPT_SNAPSHOT): snapshot j holds level j*K
@@ -204,6 +204,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
     const size_t fbytes = (size_t)L.fstride * sizeof(float);
     const size_t nphys = (size_t)L.nz * L.nx;
     take(pl.c2, fbytes);
+    take(pl.damp, fbytes);
     take(pl.u[0], fbytes * pl.ns);
     take(pl.u[1], fbytes * pl.ns);
     if (pl.need_bwd) {
@@ -337,6 +338,7 @@ StepCommon make_common(const Plan &pl, const fwi_geometry *ge, void *ws, const T
     StepCommon c{};
     c.L = pl.L;
     c.c2 = at<float>(ws, pl.c2);
+    c.damp = at<float>(ws, pl.damp);
     c.src_off = at<int>(ws, pl.tab, pl.tab_src);
     c.src_ij = at<int2>(ws, pl.tab, pl.tab_srcij);
     c.wav = ge->wavelet;
@@ -363,7 +365,10 @@ fwi_status setup(const Plan &pl, const fwi_geometry *ge, const float *v, void *w
     fwi_status s = upload_tables(pl, ge, ws, st);
     if (s != FWI_OK) return s;
     if ((e = cudaMemsetAsync(at<char>(ws, pl.c2), 0, pl.c2.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
-    if ((e = launch_prep_c2(pl.L, v, at<float>(ws, pl.c2), CFL_2D, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.damp), 0, pl.damp.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    if ((e = launch_prep_c2(pl.L, v, at<float>(ws, pl.c2), at<float>(ws, pl.damp), CFL_2D, at<int>(ws, pl.scal, 8),
+                            st)) != cudaSuccess)
         return cuda_fail(e, "prep kernel");
     t_launch[2]++;
     for (int b = 0; b < 2; ++b)

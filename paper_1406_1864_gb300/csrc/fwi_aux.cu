@@ -41,8 +41,11 @@ __device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? l
 
 // c2 = (v dt / dx)^2 on the padded grid, the sponge replicating the nearest
 // model cell; checks v > 0, finite, and the stability limit.
+// c2 = (v dt/dx)^2 and the sponge factor 1 / (1 + eta dt) of every padded
+// cell, eta dt = eta_max dt (d_z^2 + d_x^2) / P^2 with d the depth into the
+// sponge (the two parts summed in FP32, then one correctly rounded division)
 __global__ void k_prep_c2(const Lay2D L, const float *__restrict__ v, float *__restrict__ c2,
-                          float cfl_limit, int *status)
+                          float *__restrict__ damp, float cfl_limit, int *status)
 {
     const long long n = (long long)L.nzp * L.nxp;
     int bad = 0;
@@ -55,6 +58,10 @@ __global__ void k_prep_c2(const Lay2D L, const float *__restrict__ v, float *__r
         if (!(vv > 0.f) || !isfinite(vv)) bad |= ST_BAD_VELOCITY;
         else if (r > cfl_limit) bad |= ST_CFL;
         c2[fidx(L, i, j)] = r * r;
+        const int dz = sponge_depth(i, L.P, L.nz), dxs = sponge_depth(j, L.P, L.nx);
+        const float ez = L.etamax_dt * (float)(dz * dz) * L.inv_p2;
+        const float ex = L.etamax_dt * (float)(dxs * dxs) * L.inv_p2;
+        damp[fidx(L, i, j)] = 1.0f / (1.0f + (ez + ex));
     }
     if (bad) atomicOr(status, bad);
 }
@@ -284,10 +291,10 @@ int grid_for(long long n)
 
 } // namespace
 
-cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float cfl_limit,
+cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float *damp, float cfl_limit,
                            int *status, cudaStream_t st)
 {
-    k_prep_c2<<<grid_for((long long)L.nzp * L.nxp), NT1, 0, st>>>(L, v, c2, cfl_limit, status);
+    k_prep_c2<<<grid_for((long long)L.nzp * L.nxp), NT1, 0, st>>>(L, v, c2, damp, cfl_limit, status);
     return cudaGetLastError();
 }
 

@@ -75,6 +75,7 @@ struct RecTable {
 struct StepCommon {
     Lay2D L;
     const float *c2;       // (v dt / dx)^2, field layout
+    const float *damp;     // 1 / (1 + eta dt), field layout (1 in the model)
     const int *src_off;    // [ns] field offset of each source cell
     const int2 *src_ij;    // [ns] padded (row, column) of each source cell
     const float *wav;      // [ns][nt]
@@ -153,7 +154,7 @@ cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, c
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st);
 
 // auxiliary kernels (fwi_aux.cu)
-cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float cfl_limit,
+cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float *damp, float cfl_limit,
                            int *status, cudaStream_t st);
 cudaError_t launch_residual_ols(float *syn, const float *obs, long long n, double *misfit,
                                 cudaStream_t st);

@@ -94,7 +94,12 @@ __device__ __forceinline__ void lap4(float2 (&q)[2], const float *w, const float
         float2 xs[4], zs[4];
 #pragma unroll
         for (int k = 1; k <= 4; ++k) {
-            xs[k - 1] = add2(f2(w[WL + p - k], w[WL + p + 1 - k]), f2(w[WL + p + k], w[WL + p + 1 + k]));
+            // even k: both pairs are aligned register pairs (one FADD2);
+            // odd k: two scalar adds
+            if ((k & 1) == 0)
+                xs[k - 1] = add2(f2(w[WL + p - k], w[WL + p + 1 - k]), f2(w[WL + p + k], w[WL + p + 1 + k]));
+            else
+                xs[k - 1] = f2(w[WL + p - k] + w[WL + p + k], w[WL + p + 1 - k] + w[WL + p + 1 + k]);
             zs[k - 1] = add2(half2of(zc[r + 4 - k], h), half2of(zc[r + 4 + k], h));
         }
         q[h] = lap8x2(f2(w[WL + p], w[WL + p + 1]), xs, zs);
@@ -105,8 +110,9 @@ __device__ __forceinline__ void lap4(float2 (&q)[2], const float *w, const float
 //   u^{n+1} = u^n + ((1 - eta dt)(u^n - u^{n-1}) + c2 q) / (1 + eta dt),
 // algebraically the update of the header; carrying the small increment
 // u^n - u^{n-1} keeps the FP32 rounding at the increment's scale. Written out
-// in the kernels as u + fma(c2 ia, q, ((1 - e) ia)(u - u_prev)), e = eta dt,
-// ia = 1/(1 + e), which is exactly u + fma(c2, q, u - u_prev) where e = 0.
+// in the kernels as u + fma(c2 ia, q, kb (u - u_prev)) with ia = 1/(1 + eta dt)
+// (precomputed per cell) and kb = (1 - eta dt) ia = 2 ia - 1 (exact in FP32
+// for ia in (1/2, 1]); where eta = 0 it is exactly u + fma(c2, q, u - u_prev).
 
 // The reverse step in the model (eta = 0), u^{n-1} = u^n - ((u^{n+1} - u^n)
 // - c2 q^n), is written out on lane pairs in the backward kernel.
@@ -228,7 +234,9 @@ struct Ring {
 template <int STAGES>
 __device__ __forceinline__ bool stage_ready(uint64_t *bars, int k, int *s_abort)
 {
-    if (mbar_wait(smem_u32(&bars[k % STAGES]), (k / STAGES) & 1, WAIT_NS)) return true;
+    const uint32_t bar = smem_u32(&bars[k % STAGES]), parity = (k / STAGES) & 1;
+    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_wait(bar, parity, WAIT_NS)) return true;
     *s_abort = 1;
     return false;
 }
@@ -256,10 +264,10 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 // in order from an atomic counter, so the load is balanced whatever a tile
 // costs, and at any moment all CTAs work on nearby chunks: neighbouring tiles
 // of the same shots, whose halo re-reads then hit L2.
-struct ItemDesc {
+struct alignas(16) ItemDesc {
     int tile, s;   // tile and shot of the item; tile < 0: no more work
     int rb, re;    // receiver-table range of (tile, shot)
-    int si, sj;    // padded cell of the shot's source
+    int si, sj;    // padded cell of the shot's source (8-byte aligned pair)
     float amp;     // source amplitude at this time level
     int pad;
 };
@@ -315,29 +323,47 @@ __device__ __forceinline__ bool cursor_next(Cursor &cu, int *counter, int nchunk
     return true;
 }
 
-// descriptor of item (tile, s) with its per-shot scalars (global loads)
-__device__ __forceinline__ ItemDesc make_desc(const StepCommon &c, const RecTable &rt, int tile, int s,
-                                              int n_src, bool use_src, bool use_rec)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
 {
-    ItemDesc d;
-    d.tile = tile;
-    d.s = s;
-    d.pad = 0;
-    if (tile < 0) {
-        d.rb = d.re = d.si = d.sj = 0;
-        d.amp = 0.f;
-        return d;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage the descriptor of the CTA's next item into a ring slot (lane 0 of
+// warp 1 only): tile and shot from the chunk cursor (shared memory), the
+// per-shot scalars (source cell, amplitude, receiver range) copied from
+// global memory by cp.async, so that no register holds them while the loads
+// are in flight. The copies complete at cp_async_wait_all(), which the
+// staging thread calls before the barrier that publishes the slot. The
+// amplitude is stored unscaled (times src_scale at use).
+__device__ __forceinline__ void stage_desc_async(ItemDesc *slot, Cursor &cu, const StepCommon &c, const RecTable &rt,
+                                                 int nchunks, int ntiles, int n_src, bool use_src, bool use_rec)
+{
+    int t = -1, s = 0;
+    if (!cursor_next(cu, c.sched, nchunks, ntiles, c.chunk, c.ns, t, s)) t = -1;
+    slot->tile = t;
+    slot->s = s;
+    slot->pad = 0;
+    if (t < 0) {
+        slot->rb = slot->re = slot->si = slot->sj = 0;
+        slot->amp = 0.f;
+        return;
     }
-    const int2 ij = c.src_ij[s];
-    d.si = ij.x;
-    d.sj = ij.y;
-    d.amp = use_src ? c.wav[(long long)s * c.nt + n_src] * c.src_scale : 0.f;
-    d.rb = d.re = 0;
+    cp_async8(&slot->si, &c.src_ij[s]);
+    if (use_src)
+        cp_async4(&slot->amp, &c.wav[(long long)s * c.nt + n_src]);
+    else
+        slot->amp = 0.f;
     if (use_rec) {
-        d.rb = rt.ptr[tile * c.ns + s];
-        d.re = rt.ptr[tile * c.ns + s + 1];
+        cp_async4(&slot->rb, &rt.ptr[t * c.ns + s]);
+        cp_async4(&slot->re, &rt.ptr[t * c.ns + s + 1]);
+    } else {
+        slot->rb = slot->re = 0;
     }
-    return d;
 }
 
 // After a timeout (seen by the whole CTA after a barrier): record it and wait,
@@ -352,26 +378,14 @@ __device__ void abort_drain_ring(uint64_t *bars, const ItemDesc *desc, int k, in
         if (desc[j % DESC_RING].tile >= 0) mbar_wait(smem_u32(&bars[j % STAGES]), (j / STAGES) & 1, DRAIN_NS);
 }
 
-// Damping of the thread's rows / columns (eta dt is separable: rows + columns)
-// and where its float4 of each row sits in the per-step sponge checkpoint:
-// >= 0: checkpoint index of the 4 points (contiguous, 16-byte aligned);
-// -1: no sponge point; -2: mixed row (scalar path).
+// Where the thread's float4 of each row sits in the per-step sponge
+// checkpoint: >= 0: checkpoint index of the 4 points (contiguous, 16-byte
+// aligned); -1: no sponge point; -2: mixed row (scalar path).
 template <int RZ>
 struct SpongeInfo {
-    float ez[RZ], ex[4];
     int brow[RZ];
     __device__ void init(const Lay2D &L, int i0, int j0)
     {
-#pragma unroll
-        for (int r = 0; r < RZ; ++r) {
-            const int d = sponge_depth(i0 + r, L.P, L.nz);
-            ez[r] = L.etamax_dt * (float)(d * d) * L.inv_p2;
-        }
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int d = sponge_depth(j0 + p, L.P, L.nx);
-            ex[p] = L.etamax_dt * (float)(d * d) * L.inv_p2;
-        }
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
             const int i = i0 + r;
@@ -408,7 +422,8 @@ __device__ __forceinline__ int source_slot(const ItemDesc &v, int i0, int j0)
     return (dr >= 0 && dr < RZ && dc >= 0 && dc < 4) ? dr * 4 + dc : -1;
 }
 
-// load the c2 tile (TZ x TX, model + sponge cells; 0 outside) into shared memory
+// load a TZ x TX tile of a field-layout coefficient array (c2, damping) into
+// shared memory (0 below the padded grid)
 template <int TZ>
 __device__ __forceinline__ void load_c2_tile(float *dst, const float *c2, const Lay2D &L, int bi, int bj)
 {
@@ -423,7 +438,7 @@ __device__ __forceinline__ void load_c2_tile(float *dst, const float *c2, const 
 
 // ------------------------------------------------------------ forward step
 template <int RZ, int HX, bool WITH_H, int STAGES>
-using FwdRing = Ring<8 * RZ, HX, 1, 1, STAGES, 8 * RZ * TX * 4>;
+using FwdRing = Ring<8 * RZ, HX, 1, 1, STAGES, 2 * 8 * RZ * TX * 4>; // + c2 and damping tiles
 
 template <int RZ, int HX, bool WITH_H, int STAGES, int MINB>
 __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ FwdArgs a)
@@ -447,6 +462,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     unsigned char *smem = align_smem(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *c2s = reinterpret_cast<float *>(R::extra(smem));
+    float *dms = c2s + 8 * RZ * TX; // damping tile (sponge tiles)
 
     const StepCommon &c = a.c;
     const Lay2D &L = c.L;
@@ -463,14 +479,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     }
     __syncthreads();
 
-    // thread 0 walks the chunks, stages descriptors D items ahead and loads
-    // the per-shot scalars of the item after that one iteration early
-    Cursor cu;
-    ItemDesc pend;
-    auto next_desc = [&]() {
-        int t = -1, sh = 0;
-        if (!cursor_next(cu, c.sched, nchunks, ntiles, c.chunk, c.ns, t, sh)) t = -1;
-        return make_desc(c, a.rt, t, sh, a.n, !a.last, use_rec);
+    // lane 0 of warp 1 walks the chunks (cursor in shared memory) and stages
+    // descriptors D + 1 items ahead
+    __shared__ Cursor s_cu;
+    auto stage = [&](int slot) {
+        stage_desc_async(&s_desc[slot % DESC_RING], s_cu, c, a.rt, nchunks, ntiles, a.n, !a.last, use_rec);
     };
     auto issue = [&](const ItemDesc &d, int k) {
         const int bz = d.tile / c.ntx, bx = d.tile - bz * c.ntx;
@@ -484,9 +497,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     // lane 0 of warp 1 walks the chunks and stages descriptors; thread 0
     // issues the copies of a descriptor staged one barrier earlier
     if (threadIdx.x == 32) {
-        cursor_init(cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
-        for (int k = 0; k <= D; ++k) s_desc[k] = next_desc();
-        pend = next_desc();
+        cursor_init(s_cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
+        for (int k = 0; k <= D; ++k) stage(k);
+        cp_async_wait_all();
     }
     __syncthreads();
     if (threadIdx.x == 0)
@@ -536,11 +549,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
             const ItemDesc d = s_desc[(k + D) % DESC_RING];
             if (d.tile >= 0) issue(d, k + D);
         } else if (threadIdx.x == 32) {
-            s_desc[(k + D + 1) % DESC_RING] = pend;
-            pend = next_desc();
+            stage(k + D + 1);
         }
         const ItemDesc now = s_desc[k % DESC_RING];
-        if (now.tile < 0) break;
+        if (now.tile < 0) {
+            if (threadIdx.x == 32) cp_async_wait_all(); // (none in flight once the cursor is done)
+            break;
+        }
         const ItemDesc nx = s_desc[(k + 1) % DESC_RING];
         const int s = now.s;
         const int2 now_en = rec_en;
@@ -563,6 +578,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
 #pragma unroll
             for (int h = 0; h < NH; ++h) acc_h[h][0] = acc_h[h][1] = make_float2(0.f, 0.f);
             load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
+            if (tile_sponge) load_c2_tile<TZ>(dms, c.damp, L, bi, bj);
             __syncthreads();
         }
         const int st = k % STAGES;
@@ -601,10 +617,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                 if (!a.last) {
                     float2 q[2];
                     lap4<WL>(q, w, zc, r);
-                    if (sslot == r * 4 + 0) q[0].x += now.amp;
-                    if (sslot == r * 4 + 1) q[0].y += now.amp;
-                    if (sslot == r * 4 + 2) q[1].x += now.amp;
-                    if (sslot == r * 4 + 3) q[1].y += now.amp;
+                    const float amp = now.amp * c.src_scale;
+                    if (sslot == r * 4 + 0) q[0].x += amp;
+                    if (sslot == r * 4 + 1) q[0].y += amp;
+                    if (sslot == r * 4 + 2) q[1].x += amp;
+                    if (sslot == r * 4 + 3) q[1].y += amp;
                     const float4 um4 = lds4(&pm[(ty * RZ + r) * TX + 4 * tx]);
                     const float4 c24 = lds4(&c2s[(ty * RZ + r) * TX + 4 * tx]);
                     float2 out[2];
@@ -617,11 +634,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                     } else {
                         // damped update; identical to the plain one where eta = 0
                         const int i = i0 + r;
+                        const float4 ia4 = lds4(&dms[(ty * RZ + r) * TX + 4 * tx]);
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            const float2 e2 = add2(make_float2(sg.ez[r], sg.ez[r]), f2(sg.ex[2 * h], sg.ex[2 * h + 1]));
-                            const float2 ia2 = f2(__frcp_rn(1.0f + e2.x), __frcp_rn(1.0f + e2.y));
-                            const float2 kb = mul2(sub2(make_float2(1.f, 1.f), e2), ia2);
+                            const float2 ia2 = half2of(ia4, h);
+                            const float2 kb = fma2(ia2, make_float2(2.f, 2.f), make_float2(-1.f, -1.f));
                             out[h] = add2(u0[h], fma2(mul2(half2of(c24, h), ia2), q[h],
                                                       mul2(kb, sub2(u0[h], half2of(um4, h)))));
                         }
@@ -671,6 +688,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                 }
             }
         }
+        if (threadIdx.x == 32) cp_async_wait_all(); // the slot staged in this iteration
         __syncthreads();
         if (s_abort) {
             abort_drain_ring<STAGES>(bars, s_desc, k, c.status);
@@ -682,7 +700,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
 
 // ----------------------------------------------------------- backward step
 template <int RZ, int STAGES>
-using BwdRing = Ring<8 * RZ, RADIUS, 2, 2, STAGES, 2 * 8 * RZ * TX * 4>;
+using BwdRing = Ring<8 * RZ, RADIUS, 2, 2, STAGES, 3 * 8 * RZ * TX * 4>; // + c2, injection, damping tiles
 
 template <int RZ, int STAGES, int MINB>
 __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ BwdArgs a)
@@ -704,6 +722,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *c2s = reinterpret_cast<float *>(R::extra(smem));
     float *sinj = c2s + TZ * TX;
+    float *dms = sinj + TZ * TX; // damping tile (sponge tiles)
 
     const StepCommon &c = a.c;
     const Lay2D &L = c.L;
@@ -723,12 +742,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     for (int e = threadIdx.x; e < TZ * TX; e += TPB) sinj[e] = 0.f;
     __syncthreads();
 
-    Cursor cu;
-    ItemDesc pend;
-    auto next_desc = [&]() {
-        int t = -1, sh = 0;
-        if (!cursor_next(cu, c.sched, nchunks, ntiles, c.chunk, c.ns, t, sh)) t = -1;
-        return make_desc(c, a.rt, t, sh, m - 1, true, use_rec);
+    __shared__ Cursor s_cu;
+    auto stage = [&](int slot) {
+        stage_desc_async(&s_desc[slot % DESC_RING], s_cu, c, a.rt, nchunks, ntiles, m - 1, true, use_rec);
     };
     auto issue = [&](const ItemDesc &d, int k) {
         const int bz = d.tile / c.ntx, bx = d.tile - bz * c.ntx;
@@ -746,9 +762,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     // lane 0 of warp 1 walks the chunks and stages descriptors; thread 0
     // issues the copies of a descriptor staged one barrier earlier
     if (threadIdx.x == 32) {
-        cursor_init(cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
-        for (int k = 0; k <= D; ++k) s_desc[k] = next_desc();
-        pend = next_desc();
+        cursor_init(s_cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
+        for (int k = 0; k <= D; ++k) stage(k);
+        cp_async_wait_all();
     }
     __syncthreads();
     if (threadIdx.x == 0)
@@ -817,11 +833,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             const ItemDesc d = s_desc[(k + D) % DESC_RING];
             if (d.tile >= 0) issue(d, k + D);
         } else if (threadIdx.x == 32) {
-            s_desc[(k + D + 1) % DESC_RING] = pend;
-            pend = next_desc();
+            stage(k + D + 1);
         }
         const ItemDesc now = s_desc[k % DESC_RING];
-        if (now.tile < 0) break;
+        if (now.tile < 0) {
+            if (threadIdx.x == 32) cp_async_wait_all(); // (none in flight once the cursor is done)
+            break;
+        }
         const ItemDesc nx = s_desc[(k + 1) % DESC_RING];
         const int s = now.s;
         if (now.tile != cur_tile) {
@@ -838,6 +856,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 #pragma unroll
             for (int r = 0; r < RZ; ++r) acc_g[r][0] = acc_g[r][1] = make_float2(0.f, 0.f);
             load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
+            if (tile_sponge) load_c2_tile<TZ>(dms, c.damp, L, bi, bj);
             bval_ok = false;
             __syncthreads();
         }
@@ -892,10 +911,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             }
 #pragma unroll
             for (int r = 0; r < RZ; ++r) {
-                if (sslot == r * 4 + 0) qu[r][0].x += now.amp;
-                if (sslot == r * 4 + 1) qu[r][0].y += now.amp;
-                if (sslot == r * 4 + 2) qu[r][1].x += now.amp;
-                if (sslot == r * 4 + 3) qu[r][1].y += now.amp;
+                const float amp = now.amp * c.src_scale;
+                if (sslot == r * 4 + 0) qu[r][0].x += amp;
+                if (sslot == r * 4 + 1) qu[r][0].y += amp;
+                if (sslot == r * 4 + 2) qu[r][1].x += amp;
+                if (sslot == r * 4 + 3) qu[r][1].y += amp;
                 if (has_rec) {
                     const float4 inj = lds4(&sinj[(ty * RZ + r) * TX + 4 * tx]);
                     qp[r][0] = add2(qp[r][0], lo2(inj));
@@ -928,13 +948,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                     // damped adjoint update (identical to the plain one where
                     // eta = 0); sponge values of u^{m-2} from the checkpoint
                     const int i = i0 + r;
+                    const float4 ia4 = lds4(&dms[(ty * RZ + r) * TX + 4 * tx]);
                     float2 pn[2], un[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const float2 e2 = add2(make_float2(sg.ez[r], sg.ez[r]), f2(sg.ex[2 * h], sg.ex[2 * h + 1]));
-                        const float2 ia2 = f2(__frcp_rn(1.0f + e2.x), __frcp_rn(1.0f + e2.y));
+                        const float2 ia2 = half2of(ia4, h);
                         const float2 c2v = half2of(c24, h);
-                        const float2 kb = mul2(sub2(make_float2(1.f, 1.f), e2), ia2);
+                        const float2 kb = fma2(ia2, make_float2(2.f, 2.f), make_float2(-1.f, -1.f));
                         pn[h] = add2(p1[h], fma2(mul2(c2v, ia2), qp[r][h], mul2(kb, sub2(p1[h], half2of(pb4, h)))));
                         acc_g[r][h] = fma2(pn[h], qu[r][h], acc_g[r][h]);
                         un[h] = sub2(u1[h], fma2(make_float2(-c2v.x, -c2v.y), qu[r][h], sub2(half2of(ua4, h), u1[h])));
@@ -955,6 +975,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                 }
             }
         }
+        if (threadIdx.x == 32) cp_async_wait_all(); // the slot staged in this iteration
         __syncthreads();
         if (s_abort) {
             abort_drain_ring<STAGES>(bars, s_desc, k, c.status);
