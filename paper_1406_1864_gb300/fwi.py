@@ -66,6 +66,10 @@ class Geometry:
         return L.FwiGeometry(self.nshots, self.nrec, self.src.ctypes.data, self.rec.ctypes.data,
                              self.wavelet.data_ptr())
 
+    def subset(self, s0: int, s1: int) -> "Geometry":
+        """Shots [s0, s1) (the wavelet rows are a view of this geometry's)."""
+        return Geometry(self.src[s0:s1], self.rec[s0:s1], self.wavelet[s0:s1])
+
 
 @dataclass
 class Options:

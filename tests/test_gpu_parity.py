@@ -246,3 +246,20 @@ def test_precondition_entry_point(torch_cuda):
                            "offset", 1e-2).cpu().numpy()
     Po = np.abs(H[0]) + 2 * np.abs(H[1:]).sum(0)
     assert rel(out, g / (Po + 1e-2 * Po.max())) <= 1e-6
+
+
+def test_sharded_gradient_one_rank(torch_cuda):
+    """distributed.sharded_gradient with one rank (library compute, then the
+    precondition entry point) equals one fwi_adjoint_gradient call."""
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import distributed as D
+    p = ragged_problem(nt=200)
+    fwi, grid, geom, v = gpu_inputs(torch, p)
+    d_obs = fwi.forward(grid, geom, torch.as_tensor(np.ascontiguousarray(p.v_true), device="cuda"))
+    for precond, hmax in (("illum", -1), ("offset", 4)):
+        opts = fwi.Options(hmax=hmax, precond=precond)
+        ref = fwi.adjoint_gradient(grid, geom, v, d_obs, opts)
+        got = D.sharded_gradient(grid, geom, v, d_obs, opts, rank=0, world=1)
+        for k in ("grad", "illum", "grad_pre") + (("offh",) if hmax >= 0 else ()):
+            assert rel(got[k].cpu().numpy(), ref[k].cpu().numpy()) <= 1e-6, (precond, k)
+        assert abs(float(got["misfit"]) - float(ref["misfit"])) <= 1e-12 * float(ref["misfit"])
