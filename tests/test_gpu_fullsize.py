@@ -101,8 +101,11 @@ def test_c2_sum_over_shot_subsets(torch_cuda, c2):
         sub = fwi.adjoint_gradient(grid, geom.subset(s0, s0 + 32), v, d_obs[s0:s0 + 32].contiguous(), opts, ws=ws)
         for k in acc:
             acc[k] += sub[k]
-    assert rel(acc["grad"].cpu(), full["grad"].cpu()) <= 1e-5
-    assert rel(acc["illum"].cpu(), full["illum"].cpu()) <= 1e-6
+    # each cell's sums are FP32 atomic additions of ~5e4 partial sums (4000
+    # launches x 12 shot chunks), added in another order by the subsets:
+    # rounding of order sqrt(5e4) * 6e-8 ~ 1e-5; the stated bound is 1e-4
+    assert rel(acc["grad"].cpu(), full["grad"].cpu()) <= 1e-4
+    assert rel(acc["illum"].cpu(), full["illum"].cpu()) <= 1e-4
     assert abs(float(acc["misfit"]) - float(full["misfit"])) <= 1e-9 * float(full["misfit"])
 
 
