@@ -178,6 +178,26 @@ fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom,
                                 float *grad, float *grad_pre, double *misfit, float *illum,
                                 float *offh, void *ws, size_t ws_bytes, void *stream);
 
+/* Preconditioned gradients of nmodels independent models of different sizes,
+   computed together [Sec. 2, Eq. 1-2, Sec. 3, each model as in
+   fwi_adjoint_gradient]: every time level of all models is one launch of the
+   forward step and one of the backward step, whose CTAs take (model, tile,
+   shots) chunks from one counter, so small models fill the GPU next to large
+   ones. 1 <= nmodels <= FWI_BATCH_MAX. grids, geoms: HOST arrays [nmodels];
+   every grid has the same nt (dx, dt, sponge and sizes may differ); opts is
+   shared and needs ckpt = FWI_CKPT_SPONGE when nmodels > 1.
+   v, d_obs, grad: HOST arrays [nmodels] of DEVICE pointers (model k's arrays
+   as in fwi_adjoint_gradient); grad_pre, illum, offh: the same or NULL (and
+   entries may be NULL); misfit: DEVICE double [nmodels] or NULL.
+   Workspace: fwi_batch_workspace_bytes(). Errors name the model. */
+#define FWI_BATCH_MAX 4
+fwi_status fwi_batch_workspace_bytes(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms,
+                                     const fwi_options *opts, size_t *bytes);
+fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms,
+                              const fwi_options *opts, const float *const *v, const float *const *d_obs,
+                              float *const *grad, float *const *grad_pre, double *misfit, float *const *illum,
+                              float *const *offh, void *ws, size_t ws_bytes, void *stream);
+
 /* Shot illumination, the pseudo-diagonal Hessian of Eq. 1:
    illum DEVICE [nz][nx] = sum_s sum_n u_s^n(x)^2 dt (FWI_ILLUM_U2) or
    sum_s sum_n (u_tt)_s^n(x)^2 dt (FWI_ILLUM_UTT2), from a forward modelling. */

@@ -26,6 +26,7 @@ FWI_SNAP_F32, FWI_SNAP_BF16, FWI_SNAP_F16S = 0, 1, 2
 (FWI_OP_FORWARD, FWI_OP_FORWARD_SAVE, FWI_OP_GRADIENT, FWI_OP_ILLUMINATION,
  FWI_OP_OFFSET_HESSIAN, FWI_OP_PRECONDITION) = range(6)
 FWI_HMAX_LIMIT = 12
+FWI_BATCH_MAX = 4
 
 
 class FwiGrid(ctypes.Structure):
@@ -67,6 +68,10 @@ _SIGS = {
     "fwi_precondition": [P(FwiGrid), c_void_p, c_void_p, c_int, c_int, c_float, c_void_p, c_void_p,
                          c_size_t, c_void_p],
     "fwi_forward_noalloc": [P(FwiGrid), P(FwiGeometry), c_void_p, c_void_p, c_void_p],
+    "fwi_batch_workspace_bytes": [c_int, P(FwiGrid), P(FwiGeometry), P(FwiOptions), P(c_size_t)],
+    "fwi_batch_gradient": [c_int, P(FwiGrid), P(FwiGeometry), P(FwiOptions), P(c_void_p), P(c_void_p),
+                           P(c_void_p), P(c_void_p), c_void_p, P(c_void_p), P(c_void_p), c_void_p,
+                           c_size_t, c_void_p],
     "fwi_profile_enable": [c_int],
     "fwi_profile_last": [P(FwiPhaseTimes)],
 }

@@ -14,6 +14,7 @@
 #include "fwi_internal.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -419,53 +420,81 @@ fwi_status restore_snapshot(const Plan &pl, void *ws, int j, float *u, float *up
     return FWI_OK;
 }
 
-// forward time loop n = 0..nt-1
+// forward time loop n = 0..nt-1 of nm models at once (nm = 1: one model;
+// nm > 1: one batched launch per time level, sponge checkpoints only). Model
+// k's plan, geometry, workspace and outputs are pl[k], ge[k], ws[k], seis[k],
+// acc_i[k], acc_h[k] (outputs may be null).
+fwi_status run_forward_models(int nm, const Plan *pl, const fwi_geometry *const *ge, void *const *ws,
+                              float *const *seis, bool save, float *const *acc_i, float *const *acc_h, int illum_utt,
+                              cudaStream_t st)
+{
+    cudaError_t e;
+    std::vector<FwdArgs> a(nm);
+    std::vector<Tiling> til(nm);
+    std::vector<std::array<float *, 2>> U(nm);
+    std::vector<std::array<CUtensorMap, 2>> mh(nm), mp(nm);
+    const bool offh = pl[0].with_offh && acc_h[0];
+    int hx, hy, px, py;
+    step_boxes(offh ? STEP_FWD_OFFH : STEP_FWD, hx, hy, px, py);
+    for (int k = 0; k < nm; ++k) {
+        const Plan &p = pl[k];
+        void *w = ws[k];
+        if (acc_i[k] && (e = cudaMemsetAsync(acc_i[k], 0, p.acc_i.bytes, st)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+        if (acc_h[k] && (e = cudaMemsetAsync(acc_h[k], 0, p.acc_h.bytes, st)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+        a[k] = FwdArgs{};
+        a[k].c = make_common(p, ge[k], w, p.tf);
+        a[k].c.status = at<int>(ws[0], pl[0].scal, 8); // one status word per launch
+        a[k].band = (save && !p.snap) ? at<float>(w, p.band) : nullptr;
+        a[k].seis = (seis[k] && p.nrec > 0) ? seis[k] : nullptr;
+        a[k].acc_illum = acc_i[k];
+        a[k].acc_offh = acc_h[k];
+        a[k].rt.ptr = at<int>(w, p.tab, p.tab_fptr);
+        a[k].rt.ent = at<int2>(w, p.tab, p.tab_fent);
+        a[k].illum_utt = illum_utt;
+        a[k].hmax = p.hmax;
+        til[k] = p.tf;
+        U[k] = {at<float>(w, p.u[0]), at<float>(w, p.u[1])};
+        for (int b = 0; b < 2; ++b)
+            if (!encode_field_map(&mh[k][b], U[k][b], p.L, p.ns, hx, hy) ||
+                !encode_field_map(&mp[k][b], U[k][b], p.L, p.ns, px, py))
+                return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
+    }
+    const bool capture = nm == 1 && save && pl[0].snap;
+    const int nt = pl[0].nt;
+    for (int n = 0; n < nt; ++n) {
+        if (capture && n % pl[0].K == 0 && n <= nt - 2) {
+            // snapshot n / K of the state (u^n, u^{n-1}) before step n
+            fwi_status sc = capture_snapshot(pl[0], ws[0], n / pl[0].K, U[0][n & 1], U[0][(n + 1) & 1], st);
+            if (sc != FWI_OK) return sc;
+        }
+        for (int k = 0; k < nm; ++k) {
+            a[k].n = n;
+            a[k].last = (n == nt - 1);
+            a[k].tm_cur = mh[k][n & 1];
+            a[k].tm_prev = mp[k][(n + 1) & 1];
+            a[k].c.sched = at<int>(ws[0], pl[0].sched) + n;
+            a[k].uout = U[k][(n + 1) & 1];
+        }
+        e = nm == 1 ? launch_fwd_step(a[0], til[0], offh, st) : launch_fwd_batch(a.data(), til.data(), nm, offh, st);
+        if (e != cudaSuccess) return cuda_fail(e, "forward step");
+        t_launch[0]++;
+    }
+    for (int k = 0; k < nm; ++k)
+        for (int b = 0; b < 2; ++b) {
+            if ((e = launch_check_finite(U[k][b], (long long)pl[k].ns * pl[k].L.fstride, at<int>(ws[k], pl[k].scal, 8),
+                                         st)) != cudaSuccess)
+                return cuda_fail(e, "finite check");
+            t_launch[2]++;
+        }
+    return FWI_OK;
+}
+
 fwi_status run_forward(const Plan &pl, const fwi_geometry *ge, void *ws, float *seis, bool save,
                        float *acc_i, float *acc_h, int illum_utt, cudaStream_t st)
 {
-    cudaError_t e;
-    if (acc_i && (e = cudaMemsetAsync(acc_i, 0, pl.acc_i.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
-    if (acc_h && (e = cudaMemsetAsync(acc_h, 0, pl.acc_h.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
-    FwdArgs a{};
-    a.c = make_common(pl, ge, ws, pl.tf);
-    a.band = (save && !pl.snap) ? at<float>(ws, pl.band) : nullptr;
-    const bool capture = save && pl.snap;
-    a.seis = (seis && pl.nrec > 0) ? seis : nullptr;
-    a.acc_illum = acc_i;
-    a.acc_offh = acc_h;
-    a.rt.ptr = at<int>(ws, pl.tab, pl.tab_fptr);
-    a.rt.ent = at<int2>(ws, pl.tab, pl.tab_fent);
-    a.illum_utt = illum_utt;
-    a.hmax = pl.hmax;
-    float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
-    const bool offh = pl.with_offh && acc_h;
-    int hx, hy, px, py;
-    step_boxes(offh ? STEP_FWD_OFFH : STEP_FWD, hx, hy, px, py);
-    CUtensorMap mh[2], mp[2];
-    for (int b = 0; b < 2; ++b)
-        if (!encode_field_map(&mh[b], U[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&mp[b], U[b], pl.L, pl.ns, px, py))
-            return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
-    for (int n = 0; n < pl.nt; ++n) {
-        if (capture && n % pl.K == 0 && n <= pl.nt - 2) {
-            // snapshot n / K of the state (u^n, u^{n-1}) before step n
-            fwi_status sc = capture_snapshot(pl, ws, n / pl.K, U[n & 1], U[(n + 1) & 1], st);
-            if (sc != FWI_OK) return sc;
-        }
-        a.n = n;
-        a.last = (n == pl.nt - 1);
-        a.tm_cur = mh[n & 1];
-        a.tm_prev = mp[(n + 1) & 1];
-        a.c.sched = at<int>(ws, pl.sched) + n;
-        a.uout = U[(n + 1) & 1];
-        if ((e = launch_fwd_step(a, pl.tf, offh, st)) != cudaSuccess)
-            return cuda_fail(e, "forward step");
-        t_launch[0]++;
-    }
-    for (int b = 0; b < 2; ++b)
-        if ((e = launch_check_finite(U[b], (long long)pl.ns * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
-            return cuda_fail(e, "finite check");
-    t_launch[2] += 2;
-    return FWI_OK;
+    return run_forward_models(1, &pl, &ge, &ws, &seis, save, &acc_i, &acc_h, illum_utt, st);
 }
 
 // Backward loop with snapshot checkpoints. For segment j = nck-1..0 (levels
@@ -535,69 +564,104 @@ fwi_status run_backward_segments(const Plan &pl, const fwi_geometry *ge, void *w
     return FWI_OK;
 }
 
-// backward time loop m = nt-1..1, adjoint source adj [ns][nt][nrec]
-fwi_status run_backward(const Plan &pl, const fwi_geometry *ge, void *ws, const float *adj,
-                        cudaStream_t st)
+// backward time loop m = nt-1..1 of nm models at once (nm > 1: one batched
+// launch per time level, sponge checkpoints only), adjoint source adj[k]
+// [ns][nt][nrec] of model k
+fwi_status run_backward_models(int nm, const Plan *pl, const fwi_geometry *const *ge, void *const *ws,
+                               const float *const *adj, cudaStream_t st)
 {
     cudaError_t e;
-    for (int b = 0; b < 2; ++b)
-        if ((e = cudaMemsetAsync(at<char>(ws, pl.p[b]), 0, pl.p[b].bytes, st)) != cudaSuccess)
-            return cuda_fail(e, "memset");
-    if ((e = cudaMemsetAsync(at<char>(ws, pl.acc_g), 0, pl.acc_g.bytes, st)) != cudaSuccess)
-        return cuda_fail(e, "memset");
-    BwdArgs a{};
-    a.c = make_common(pl, ge, ws, pl.tb);
-    a.band = at<float>(ws, pl.band);
-    a.adj = nullptr;
-    if (pl.nrec > 0) {
-        // adjoint source in the order of the backward receiver table: each
-        // (tile, shot) reads one contiguous run per time level
-        if ((e = launch_permute_adj(adj, at<int2>(ws, pl.tab, pl.tab_bent), at<int>(ws, pl.tab, pl.tab_bshot),
-                                    pl.ns * pl.nrec, pl.nt, pl.nrec, at<float>(ws, pl.adj_t), st)) != cudaSuccess)
-            return cuda_fail(e, "adjoint-source permutation");
-        t_launch[2]++;
-        a.adj = at<float>(ws, pl.adj_t);
-    }
-    a.nent = pl.ns * pl.nrec;
-    a.acc_grad = at<float>(ws, pl.acc_g);
-    a.rt.ptr = at<int>(ws, pl.tab, pl.tab_bptr);
-    a.rt.ent = at<int2>(ws, pl.tab, pl.tab_bent);
-    a.adj_scale = pl.L.dx * pl.L.dx;
-    a.recon = pl.snap ? 0 : 1;
-    float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
-    float *Pp[2] = {at<float>(ws, pl.p[0]), at<float>(ws, pl.p[1])};
+    std::vector<BwdArgs> a(nm);
+    std::vector<Tiling> til(nm);
+    std::vector<std::array<float *, 2>> U(nm), Pp(nm);
+    std::vector<std::array<CUtensorMap, 2>> uh(nm), up(nm), ph(nm), pp(nm);
     int hx, hy, px, py;
     step_boxes(STEP_BWD, hx, hy, px, py);
-    CUtensorMap uh[2], up[2], ph[2], pp[2];
-    for (int b = 0; b < 2; ++b)
-        if (!encode_field_map(&uh[b], U[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&up[b], U[b], pl.L, pl.ns, px, py) ||
-            !encode_field_map(&ph[b], Pp[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&pp[b], Pp[b], pl.L, pl.ns, px, py))
-            return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
-    if (pl.snap) return run_backward_segments(pl, ge, ws, a, U, Pp, ph, pp, st);
-    for (int m = pl.nt - 1; m >= 1; --m) {
-        a.m = m;
-        a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
-        a.tm_ub = uh[(m - 1) & 1];
-        a.tm_pa = ph[(m + 1) & 1];
-        a.tm_ua = up[m & 1];
-        a.tm_pb = pp[m & 1];
-        a.ua = U[m & 1];
-        a.pb = Pp[m & 1];
-        if ((e = launch_bwd_step(a, pl.tb, st)) != cudaSuccess) return cuda_fail(e, "backward step");
+    for (int k = 0; k < nm; ++k) {
+        const Plan &p = pl[k];
+        void *w = ws[k];
+        for (int b = 0; b < 2; ++b)
+            if ((e = cudaMemsetAsync(at<char>(w, p.p[b]), 0, p.p[b].bytes, st)) != cudaSuccess)
+                return cuda_fail(e, "memset");
+        if ((e = cudaMemsetAsync(at<char>(w, p.acc_g), 0, p.acc_g.bytes, st)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+        a[k] = BwdArgs{};
+        a[k].c = make_common(p, ge[k], w, p.tb);
+        a[k].c.status = at<int>(ws[0], pl[0].scal, 8); // one status word per launch
+        a[k].band = p.snap ? nullptr : at<float>(w, p.band);
+        a[k].adj = nullptr;
+        if (p.nrec > 0) {
+            // adjoint source in the order of the backward receiver table: each
+            // (tile, shot) reads one contiguous run per time level
+            if ((e = launch_permute_adj(adj[k], at<int2>(w, p.tab, p.tab_bent), at<int>(w, p.tab, p.tab_bshot),
+                                        p.ns * p.nrec, p.nt, p.nrec, at<float>(w, p.adj_t), st)) != cudaSuccess)
+                return cuda_fail(e, "adjoint-source permutation");
+            t_launch[2]++;
+            a[k].adj = at<float>(w, p.adj_t);
+        }
+        a[k].nent = p.ns * p.nrec;
+        a[k].acc_grad = at<float>(w, p.acc_g);
+        a[k].rt.ptr = at<int>(w, p.tab, p.tab_bptr);
+        a[k].rt.ent = at<int2>(w, p.tab, p.tab_bent);
+        a[k].adj_scale = p.L.dx * p.L.dx;
+        a[k].recon = p.snap ? 0 : 1;
+        til[k] = p.tb;
+        U[k] = {at<float>(w, p.u[0]), at<float>(w, p.u[1])};
+        Pp[k] = {at<float>(w, p.p[0]), at<float>(w, p.p[1])};
+        for (int b = 0; b < 2; ++b)
+            if (!encode_field_map(&uh[k][b], U[k][b], p.L, p.ns, hx, hy) ||
+                !encode_field_map(&up[k][b], U[k][b], p.L, p.ns, px, py) ||
+                !encode_field_map(&ph[k][b], Pp[k][b], p.L, p.ns, hx, hy) ||
+                !encode_field_map(&pp[k][b], Pp[k][b], p.L, p.ns, px, py))
+                return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
+    }
+    if (nm == 1 && pl[0].snap) {
+        float *U0[2] = {U[0][0], U[0][1]}, *P0[2] = {Pp[0][0], Pp[0][1]};
+        CUtensorMap ph0[2] = {ph[0][0], ph[0][1]}, pp0[2] = {pp[0][0], pp[0][1]};
+        return run_backward_segments(pl[0], ge[0], ws[0], a[0], U0, P0, ph0, pp0, st);
+    }
+    const int nt = pl[0].nt;
+    for (int m = nt - 1; m >= 1; --m) {
+        for (int k = 0; k < nm; ++k) {
+            a[k].m = m;
+            a[k].c.sched = at<int>(ws[0], pl[0].sched) + nt + m;
+            a[k].tm_ub = uh[k][(m - 1) & 1];
+            a[k].tm_pa = ph[k][(m + 1) & 1];
+            a[k].tm_ua = up[k][m & 1];
+            a[k].tm_pb = pp[k][m & 1];
+            a[k].ua = U[k][m & 1];
+            a[k].pb = Pp[k][m & 1];
+        }
+        e = nm == 1 ? launch_bwd_step(a[0], til[0], st) : launch_bwd_batch(a.data(), til.data(), nm, st);
+        if (e != cudaSuccess) return cuda_fail(e, "backward step");
         t_launch[1]++;
     }
-    if ((e = launch_check_finite(Pp[0], (long long)pl.ns * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
-        return cuda_fail(e, "finite check");
-    t_launch[2]++;
+    for (int k = 0; k < nm; ++k) {
+        if ((e = launch_check_finite(Pp[k][0], (long long)pl[k].ns * pl[k].L.fstride, at<int>(ws[k], pl[k].scal, 8),
+                                     st)) != cudaSuccess)
+            return cuda_fail(e, "finite check");
+        t_launch[2]++;
+    }
     return FWI_OK;
 }
 
-fwi_status finish(const Plan &pl, void *ws, cudaStream_t st)
+fwi_status run_backward(const Plan &pl, const fwi_geometry *ge, void *ws, const float *adj, cudaStream_t st)
 {
-    int status = 0;
-    cudaError_t e = cudaMemcpyAsync(&status, at<int>(ws, pl.scal, 8), sizeof(int), cudaMemcpyDeviceToHost, st);
+    return run_backward_models(1, &pl, &ge, &ws, &adj, st);
+}
+
+// end of a call: read the status words of the call's models (one stream
+// synchronisation), then the profile events
+fwi_status finish_models(int nm, const Plan *pl, void *const *ws, cudaStream_t st)
+{
+    std::vector<int> status(nm, 0);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < nm && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(&status[k], at<int>(ws[k], pl[k].scal, 8), sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "status read-back");
+    int any = 0;
+    for (int k = 0; k < nm; ++k) any |= status[k];
     if (t_ev_recorded && t_prof) {
         float ms[3] = {0, 0, 0}, tot = 0;
         cudaEventElapsedTime(&ms[0], t_ev[0], t_ev[1]);
@@ -610,19 +674,136 @@ fwi_status finish(const Plan &pl, void *ws, cudaStream_t st)
         t_times.adjoint_launches = t_launch[1];
         t_times.other_launches = t_launch[2];
     }
-    if (status & ST_BAD_VELOCITY) return fail(FWI_ERR_INVALID_ARG, "velocity not finite and positive");
-    if (status & ST_CFL) return fail(FWI_ERR_CFL, "v dt/dx above the stability limit %g", CFL_2D);
-    if (status & ST_TIMEOUT) return fail(FWI_ERR_TIMEOUT, "a device wait timed out");
-    if (status & ST_NONFINITE) return fail(FWI_ERR_UNSTABLE, "non-finite wavefield");
+    if (any & ST_BAD_VELOCITY) return fail(FWI_ERR_INVALID_ARG, "velocity not finite and positive");
+    if (any & ST_CFL) return fail(FWI_ERR_CFL, "v dt/dx above the stability limit %g", CFL_2D);
+    if (any & ST_TIMEOUT) return fail(FWI_ERR_TIMEOUT, "a device wait timed out");
+    if (any & ST_NONFINITE) return fail(FWI_ERR_UNSTABLE, "non-finite wavefield");
     t_err.clear();
     return FWI_OK;
 }
+
+fwi_status finish(const Plan &pl, void *ws, cudaStream_t st) { return finish_models(1, &pl, &ws, st); }
 
 void begin_call(cudaStream_t st)
 {
     t_launch[0] = t_launch[1] = t_launch[2] = 0;
     t_ev_recorded = false;
     prof_record(0, st);
+}
+
+// Device pointers of one model's gradient call (grad_pre, misfit, illum,
+// offh may be null).
+struct GradientIO {
+    const float *v, *d_obs;
+    float *grad, *grad_pre;
+    double *misfit;
+    float *illum, *offh;
+};
+
+// The whole preconditioned gradient of nm models (fwi_adjoint_gradient,
+// fwi_batch_gradient): set-up, forward time loop, misfit and adjoint source,
+// backward time loop, fold, illumination / offset-Hessian outputs and
+// preconditioning. The time loops of all models run as one launch per level.
+fwi_status gradient_models(int nm, const Plan *pl, const fwi_geometry *const *ge, const fwi_options *opts,
+                           void *const *ws, const GradientIO *io, cudaStream_t st)
+{
+    fwi_status s;
+    cudaError_t e;
+    begin_call(st);
+    std::vector<float *> acc_i(nm), acc_h(nm), syn(nm);
+    for (int k = 0; k < nm; ++k) {
+        if ((s = setup(pl[k], ge[k], io[k].v, ws[k], st)) != FWI_OK) return s;
+        acc_i[k] = at<float>(ws[k], pl[k].acc_i);
+        acc_h[k] = pl[k].with_offh ? at<float>(ws[k], pl[k].acc_h) : nullptr;
+        syn[k] = at<float>(ws[k], pl[k].syn);
+    }
+    if ((s = run_forward_models(nm, pl, ge, ws, syn.data(), true, acc_i.data(), acc_h.data(), opts->illum_mode, st)) !=
+        FWI_OK)
+        return s;
+    prof_record(1, st);
+    for (int k = 0; k < nm; ++k) {
+        double *J = at<double>(ws[k], pl[k].scal, 0);
+        const long long nsamp = (long long)pl[k].ns * pl[k].nt * pl[k].nrec;
+        if (nsamp == 0) continue;
+        if ((e = launch_residual_ols(syn[k], io[k].d_obs, nsamp, opts->misfit == FWI_MISFIT_OLS ? J : nullptr, st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "residual kernel");
+        t_launch[2]++;
+        if (opts->misfit == FWI_MISFIT_TIME_INTEGRAL) {
+            if ((e = launch_time_integral(syn[k], pl[k].ns, pl[k].nt, pl[k].nrec, pl[k].L.dt, J, st)) != cudaSuccess)
+                return cuda_fail(e, "time-integral kernel");
+            t_launch[2]++;
+        }
+    }
+    std::vector<const float *> adj(syn.begin(), syn.end());
+    if ((s = run_backward_models(nm, pl, ge, ws, adj.data(), st)) != FWI_OK) return s;
+    prof_record(2, st);
+    for (int k = 0; k < nm; ++k) {
+        const Plan &p = pl[k];
+        void *w = ws[k];
+        const GradientIO &o = io[k];
+        if ((e = launch_fold_grad(p.L, at<float>(w, p.acc_g), 1, o.v, o.grad, st)) != cudaSuccess)
+            return cuda_fail(e, "fold kernel");
+        t_launch[2]++;
+        // illumination: dt sum u^2, or (1/dt^3) sum (second difference)^2
+        const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? p.L.dt : 1.0f / (p.L.dt * p.L.dt * p.L.dt);
+        float *ill_out = o.illum ? o.illum : acc_i[k]; // in place into group 0 when not requested
+        if ((e = launch_finish_accum(p.L, acc_i[k], 1, 1, iscale, ill_out, st)) != cudaSuccess)
+            return cuda_fail(e, "illumination output");
+        t_launch[2]++;
+        float *off_out = nullptr;
+        if (acc_h[k]) {
+            off_out = o.offh ? o.offh : acc_h[k];
+            if ((e = launch_finish_accum(p.L, acc_h[k], 1, p.hmax + 1, p.L.dt, off_out, st)) != cudaSuccess)
+                return cuda_fail(e, "offset-Hessian output");
+            t_launch[2]++;
+        }
+        if (o.grad_pre) {
+            if (opts->precond == FWI_PRECOND_NONE) {
+                if ((e = cudaMemcpyAsync(o.grad_pre, o.grad, (size_t)p.L.nz * p.L.nx * sizeof(float),
+                                         cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                    return cuda_fail(e, "copy");
+            } else {
+                const bool ill = opts->precond == FWI_PRECOND_ILLUM;
+                if ((e = launch_precond(p.L, o.grad, ill ? ill_out : off_out, ill ? 1 : 2, p.hmax, opts->eps,
+                                        o.grad_pre, at<unsigned>(w, p.scal, 12), st)) != cudaSuccess)
+                    return cuda_fail(e, "precondition kernel");
+                t_launch[2] += 2;
+            }
+        }
+        if (o.misfit &&
+            (e = cudaMemcpyAsync(o.misfit, at<double>(w, p.scal, 0), sizeof(double), cudaMemcpyDeviceToDevice, st)) !=
+                cudaSuccess)
+            return cuda_fail(e, "copy");
+    }
+    prof_record(3, st);
+    return FWI_OK;
+}
+
+// Plans of a batch of models in one workspace: model k's parts start at
+// base[k]. Every model is checked as in fwi_adjoint_gradient; the models
+// share opts and nt.
+fwi_status make_batch(int nm, const fwi_grid *grids, const fwi_geometry *geoms, const fwi_options *opts,
+                      bool coords, std::vector<Plan> &pl, std::vector<size_t> &base, size_t &total)
+{
+    if (nm < 1 || nm > FWI_BATCH_MAX) return fail(FWI_ERR_INVALID_ARG, "nmodels=%d outside 1..%d", nm, FWI_BATCH_MAX);
+    if (!grids || !geoms) return fail(FWI_ERR_INVALID_ARG, "grids or geoms is NULL");
+    if (!opts) return fail(FWI_ERR_INVALID_ARG, "options are NULL");
+    if (nm > 1 && opts->ckpt != FWI_CKPT_SPONGE)
+        return fail(FWI_ERR_INVALID_ARG, "a batch of several models needs ckpt = FWI_CKPT_SPONGE");
+    pl.assign(nm, Plan{});
+    base.assign(nm, 0);
+    total = 0;
+    for (int k = 0; k < nm; ++k) {
+        fwi_status s = make_plan(&grids[k], &geoms[k], opts, FWI_OP_GRADIENT, coords, pl[k]);
+        if (s != FWI_OK) return fail(s, "model %d: %s", k, t_err.c_str());
+        if (grids[k].nt != grids[0].nt)
+            return fail(FWI_ERR_INVALID_ARG, "model %d has nt=%d, model 0 nt=%d: a batch shares nt", k, grids[k].nt,
+                        grids[0].nt);
+        base[k] = total;
+        total = align_up(total + pl[k].total);
+    }
+    return FWI_OK;
 }
 
 // events 1 and 2 bracket the backward loop; for calls without one they
@@ -715,60 +896,8 @@ fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom, 
     if (offh && opts->hmax < 0) return fail(FWI_ERR_INVALID_ARG, "offh requested with hmax < 0");
     if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    begin_call(st);
-    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
-    float *acc_i = at<float>(ws, pl.acc_i);
-    float *acc_h = pl.with_offh ? at<float>(ws, pl.acc_h) : nullptr;
-    float *syn = at<float>(ws, pl.syn);
-    if ((s = run_forward(pl, geom, ws, syn, true, acc_i, acc_h, opts->illum_mode, st)) != FWI_OK) return s;
-    prof_record(1, st);
-    double *J = at<double>(ws, pl.scal, 0);
-    const long long nsamp = (long long)pl.ns * pl.nt * pl.nrec;
-    if (nsamp > 0) {
-        if ((e = launch_residual_ols(syn, d_obs, nsamp, opts->misfit == FWI_MISFIT_OLS ? J : nullptr, st)) != cudaSuccess)
-            return cuda_fail(e, "residual kernel");
-        t_launch[2]++;
-        if (opts->misfit == FWI_MISFIT_TIME_INTEGRAL) {
-            if ((e = launch_time_integral(syn, pl.ns, pl.nt, pl.nrec, pl.L.dt, J, st)) != cudaSuccess)
-                return cuda_fail(e, "time-integral kernel");
-            t_launch[2]++;
-        }
-    }
-    if ((s = run_backward(pl, geom, ws, syn, st)) != FWI_OK) return s;
-    prof_record(2, st);
-    if ((e = launch_fold_grad(pl.L, at<float>(ws, pl.acc_g), 1, v, grad, st)) != cudaSuccess)
-        return cuda_fail(e, "fold kernel");
-    t_launch[2]++;
-    // illumination: dt sum u^2, or (1/dt^3) sum (second difference)^2
-    const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
-    float *ill_out = illum ? illum : acc_i; // in place into group 0 when not requested
-    if ((e = launch_finish_accum(pl.L, acc_i, 1, 1, iscale, ill_out, st)) != cudaSuccess)
-        return cuda_fail(e, "illumination output");
-    t_launch[2]++;
-    float *off_out = nullptr;
-    if (acc_h) {
-        off_out = offh ? offh : acc_h;
-        if ((e = launch_finish_accum(pl.L, acc_h, 1, pl.hmax + 1, pl.L.dt, off_out, st)) != cudaSuccess)
-            return cuda_fail(e, "offset-Hessian output");
-        t_launch[2]++;
-    }
-    if (grad_pre) {
-        if (opts->precond == FWI_PRECOND_NONE) {
-            if ((e = cudaMemcpyAsync(grad_pre, grad, (size_t)pl.L.nz * pl.L.nx * sizeof(float),
-                                     cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-                return cuda_fail(e, "copy");
-        } else {
-            const bool ill = opts->precond == FWI_PRECOND_ILLUM;
-            if ((e = launch_precond(pl.L, grad, ill ? ill_out : off_out, ill ? 1 : 2, pl.hmax, opts->eps, grad_pre,
-                                    at<unsigned>(ws, pl.scal, 12), st)) != cudaSuccess)
-                return cuda_fail(e, "precondition kernel");
-            t_launch[2] += 2;
-        }
-    }
-    if (misfit && (e = cudaMemcpyAsync(misfit, J, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-        return cuda_fail(e, "copy");
-    prof_record(3, st);
+    GradientIO io{v, d_obs, grad, grad_pre, misfit, illum, offh};
+    if ((s = gradient_models(1, &pl, &geom, opts, &ws, &io, st)) != FWI_OK) return s;
     return finish(pl, ws, st);
 }
 
@@ -842,6 +971,52 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
     t_launch[2] += 2;
     prof_record(3, st);
     return finish(pl, ws, st);
+}
+
+fwi_status fwi_batch_workspace_bytes(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms,
+                                     const fwi_options *opts, size_t *bytes)
+{
+    if (!bytes) return fail(FWI_ERR_INVALID_ARG, "bytes is NULL");
+    std::vector<Plan> pl;
+    std::vector<size_t> base;
+    size_t total = 0;
+    fwi_status s = make_batch(nmodels, grids, geoms, opts, false, pl, base, total);
+    if (s != FWI_OK) return s;
+    *bytes = total;
+    t_err.clear();
+    return FWI_OK;
+}
+
+fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms,
+                              const fwi_options *opts, const float *const *v, const float *const *d_obs,
+                              float *const *grad, float *const *grad_pre, double *misfit, float *const *illum,
+                              float *const *offh, void *ws, size_t ws_bytes, void *stream)
+{
+    std::vector<Plan> pl;
+    std::vector<size_t> base;
+    size_t total = 0;
+    fwi_status s = make_batch(nmodels, grids, geoms, opts, true, pl, base, total);
+    if (s != FWI_OK) return s;
+    if (!v || !grad || !d_obs) return fail(FWI_ERR_INVALID_ARG, "v, d_obs or grad is NULL");
+    std::vector<GradientIO> io(nmodels);
+    std::vector<void *> wk(nmodels);
+    for (int k = 0; k < nmodels; ++k) {
+        if (!v[k] || !grad[k] || (!d_obs[k] && geoms[k].nrec > 0))
+            return fail(FWI_ERR_INVALID_ARG, "model %d: v, d_obs or grad is NULL", k);
+        io[k] = GradientIO{v[k], d_obs[k], grad[k], grad_pre ? grad_pre[k] : nullptr,
+                           misfit ? misfit + k : nullptr, illum ? illum[k] : nullptr, offh ? offh[k] : nullptr};
+        if (io[k].offh && opts->hmax < 0) return fail(FWI_ERR_INVALID_ARG, "offh requested with hmax < 0");
+        wk[k] = static_cast<char *>(ws) + base[k];
+    }
+    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
+        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
+    if (ws_bytes < total) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, total);
+    std::vector<const fwi_geometry *> gp(nmodels);
+    for (int k = 0; k < nmodels; ++k) gp[k] = &geoms[k];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((s = gradient_models(nmodels, pl.data(), gp.data(), opts, wk.data(), io.data(), st)) != FWI_OK) return s;
+    return finish_models(nmodels, pl.data(), wk.data(), st);
 }
 
 } // extern "C"

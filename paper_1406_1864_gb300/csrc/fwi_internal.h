@@ -7,6 +7,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "fwi.h"
+
 namespace fwi {
 
 // ---------------------------------------------------------------- layout
@@ -127,6 +129,22 @@ struct BwdArgs {
                            // 0: u^{m-1} comes from a re-propagated segment
 };
 
+// The work of one step launch: the (tile, shot) pairs of one model, or of up
+// to BATCH_MAX independent models of different sizes (one argument block
+// each). Chunks of the models are numbered consecutively; chunk_end[m] is the
+// end of model m's. All models of a launch share the time level, the status
+// flags, the chunk counter and the chunk size.
+constexpr int BATCH_MAX = FWI_BATCH_MAX;
+template <class A, int N>
+struct Batch {
+    static constexpr int NM = N;
+    A m[N];
+    int chunk_end[N];
+    int nm;
+    int chunk;  // shots per chunk
+    int *sched; // the launch's chunk counter (zero at launch)
+};
+
 // status bits written by kernels
 enum : int {
     ST_NONFINITE = 1,
@@ -152,6 +170,10 @@ void step_boxes(StepKind kind, int &hx, int &hy, int &px, int &py);
 bool encode_field_map(CUtensorMap *map, const float *base, const Lay2D &L, int nfields, int bx, int by);
 cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st);
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st);
+// one launch over the (tile, shot) pairs of nm <= BATCH_MAX models at the
+// same time level (per-model arguments and tilings of the same kind)
+cudaError_t launch_fwd_batch(const FwdArgs *a, const Tiling *t, int nm, bool with_offh, cudaStream_t st);
+cudaError_t launch_bwd_batch(const BwdArgs *a, const Tiling *t, int nm, cudaStream_t st);
 
 // auxiliary kernels (fwi_aux.cu)
 cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float *damp, float cfl_limit,

@@ -85,7 +85,10 @@ __device__ __forceinline__ float2 lap8x2(float2 c, const float2 (&xs)[4], const 
 
 // Lhat of the 4 points of one thread row r: x-window w (the row, w[WL] the
 // first point) and the column window zc (rows r .. r+8 of the stage tile).
-template <int WL, int NZ>
+// ODD_SCALAR: odd-distance x pairs as two scalar adds instead of one paired
+// add on moved registers (the same bits either way; the choice that the
+// register allocation of each kernel prefers).
+template <int WL, int NZ, bool ODD_SCALAR = true>
 __device__ __forceinline__ void lap4(float2 (&q)[2], const float *w, const float4 (&zc)[NZ], int r)
 {
 #pragma unroll
@@ -96,7 +99,7 @@ __device__ __forceinline__ void lap4(float2 (&q)[2], const float *w, const float
         for (int k = 1; k <= 4; ++k) {
             // even k: both pairs are aligned register pairs (one FADD2);
             // odd k: two scalar adds
-            if ((k & 1) == 0)
+            if ((k & 1) == 0 || !ODD_SCALAR)
                 xs[k - 1] = add2(f2(w[WL + p - k], w[WL + p + 1 - k]), f2(w[WL + p + k], w[WL + p + 1 + k]));
             else
                 xs[k - 1] = f2(w[WL + p - k] + w[WL + p + k], w[WL + p + 1 - k] + w[WL + p + 1 + k]);
@@ -269,13 +272,13 @@ struct alignas(16) ItemDesc {
     int rb, re;    // receiver-table range of (tile, shot)
     int si, sj;    // padded cell of the shot's source (8-byte aligned pair)
     float amp;     // source amplitude at this time level
-    int pad;
+    int model;     // model of the item in a batched launch
 };
 
-// Thread-0 state that walks the CTA's chunks.
+// State of the staging lane that walks the CTA's chunks.
 struct Cursor {
-    int tile, s, s_end; // current chunk
-    int q_next;         // next chunk, taken one chunk ahead (-1: none)
+    int model, tile, s, s_end; // current chunk
+    int q_next;                // next chunk, taken one chunk ahead (-1: none)
     bool done;
 };
 
@@ -285,29 +288,42 @@ __device__ __forceinline__ int grab_chunk(int *counter, int nchunks)
     return q < nchunks ? q : -1;
 }
 
-__device__ __forceinline__ void cursor_set(Cursor &cu, int q, int ntiles, int S, int ns)
+// chunk q of a launch: its model (chunks of the models are consecutive),
+// tile and shot range
+template <class BT>
+__device__ __forceinline__ void cursor_set(Cursor &cu, int q, const BT &B)
 {
-    const int blk = q / ntiles;
-    cu.tile = q - blk * ntiles;
-    cu.s = blk * S;
-    cu.s_end = min(ns, cu.s + S);
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k + 1 < BT::NM; ++k)
+        if (k + 1 < B.nm && q >= B.chunk_end[k]) m = k + 1;
+    const StepCommon &c = B.m[m].c;
+    const int ntiles = c.ntx * c.ntz;
+    const int local = q - (m > 0 ? B.chunk_end[m - 1] : 0);
+    const int blk = local / ntiles;
+    cu.model = m;
+    cu.tile = local - blk * ntiles;
+    cu.s = blk * B.chunk;
+    cu.s_end = min(c.ns, cu.s + B.chunk);
 }
 
-__device__ __forceinline__ void cursor_init(Cursor &cu, int *counter, int nchunks, int ntiles, int S, int ns)
+template <class BT>
+__device__ __forceinline__ void cursor_init(Cursor &cu, const BT &B)
 {
-    const int q = grab_chunk(counter, nchunks);
+    const int nchunks = B.chunk_end[B.nm - 1];
+    const int q = grab_chunk(B.sched, nchunks);
     cu.done = q < 0;
     cu.q_next = -1;
-    cu.tile = cu.s = cu.s_end = 0;
+    cu.model = cu.tile = cu.s = cu.s_end = 0;
     if (!cu.done) {
-        cursor_set(cu, q, ntiles, S, ns);
-        cu.q_next = grab_chunk(counter, nchunks);
+        cursor_set(cu, q, B);
+        cu.q_next = grab_chunk(B.sched, nchunks);
     }
 }
 
-// next (tile, shot) of this CTA; false when the launch's work is exhausted
-__device__ __forceinline__ bool cursor_next(Cursor &cu, int *counter, int nchunks, int ntiles, int S, int ns,
-                                            int &tile, int &s)
+// next (model, tile, shot) of this CTA; false when the launch's work is exhausted
+template <class BT>
+__device__ __forceinline__ bool cursor_next(Cursor &cu, const BT &B, int &model, int &tile, int &s)
 {
     if (cu.done) return false;
     if (cu.s >= cu.s_end) {
@@ -315,9 +331,10 @@ __device__ __forceinline__ bool cursor_next(Cursor &cu, int *counter, int nchunk
             cu.done = true;
             return false;
         }
-        cursor_set(cu, cu.q_next, ntiles, S, ns);
-        cu.q_next = grab_chunk(counter, nchunks);
+        cursor_set(cu, cu.q_next, B);
+        cu.q_next = grab_chunk(B.sched, B.chunk_end[B.nm - 1]);
     }
+    model = cu.model;
     tile = cu.tile;
     s = cu.s++;
     return true;
@@ -333,34 +350,39 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+__device__ __forceinline__ bool has_rec(const FwdArgs &a) { return a.seis != nullptr; }
+__device__ __forceinline__ bool has_rec(const BwdArgs &a) { return a.adj != nullptr; }
+
 // Stage the descriptor of the CTA's next item into a ring slot (lane 0 of
-// warp 1 only): tile and shot from the chunk cursor (shared memory), the
-// per-shot scalars (source cell, amplitude, receiver range) copied from
+// warp 1 only): model, tile and shot from the chunk cursor (shared memory),
+// the per-shot scalars (source cell, amplitude, receiver range) copied from
 // global memory by cp.async, so that no register holds them while the loads
 // are in flight. The copies complete at cp_async_wait_all(), which the
 // staging thread calls before the barrier that publishes the slot. The
 // amplitude is stored unscaled (times src_scale at use).
-__device__ __forceinline__ void stage_desc_async(ItemDesc *slot, Cursor &cu, const StepCommon &c, const RecTable &rt,
-                                                 int nchunks, int ntiles, int n_src, bool use_src, bool use_rec)
+template <class BT>
+__device__ __forceinline__ void stage_desc_async(ItemDesc *slot, Cursor &cu, const BT &B, int n_src, bool use_src)
 {
-    int t = -1, s = 0;
-    if (!cursor_next(cu, c.sched, nchunks, ntiles, c.chunk, c.ns, t, s)) t = -1;
+    int mdl = 0, t = -1, s = 0;
+    if (!cursor_next(cu, B, mdl, t, s)) t = -1;
     slot->tile = t;
     slot->s = s;
-    slot->pad = 0;
+    slot->model = mdl;
     if (t < 0) {
         slot->rb = slot->re = slot->si = slot->sj = 0;
         slot->amp = 0.f;
         return;
     }
+    const auto &a = B.m[mdl];
+    const StepCommon &c = a.c;
     cp_async8(&slot->si, &c.src_ij[s]);
     if (use_src)
         cp_async4(&slot->amp, &c.wav[(long long)s * c.nt + n_src]);
     else
         slot->amp = 0.f;
-    if (use_rec) {
-        cp_async4(&slot->rb, &rt.ptr[t * c.ns + s]);
-        cp_async4(&slot->re, &rt.ptr[t * c.ns + s + 1]);
+    if (has_rec(a)) {
+        cp_async4(&slot->rb, &a.rt.ptr[t * c.ns + s]);
+        cp_async4(&slot->re, &a.rt.ptr[t * c.ns + s + 1]);
     } else {
         slot->rb = slot->re = 0;
     }
@@ -440,8 +462,8 @@ __device__ __forceinline__ void load_c2_tile(float *dst, const float *c2, const 
 template <int RZ, int HX, bool WITH_H, int STAGES>
 using FwdRing = Ring<8 * RZ, HX, 1, 1, STAGES, 2 * 8 * RZ * TX * 4>; // + c2 and damping tiles
 
-template <int RZ, int HX, bool WITH_H, int STAGES, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ FwdArgs a)
+template <int RZ, int HX, bool WITH_H, int STAGES, int MINB, int NM>
+__global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ Batch<FwdArgs, NM> B)
 {
     using R = FwdRing<RZ, HX, WITH_H, STAGES>;
     constexpr int TZ = 8 * RZ;
@@ -464,13 +486,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     float *c2s = reinterpret_cast<float *>(R::extra(smem));
     float *dms = c2s + 8 * RZ * TX; // damping tile (sponge tiles)
 
-    const StepCommon &c = a.c;
-    const Lay2D &L = c.L;
+    // launch-wide values (time level, flags) are those of model 0
+    const FwdArgs &a0 = B.m[0];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const long long nphys = (long long)L.nz * L.nx;
-    const bool use_rec = a.seis != nullptr;
-    const int ntiles = c.ntx * c.ntz;
-    const int nchunks = ntiles * ((c.ns + c.chunk - 1) / c.chunk);
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < STAGES; ++k) mbar_init(smem_u32(&bars[k]), 1);
@@ -482,22 +500,22 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     // lane 0 of warp 1 walks the chunks (cursor in shared memory) and stages
     // descriptors D + 1 items ahead
     __shared__ Cursor s_cu;
-    auto stage = [&](int slot) {
-        stage_desc_async(&s_desc[slot % DESC_RING], s_cu, c, a.rt, nchunks, ntiles, a.n, !a.last, use_rec);
-    };
+    auto stage = [&](int slot) { stage_desc_async(&s_desc[slot % DESC_RING], s_cu, B, a0.n, !a0.last); };
     auto issue = [&](const ItemDesc &d, int k) {
-        const int bz = d.tile / c.ntx, bx = d.tile - bz * c.ntx;
+        const FwdArgs &ad = B.m[NM == 1 ? 0 : d.model];
+        const int bz = d.tile / ad.c.ntx, bx = d.tile - bz * ad.c.ntx;
         const int st = k % STAGES;
         const uint32_t bar = smem_u32(&bars[st]);
         fence_proxy_async_smem();
-        mbar_expect_tx(bar, (R::HALO + (a.last ? 0 : R::PT)) * 4);
-        tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_cur, GXL + bx * TX - HX, bz * TZ, d.s, bar);
-        if (!a.last) tma_load_3d(smem_u32(R::point(smem, st, 0)), &a.tm_prev, GXL + bx * TX, bz * TZ + GZ, d.s, bar);
+        mbar_expect_tx(bar, (R::HALO + (a0.last ? 0 : R::PT)) * 4);
+        tma_load_3d(smem_u32(R::halo(smem, st, 0)), &ad.tm_cur, GXL + bx * TX - HX, bz * TZ, d.s, bar);
+        if (!a0.last)
+            tma_load_3d(smem_u32(R::point(smem, st, 0)), &ad.tm_prev, GXL + bx * TX, bz * TZ + GZ, d.s, bar);
     };
     // lane 0 of warp 1 walks the chunks and stages descriptors; thread 0
     // issues the copies of a descriptor staged one barrier earlier
     if (threadIdx.x == 32) {
-        cursor_init(s_cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
+        cursor_init(s_cu, B);
         for (int k = 0; k <= D; ++k) stage(k);
         cp_async_wait_all();
     }
@@ -508,11 +526,15 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
 
     float2 acc_i[RZ][2];
     float2 acc_h[NH][2];
-    int cur_tile = -1, bi = 0, bj = 0, i0 = 0, j0 = 0;
+    int cur_tile = -1, cur_model = 0, bi = 0, bj = 0, i0 = 0, j0 = 0;
     bool tile_sponge = false, colok = false;
     SpongeInfo<RZ> sg;
 
+    // accumulators of the current tile to global memory
     auto flush = [&]() {
+        const FwdArgs &a = B.m[NM == 1 ? 0 : cur_model];
+        const Lay2D &L = a.c.L;
+        const long long nphys = (long long)L.nz * L.nx;
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
             const int iz = i0 + r - L.P;
@@ -527,7 +549,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                 if (WITH_H) {
 #pragma unroll
                     for (int h = 0; h < NH; ++h)
-                        if (h <= a.hmax)
+                        if (h <= a0.hmax)
                             atomicAdd(a.acc_offh + h * nphys + o, (p & 1) ? acc_h[h][p >> 1].y : acc_h[h][p >> 1].x);
                 }
             }
@@ -538,7 +560,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     auto fetch_rec = [&](const ItemDesc &v, int2 &en) {
         en = make_int2(-1, 0);
         const int e = v.rb + (int)threadIdx.x;
-        if (v.tile >= 0 && e < v.re) en = a.rt.ent[e];
+        if (v.tile >= 0 && e < v.re) en = B.m[NM == 1 ? 0 : v.model].rt.ent[e];
     };
     int2 rec_en;
     fetch_rec(s_desc[0], rec_en);
@@ -558,11 +580,16 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
         }
         const ItemDesc nx = s_desc[(k + 1) % DESC_RING];
         const int s = now.s;
+        const int mi = NM == 1 ? 0 : now.model;
+        const FwdArgs &a = B.m[mi];
+        const StepCommon &c = a.c;
+        const Lay2D &L = c.L;
         const int2 now_en = rec_en;
         fetch_rec(nx, rec_en);
-        if (now.tile != cur_tile) {
+        if (now.tile != cur_tile || mi != cur_model) {
             if (cur_tile >= 0) flush();
             cur_tile = now.tile;
+            cur_model = mi;
             const int bz = cur_tile / c.ntx, bx = cur_tile - bz * c.ntx;
             bi = bz * TZ;
             bj = bx * TX;
@@ -691,7 +718,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
         if (threadIdx.x == 32) cp_async_wait_all(); // the slot staged in this iteration
         __syncthreads();
         if (s_abort) {
-            abort_drain_ring<STAGES>(bars, s_desc, k, c.status);
+            abort_drain_ring<STAGES>(bars, s_desc, k, a0.c.status);
             return;
         }
     }
@@ -702,8 +729,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
 template <int RZ, int STAGES>
 using BwdRing = Ring<8 * RZ, RADIUS, 2, 2, STAGES, 3 * 8 * RZ * TX * 4>; // + c2, injection, damping tiles
 
-template <int RZ, int STAGES, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ BwdArgs a)
+template <int RZ, int STAGES, int MINB, int NM>
+__global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ Batch<BwdArgs, NM> B)
 {
     using R = BwdRing<RZ, STAGES>;
     constexpr int TZ = 8 * RZ;
@@ -724,15 +751,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     float *sinj = c2s + TZ * TX;
     float *dms = sinj + TZ * TX; // damping tile (sponge tiles)
 
-    const StepCommon &c = a.c;
-    const Lay2D &L = c.L;
+    // launch-wide values (time level, mode) are those of model 0
+    const BwdArgs &a0 = B.m[0];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m = a.m;
-    const bool use_rec = a.adj != nullptr;
-    const bool recon = a.recon != 0;
+    const int m = a0.m;
+    const bool recon = a0.recon != 0;
     const bool need_band = recon && m >= 3; // u^{m-2} in the sponge comes from checkpoint m-2 >= 1
-    const int ntiles = c.ntx * c.ntz;
-    const int nchunks = ntiles * ((c.ns + c.chunk - 1) / c.chunk);
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < STAGES; ++k) mbar_init(smem_u32(&bars[k]), 1);
@@ -743,11 +767,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     __syncthreads();
 
     __shared__ Cursor s_cu;
-    auto stage = [&](int slot) {
-        stage_desc_async(&s_desc[slot % DESC_RING], s_cu, c, a.rt, nchunks, ntiles, m - 1, true, use_rec);
-    };
+    auto stage = [&](int slot) { stage_desc_async(&s_desc[slot % DESC_RING], s_cu, B, m - 1, true); };
     auto issue = [&](const ItemDesc &d, int k) {
-        const int bz = d.tile / c.ntx, bx = d.tile - bz * c.ntx;
+        const BwdArgs &a = B.m[NM == 1 ? 0 : d.model];
+        const int bz = d.tile / a.c.ntx, bx = d.tile - bz * a.c.ntx;
         const int bi = bz * TZ, bj = bx * TX;
         const int st = k % STAGES;
         const uint32_t bar = smem_u32(&bars[st]);
@@ -762,7 +785,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     // lane 0 of warp 1 walks the chunks and stages descriptors; thread 0
     // issues the copies of a descriptor staged one barrier earlier
     if (threadIdx.x == 32) {
-        cursor_init(s_cu, c.sched, nchunks, ntiles, c.chunk, c.ns);
+        cursor_init(s_cu, B);
         for (int k = 0; k <= D; ++k) stage(k);
         cp_async_wait_all();
     }
@@ -772,11 +795,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             if (s_desc[k].tile >= 0) issue(s_desc[k], k);
 
     float2 acc_g[RZ][2];
-    int cur_tile = -1, bi = 0, bj = 0, i0 = 0, j0 = 0;
+    int cur_tile = -1, cur_model = 0, bi = 0, bj = 0, i0 = 0, j0 = 0;
     bool tile_sponge = false, colok = false;
     SpongeInfo<RZ> sg;
 
+    // gradient accumulators of the current tile to global memory
     auto flush = [&]() {
+        const BwdArgs &a = B.m[NM == 1 ? 0 : cur_model];
+        const Lay2D &L = a.c.L;
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
             const int i = i0 + r;
@@ -796,6 +822,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         val = 0.f;
         const int e = v.rb + (int)threadIdx.x;
         if (v.tile >= 0 && e < v.re) {
+            const BwdArgs &a = B.m[NM == 1 ? 0 : v.model];
             loc = a.rt.ent[e].x;
             val = a.adj[(long long)m * a.nent + e] * a.adj_scale;
         }
@@ -803,6 +830,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 
     // checkpointed sponge values of u^{m-2} of one item of the current tile
     auto fetch_band = [&](int s, float4 (&bv)[RZ]) {
+        const BwdArgs &a = B.m[NM == 1 ? 0 : cur_model];
+        const StepCommon &c = a.c;
+        const Lay2D &L = c.L;
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
             bv[r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -842,9 +872,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         }
         const ItemDesc nx = s_desc[(k + 1) % DESC_RING];
         const int s = now.s;
-        if (now.tile != cur_tile) {
+        const int mi = NM == 1 ? 0 : now.model;
+        const BwdArgs &a = B.m[mi];
+        const StepCommon &c = a.c;
+        const Lay2D &L = c.L;
+        if (now.tile != cur_tile || mi != cur_model) {
             if (cur_tile >= 0) flush();
             cur_tile = now.tile;
+            cur_model = mi;
             const int bz = cur_tile / c.ntx, bx = cur_tile - bz * c.ntx;
             bi = bz * TZ;
             bj = bx * TX;
@@ -876,7 +911,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         // prefetch for the next item: adjoint entry, and its checkpoint values
         // when it is on the same tile
         fetch_adj(nx, adj_loc, adj_val);
-        bval_ok = tile_sponge && nx.tile == cur_tile;
+        bval_ok = tile_sponge && nx.tile == cur_tile && (NM == 1 || nx.model == cur_model);
         if (bval_ok) fetch_band(nx.s, bval);
         if (has_rec) __syncthreads();
         const int st = k % STAGES;
@@ -904,9 +939,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                     const float4 a1 = zc[r + RADIUS];
                     const float w[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
                     if (fld == 0)
-                        lap4<4>(qu[r], w, zc, r);
+                        lap4<4, RZ + 2 * RADIUS, false>(qu[r], w, zc, r);
                     else
-                        lap4<4>(qp[r], w, zc, r);
+                        lap4<4, RZ + 2 * RADIUS, false>(qp[r], w, zc, r);
                 }
             }
 #pragma unroll
@@ -978,7 +1013,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         if (threadIdx.x == 32) cp_async_wait_all(); // the slot staged in this iteration
         __syncthreads();
         if (s_abort) {
-            abort_drain_ring<STAGES>(bars, s_desc, k, c.status);
+            abort_drain_ring<STAGES>(bars, s_desc, k, a0.c.status);
             return;
         }
         if (has_rec) {
@@ -1030,14 +1065,19 @@ constexpr int H_RZ = 1, H_ST = FWI_H_ST, H_MINB = FWI_H_MINB;
 // backward: 64 x 16 tiles
 constexpr int B_RZ = FWI_B_RZ, B_ST = FWI_B_ST, B_MINB = FWI_B_MINB;
 
-#define K_FWD k_fwd_step<F_RZ, RADIUS, false, F_ST, F_MINB>
-#define K_FWDH k_fwd_step<H_RZ, HMAX_LIMIT, true, H_ST, H_MINB>
-#define K_BWD k_bwd_step<B_RZ, B_ST, B_MINB>
+// one model per launch, and batches of up to BATCH_MAX models
+#define K_FWD k_fwd_step<F_RZ, RADIUS, false, F_ST, F_MINB, 1>
+#define K_FWDH k_fwd_step<H_RZ, HMAX_LIMIT, true, H_ST, H_MINB, 1>
+#define K_BWD k_bwd_step<B_RZ, B_ST, B_MINB, 1>
+#define K_FWD_B k_fwd_step<F_RZ, RADIUS, false, F_ST, F_MINB, BATCH_MAX>
+#define K_FWDH_B k_fwd_step<H_RZ, HMAX_LIMIT, true, H_ST, H_MINB, BATCH_MAX>
+#define K_BWD_B k_bwd_step<B_RZ, B_ST, B_MINB, BATCH_MAX>
 constexpr int SMEM_FWD = FwdRing<F_RZ, RADIUS, false, F_ST>::SMEM;
 constexpr int SMEM_FWDH = FwdRing<H_RZ, HMAX_LIMIT, true, H_ST>::SMEM;
 constexpr int SMEM_BWD = BwdRing<B_RZ, B_ST>::SMEM;
 
-int g_occ[3] = {0, 0, 0};
+int g_occ[3] = {0, 0, 0};   // resident CTAs per SM: forward, forward + offset Hessian, backward
+int g_occ_b[3] = {0, 0, 0}; // the same for the batched instances
 
 void prepare_kernels()
 {
@@ -1047,7 +1087,7 @@ void prepare_kernels()
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
-        g_occ[0] = g_occ[1] = g_occ[2] = 2;
+        for (int k = 0; k < 3; ++k) g_occ[k] = g_occ_b[k] = 2;
         return;
     }
     cudaFuncSetAttribute(K_FWD, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FWD);
@@ -1056,9 +1096,20 @@ void prepare_kernels()
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[0], K_FWD, TPB, SMEM_FWD) != cudaSuccess) g_occ[0] = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[1], K_FWDH, TPB, SMEM_FWDH) != cudaSuccess) g_occ[1] = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[2], K_BWD, TPB, SMEM_BWD) != cudaSuccess) g_occ[2] = 0;
+    cudaFuncSetAttribute(K_FWD_B, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FWD);
+    cudaFuncSetAttribute(K_FWDH_B, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FWDH);
+    cudaFuncSetAttribute(K_BWD_B, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BWD);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_b[0], K_FWD_B, TPB, SMEM_FWD) != cudaSuccess)
+        g_occ_b[0] = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_b[1], K_FWDH_B, TPB, SMEM_FWDH) != cudaSuccess)
+        g_occ_b[1] = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_b[2], K_BWD_B, TPB, SMEM_BWD) != cudaSuccess)
+        g_occ_b[2] = 0;
     cudaGetLastError();
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k) {
         if (g_occ[k] < 1) g_occ[k] = 2;
+        if (g_occ_b[k] < 1) g_occ_b[k] = 2;
+    }
 }
 
 int sm_count_dev()
@@ -1076,6 +1127,25 @@ int sm_count_dev()
     }
     return n;
 }
+
+// chunk counts of a launch's models and the number of CTAs to launch
+template <class A, int N>
+int batch_fill(Batch<A, N> &b, const A *a, const Tiling *t, int nm, int occ)
+{
+    long long total = 0;
+    for (int k = 0; k < nm; ++k) {
+        b.m[k] = a[k];
+        total += (long long)t[k].ntx * t[k].ntz * ((a[k].c.ns + t[0].chunk - 1) / t[0].chunk);
+        b.chunk_end[k] = (int)total;
+    }
+    for (int k = nm; k < N; ++k) b.chunk_end[k] = (int)total;
+    b.nm = nm;
+    b.chunk = t[0].chunk;
+    b.sched = a[0].c.sched;
+    const long long slots = (long long)sm_count_dev() * occ;
+    return (int)(total < slots ? total : slots);
+}
+
 } // namespace
 
 void step_boxes(StepKind kind, int &hx, int &hy, int &px, int &py)
@@ -1108,16 +1178,45 @@ Tiling make_tiling(const Lay2D &L, int ns, StepKind kind)
 
 cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st)
 {
+    Batch<FwdArgs, 1> b;
+    const int ctas = batch_fill(b, &a, &t, 1, g_occ[with_offh ? STEP_FWD_OFFH : STEP_FWD]);
+    if (ctas <= 0) return cudaSuccess;
     if (with_offh)
-        K_FWDH<<<t.ctas, TPB, SMEM_FWDH, st>>>(a);
+        K_FWDH<<<ctas, TPB, SMEM_FWDH, st>>>(b);
     else
-        K_FWD<<<t.ctas, TPB, SMEM_FWD, st>>>(a);
+        K_FWD<<<ctas, TPB, SMEM_FWD, st>>>(b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st)
 {
-    K_BWD<<<t.ctas, TPB, SMEM_BWD, st>>>(a);
+    Batch<BwdArgs, 1> b;
+    const int ctas = batch_fill(b, &a, &t, 1, g_occ[STEP_BWD]);
+    if (ctas <= 0) return cudaSuccess;
+    K_BWD<<<ctas, TPB, SMEM_BWD, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_batch(const FwdArgs *a, const Tiling *t, int nm, bool with_offh, cudaStream_t st)
+{
+    if (nm < 1 || nm > BATCH_MAX) return cudaErrorInvalidValue;
+    Batch<FwdArgs, BATCH_MAX> b;
+    const int ctas = batch_fill(b, a, t, nm, g_occ_b[with_offh ? STEP_FWD_OFFH : STEP_FWD]);
+    if (ctas <= 0) return cudaSuccess;
+    if (with_offh)
+        K_FWDH_B<<<ctas, TPB, SMEM_FWDH, st>>>(b);
+    else
+        K_FWD_B<<<ctas, TPB, SMEM_FWD, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_batch(const BwdArgs *a, const Tiling *t, int nm, cudaStream_t st)
+{
+    if (nm < 1 || nm > BATCH_MAX) return cudaErrorInvalidValue;
+    Batch<BwdArgs, BATCH_MAX> b;
+    const int ctas = batch_fill(b, a, t, nm, g_occ_b[STEP_BWD]);
+    if (ctas <= 0) return cudaSuccess;
+    K_BWD_B<<<ctas, TPB, SMEM_BWD, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -205,6 +205,61 @@ def adjoint_gradient(grid: Grid, geom: Geometry, v: torch.Tensor, d_obs: torch.T
     return res
 
 
+def batch_workspace_bytes(grids, geoms, opts: Options) -> int:
+    n = len(grids)
+    g = (L.FwiGrid * n)(*[x.c() for x in grids])
+    ge = (L.FwiGeometry * n)(*[x.c() for x in geoms])
+    oc = opts.c()
+    nb = ctypes.c_size_t(0)
+    L.check(L.load().fwi_batch_workspace_bytes(n, g, ge, ctypes.byref(oc), ctypes.byref(nb)),
+            "fwi_batch_workspace_bytes")
+    return int(nb.value)
+
+
+def batch_gradient(grids, geoms, vs, d_obs, opts: Options | None = None, *, want_pre=True,
+                   want_illum=True, want_offh=None, ws=None, stream=None) -> list:
+    """fwi_batch_gradient: the gradients of several independent models of
+    different sizes (same nt), every time level of all models in one launch.
+    Returns one dict per model, as adjoint_gradient."""
+    opts = opts or Options()
+    n = len(grids)
+    if not (len(geoms) == len(vs) == len(d_obs) == n):
+        raise ValueError("grids, geoms, vs and d_obs must have the same length")
+    want_offh = opts.hmax >= 0 if want_offh is None else want_offh
+    res = []
+    for g, ge, v, d in zip(grids, geoms, vs, d_obs):
+        _dev(v, "v", g.shape)
+        _dev(d, "d_obs", (ge.nshots, g.nt, ge.nrec))
+        r = {"grad": torch.empty(g.shape, dtype=torch.float32, device=v.device)}
+        if want_pre:
+            r["grad_pre"] = torch.empty(g.shape, dtype=torch.float32, device=v.device)
+        if want_illum:
+            r["illum"] = torch.empty(g.shape, dtype=torch.float32, device=v.device)
+        if want_offh:
+            r["offh"] = torch.empty((opts.hmax + 1,) + g.shape, dtype=torch.float32, device=v.device)
+        res.append(r)
+    misfit = torch.zeros(n, dtype=torch.float64, device=vs[0].device)
+    buf, nb = _ws(ws, batch_workspace_bytes(grids, geoms, opts))
+    g = (L.FwiGrid * n)(*[x.c() for x in grids])
+    ge = (L.FwiGeometry * n)(*[x.c() for x in geoms])
+    oc = opts.c()
+
+    def ptrs(key, src=None):
+        vals = [t.data_ptr() for t in src] if src is not None else [r[key].data_ptr() if key in r else None
+                                                                     for r in res]
+        return (ctypes.c_void_p * n)(*vals)
+
+    pre = ptrs("grad_pre") if want_pre else None
+    ill = ptrs("illum") if want_illum else None
+    off = ptrs("offh") if want_offh else None
+    L.check(L.load().fwi_batch_gradient(n, g, ge, ctypes.byref(oc), ptrs(None, vs), ptrs(None, d_obs),
+                                        ptrs("grad"), pre, _ptr(misfit), ill, off, _ptr(buf), nb,
+                                        _stream(stream)), "fwi_batch_gradient")
+    for k, r in enumerate(res):
+        r["misfit"] = misfit[k]
+    return res
+
+
 def illumination(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options | None = None, *,
                  ws=None, stream=None) -> torch.Tensor:
     """fwi_illumination: sum_s sum_n u^2 dt (or u_tt^2 dt), [nz, nx]."""

@@ -180,6 +180,13 @@ def smooth_perturbation(shape, seed, sigma_cells=5.0, amplitude=1.0):
 
 # ------------------------------------------------------------------ named workloads
 
+def uneven_batch(nt=4000, ns=32, sizes=((200, 400), (350, 900), (500, 1500)), seed=1) -> list:
+    """Independent models of uneven sizes sharing nt: the dipping-layer
+    generator at each size (its own seed), ns shots and nx / 2 receivers each."""
+    return [dipping(nz=nz, nx=nx, nt=nt, ns=ns, nrec=nx // 2, seed=seed + k, name=f"dipping_{nz}x{nx}")
+            for k, (nz, nx) in enumerate(sizes)]
+
+
 def workload(name: str) -> Problem:
     """The named workloads of the benchmark suite (full sizes)."""
     if name == "two_layer_100x200":

@@ -31,7 +31,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ["fwi_forward", "fwi_adjoint_gradient", "fwi_illumination", "fwi_offset_hessian_diag",
-                 "fwi_adjoint_apply", "fwi_workspace_bytes", "fwi_last_error"]:
+                 "fwi_adjoint_apply", "fwi_workspace_bytes", "fwi_last_error", "fwi_batch_gradient",
+                 "fwi_batch_workspace_bytes"]:
         assert must in names
 
 
@@ -181,3 +182,33 @@ def test_product_path_does_not_import_the_oracle():
         if f.endswith((".py", ".cu", ".h", ".cuh")):
             txt = open(f).read()
             assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_batch_workspace_and_errors(lib):
+    """A batch of models lays the models' gradient workspaces end to end; it
+    refuses mismatched nt, snapshot checkpoints with several models, and a
+    model count outside 1..FWI_BATCH_MAX (all before any device work)."""
+    from paper_1406_1864_gb300 import _lib as L
+    (g1, ge1, o, k1), (g2, ge2, _, k2) = _structs(nz=30, nx=40), _structs(nz=50, nx=70, ns=2)
+    singles = [ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[1] for g, ge in ((g1, ge1), (g2, ge2))]
+    G = (L.FwiGrid * 2)(g1, g2)
+    GE = (L.FwiGeometry * 2)(ge1, ge2)
+    n = ctypes.c_size_t(0)
+    assert lib.fwi_batch_workspace_bytes(2, G, GE, ctypes.byref(o), ctypes.byref(n)) == L.FWI_OK
+    align = lambda x: (x + 255) // 256 * 256
+    assert n.value == align(singles[0]) + align(singles[1])
+    assert lib.fwi_batch_workspace_bytes(1, G, GE, ctypes.byref(o), ctypes.byref(n)) == L.FWI_OK
+    assert n.value == align(singles[0])
+    for bad in (0, L.FWI_BATCH_MAX + 1):
+        assert lib.fwi_batch_workspace_bytes(bad, G, GE, ctypes.byref(o), ctypes.byref(n)) == L.FWI_ERR_INVALID_ARG
+    G[1].nt = 99
+    assert lib.fwi_batch_workspace_bytes(2, G, GE, ctypes.byref(o), ctypes.byref(n)) == L.FWI_ERR_INVALID_ARG
+    assert b"nt" in lib.fwi_last_error()
+    G[1].nt = G[0].nt
+    o.ckpt = L.FWI_CKPT_SNAPSHOT
+    assert lib.fwi_batch_workspace_bytes(2, G, GE, ctypes.byref(o), ctypes.byref(n)) == L.FWI_ERR_INVALID_ARG
+    assert lib.fwi_batch_workspace_bytes(1, G, GE, ctypes.byref(o), ctypes.byref(n)) == L.FWI_OK
+    o.ckpt = L.FWI_CKPT_SPONGE
+    G[1].nz = 0
+    assert lib.fwi_batch_workspace_bytes(2, G, GE, ctypes.byref(o), ctypes.byref(n)) == L.FWI_ERR_INVALID_ARG
+    assert b"model 1" in lib.fwi_last_error()
