@@ -198,6 +198,24 @@ fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geom
                               float *const *grad, float *const *grad_pre, double *misfit, float *const *illum,
                               float *const *offh, void *ws, size_t ws_bytes, void *stream);
 
+/* A recorded gradient: fwi_exec_gradient_create() checks its arguments as
+   fwi_batch_gradient() does (nmodels = 1 is fwi_adjoint_gradient), uploads
+   the geometry tables into ws, and records the call's device work -- set-up,
+   both time loops, misfit, outputs: some 2 nt kernel launches -- into a CUDA
+   graph bound to these buffers. fwi_exec_run() replays it on `stream` (one
+   graph launch) and reads the status like a direct call; change the contents
+   of v[] and d_obs[] between runs, not their addresses. `stream` must not be
+   the legacy default stream (it cannot be captured). The exec holds no
+   device memory of its own; ws and the buffers must outlive it. */
+typedef struct fwi_exec_s fwi_exec;
+fwi_status fwi_exec_gradient_create(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms,
+                                    const fwi_options *opts, const float *const *v, const float *const *d_obs,
+                                    float *const *grad, float *const *grad_pre, double *misfit,
+                                    float *const *illum, float *const *offh, void *ws, size_t ws_bytes,
+                                    void *stream, fwi_exec **out);
+fwi_status fwi_exec_run(fwi_exec *ex, void *stream);
+fwi_status fwi_exec_destroy(fwi_exec *ex);
+
 /* Shot illumination, the pseudo-diagonal Hessian of Eq. 1:
    illum DEVICE [nz][nx] = sum_s sum_n u_s^n(x)^2 dt (FWI_ILLUM_U2) or
    sum_s sum_n (u_tt)_s^n(x)^2 dt (FWI_ILLUM_UTT2), from a forward modelling. */

@@ -72,6 +72,11 @@ _SIGS = {
     "fwi_batch_gradient": [c_int, P(FwiGrid), P(FwiGeometry), P(FwiOptions), P(c_void_p), P(c_void_p),
                            P(c_void_p), P(c_void_p), c_void_p, P(c_void_p), P(c_void_p), c_void_p,
                            c_size_t, c_void_p],
+    "fwi_exec_gradient_create": [c_int, P(FwiGrid), P(FwiGeometry), P(FwiOptions), P(c_void_p),
+                                 P(c_void_p), P(c_void_p), P(c_void_p), c_void_p, P(c_void_p),
+                                 P(c_void_p), c_void_p, c_size_t, c_void_p, P(c_void_p)],
+    "fwi_exec_run": [c_void_p, c_void_p],
+    "fwi_exec_destroy": [c_void_p],
     "fwi_profile_enable": [c_int],
     "fwi_profile_last": [P(FwiPhaseTimes)],
 }

@@ -32,6 +32,7 @@ thread_local bool t_prof = false;
 thread_local fwi_phase_times t_times{};
 thread_local cudaEvent_t t_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 thread_local bool t_ev_recorded = false;
+thread_local bool t_capturing = false; // recording a graph: events become graph nodes
 thread_local int t_launch[3] = {0, 0, 0};
 
 fwi_status fail(fwi_status s, const char *fmt, ...)
@@ -330,7 +331,10 @@ void prof_record(int k, cudaStream_t st)
     if (!t_prof) return;
     if (!t_ev[0])
         for (int i = 0; i < 4; ++i) cudaEventCreate(&t_ev[i]);
-    cudaEventRecord(t_ev[k], st);
+    if (t_capturing)
+        cudaEventRecordWithFlags(t_ev[k], st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(t_ev[k], st);
     if (k == 3) t_ev_recorded = true;
 }
 
@@ -356,15 +360,20 @@ StepCommon make_common(const Plan &pl, const fwi_geometry *ge, void *ws, const T
 }
 
 // set-up shared by every propagation: status, tables, c2, zero fields
-fwi_status setup(const Plan &pl, const fwi_geometry *ge, const float *v, void *ws, cudaStream_t st)
+// (tables = false: the geometry tables are already in ws, as in a recorded
+// graph, which cannot copy from pageable host memory)
+fwi_status setup(const Plan &pl, const fwi_geometry *ge, const float *v, void *ws, cudaStream_t st,
+                 bool tables = true)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(at<char>(ws, pl.scal), 0, pl.scal.bytes, st)) != cudaSuccess)
         return cuda_fail(e, "memset");
     if ((e = cudaMemsetAsync(at<char>(ws, pl.sched), 0, pl.sched.bytes, st)) != cudaSuccess)
         return cuda_fail(e, "memset");
-    fwi_status s = upload_tables(pl, ge, ws, st);
-    if (s != FWI_OK) return s;
+    if (tables) {
+        fwi_status s = upload_tables(pl, ge, ws, st);
+        if (s != FWI_OK) return s;
+    }
     if ((e = cudaMemsetAsync(at<char>(ws, pl.c2), 0, pl.c2.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
     if ((e = cudaMemsetAsync(at<char>(ws, pl.damp), 0, pl.damp.bytes, st)) != cudaSuccess)
         return cuda_fail(e, "memset");
@@ -705,14 +714,14 @@ struct GradientIO {
 // backward time loop, fold, illumination / offset-Hessian outputs and
 // preconditioning. The time loops of all models run as one launch per level.
 fwi_status gradient_models(int nm, const Plan *pl, const fwi_geometry *const *ge, const fwi_options *opts,
-                           void *const *ws, const GradientIO *io, cudaStream_t st)
+                           void *const *ws, const GradientIO *io, cudaStream_t st, bool tables = true)
 {
     fwi_status s;
     cudaError_t e;
     begin_call(st);
     std::vector<float *> acc_i(nm), acc_h(nm), syn(nm);
     for (int k = 0; k < nm; ++k) {
-        if ((s = setup(pl[k], ge[k], io[k].v, ws[k], st)) != FWI_OK) return s;
+        if ((s = setup(pl[k], ge[k], io[k].v, ws[k], st, tables)) != FWI_OK) return s;
         acc_i[k] = at<float>(ws[k], pl[k].acc_i);
         acc_h[k] = pl[k].with_offh ? at<float>(ws[k], pl[k].acc_h) : nullptr;
         syn[k] = at<float>(ws[k], pl[k].syn);
@@ -987,19 +996,31 @@ fwi_status fwi_batch_workspace_bytes(int nmodels, const fwi_grid *grids, const f
     return FWI_OK;
 }
 
-fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms,
-                              const fwi_options *opts, const float *const *v, const float *const *d_obs,
-                              float *const *grad, float *const *grad_pre, double *misfit, float *const *illum,
-                              float *const *offh, void *ws, size_t ws_bytes, void *stream)
-{
+} // extern "C"
+
+namespace {
+// Checked arguments of a gradient over a batch of models.
+struct BatchCall {
     std::vector<Plan> pl;
+    std::vector<GradientIO> io;
+    std::vector<void *> wk;
+    std::vector<const fwi_geometry *> gp;
+};
+
+fwi_status batch_prepare(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms, const fwi_options *opts,
+                         const float *const *v, const float *const *d_obs, float *const *grad,
+                         float *const *grad_pre, double *misfit, float *const *illum, float *const *offh, void *ws,
+                         size_t ws_bytes, BatchCall &bc)
+{
     std::vector<size_t> base;
     size_t total = 0;
-    fwi_status s = make_batch(nmodels, grids, geoms, opts, true, pl, base, total);
+    fwi_status s = make_batch(nmodels, grids, geoms, opts, true, bc.pl, base, total);
     if (s != FWI_OK) return s;
     if (!v || !grad || !d_obs) return fail(FWI_ERR_INVALID_ARG, "v, d_obs or grad is NULL");
-    std::vector<GradientIO> io(nmodels);
-    std::vector<void *> wk(nmodels);
+    std::vector<GradientIO> &io = bc.io;
+    std::vector<void *> &wk = bc.wk;
+    io.assign(nmodels, GradientIO{});
+    wk.assign(nmodels, nullptr);
     for (int k = 0; k < nmodels; ++k) {
         if (!v[k] || !grad[k] || (!d_obs[k] && geoms[k].nrec > 0))
             return fail(FWI_ERR_INVALID_ARG, "model %d: v, d_obs or grad is NULL", k);
@@ -1012,11 +1033,103 @@ fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geom
     if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
         return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
     if (ws_bytes < total) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, total);
-    std::vector<const fwi_geometry *> gp(nmodels);
-    for (int k = 0; k < nmodels; ++k) gp[k] = &geoms[k];
+    bc.gp.assign(nmodels, nullptr);
+    for (int k = 0; k < nmodels; ++k) bc.gp[k] = &geoms[k];
+    return FWI_OK;
+}
+} // namespace
+
+// A recorded gradient: the device work of one gradient call as a CUDA graph,
+// bound to the buffers it was recorded with.
+struct fwi_exec_s {
+    std::vector<Plan> pl;
+    std::vector<void *> wk;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool prof = false;
+    int launches[3] = {0, 0, 0};
+};
+
+extern "C" {
+
+fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms,
+                              const fwi_options *opts, const float *const *v, const float *const *d_obs,
+                              float *const *grad, float *const *grad_pre, double *misfit, float *const *illum,
+                              float *const *offh, void *ws, size_t ws_bytes, void *stream)
+{
+    BatchCall bc;
+    fwi_status s = batch_prepare(nmodels, grids, geoms, opts, v, d_obs, grad, grad_pre, misfit, illum, offh, ws,
+                                 ws_bytes, bc);
+    if (s != FWI_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if ((s = gradient_models(nmodels, pl.data(), gp.data(), opts, wk.data(), io.data(), st)) != FWI_OK) return s;
-    return finish_models(nmodels, pl.data(), wk.data(), st);
+    if ((s = gradient_models(nmodels, bc.pl.data(), bc.gp.data(), opts, bc.wk.data(), bc.io.data(), st)) != FWI_OK)
+        return s;
+    return finish_models(nmodels, bc.pl.data(), bc.wk.data(), st);
+}
+
+fwi_status fwi_exec_gradient_create(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms,
+                                    const fwi_options *opts, const float *const *v, const float *const *d_obs,
+                                    float *const *grad, float *const *grad_pre, double *misfit,
+                                    float *const *illum, float *const *offh, void *ws, size_t ws_bytes,
+                                    void *stream, fwi_exec **out)
+{
+    if (!out) return fail(FWI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!stream) return fail(FWI_ERR_INVALID_ARG, "recording a graph needs a stream other than the default stream");
+    BatchCall bc;
+    fwi_status s = batch_prepare(nmodels, grids, geoms, opts, v, d_obs, grad, grad_pre, misfit, illum, offh, ws,
+                                 ws_bytes, bc);
+    if (s != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the geometry tables do not change between runs: uploaded once, here
+    for (int k = 0; k < nmodels; ++k)
+        if ((s = upload_tables(bc.pl[k], bc.gp[k], bc.wk[k], st)) != FWI_OK) return s;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    fwi_exec *ex = new fwi_exec_s;
+    ex->pl = bc.pl;
+    ex->wk = bc.wk;
+    ex->prof = t_prof;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        delete ex;
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    t_capturing = true;
+    s = gradient_models(nmodels, bc.pl.data(), bc.gp.data(), opts, bc.wk.data(), bc.io.data(), st, false);
+    t_capturing = false;
+    e = cudaStreamEndCapture(st, &ex->graph);
+    if (s == FWI_OK && e != cudaSuccess) s = cuda_fail(e, "cudaStreamEndCapture");
+    if (s == FWI_OK && (e = cudaGraphInstantiate(&ex->exec, ex->graph, 0)) != cudaSuccess)
+        s = cuda_fail(e, "cudaGraphInstantiate");
+    if (s != FWI_OK) {
+        if (ex->graph) cudaGraphDestroy(ex->graph);
+        delete ex;
+        return s;
+    }
+    for (int i = 0; i < 3; ++i) ex->launches[i] = t_launch[i];
+    *out = ex;
+    t_err.clear();
+    return FWI_OK;
+}
+
+fwi_status fwi_exec_run(fwi_exec *ex, void *stream)
+{
+    if (!ex || !ex->exec) return fail(FWI_ERR_INVALID_ARG, "exec is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    t_ev_recorded = ex->prof && t_prof && t_ev[0];
+    cudaError_t e = cudaGraphLaunch(ex->exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    for (int i = 0; i < 3; ++i) t_launch[i] = ex->launches[i];
+    return finish_models((int)ex->pl.size(), ex->pl.data(), ex->wk.data(), st);
+}
+
+fwi_status fwi_exec_destroy(fwi_exec *ex)
+{
+    if (!ex) return FWI_OK;
+    if (ex->exec) cudaGraphExecDestroy(ex->exec);
+    if (ex->graph) cudaGraphDestroy(ex->graph);
+    delete ex;
+    return FWI_OK;
 }
 
 } // extern "C"

@@ -216,12 +216,8 @@ def batch_workspace_bytes(grids, geoms, opts: Options) -> int:
     return int(nb.value)
 
 
-def batch_gradient(grids, geoms, vs, d_obs, opts: Options | None = None, *, want_pre=True,
-                   want_illum=True, want_offh=None, ws=None, stream=None) -> list:
-    """fwi_batch_gradient: the gradients of several independent models of
-    different sizes (same nt), every time level of all models in one launch.
-    Returns one dict per model, as adjoint_gradient."""
-    opts = opts or Options()
+def _batch_args(grids, geoms, vs, d_obs, opts, want_pre, want_illum, want_offh):
+    """Output tensors and ctypes arrays of a call over several models."""
     n = len(grids)
     if not (len(geoms) == len(vs) == len(d_obs) == n):
         raise ValueError("grids, geoms, vs and d_obs must have the same length")
@@ -239,25 +235,77 @@ def batch_gradient(grids, geoms, vs, d_obs, opts: Options | None = None, *, want
             r["offh"] = torch.empty((opts.hmax + 1,) + g.shape, dtype=torch.float32, device=v.device)
         res.append(r)
     misfit = torch.zeros(n, dtype=torch.float64, device=vs[0].device)
-    buf, nb = _ws(ws, batch_workspace_bytes(grids, geoms, opts))
-    g = (L.FwiGrid * n)(*[x.c() for x in grids])
-    ge = (L.FwiGeometry * n)(*[x.c() for x in geoms])
-    oc = opts.c()
+    for k, r in enumerate(res):
+        r["misfit"] = misfit[k]
 
-    def ptrs(key, src=None):
+    def ptrs(key=None, src=None):
         vals = [t.data_ptr() for t in src] if src is not None else [r[key].data_ptr() if key in r else None
                                                                      for r in res]
         return (ctypes.c_void_p * n)(*vals)
 
-    pre = ptrs("grad_pre") if want_pre else None
-    ill = ptrs("illum") if want_illum else None
-    off = ptrs("offh") if want_offh else None
-    L.check(L.load().fwi_batch_gradient(n, g, ge, ctypes.byref(oc), ptrs(None, vs), ptrs(None, d_obs),
-                                        ptrs("grad"), pre, _ptr(misfit), ill, off, _ptr(buf), nb,
-                                        _stream(stream)), "fwi_batch_gradient")
-    for k, r in enumerate(res):
-        r["misfit"] = misfit[k]
+    c = {"g": (L.FwiGrid * n)(*[x.c() for x in grids]), "ge": (L.FwiGeometry * n)(*[x.c() for x in geoms]),
+         "o": opts.c(), "v": ptrs(src=vs), "d": ptrs(src=d_obs), "grad": ptrs("grad"),
+         "pre": ptrs("grad_pre") if want_pre else None, "ill": ptrs("illum") if want_illum else None,
+         "off": ptrs("offh") if want_offh else None, "misfit": misfit}
+    return res, c
+
+
+def batch_gradient(grids, geoms, vs, d_obs, opts: Options | None = None, *, want_pre=True,
+                   want_illum=True, want_offh=None, ws=None, stream=None) -> list:
+    """fwi_batch_gradient: the gradients of several independent models of
+    different sizes (same nt), every time level of all models in one launch.
+    Returns one dict per model, as adjoint_gradient."""
+    opts = opts or Options()
+    res, c = _batch_args(grids, geoms, vs, d_obs, opts, want_pre, want_illum, want_offh)
+    buf, nb = _ws(ws, batch_workspace_bytes(grids, geoms, opts))
+    L.check(L.load().fwi_batch_gradient(len(grids), c["g"], c["ge"], ctypes.byref(c["o"]), c["v"], c["d"],
+                                        c["grad"], c["pre"], _ptr(c["misfit"]), c["ill"], c["off"], _ptr(buf),
+                                        nb, _stream(stream)), "fwi_batch_gradient")
     return res
+
+
+class GradientGraph:
+    """fwi_exec: the gradient of one or several models recorded once as a CUDA
+    graph, bound to fixed buffers, and replayed by run(). Inputs: the tensors
+    `vs` and `d_obs` given here (update them in place between runs). Outputs:
+    the same dicts, rewritten by every run. The graph runs on its own stream,
+    ordered after the caller's current stream and before its next work."""
+
+    def __init__(self, grids, geoms, vs, d_obs, opts: Options | None = None, *, want_pre=True,
+                 want_illum=True, want_offh=None, ws=None):
+        opts = opts or Options()
+        self.inputs = (list(vs), list(d_obs))
+        self.results, c = _batch_args(grids, geoms, vs, d_obs, opts, want_pre, want_illum, want_offh)
+        self._c = c  # keep the ctypes arrays alive with the graph
+        self.buf, nb = _ws(ws, batch_workspace_bytes(grids, geoms, opts))
+        self.stream = torch.cuda.Stream(device=vs[0].device)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        h = ctypes.c_void_p(0)
+        L.check(L.load().fwi_exec_gradient_create(len(grids), c["g"], c["ge"], ctypes.byref(c["o"]), c["v"],
+                                                  c["d"], c["grad"], c["pre"], _ptr(c["misfit"]), c["ill"],
+                                                  c["off"], _ptr(self.buf), nb, _stream(self.stream),
+                                                  ctypes.byref(h)), "fwi_exec_gradient_create")
+        self._h = h
+
+    def run(self) -> list:
+        if not self._h:
+            raise RuntimeError("the graph was closed")
+        cur = torch.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        L.check(L.load().fwi_exec_run(self._h, _stream(self.stream)), "fwi_exec_run")
+        cur.wait_stream(self.stream)
+        return self.results
+
+    def close(self):
+        if self._h:
+            L.load().fwi_exec_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def illumination(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options | None = None, *,

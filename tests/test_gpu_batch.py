@@ -122,3 +122,31 @@ def test_uneven_batch_full_size(torch_cuda):
         assert rel(batch[k]["grad"].cpu(), one["grad"].cpu()) <= 1e-4, k
         assert rel(batch[k]["illum"].cpu(), one["illum"].cpu()) <= 1e-4, k
         assert abs(float(batch[k]["misfit"]) - float(one["misfit"])) <= 1e-9 * float(one["misfit"])
+
+
+def test_recorded_gradient_graph(torch_cuda):
+    """fwi_exec: the gradient recorded once as a CUDA graph and replayed gives
+    the direct call's outputs, run after run, and follows in-place changes of
+    the velocity between runs."""
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import fwi
+    probs = small_models(nt=200)
+    grids, geoms, vs, dobs = gpu_case(torch, probs)
+    opts = fwi.Options(misfit="integral", hmax=2, precond="offset")
+    g1 = fwi.GradientGraph(grids[1:2], geoms[1:2], [vs[1]], [dobs[1]], opts)
+    gb = fwi.GradientGraph(grids, geoms, vs, dobs, opts)
+    try:
+        for rep in range(2):
+            r1 = g1.run()[0]
+            direct = fwi.adjoint_gradient(grids[1], geoms[1], vs[1], dobs[1], opts)
+            for key in ("grad", "grad_pre", "illum", "offh"):
+                assert rel(r1[key].cpu(), direct[key].cpu()) <= 1e-6, (rep, key)
+            assert abs(float(r1["misfit"]) - float(direct["misfit"])) <= 1e-12 * float(direct["misfit"])
+            vs[1].mul_(1.01)  # the next run models the changed velocity
+        rb = gb.run()
+        batch = fwi.batch_gradient(grids, geoms, vs, dobs, opts)
+        for k in range(3):
+            assert rel(rb[k]["grad"].cpu(), batch[k]["grad"].cpu()) <= 1e-6, k
+    finally:
+        g1.close()
+        gb.close()
