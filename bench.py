@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--variant", choices=["full", "plain"], default="full")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="call fwi_adjoint_gradient directly instead of replaying the recorded gradient")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
     ap.add_argument("--shots", type=int, default=0, help="use only the first N shots (profiling)")
     ap.add_argument("--nt", type=int, default=0, help="use only the first N time levels (profiling)")
@@ -272,6 +274,17 @@ def run_ours(args):
         def gradient(v_, d_, wav_):
             gg = fwi.Geometry(gsrc, grec, torch.cat([wav_] * world))
             return D.sharded_gradient(grid, gg, v_, d_, opts, rank=rank, world=world, compute=compute)
+    elif not args.no_graph:
+        # the gradient recorded once as a CUDA graph on these buffers (inputs
+        # are updated in place: v, d_obs, the wavelet), replayed every step
+        fwi.profile(True)  # phase events recorded into the graph
+        graph = fwi.GradientGraph([grid], [geom], [v], [d_obs], opts, ws=ws)
+
+        def gradient(v_, d_, wav_):
+            assert v_ is v and d_ is d_obs and wav_ is geom.wavelet
+            r = graph.run()[0]
+            phase_box.append(fwi.last_phase_times())
+            return r
     else:
         def gradient(v_, d_, wav_):
             nonlocal out
@@ -313,9 +326,8 @@ def run_ours(args):
         h_obs = d_obs.cpu().pin_memory()
         h_wav = geom.wavelet.cpu().pin_memory()
         hosts = {k: torch.empty(t.shape, dtype=t.dtype).pin_memory() for k, t in out.items()}
-        d_v = torch.empty_like(v)
-        d_o = torch.empty_like(d_obs)
-        d_w = torch.empty_like(geom.wavelet)
+        # the step's own input buffers receive each step's host inputs
+        d_v, d_o, d_w = v, d_obs, geom.wavelet
         h2d = h_v.numel() * 4 + h_obs.numel() * 4 + h_wav.numel() * 4
         d2h = sum(t.numel() * t.element_size() for t in hosts.values())
         barrier()
