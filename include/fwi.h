@@ -198,6 +198,23 @@ fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geom
                               float *const *grad, float *const *grad_pre, double *misfit, float *const *illum,
                               float *const *offh, void *ws, size_t ws_bytes, void *stream);
 
+/* Tile autotuning: times every compiled tile variant and shot-chunk size of
+   the gradient's forward step (with the offset Hessian if opts->hmax >= 0)
+   and of its backward step, for a few time levels of this very problem (v,
+   geometry, a workspace of FWI_OP_GRADIENT), and keeps the fastest for the
+   process, keyed by kind of step, padded grid shape and shot count: later
+   plans of the same shape use them (a batch uses model 0's). choice: NULL
+   or int[4] = forward variant, forward chunk, backward variant, backward
+   chunk. The timing leaves ws in an unspecified state (the next call's
+   set-up rewrites it). fwi_autotune_reset() forgets all choices. */
+fwi_status fwi_autotune(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
+                        void *ws, size_t ws_bytes, void *stream, int *choice);
+/* Keep a given choice (int[4] as above) for this problem's shape, as if
+   fwi_autotune had picked it: to reproduce a tuning, or to pin a variant. */
+fwi_status fwi_autotune_set(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                            const int *choice);
+fwi_status fwi_autotune_reset(void);
+
 /* A recorded gradient: fwi_exec_gradient_create() checks its arguments as
    fwi_batch_gradient() does (nmodels = 1 is fwi_adjoint_gradient), uploads
    the geometry tables into ws, and records the call's device work -- set-up,

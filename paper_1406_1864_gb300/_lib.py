@@ -76,6 +76,10 @@ _SIGS = {
                                  P(c_void_p), P(c_void_p), P(c_void_p), c_void_p, P(c_void_p),
                                  P(c_void_p), c_void_p, c_size_t, c_void_p, P(c_void_p)],
     "fwi_exec_run": [c_void_p, c_void_p],
+    "fwi_autotune": [P(FwiGrid), P(FwiGeometry), P(FwiOptions), c_void_p, c_void_p, c_size_t, c_void_p,
+                     P(c_int)],
+    "fwi_autotune_reset": [],
+    "fwi_autotune_set": [P(FwiGrid), P(FwiGeometry), P(FwiOptions), P(c_int)],
     "fwi_exec_destroy": [c_void_p],
     "fwi_profile_enable": [c_int],
     "fwi_profile_last": [P(FwiPhaseTimes)],

@@ -245,10 +245,12 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
     tk(pl.tab_src, (size_t)pl.ns * sizeof(int));
     tk(pl.tab_srcij, (size_t)pl.ns * sizeof(int2));
     const size_t nent = (size_t)pl.ns * pl.nrec;
-    tk(pl.tab_fptr, ((size_t)pl.tf.ntx * pl.tf.ntz * pl.ns + 1) * sizeof(int));
+    // receiver tables: room for the tiling with the most tiles (any variant)
+    const size_t mt = (size_t)max_tiles(L);
+    tk(pl.tab_fptr, (mt * pl.ns + 1) * sizeof(int));
     tk(pl.tab_fent, std::max<size_t>(nent, 1) * sizeof(int2));
     if (pl.need_bwd) {
-        tk(pl.tab_bptr, ((size_t)pl.tb.ntx * pl.tb.ntz * pl.ns + 1) * sizeof(int));
+        tk(pl.tab_bptr, (mt * pl.ns + 1) * sizeof(int));
         tk(pl.tab_bent, std::max<size_t>(nent, 1) * sizeof(int2));
         tk(pl.tab_bshot, std::max<size_t>(nent, 1) * sizeof(int));
     }
@@ -433,9 +435,12 @@ fwi_status restore_snapshot(const Plan &pl, void *ws, int j, float *u, float *up
 // nm > 1: one batched launch per time level, sponge checkpoints only). Model
 // k's plan, geometry, workspace and outputs are pl[k], ge[k], ws[k], seis[k],
 // acc_i[k], acc_h[k] (outputs may be null).
+// (levels [n0, n1) only, and events around the step launches, when timing
+// tile variants)
 fwi_status run_forward_models(int nm, const Plan *pl, const fwi_geometry *const *ge, void *const *ws,
                               float *const *seis, bool save, float *const *acc_i, float *const *acc_h, int illum_utt,
-                              cudaStream_t st)
+                              cudaStream_t st, int n0 = 0, int n1 = -1, cudaEvent_t ev0 = nullptr,
+                              cudaEvent_t ev1 = nullptr)
 {
     cudaError_t e;
     std::vector<FwdArgs> a(nm);
@@ -443,9 +448,9 @@ fwi_status run_forward_models(int nm, const Plan *pl, const fwi_geometry *const 
     std::vector<std::array<float *, 2>> U(nm);
     std::vector<std::array<CUtensorMap, 2>> mh(nm), mp(nm);
     const bool offh = pl[0].with_offh && acc_h[0];
-    int hx, hy, px, py;
-    step_boxes(offh ? STEP_FWD_OFFH : STEP_FWD, hx, hy, px, py);
     for (int k = 0; k < nm; ++k) {
+        int hx, hy, px, py;
+        step_boxes(offh ? STEP_FWD_OFFH : STEP_FWD, pl[k].tf, hx, hy, px, py);
         const Plan &p = pl[k];
         void *w = ws[k];
         if (acc_i[k] && (e = cudaMemsetAsync(acc_i[k], 0, p.acc_i.bytes, st)) != cudaSuccess)
@@ -472,7 +477,9 @@ fwi_status run_forward_models(int nm, const Plan *pl, const fwi_geometry *const 
     }
     const bool capture = nm == 1 && save && pl[0].snap;
     const int nt = pl[0].nt;
-    for (int n = 0; n < nt; ++n) {
+    if (n1 < 0) n1 = nt;
+    if (ev0) cudaEventRecord(ev0, st);
+    for (int n = n0; n < n1; ++n) {
         if (capture && n % pl[0].K == 0 && n <= nt - 2) {
             // snapshot n / K of the state (u^n, u^{n-1}) before step n
             fwi_status sc = capture_snapshot(pl[0], ws[0], n / pl[0].K, U[0][n & 1], U[0][(n + 1) & 1], st);
@@ -490,6 +497,7 @@ fwi_status run_forward_models(int nm, const Plan *pl, const fwi_geometry *const 
         if (e != cudaSuccess) return cuda_fail(e, "forward step");
         t_launch[0]++;
     }
+    if (ev1) cudaEventRecord(ev1, st);
     for (int k = 0; k < nm; ++k)
         for (int b = 0; b < 2; ++b) {
             if ((e = launch_check_finite(U[k][b], (long long)pl[k].ns * pl[k].L.fstride, at<int>(ws[k], pl[k].scal, 8),
@@ -528,8 +536,8 @@ fwi_status run_backward_segments(const Plan &pl, const fwi_geometry *ge, void *w
     if (pl.seg.bytes && (e = cudaMemsetAsync(at<char>(ws, pl.seg), 0, pl.seg.bytes, st)) != cudaSuccess)
         return cuda_fail(e, "memset");
     int fhx, fhy, fpx, fpy, bhx, bhy, bpx, bpy;
-    step_boxes(STEP_FWD, fhx, fhy, fpx, fpy);
-    step_boxes(STEP_BWD, bhx, bhy, bpx, bpy);
+    step_boxes(STEP_FWD, pl.tr, fhx, fhy, fpx, fpy);
+    step_boxes(STEP_BWD, pl.tb, bhx, bhy, bpx, bpy);
     std::vector<CUtensorMap> fh(K + 1), fp(K + 1), bh(K + 1);
     for (int i = 0; i <= K; ++i)
         if (!encode_field_map(&fh[i], S[i], pl.L, pl.ns, fhx, fhy) ||
@@ -577,17 +585,18 @@ fwi_status run_backward_segments(const Plan &pl, const fwi_geometry *ge, void *w
 // launch per time level, sponge checkpoints only), adjoint source adj[k]
 // [ns][nt][nrec] of model k
 fwi_status run_backward_models(int nm, const Plan *pl, const fwi_geometry *const *ge, void *const *ws,
-                               const float *const *adj, cudaStream_t st)
+                               const float *const *adj, cudaStream_t st, int m_hi = -1, int m_lo = 1,
+                               cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
 {
     cudaError_t e;
     std::vector<BwdArgs> a(nm);
     std::vector<Tiling> til(nm);
     std::vector<std::array<float *, 2>> U(nm), Pp(nm);
     std::vector<std::array<CUtensorMap, 2>> uh(nm), up(nm), ph(nm), pp(nm);
-    int hx, hy, px, py;
-    step_boxes(STEP_BWD, hx, hy, px, py);
     for (int k = 0; k < nm; ++k) {
         const Plan &p = pl[k];
+        int hx, hy, px, py;
+        step_boxes(STEP_BWD, p.tb, hx, hy, px, py);
         void *w = ws[k];
         for (int b = 0; b < 2; ++b)
             if ((e = cudaMemsetAsync(at<char>(w, p.p[b]), 0, p.p[b].bytes, st)) != cudaSuccess)
@@ -630,7 +639,9 @@ fwi_status run_backward_models(int nm, const Plan *pl, const fwi_geometry *const
         return run_backward_segments(pl[0], ge[0], ws[0], a[0], U0, P0, ph0, pp0, st);
     }
     const int nt = pl[0].nt;
-    for (int m = nt - 1; m >= 1; --m) {
+    if (m_hi < 0) m_hi = nt - 1;
+    if (ev0) cudaEventRecord(ev0, st);
+    for (int m = m_hi; m >= m_lo; --m) {
         for (int k = 0; k < nm; ++k) {
             a[k].m = m;
             a[k].c.sched = at<int>(ws[0], pl[0].sched) + nt + m;
@@ -645,6 +656,7 @@ fwi_status run_backward_models(int nm, const Plan *pl, const fwi_geometry *const
         if (e != cudaSuccess) return cuda_fail(e, "backward step");
         t_launch[1]++;
     }
+    if (ev1) cudaEventRecord(ev1, st);
     for (int k = 0; k < nm; ++k) {
         if ((e = launch_check_finite(Pp[k][0], (long long)pl[k].ns * pl[k].L.fstride, at<int>(ws[k], pl[k].scal, 8),
                                      st)) != cudaSuccess)
@@ -809,6 +821,11 @@ fwi_status make_batch(int nm, const fwi_grid *grids, const fwi_geometry *geoms, 
         if (grids[k].nt != grids[0].nt)
             return fail(FWI_ERR_INVALID_ARG, "model %d has nt=%d, model 0 nt=%d: a batch shares nt", k, grids[k].nt,
                         grids[0].nt);
+        if (k > 0) { // a launch runs one kernel: model 0's tile variants for all
+            const StepKind fk = pl[k].with_offh ? STEP_FWD_OFFH : STEP_FWD;
+            pl[k].tf = make_tiling(pl[k].L, pl[k].ns, fk, pl[0].tf.variant, pl[0].tf.chunk);
+            pl[k].tb = make_tiling(pl[k].L, pl[k].ns, STEP_BWD, pl[0].tb.variant, pl[0].tb.chunk);
+        }
         base[k] = total;
         total = align_up(total + pl[k].total);
     }
@@ -980,6 +997,119 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
     t_launch[2] += 2;
     prof_record(3, st);
     return finish(pl, ws, st);
+}
+
+fwi_status fwi_autotune(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
+                        void *ws, size_t ws_bytes, void *stream, int *choice)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_GRADIENT, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v) return fail(FWI_ERR_INVALID_ARG, "v is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool prof = t_prof;
+    t_prof = false;
+    struct Ev {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Ev()
+        {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&ev.a)) != cudaSuccess || (e = cudaEventCreate(&ev.b)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    const int nt = pl.nt;
+    const int nlev = std::min(8, nt - 1), n0 = std::max(0, (nt - nlev) / 2);
+    float *acc_i = at<float>(ws, pl.acc_i), *acc_h = pl.with_offh ? at<float>(ws, pl.acc_h) : nullptr;
+    float *syn = at<float>(ws, pl.syn);
+    const StepKind fk = pl.with_offh ? STEP_FWD_OFFH : STEP_FWD;
+    const StepKind kinds[2] = {fk, STEP_BWD};
+    int best[2][2] = {{0, 0}, {0, 0}};
+    for (int kk = 0; kk < 2; ++kk) {
+        const StepKind kind = kinds[kk];
+        const int *chunks = nullptr;
+        const int nc = step_chunks(kind, &chunks), nv = step_variants(kind);
+        float best_ms = 1e30f;
+        for (int vi = 0; vi < nv; ++vi)
+            for (int ci = 0; ci < nc; ++ci) {
+                Plan p = pl;
+                if (kk == 0)
+                    p.tf = make_tiling(p.L, p.ns, kind, vi, chunks[ci]);
+                else
+                    p.tb = make_tiling(p.L, p.ns, kind, vi, chunks[ci]);
+                if ((s = upload_tables(p, geom, ws, st)) != FWI_OK) break;
+                float ms = 0.f;
+                for (int rep = 0; rep < 2 && s == FWI_OK; ++rep) { // first pass warms up
+                    if ((e = cudaMemsetAsync(at<char>(ws, p.sched), 0, p.sched.bytes, st)) != cudaSuccess) {
+                        s = cuda_fail(e, "memset");
+                        break;
+                    }
+                    const fwi_geometry *gp = geom;
+                    void *wp = ws;
+                    if (kk == 0) {
+                        float *sp = syn;
+                        s = run_forward_models(1, &p, &gp, &wp, &sp, true, &acc_i, &acc_h, opts->illum_mode, st, n0,
+                                               n0 + nlev, ev.a, ev.b);
+                    } else {
+                        const float *ap = syn;
+                        // levels m in [1, nt-1] (the adjoint source has nt levels)
+                        s = run_backward_models(1, &p, &gp, &wp, &ap, st, std::min(nt - 1, n0 + nlev),
+                                                std::max(1, n0 + 1), ev.a, ev.b);
+                    }
+                    if (s == FWI_OK && (e = cudaEventSynchronize(ev.b)) != cudaSuccess) s = cuda_fail(e, "sync");
+                    if (s == FWI_OK) cudaEventElapsedTime(&ms, ev.a, ev.b);
+                }
+                if (s != FWI_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best[kk][0] = vi;
+                    best[kk][1] = chunks[ci];
+                }
+            }
+        if (s != FWI_OK) break;
+        step_tuned_store(kind, pl.L, pl.ns, best[kk][0], best[kk][1]);
+    }
+    t_prof = prof;
+    if (s != FWI_OK) return s;
+    // status words written while timing (the timing fields are not a
+    // gradient) are cleared by the next call's set-up
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronize");
+    if (choice) {
+        choice[0] = best[0][0];
+        choice[1] = best[0][1];
+        choice[2] = best[1][0];
+        choice[3] = best[1][1];
+    }
+    t_err.clear();
+    return FWI_OK;
+}
+
+fwi_status fwi_autotune_set(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                            const int *choice)
+{
+    if (!choice) return fail(FWI_ERR_INVALID_ARG, "choice is NULL");
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_GRADIENT, false, pl);
+    if (s != FWI_OK) return s;
+    const StepKind fk = pl.with_offh ? STEP_FWD_OFFH : STEP_FWD;
+    if (choice[0] < 0 || choice[0] >= step_variants(fk) || choice[2] < 0 || choice[2] >= step_variants(STEP_BWD))
+        return fail(FWI_ERR_INVALID_ARG, "variant outside the compiled ones (%d forward, %d backward)",
+                    step_variants(fk), step_variants(STEP_BWD));
+    if (choice[1] < 1 || choice[3] < 1) return fail(FWI_ERR_INVALID_ARG, "chunk must be >= 1");
+    step_tuned_store(fk, pl.L, pl.ns, choice[0], choice[1]);
+    step_tuned_store(STEP_BWD, pl.L, pl.ns, choice[2], choice[3]);
+    t_err.clear();
+    return FWI_OK;
+}
+
+fwi_status fwi_autotune_reset(void)
+{
+    step_tuned_clear();
+    return FWI_OK;
 }
 
 fwi_status fwi_batch_workspace_bytes(int nmodels, const fwi_grid *grids, const fwi_geometry *geoms,

@@ -157,15 +157,27 @@ enum : int {
 // Step kernels: `ctas` CTAs (one per resident slot) take chunks of `chunk`
 // shots of one tile from an atomic counter.
 struct Tiling {
+    int variant;   // compiled tile variant of the kind (0 = default)
     int tz;        // tile height
     int ntx, ntz;  // tiles
     int ctas;      // CTAs of one launch
     int chunk;     // shots per chunk
 };
 enum StepKind { STEP_FWD = 0, STEP_FWD_OFFH = 1, STEP_BWD = 2 };
-Tiling make_tiling(const Lay2D &L, int ns, StepKind kind);
+// tiling of a kind of step: the given variant / chunk, or (variant < 0,
+// chunk <= 0) the autotuned ones of this problem shape, else the defaults
+Tiling make_tiling(const Lay2D &L, int ns, StepKind kind, int variant = -1, int chunk = 0);
 // box sizes (x, y) of the halo and point tiles of a step kernel
-void step_boxes(StepKind kind, int &hx, int &hy, int &px, int &py);
+void step_boxes(StepKind kind, const Tiling &t, int &hx, int &hy, int &px, int &py);
+// most tiles of any variant (receiver tables are sized for it)
+int max_tiles(const Lay2D &L);
+// autotuning: compiled variants and chunk sizes of a kind, and the choices
+// kept per (kind, padded shape, shots) for the process
+int step_variants(StepKind kind);
+int step_chunks(StepKind kind, const int **chunks);
+void step_tuned_store(StepKind kind, const Lay2D &L, int ns, int variant, int chunk);
+bool step_tuned_lookup(StepKind kind, const Lay2D &L, int ns, int &variant, int &chunk);
+void step_tuned_clear();
 
 bool encode_field_map(CUtensorMap *map, const float *base, const Lay2D &L, int nfields, int bx, int by);
 cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st);

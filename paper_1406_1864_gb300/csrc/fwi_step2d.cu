@@ -40,6 +40,10 @@
 
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace fwi {
 
 
@@ -1027,89 +1031,80 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 
 // ---------------------------------------------------------------- launchers
 namespace {
-#ifndef FWI_F_ST
-#define FWI_F_ST 3
-#endif
-#ifndef FWI_H_ST
-#define FWI_H_ST 3
-#endif
-#ifndef FWI_B_ST
-#define FWI_B_ST 2
-#endif
-#ifndef FWI_CHUNK
-#define FWI_CHUNK 8
-#endif
-#ifndef FWI_CHUNK_OFFH
-#define FWI_CHUNK_OFFH 16
-#endif
-constexpr int CHUNK = FWI_CHUNK, CHUNK_OFFH = FWI_CHUNK_OFFH;
-#ifndef FWI_F_MINB
-#define FWI_F_MINB 4
-#endif
-#ifndef FWI_B_MINB
-#define FWI_B_MINB 4
-#endif
-#ifndef FWI_F_RZ
-#define FWI_F_RZ 2
-#endif
-#ifndef FWI_B_RZ
-#define FWI_B_RZ 2
-#endif
-// forward without the offset Hessian: 64 x 16 tiles
-constexpr int F_RZ = FWI_F_RZ, F_ST = FWI_F_ST, F_MINB = FWI_F_MINB;
-#ifndef FWI_H_MINB
-#define FWI_H_MINB 4
-#endif
-// forward with the offset Hessian: 64 x 8 tiles, halo 12
-constexpr int H_RZ = 1, H_ST = FWI_H_ST, H_MINB = FWI_H_MINB;
-// backward: 64 x 16 tiles
-constexpr int B_RZ = FWI_B_RZ, B_ST = FWI_B_ST, B_MINB = FWI_B_MINB;
+// Compiled tile variants of each kind of step (index 0 is the default; the
+// autotuner may pick another per problem shape): tile height 8 RZ rows,
+// ring stages, minimum resident CTAs per SM (the register cap).
+struct Variant {
+    int rz, smem;
+    const void *fn[2]; // one model per launch, batch of up to BATCH_MAX models
+    int occ[2];        // resident CTAs per SM (from the occupancy calculator)
+};
 
-// one model per launch, and batches of up to BATCH_MAX models
-#define K_FWD k_fwd_step<F_RZ, RADIUS, false, F_ST, F_MINB, 1>
-#define K_FWDH k_fwd_step<H_RZ, HMAX_LIMIT, true, H_ST, H_MINB, 1>
-#define K_BWD k_bwd_step<B_RZ, B_ST, B_MINB, 1>
-#define K_FWD_B k_fwd_step<F_RZ, RADIUS, false, F_ST, F_MINB, BATCH_MAX>
-#define K_FWDH_B k_fwd_step<H_RZ, HMAX_LIMIT, true, H_ST, H_MINB, BATCH_MAX>
-#define K_BWD_B k_bwd_step<B_RZ, B_ST, B_MINB, BATCH_MAX>
-constexpr int SMEM_FWD = FwdRing<F_RZ, RADIUS, false, F_ST>::SMEM;
-constexpr int SMEM_FWDH = FwdRing<H_RZ, HMAX_LIMIT, true, H_ST>::SMEM;
-constexpr int SMEM_BWD = BwdRing<B_RZ, B_ST>::SMEM;
+#define FWD_VARIANT(RZ, ST, MINB)                                                          \
+    {RZ, FwdRing<RZ, RADIUS, false, ST>::SMEM,                                             \
+     {(const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, 1>,                            \
+      (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, BATCH_MAX>},                   \
+     {0, 0}}
+#define FWDH_VARIANT(ST, MINB)                                                             \
+    {1, FwdRing<1, HMAX_LIMIT, true, ST>::SMEM,                                            \
+     {(const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, 1>,                          \
+      (const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, BATCH_MAX>},                 \
+     {0, 0}}
+#define BWD_VARIANT(RZ, ST, MINB)                                                          \
+    {RZ, BwdRing<RZ, ST>::SMEM,                                                            \
+     {(const void *)k_bwd_step<RZ, ST, MINB, 1>, (const void *)k_bwd_step<RZ, ST, MINB, BATCH_MAX>}, \
+     {0, 0}}
 
-int g_occ[3] = {0, 0, 0};   // resident CTAs per SM: forward, forward + offset Hessian, backward
-int g_occ_b[3] = {0, 0, 0}; // the same for the batched instances
+// forward: 64 x 16 tiles (3 stages, 4 CTAs/SM), 64 x 32 (2 stages), 64 x 8 (6 CTAs/SM)
+Variant g_var_f[] = {FWD_VARIANT(2, 3, 4), FWD_VARIANT(4, 2, 4), FWD_VARIANT(1, 3, 6)};
+// forward with the offset Hessian: 64 x 8 tiles, halo 12 (its 44 register
+// accumulators rule out taller tiles)
+Variant g_var_h[] = {FWDH_VARIANT(3, 4)};
+// backward: 64 x 16 tiles (2 stages, 4 CTAs/SM), 64 x 8 (5 CTAs/SM)
+Variant g_var_b[] = {BWD_VARIANT(2, 2, 4), BWD_VARIANT(1, 2, 5)};
+
+Variant *variants(StepKind k, int &n)
+{
+    if (k == STEP_FWD) {
+        n = (int)(sizeof g_var_f / sizeof g_var_f[0]);
+        return g_var_f;
+    }
+    if (k == STEP_FWD_OFFH) {
+        n = (int)(sizeof g_var_h / sizeof g_var_h[0]);
+        return g_var_h;
+    }
+    n = (int)(sizeof g_var_b / sizeof g_var_b[0]);
+    return g_var_b;
+}
+
+// shots per chunk tried by the autotuner (index 0 = default of the kind)
+const int CHUNKS_F[] = {8, 16};
+const int CHUNKS_H[] = {16, 8};
+
+std::once_flag g_prep_once;
 
 void prepare_kernels()
 {
-    static bool done = false;
-    if (done) return;
-    done = true;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    std::call_once(g_prep_once, [] {
+        int dev = 0;
+        const bool have_dev = cudaGetDevice(&dev) == cudaSuccess;
+        for (int k = 0; k < 3; ++k) {
+            int n = 0;
+            Variant *v = variants((StepKind)k, n);
+            for (int i = 0; i < n; ++i)
+                for (int b = 0; b < 2; ++b) {
+                    int occ = 0;
+                    if (have_dev) {
+                        cudaFuncSetAttribute(v[i].fn[b], cudaFuncAttributeMaxDynamicSharedMemorySize, v[i].smem);
+                        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v[i].fn[b], TPB, v[i].smem) !=
+                            cudaSuccess)
+                            occ = 0;
+                    }
+                    v[i].occ[b] = occ > 0 ? occ : 2;
+                }
+        }
         cudaGetLastError();
-        for (int k = 0; k < 3; ++k) g_occ[k] = g_occ_b[k] = 2;
-        return;
-    }
-    cudaFuncSetAttribute(K_FWD, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FWD);
-    cudaFuncSetAttribute(K_FWDH, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FWDH);
-    cudaFuncSetAttribute(K_BWD, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BWD);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[0], K_FWD, TPB, SMEM_FWD) != cudaSuccess) g_occ[0] = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[1], K_FWDH, TPB, SMEM_FWDH) != cudaSuccess) g_occ[1] = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[2], K_BWD, TPB, SMEM_BWD) != cudaSuccess) g_occ[2] = 0;
-    cudaFuncSetAttribute(K_FWD_B, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FWD);
-    cudaFuncSetAttribute(K_FWDH_B, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FWDH);
-    cudaFuncSetAttribute(K_BWD_B, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BWD);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_b[0], K_FWD_B, TPB, SMEM_FWD) != cudaSuccess)
-        g_occ_b[0] = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_b[1], K_FWDH_B, TPB, SMEM_FWDH) != cudaSuccess)
-        g_occ_b[1] = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_b[2], K_BWD_B, TPB, SMEM_BWD) != cudaSuccess)
-        g_occ_b[2] = 0;
-    cudaGetLastError();
-    for (int k = 0; k < 3; ++k) {
-        if (g_occ[k] < 1) g_occ[k] = 2;
-        if (g_occ_b[k] < 1) g_occ_b[k] = 2;
-    }
+    });
 }
 
 int sm_count_dev()
@@ -1127,6 +1122,17 @@ int sm_count_dev()
     }
     return n;
 }
+
+// autotuned (variant, chunk) per problem shape
+struct TuneKey {
+    int kind, nzp, nxp, ns;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(kind, nzp, nxp, ns) < std::tie(o.kind, o.nzp, o.nxp, o.ns);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tuned;
 
 // chunk counts of a launch's models and the number of CTAs to launch
 template <class A, int N>
@@ -1146,78 +1152,121 @@ int batch_fill(Batch<A, N> &b, const A *a, const Tiling *t, int nm, int occ)
     return (int)(total < slots ? total : slots);
 }
 
+template <class A, int N>
+cudaError_t launch_variant(const Variant &v, int b, Batch<A, N> &args, int ctas, cudaStream_t st)
+{
+    if (ctas <= 0) return cudaSuccess;
+    void *params[] = {&args};
+    return cudaLaunchKernel(v.fn[b], dim3(ctas), dim3(TPB), params, (size_t)v.smem, st);
+}
 } // namespace
 
-void step_boxes(StepKind kind, int &hx, int &hy, int &px, int &py)
+int step_variants(StepKind kind)
 {
-    int rz = kind == STEP_FWD ? F_RZ : (kind == STEP_FWD_OFFH ? H_RZ : B_RZ);
-    int halo = kind == STEP_FWD_OFFH ? HMAX_LIMIT : RADIUS;
-    hx = TX + 2 * halo;
-    hy = 8 * rz + 2 * RADIUS;
-    px = TX;
-    py = 8 * rz;
+    int n = 0;
+    variants(kind, n);
+    return n;
 }
 
-Tiling make_tiling(const Lay2D &L, int ns, StepKind kind)
+int step_chunks(StepKind kind, const int **chunks)
+{
+    *chunks = kind == STEP_FWD_OFFH ? CHUNKS_H : CHUNKS_F;
+    return 2;
+}
+
+void step_tuned_store(StepKind kind, const Lay2D &L, int ns, int variant, int chunk)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[TuneKey{kind, L.nzp, L.nxp, ns}] = {variant, chunk};
+}
+
+bool step_tuned_lookup(StepKind kind, const Lay2D &L, int ns, int &variant, int &chunk)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(TuneKey{kind, L.nzp, L.nxp, ns});
+    if (it == g_tuned.end()) return false;
+    variant = it->second.first;
+    chunk = it->second.second;
+    return true;
+}
+
+void step_tuned_clear()
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned.clear();
+}
+
+void step_boxes(StepKind kind, const Tiling &t, int &hx, int &hy, int &px, int &py)
+{
+    const int halo = kind == STEP_FWD_OFFH ? HMAX_LIMIT : RADIUS;
+    hx = TX + 2 * halo;
+    hy = t.tz + 2 * RADIUS;
+    px = TX;
+    py = t.tz;
+}
+
+int max_tiles(const Lay2D &L) { return ((L.nxp + TX - 1) / TX) * ((L.nzp + 7) / 8); }
+
+Tiling make_tiling(const Lay2D &L, int ns, StepKind kind, int variant, int chunk)
 {
     prepare_kernels();
+    int n = 0;
+    Variant *vs = variants(kind, n);
+    if (variant < 0 || variant >= n) {
+        int tv = 0, tc = 0;
+        if (step_tuned_lookup(kind, L, ns, tv, tc) && tv >= 0 && tv < n) {
+            variant = tv;
+            if (chunk <= 0) chunk = tc;
+        } else {
+            variant = 0;
+        }
+    }
+    if (chunk <= 0) chunk = kind == STEP_FWD_OFFH ? CHUNKS_H[0] : CHUNKS_F[0];
     Tiling t;
-    int hx, hy, px, py;
-    step_boxes(kind, hx, hy, px, py);
-    t.tz = py;
+    t.variant = variant;
+    t.tz = 8 * vs[variant].rz;
     t.ntx = (L.nxp + TX - 1) / TX;
     t.ntz = (L.nzp + t.tz - 1) / t.tz;
     const int tiles = t.ntx * t.ntz;
-    t.chunk = kind == STEP_FWD_OFFH ? CHUNK_OFFH : CHUNK;
-    if (t.chunk > ns) t.chunk = ns;
+    t.chunk = chunk > ns ? ns : chunk;
     const long long chunks = (long long)tiles * ((ns + t.chunk - 1) / t.chunk);
-    const long long slots = (long long)sm_count_dev() * g_occ[kind];
+    const long long slots = (long long)sm_count_dev() * vs[variant].occ[0];
     t.ctas = (int)(chunks < slots ? chunks : slots);
     return t;
 }
 
 cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st)
 {
+    int n = 0;
+    const Variant &v = variants(with_offh ? STEP_FWD_OFFH : STEP_FWD, n)[t.variant];
     Batch<FwdArgs, 1> b;
-    const int ctas = batch_fill(b, &a, &t, 1, g_occ[with_offh ? STEP_FWD_OFFH : STEP_FWD]);
-    if (ctas <= 0) return cudaSuccess;
-    if (with_offh)
-        K_FWDH<<<ctas, TPB, SMEM_FWDH, st>>>(b);
-    else
-        K_FWD<<<ctas, TPB, SMEM_FWD, st>>>(b);
-    return cudaGetLastError();
+    return launch_variant(v, 0, b, batch_fill(b, &a, &t, 1, v.occ[0]), st);
 }
 
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st)
 {
+    int n = 0;
+    const Variant &v = variants(STEP_BWD, n)[t.variant];
     Batch<BwdArgs, 1> b;
-    const int ctas = batch_fill(b, &a, &t, 1, g_occ[STEP_BWD]);
-    if (ctas <= 0) return cudaSuccess;
-    K_BWD<<<ctas, TPB, SMEM_BWD, st>>>(b);
-    return cudaGetLastError();
+    return launch_variant(v, 0, b, batch_fill(b, &a, &t, 1, v.occ[0]), st);
 }
 
 cudaError_t launch_fwd_batch(const FwdArgs *a, const Tiling *t, int nm, bool with_offh, cudaStream_t st)
 {
     if (nm < 1 || nm > BATCH_MAX) return cudaErrorInvalidValue;
+    int n = 0;
+    const Variant &v = variants(with_offh ? STEP_FWD_OFFH : STEP_FWD, n)[t[0].variant];
     Batch<FwdArgs, BATCH_MAX> b;
-    const int ctas = batch_fill(b, a, t, nm, g_occ_b[with_offh ? STEP_FWD_OFFH : STEP_FWD]);
-    if (ctas <= 0) return cudaSuccess;
-    if (with_offh)
-        K_FWDH_B<<<ctas, TPB, SMEM_FWDH, st>>>(b);
-    else
-        K_FWD_B<<<ctas, TPB, SMEM_FWD, st>>>(b);
-    return cudaGetLastError();
+    return launch_variant(v, 1, b, batch_fill(b, a, t, nm, v.occ[1]), st);
 }
 
 cudaError_t launch_bwd_batch(const BwdArgs *a, const Tiling *t, int nm, cudaStream_t st)
 {
     if (nm < 1 || nm > BATCH_MAX) return cudaErrorInvalidValue;
+    int n = 0;
+    const Variant &v = variants(STEP_BWD, n)[t[0].variant];
     Batch<BwdArgs, BATCH_MAX> b;
-    const int ctas = batch_fill(b, a, t, nm, g_occ_b[STEP_BWD]);
-    if (ctas <= 0) return cudaSuccess;
-    K_BWD_B<<<ctas, TPB, SMEM_BWD, st>>>(b);
-    return cudaGetLastError();
+    return launch_variant(v, 1, b, batch_fill(b, a, t, nm, v.occ[1]), st);
 }
 
 // Tensor map over `nfields` stored fields [nfields][rows][pitch] (float32)

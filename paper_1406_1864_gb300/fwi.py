@@ -352,6 +352,35 @@ def precondition(grid: Grid, grad: torch.Tensor, scale: torch.Tensor, kind: str,
     return out
 
 
+def autotune(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options | None = None, *, ws=None,
+             stream=None) -> dict:
+    """fwi_autotune: time the compiled tile variants and chunk sizes of this
+    problem's forward and backward steps and keep the fastest for later calls
+    of the same shape. Returns the choice."""
+    opts = opts or Options()
+    _dev(v, "v", grid.shape)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "gradient"))
+    g, ge, oc = grid.c(), geom.c(), opts.c()
+    ch = (ctypes.c_int * 4)()
+    L.check(L.load().fwi_autotune(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(oc), _ptr(v), _ptr(buf), nb,
+                                  _stream(stream), ch), "fwi_autotune")
+    return {"forward_variant": ch[0], "forward_chunk": ch[1], "backward_variant": ch[2], "backward_chunk": ch[3]}
+
+
+def autotune_set(grid: Grid, geom: Geometry, opts: Options | None, choice: dict):
+    """fwi_autotune_set: keep this choice (as returned by autotune) for the shape."""
+    opts = opts or Options()
+    g, ge, oc = grid.c(), geom.c(), opts.c()
+    ch = (ctypes.c_int * 4)(choice["forward_variant"], choice["forward_chunk"], choice["backward_variant"],
+                            choice["backward_chunk"])
+    L.check(L.load().fwi_autotune_set(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(oc), ch),
+            "fwi_autotune_set")
+
+
+def autotune_reset():
+    L.check(L.load().fwi_autotune_reset(), "fwi_autotune_reset")
+
+
 def profile(on: bool = True):
     L.check(L.load().fwi_profile_enable(int(on)), "fwi_profile_enable")
 

@@ -32,7 +32,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ["fwi_forward", "fwi_adjoint_gradient", "fwi_illumination", "fwi_offset_hessian_diag",
                  "fwi_adjoint_apply", "fwi_workspace_bytes", "fwi_last_error", "fwi_batch_gradient",
-                 "fwi_batch_workspace_bytes", "fwi_exec_gradient_create", "fwi_exec_run", "fwi_exec_destroy"]:
+                 "fwi_batch_workspace_bytes", "fwi_exec_gradient_create", "fwi_exec_run", "fwi_exec_destroy",
+                 "fwi_autotune", "fwi_autotune_reset", "fwi_autotune_set"]:
         assert must in names
 
 
