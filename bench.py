@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--variant", choices=["full", "plain"], default="full")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default tile variants (no fwi_autotune)")
     ap.add_argument("--no-graph", action="store_true",
                     help="call fwi_adjoint_gradient directly instead of replaying the recorded gradient")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
@@ -259,6 +260,9 @@ def run_ours(args):
     del v_true
     out = None
     phase_box = []
+    tiles = None
+    if not args.no_autotune:  # tile variants timed on this problem (not timed)
+        tiles = fwi.autotune(grid, geom, v, opts, ws=ws)
 
     if world > 1:
         # the global batch: every rank's shard is this per-GPU batch
@@ -393,7 +397,9 @@ def run_ours(args):
                        "grid": [prob.nz, prob.nx], "dx_m": prob.dx, "dt_s": prob.dt, "nt": prob.nt,
                        "shots": prob.nshots, "receivers": prob.nrec, "sponge": prob.sponge,
                        "misfit": opts.misfit, "offset_hessian_hmax": opts.hmax,
-                       "precond": opts.precond, "parallelism": "1 GPU" if world == 1 else
+                       "precond": opts.precond, "tiles": tiles or "default",
+                       "graph": world == 1 and not args.no_graph,
+                       "parallelism": "1 GPU" if world == 1 else
                        f"shots x{world} (each GPU {prob.nshots} shots; NCCL all-reduce of the sums)",
                        "l2": "inputs larger than L2 (wavefields of all shots ~0.6 GB per step)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
