@@ -122,6 +122,9 @@ typedef struct {
                        FWI_SNAP_BF16 / FWI_SNAP_F16S (u^n and u^n - u^{n-1},
                        each scaled by its own max-abs, as bfloat16 / float16) */
     int snap_interval; /* levels between snapshots; 0: ceil(sqrt(nt))       */
+    int shot_group; /* 3-D: shots modelled at a time (the workspace holds one
+                       group; the sums over groups are the sums over shots);
+                       0: all shots at once                                    */
 } fwi_options;
 
 /* Per-phase device times of the last call on this host thread, when enabled

@@ -143,6 +143,7 @@ fwi_status check_opts(const fwi_options *o, int op)
     if (o->snap_prec < FWI_SNAP_F32 || o->snap_prec > FWI_SNAP_F16S)
         return fail(FWI_ERR_INVALID_ARG, "snap_prec=%d unknown", o->snap_prec);
     if (o->snap_interval < 0) return fail(FWI_ERR_INVALID_ARG, "snap_interval=%d must be >= 0", o->snap_interval);
+    if (o->shot_group < 0) return fail(FWI_ERR_INVALID_ARG, "shot_group=%d must be >= 0", o->shot_group);
     return FWI_OK;
 }
 
@@ -801,6 +802,543 @@ fwi_status gradient_models(int nm, const Plan *pl, const fwi_geometry *const *ge
     return FWI_OK;
 }
 
+// ---------------------------------------------------------------------- 3-D
+// Stability limit of v dt / dx in 3-D: (v dt/dx)^2 * 3 * max|symbol| <= 4
+// with the 1-D max|symbol| of the 2-D limit above.
+constexpr float CFL_3D = 0.4529f;
+
+fwi_status check_grid3(const fwi_grid *g)
+{
+    if (!g) return fail(FWI_ERR_INVALID_ARG, "grid is NULL");
+    if (g->nz < 1 || g->ny < 1 || g->nx < 1)
+        return fail(FWI_ERR_INVALID_ARG, "nz=%d ny=%d nx=%d must be >= 1", g->nz, g->ny, g->nx);
+    if (g->nt < 2) return fail(FWI_ERR_INVALID_ARG, "nt=%d must be >= 2", g->nt);
+    if (g->sponge < 1 || g->sponge > 64) return fail(FWI_ERR_INVALID_ARG, "sponge=%d outside 1..64", g->sponge);
+    if (!(g->dx > 0.f) || !std::isfinite(g->dx)) return fail(FWI_ERR_INVALID_ARG, "dx must be > 0");
+    if (!(g->dt > 0.f) || !std::isfinite(g->dt)) return fail(FWI_ERR_INVALID_ARG, "dt must be > 0");
+    if (!(g->vref > 0.f) || !std::isfinite(g->vref)) return fail(FWI_ERR_INVALID_ARG, "vref must be > 0");
+    if (!(g->refl > 0.f && g->refl < 1.f)) return fail(FWI_ERR_INVALID_ARG, "refl must be in (0,1)");
+    return FWI_OK;
+}
+
+fwi_status check_geom3(const fwi_grid *g, const fwi_geometry *ge, bool coords)
+{
+    if (!ge) return fail(FWI_ERR_INVALID_ARG, "geometry is NULL");
+    if (ge->nshots < 1) return fail(FWI_ERR_INVALID_ARG, "nshots=%d must be >= 1", ge->nshots);
+    if (ge->nrec < 0) return fail(FWI_ERR_INVALID_ARG, "nrec=%d must be >= 0", ge->nrec);
+    if ((long long)ge->nshots * ge->nrec >= (1LL << 31)) return fail(FWI_ERR_INVALID_ARG, "too many receivers");
+    if (!coords) return FWI_OK;
+    if (!ge->src) return fail(FWI_ERR_INVALID_ARG, "geometry.src is NULL");
+    if (ge->nrec > 0 && !ge->rec) return fail(FWI_ERR_INVALID_ARG, "geometry.rec is NULL");
+    if (!ge->wavelet) return fail(FWI_ERR_INVALID_ARG, "geometry.wavelet is NULL");
+    auto inside = [&](const int *c) {
+        return c[0] >= 0 && c[0] < g->nz && c[1] >= 0 && c[1] < g->ny && c[2] >= 0 && c[2] < g->nx;
+    };
+    for (int s = 0; s < ge->nshots; ++s) {
+        const int *c = ge->src + 3 * s;
+        if (!inside(c))
+            return fail(FWI_ERR_INVALID_ARG, "source of shot %d at (%d,%d,%d) outside the model", s, c[0], c[1], c[2]);
+        for (int r = 0; r < ge->nrec; ++r) {
+            const int *q = ge->rec + 3 * ((long long)s * ge->nrec + r);
+            if (!inside(q))
+                return fail(FWI_ERR_INVALID_ARG, "receiver %d of shot %d at (%d,%d,%d) outside the model", r, s, q[0],
+                            q[1], q[2]);
+        }
+    }
+    return FWI_OK;
+}
+
+Lay3D make_layout3(const fwi_grid *g)
+{
+    Lay3D L{};
+    L.nz = g->nz;
+    L.ny = g->ny;
+    L.nx = g->nx;
+    L.P = g->sponge;
+    L.nzp = g->nz + 2 * g->sponge;
+    L.nyp = g->ny + 2 * g->sponge;
+    L.nxp = g->nx + 2 * g->sponge;
+    L.pitch = (int)align_up((size_t)(GXL + L.nxp + GXR), 32);
+    L.rows = L.nyp + 2 * GY;
+    L.planes = L.nzp + 2 * GZ;
+    L.plane = (long long)L.rows * L.pitch;
+    L.fstride = (long long)align_up((size_t)(L.planes * L.plane), 64);
+    L.dt = g->dt;
+    L.dx = g->dx;
+    const double etamax = 3.0 * g->vref * std::log(1.0 / g->refl) / (2.0 * g->sponge * g->dx);
+    L.etamax_dt = (float)(etamax * g->dt);
+    L.inv_p2 = (float)(1.0 / ((double)g->sponge * g->sponge));
+    return L;
+}
+
+// One 3-D call: the shots are modelled in groups of G (opts->shot_group), each
+// group in the same workspace; accumulators and the misfit sum over groups.
+struct Plan3 {
+    Lay3D L;
+    int ns_all = 0, G = 0, nt = 0, nrec = 0, op = 0;
+    bool need_bwd = false;
+    Tiling3 tf{}, tb{};
+    Part scal, sched, c2, damp, u[2], p[2], syn, acc_i, acc_g, tab, snaps, snap_max, seg;
+    size_t tab_src = 0, tab_ptr = 0, tab_ent = 0, tab_zr = 0;
+    int snap_prec = FWI_SNAP_F32, K = 0, nck = 0;
+    size_t total = 0;
+};
+
+fwi_status make_plan3(const fwi_grid *g, const fwi_geometry *ge, const fwi_options *o, int op, bool coords,
+                      Plan3 &pl)
+{
+    fwi_status st;
+    if ((st = check_grid3(g)) != FWI_OK) return st;
+    if ((st = check_geom3(g, ge, coords)) != FWI_OK) return st;
+    if ((st = check_opts(o, op)) != FWI_OK) return st;
+    if (op != FWI_OP_FORWARD && op != FWI_OP_GRADIENT && op != FWI_OP_ILLUMINATION)
+        return fail(FWI_ERR_INVALID_ARG, "3-D grids support forward modelling, gradients and illumination");
+    if (o && o->hmax >= 0) return fail(FWI_ERR_INVALID_ARG, "the offset Hessian is 2-D only (hmax must be -1)");
+    if (op == FWI_OP_GRADIENT && o->ckpt != FWI_CKPT_SNAPSHOT)
+        return fail(FWI_ERR_INVALID_ARG, "3-D gradients need ckpt = FWI_CKPT_SNAPSHOT (a per-level sponge band "
+                                         "of a 3-D grid does not fit)");
+    if (op == FWI_OP_GRADIENT && o->precond == FWI_PRECOND_OFFSET)
+        return fail(FWI_ERR_INVALID_ARG, "precond=OFFSET needs the offset Hessian (2-D only)");
+    pl.L = make_layout3(g);
+    pl.op = op;
+    pl.nt = g->nt;
+    pl.ns_all = ge->nshots;
+    pl.nrec = ge->nrec;
+    pl.G = (o && o->shot_group > 0 && o->shot_group < ge->nshots) ? o->shot_group : ge->nshots;
+    pl.need_bwd = op == FWI_OP_GRADIENT;
+    const Lay3D &L = pl.L;
+    pl.tf = make_tiling3(L, pl.G, false);
+    pl.tb = make_tiling3(L, pl.G, true);
+    size_t off = 0;
+    auto take = [&](Part &p, size_t bytes) {
+        p.off = off;
+        p.bytes = bytes;
+        off = align_up(off + bytes);
+    };
+    const size_t fbytes = (size_t)L.fstride * sizeof(float);
+    const size_t nphys = (size_t)L.nz * L.ny * L.nx;
+    take(pl.scal, 256);
+    take(pl.sched, (size_t)3 * pl.nt * sizeof(int));
+    take(pl.c2, fbytes);
+    take(pl.damp, fbytes);
+    take(pl.u[0], fbytes * pl.G);
+    take(pl.u[1], fbytes * pl.G);
+    if (op != FWI_OP_FORWARD) take(pl.acc_i, nphys * sizeof(float));
+    if (pl.need_bwd) {
+        take(pl.p[0], fbytes * pl.G);
+        take(pl.p[1], fbytes * pl.G);
+        take(pl.syn, (size_t)pl.G * pl.nt * pl.nrec * sizeof(float));
+        take(pl.acc_g, (size_t)L.nzp * L.nyp * L.nxp * sizeof(float));
+        pl.snap_prec = o->snap_prec;
+        pl.K = o->snap_interval > 0 ? o->snap_interval : (int)std::ceil(std::sqrt((double)pl.nt));
+        pl.K = std::max(1, std::min(pl.K, pl.nt - 1));
+        pl.nck = (pl.nt - 1 + pl.K - 1) / pl.K;
+        const size_t esz = pl.snap_prec == FWI_SNAP_F32 ? 4 : 2;
+        take(pl.snaps, (size_t)pl.nck * 2 * pl.G * L.fstride * esz);
+        if (pl.snap_prec != FWI_SNAP_F32) take(pl.snap_max, (size_t)pl.nck * 2 * pl.G * sizeof(float));
+        if (pl.K + 1 > 2) take(pl.seg, fbytes * pl.G * (size_t)(pl.K - 1));
+    }
+    const size_t ntiles = (size_t)pl.tf.nty * pl.tf.ntx;
+    size_t t = 0;
+    auto tk = [&](size_t &o2, size_t bytes) {
+        o2 = t;
+        t = align_up(t + bytes, 16);
+    };
+    tk(pl.tab_src, (size_t)pl.G * sizeof(int4));
+    tk(pl.tab_ptr, (ntiles * pl.G + 1) * sizeof(int));
+    tk(pl.tab_ent, std::max<size_t>((size_t)pl.G * pl.nrec, 1) * sizeof(int4));
+    tk(pl.tab_zr, ntiles * pl.G * sizeof(int2));
+    take(pl.tab, t);
+    pl.total = off;
+    return FWI_OK;
+}
+
+// geometry tables of shots [s0, s0 + g) of the call
+fwi_status upload_tables3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, void *ws, cudaStream_t st)
+{
+    const Lay3D &L = pl.L;
+    std::vector<char> buf(pl.tab.bytes, 0);
+    int4 *src = reinterpret_cast<int4 *>(buf.data() + pl.tab_src);
+    for (int s = 0; s < g; ++s) {
+        const int *c = ge->src + 3 * (s0 + s);
+        src[s] = make_int4(c[0] + L.P, c[1] + L.P, c[2] + L.P, 0);
+    }
+    const int ntiles = pl.tf.nty * pl.tf.ntx;
+    int *ptr = reinterpret_cast<int *>(buf.data() + pl.tab_ptr);
+    int4 *ent = reinterpret_cast<int4 *>(buf.data() + pl.tab_ent);
+    int2 *zr = reinterpret_cast<int2 *>(buf.data() + pl.tab_zr);
+    // entries of (tile, shot) in tile-major order, sorted by plane in each
+    struct E {
+        int key, plane, loc, r;
+    };
+    std::vector<E> es;
+    es.reserve((size_t)g * pl.nrec);
+    for (int s = 0; s < g; ++s)
+        for (int r = 0; r < pl.nrec; ++r) {
+            const int *q = ge->rec + 3 * ((long long)(s0 + s) * pl.nrec + r);
+            const int i = q[0] + L.P, k = q[1] + L.P, j = q[2] + L.P;
+            const int ty = k / TY3, tx = j / TX;
+            es.push_back(E{(ty * pl.tf.ntx + tx) * g + s, i, (k - ty * TY3) * TX + (j - tx * TX), r});
+        }
+    std::stable_sort(es.begin(), es.end(), [](const E &a, const E &b) {
+        return a.key != b.key ? a.key < b.key : a.plane < b.plane;
+    });
+    for (int k = 0; k < ntiles * g; ++k) zr[k] = make_int2(1, 0);
+    size_t e = 0;
+    for (int key = 0; key < ntiles * g; ++key) {
+        ptr[key] = (int)e;
+        while (e < es.size() && es[e].key == key) {
+            ent[e] = make_int4(es[e].plane, es[e].loc, es[e].r, 0);
+            if (zr[key].y < zr[key].x) zr[key] = make_int2(es[e].plane, es[e].plane);
+            zr[key].x = std::min(zr[key].x, es[e].plane);
+            zr[key].y = std::max(zr[key].y, es[e].plane);
+            ++e;
+        }
+    }
+    ptr[ntiles * g] = (int)e;
+    cudaError_t err = cudaMemcpyAsync(at<char>(ws, pl.tab), buf.data(), buf.size(), cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess) return cuda_fail(err, "upload of geometry tables");
+    return FWI_OK;
+}
+
+Step3Common make_common3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, void *ws, const Tiling3 &t)
+{
+    Step3Common c{};
+    c.L = pl.L;
+    c.c2 = at<float>(ws, pl.c2);
+    c.damp = at<float>(ws, pl.damp);
+    c.src = at<int4>(ws, pl.tab, pl.tab_src);
+    c.wav = ge->wavelet + (size_t)s0 * pl.nt;
+    c.src_scale = 1.0f / pl.L.dx; // dx^(2 - 3)
+    c.ns = g;
+    c.nt = pl.nt;
+    c.nrec = pl.nrec;
+    c.nty = t.nty;
+    c.ntx = t.ntx;
+    c.status = at<int>(ws, pl.scal, 8);
+    c.sched = at<int>(ws, pl.sched);
+    return c;
+}
+
+Rec3Table rec_table3(const Plan3 &pl, void *ws)
+{
+    return Rec3Table{at<int>(ws, pl.tab, pl.tab_ptr), at<int4>(ws, pl.tab, pl.tab_ent), at<int2>(ws, pl.tab, pl.tab_zr)};
+}
+
+// point- and halo-box maps of a buffer of g 3-D fields
+fwi_status maps3(const Plan3 &pl, const float *buf, int g, CUtensorMap *halo, CUtensorMap *pt)
+{
+    if ((halo && !encode_field_map3(halo, buf, pl.L, g, TX + 2 * RADIUS, TY3 + 2 * RADIUS)) ||
+        (pt && !encode_field_map3(pt, buf, pl.L, g, TX, TY3)))
+        return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a 3-D buffer");
+    return FWI_OK;
+}
+
+fwi_status snap3_capture(const Plan3 &pl, void *ws, int g, int j, const float *u, const float *up, cudaStream_t st)
+{
+    const long long ne = (long long)g * pl.L.fstride;
+    cudaError_t e;
+    if (pl.snap_prec == FWI_SNAP_F32) {
+        float *dst = at<float>(ws, pl.snaps) + (size_t)j * 2 * ne;
+        if ((e = cudaMemcpyAsync(dst, u, ne * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(dst + ne, up, ne * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "snapshot copy");
+        return FWI_OK;
+    }
+    float *mx = at<float>(ws, pl.snap_max) + (size_t)j * 2 * g;
+    void *dst = at<char>(ws, pl.snaps) + (size_t)j * 2 * ne * 2;
+    if ((e = launch_snap_absmax(u, up, g, pl.L.fstride, mx, st)) != cudaSuccess) return cuda_fail(e, "snapshot max");
+    if ((e = launch_snap_encode(u, up, g, pl.L.fstride, mx, pl.snap_prec, dst, st)) != cudaSuccess)
+        return cuda_fail(e, "snapshot encode");
+    t_launch[2] += 2;
+    return FWI_OK;
+}
+
+fwi_status snap3_restore(const Plan3 &pl, void *ws, int g, int j, float *u, float *up, cudaStream_t st)
+{
+    const long long ne = (long long)g * pl.L.fstride;
+    cudaError_t e;
+    if (pl.snap_prec == FWI_SNAP_F32) {
+        const float *src = at<float>(ws, pl.snaps) + (size_t)j * 2 * ne;
+        if ((e = cudaMemcpyAsync(u, src, ne * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(up, src + ne, ne * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "snapshot copy");
+        return FWI_OK;
+    }
+    const float *mx = at<float>(ws, pl.snap_max) + (size_t)j * 2 * g;
+    const void *src = at<char>(ws, pl.snaps) + (size_t)j * 2 * ne * 2;
+    if ((e = launch_snap_decode(src, mx, pl.snap_prec, g, pl.L.fstride, u, up, st)) != cudaSuccess)
+        return cuda_fail(e, "snapshot decode");
+    t_launch[2]++;
+    return FWI_OK;
+}
+
+// forward time loop of one shot group [s0, s0 + g): traces into seis (the
+// group's rows) or null, illumination into acc_i or null, snapshots if `save`
+fwi_status run_forward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, void *ws, float *seis,
+                        float *acc_i, int illum_utt, bool save, cudaStream_t st)
+{
+    cudaError_t e;
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaMemsetAsync(at<char>(ws, pl.u[b]), 0, (size_t)g * pl.L.fstride * sizeof(float), st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.sched), 0, pl.sched.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    Fwd3Args a{};
+    a.c = make_common3(pl, ge, s0, g, ws, pl.tf);
+    a.seis = (seis && pl.nrec > 0) ? seis : nullptr;
+    a.acc_illum = acc_i;
+    a.rt = rec_table3(pl, ws);
+    a.illum_utt = illum_utt;
+    float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
+    CUtensorMap mh[2], mp[2];
+    fwi_status s;
+    for (int b = 0; b < 2; ++b)
+        if ((s = maps3(pl, U[b], g, &mh[b], &mp[b])) != FWI_OK) return s;
+    if ((s = maps3(pl, at<float>(ws, pl.c2), 1, nullptr, &a.tm_c2)) != FWI_OK) return s;
+    if ((s = maps3(pl, at<float>(ws, pl.damp), 1, nullptr, &a.tm_damp)) != FWI_OK) return s;
+    for (int n = 0; n < pl.nt; ++n) {
+        if (save && n % pl.K == 0 && n <= pl.nt - 2)
+            if ((s = snap3_capture(pl, ws, g, n / pl.K, U[n & 1], U[(n + 1) & 1], st)) != FWI_OK) return s;
+        a.n = n;
+        a.last = n == pl.nt - 1;
+        a.tm_u = mh[n & 1];
+        a.tm_upt = mp[n & 1];
+        a.tm_prev = mp[(n + 1) & 1];
+        a.uout = U[(n + 1) & 1];
+        a.c.sched = at<int>(ws, pl.sched) + n;
+        if ((e = launch_fwd3d(a, pl.tf, st)) != cudaSuccess) return cuda_fail(e, "3-D forward step");
+        t_launch[0]++;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if ((e = launch_check_finite(U[b], (long long)g * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
+            return cuda_fail(e, "finite check");
+        t_launch[2]++;
+    }
+    return FWI_OK;
+}
+
+// backward loop of one shot group from its snapshots (as in 2-D: segment by
+// segment, last first, re-propagated then back-propagated); adj: the group's
+// adjoint source [g][nt][nrec]
+fwi_status run_backward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, void *ws, const float *adj,
+                         cudaStream_t st)
+{
+    cudaError_t e;
+    fwi_status s;
+    const int K = pl.K;
+    const size_t gbytes = (size_t)g * pl.L.fstride * sizeof(float);
+    std::vector<float *> S(K + 1);
+    for (int i = 0; i <= K; ++i)
+        S[i] = i < 2 ? at<float>(ws, pl.u[i]) : at<float>(ws, pl.seg) + (size_t)(i - 2) * g * pl.L.fstride;
+    for (int i = 0; i <= K; ++i)
+        if ((e = cudaMemsetAsync(S[i], 0, gbytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    float *Pp[2] = {at<float>(ws, pl.p[0]), at<float>(ws, pl.p[1])};
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaMemsetAsync(Pp[b], 0, gbytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    std::vector<CUtensorMap> sh(K + 1), sp(K + 1);
+    for (int i = 0; i <= K; ++i)
+        if ((s = maps3(pl, S[i], g, &sh[i], &sp[i])) != FWI_OK) return s;
+    CUtensorMap ph[2], pp[2], c2m, dm;
+    for (int b = 0; b < 2; ++b)
+        if ((s = maps3(pl, Pp[b], g, &ph[b], &pp[b])) != FWI_OK) return s;
+    if ((s = maps3(pl, at<float>(ws, pl.c2), 1, nullptr, &c2m)) != FWI_OK) return s;
+    if ((s = maps3(pl, at<float>(ws, pl.damp), 1, nullptr, &dm)) != FWI_OK) return s;
+    Fwd3Args f{};
+    f.c = make_common3(pl, ge, s0, g, ws, pl.tf);
+    f.rt = rec_table3(pl, ws);
+    f.tm_c2 = c2m;
+    f.tm_damp = dm;
+    Bwd3Args a{};
+    a.c = make_common3(pl, ge, s0, g, ws, pl.tb);
+    a.rt = rec_table3(pl, ws);
+    a.adj = pl.nrec > 0 ? adj : nullptr;
+    a.acc_grad = at<float>(ws, pl.acc_g);
+    a.adj_scale = pl.L.dx * pl.L.dx;
+    a.tm_c2 = c2m;
+    a.tm_damp = dm;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.sched), 0, pl.sched.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    for (int j = pl.nck - 1; j >= 0; --j) {
+        const int n0 = j * K, n1 = std::min(n0 + K - 1, pl.nt - 2);
+        if ((s = snap3_restore(pl, ws, g, j, S[0], S[K], st)) != FWI_OK) return s;
+        for (int n = n0; n < n1; ++n) {
+            const int i = n - n0;
+            f.n = n;
+            f.last = 0;
+            f.tm_u = sh[i];
+            f.tm_upt = sp[i];
+            f.tm_prev = sp[i == 0 ? K : i - 1];
+            f.uout = S[i + 1];
+            f.c.sched = at<int>(ws, pl.sched) + 2 * pl.nt + n;
+            if ((e = launch_fwd3d(f, pl.tf, st)) != cudaSuccess) return cuda_fail(e, "3-D segment step");
+            t_launch[1]++;
+        }
+        for (int m = n1 + 1; m >= n0 + 1; --m) {
+            a.m = m;
+            a.tm_u = sh[m - 1 - n0];
+            a.tm_upt = sp[m - 1 - n0];
+            a.tm_p = ph[(m + 1) & 1];
+            a.tm_ppt = pp[(m + 1) & 1];
+            a.tm_pb = pp[m & 1];
+            a.pb = Pp[m & 1];
+            a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
+            if ((e = launch_bwd3d(a, pl.tb, st)) != cudaSuccess) return cuda_fail(e, "3-D backward step");
+            t_launch[1]++;
+        }
+    }
+    if ((e = launch_check_finite(Pp[0], (long long)g * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
+        return cuda_fail(e, "finite check");
+    t_launch[2]++;
+    return FWI_OK;
+}
+
+fwi_status setup3(const Plan3 &pl, const float *v, void *ws, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.scal), 0, pl.scal.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.c2), 0, pl.c2.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.damp), 0, pl.damp.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    if ((e = launch_prep3d(pl.L, v, at<float>(ws, pl.c2), at<float>(ws, pl.damp), CFL_3D, at<int>(ws, pl.scal, 8),
+                           st)) != cudaSuccess)
+        return cuda_fail(e, "prep kernel");
+    t_launch[2]++;
+    if (pl.acc_i.bytes && (e = cudaMemsetAsync(at<char>(ws, pl.acc_i), 0, pl.acc_i.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    if (pl.acc_g.bytes && (e = cudaMemsetAsync(at<char>(ws, pl.acc_g), 0, pl.acc_g.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    return FWI_OK;
+}
+
+fwi_status finish3(const Plan3 &pl, void *ws, cudaStream_t st)
+{
+    int status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, at<int>(ws, pl.scal, 8), sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "status read-back");
+    if (t_ev_recorded && t_prof) {
+        float ms[3] = {0, 0, 0}, tot = 0;
+        cudaEventElapsedTime(&ms[0], t_ev[0], t_ev[1]);
+        cudaEventElapsedTime(&ms[1], t_ev[1], t_ev[2]);
+        cudaEventElapsedTime(&tot, t_ev[0], t_ev[3]);
+        t_times.forward_ms = ms[0];
+        t_times.adjoint_ms = ms[1];
+        t_times.other_ms = tot - ms[0] - ms[1];
+        t_times.forward_launches = t_launch[0];
+        t_times.adjoint_launches = t_launch[1];
+        t_times.other_launches = t_launch[2];
+    }
+    if (status & ST_BAD_VELOCITY) return fail(FWI_ERR_INVALID_ARG, "velocity not finite and positive");
+    if (status & ST_CFL) return fail(FWI_ERR_CFL, "v dt/dx above the 3-D stability limit %g", CFL_3D);
+    if (status & ST_TIMEOUT) return fail(FWI_ERR_TIMEOUT, "a device wait timed out");
+    if (status & ST_NONFINITE) return fail(FWI_ERR_UNSTABLE, "non-finite wavefield");
+    t_err.clear();
+    return FWI_OK;
+}
+
+fwi_status check_ws3(const Plan3 &pl, void *ws, size_t ws_bytes)
+{
+    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
+        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
+    if (ws_bytes < pl.total) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, pl.total);
+    return FWI_OK;
+}
+
+// forward modelling (seis) and / or illumination (illum) of all shots
+fwi_status forward3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int op,
+                    const float *v, float *seis, float *illum, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    Plan3 pl;
+    fwi_status s = make_plan3(grid, geom, opts, op, true, pl);
+    if (s != FWI_OK) return s;
+    if ((s = check_ws3(pl, ws, ws_bytes)) != FWI_OK) return s;
+    begin_call(st);
+    if ((s = setup3(pl, v, ws, st)) != FWI_OK) return s;
+    float *acc_i = illum ? at<float>(ws, pl.acc_i) : nullptr;
+    const int utt = opts ? opts->illum_mode : 0;
+    for (int s0 = 0; s0 < pl.ns_all; s0 += pl.G) {
+        const int g = std::min(pl.G, pl.ns_all - s0);
+        if ((s = upload_tables3(pl, geom, s0, g, ws, st)) != FWI_OK) return s;
+        float *sg = seis ? seis + (size_t)s0 * pl.nt * pl.nrec : nullptr;
+        if ((s = run_forward3(pl, geom, s0, g, ws, sg, acc_i, utt, false, st)) != FWI_OK) return s;
+    }
+    prof_record(1, st);
+    prof_record(2, st);
+    if (illum) {
+        const float iscale = utt == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
+        cudaError_t e = launch_finish_accum_n((long long)pl.L.nz * pl.L.ny * pl.L.nx, acc_i, 1, 1, iscale, illum, st);
+        if (e != cudaSuccess) return cuda_fail(e, "illumination output");
+        t_launch[2]++;
+    }
+    prof_record(3, st);
+    return finish3(pl, ws, st);
+}
+
+fwi_status gradient3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
+                     const float *d_obs, float *grad, float *grad_pre, double *misfit, float *illum, void *ws,
+                     size_t ws_bytes, cudaStream_t st)
+{
+    Plan3 pl;
+    fwi_status s = make_plan3(grid, geom, opts, FWI_OP_GRADIENT, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || !grad || (!d_obs && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v, d_obs or grad is NULL");
+    if ((s = check_ws3(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaError_t e;
+    begin_call(st);
+    if ((s = setup3(pl, v, ws, st)) != FWI_OK) return s;
+    float *acc_i = at<float>(ws, pl.acc_i), *syn = at<float>(ws, pl.syn);
+    double *J = at<double>(ws, pl.scal, 0);
+    for (int s0 = 0; s0 < pl.ns_all; s0 += pl.G) {
+        const int g = std::min(pl.G, pl.ns_all - s0);
+        if ((s = upload_tables3(pl, geom, s0, g, ws, st)) != FWI_OK) return s;
+        if ((s = run_forward3(pl, geom, s0, g, ws, syn, acc_i, opts->illum_mode, true, st)) != FWI_OK) return s;
+        const long long nsamp = (long long)g * pl.nt * pl.nrec;
+        if (nsamp > 0) {
+            const float *dg = d_obs + (size_t)s0 * pl.nt * pl.nrec;
+            if ((e = launch_residual_ols(syn, dg, nsamp, opts->misfit == FWI_MISFIT_OLS ? J : nullptr, st)) !=
+                cudaSuccess)
+                return cuda_fail(e, "residual kernel");
+            t_launch[2]++;
+            if (opts->misfit == FWI_MISFIT_TIME_INTEGRAL) {
+                if ((e = launch_time_integral(syn, g, pl.nt, pl.nrec, pl.L.dt, J, st)) != cudaSuccess)
+                    return cuda_fail(e, "time-integral kernel");
+                t_launch[2]++;
+            }
+        }
+        if ((s = run_backward3(pl, geom, s0, g, ws, syn, st)) != FWI_OK) return s;
+    }
+    prof_record(1, st); // groups interleave the loops: the phase split is not kept
+    prof_record(2, st);
+    if ((e = launch_fold_grad3d(pl.L, at<float>(ws, pl.acc_g), v, grad, st)) != cudaSuccess)
+        return cuda_fail(e, "fold kernel");
+    t_launch[2]++;
+    const long long nphys = (long long)pl.L.nz * pl.L.ny * pl.L.nx;
+    const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
+    float *ill_out = illum ? illum : acc_i;
+    if ((e = launch_finish_accum_n(nphys, acc_i, 1, 1, iscale, ill_out, st)) != cudaSuccess)
+        return cuda_fail(e, "illumination output");
+    t_launch[2]++;
+    if (grad_pre) {
+        if (opts->precond == FWI_PRECOND_NONE) {
+            if ((e = cudaMemcpyAsync(grad_pre, grad, nphys * sizeof(float), cudaMemcpyDeviceToDevice, st)) !=
+                cudaSuccess)
+                return cuda_fail(e, "copy");
+        } else {
+            if ((e = launch_precond_n(nphys, grad, ill_out, 1, 0, opts->eps, grad_pre, at<unsigned>(ws, pl.scal, 12),
+                                      st)) != cudaSuccess)
+                return cuda_fail(e, "precondition kernel");
+            t_launch[2] += 2;
+        }
+    }
+    if (misfit && (e = cudaMemcpyAsync(misfit, J, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    prof_record(3, st);
+    return finish3(pl, ws, st);
+}
+
 // Plans of a batch of models in one workspace: model k's parts start at
 // base[k]. Every model is checked as in fwi_adjoint_gradient; the models
 // share opts and nt.
@@ -860,6 +1398,14 @@ fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, c
 {
     if (!bytes) return fail(FWI_ERR_INVALID_ARG, "bytes is NULL");
     if (op < FWI_OP_FORWARD || op > FWI_OP_PRECONDITION) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
+    if (grid && grid->ndim == 3) {
+        Plan3 p3;
+        fwi_status s3 = make_plan3(grid, geom, opts, op, false, p3);
+        if (s3 != FWI_OK) return s3;
+        *bytes = p3.total;
+        t_err.clear();
+        return FWI_OK;
+    }
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, op, false, pl);
     if (s != FWI_OK) return s;
@@ -871,6 +1417,12 @@ fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, c
 fwi_status fwi_forward(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
                        const float *v, float *seis, int save, void *ws, size_t ws_bytes, void *stream)
 {
+    if (grid && grid->ndim == 3) {
+        if (save) return fail(FWI_ERR_INVALID_ARG, "3-D grids: fwi_forward(save = 1) is not available");
+        if (!v || (!seis && geom && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v or seis is NULL");
+        return forward3(grid, geom, opts, FWI_OP_FORWARD, v, seis, nullptr, ws, ws_bytes,
+                        static_cast<cudaStream_t>(stream));
+    }
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, save ? FWI_OP_FORWARD_SAVE : FWI_OP_FORWARD, true, pl);
     if (s != FWI_OK) return s;
@@ -915,6 +1467,11 @@ fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom, 
                                 const float *v, const float *d_obs, float *grad, float *grad_pre, double *misfit,
                                 float *illum, float *offh, void *ws, size_t ws_bytes, void *stream)
 {
+    if (grid && grid->ndim == 3) {
+        if (offh) return fail(FWI_ERR_INVALID_ARG, "the offset Hessian is 2-D only");
+        return gradient3(grid, geom, opts, v, d_obs, grad, grad_pre, misfit, illum, ws, ws_bytes,
+                         static_cast<cudaStream_t>(stream));
+    }
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_GRADIENT, true, pl);
     if (s != FWI_OK) return s;
@@ -930,6 +1487,11 @@ fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom, 
 fwi_status fwi_illumination(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
                             const float *v, float *illum, void *ws, size_t ws_bytes, void *stream)
 {
+    if (grid && grid->ndim == 3) {
+        if (!v || !illum) return fail(FWI_ERR_INVALID_ARG, "v or illum is NULL");
+        return forward3(grid, geom, opts, FWI_OP_ILLUMINATION, v, nullptr, illum, ws, ws_bytes,
+                        static_cast<cudaStream_t>(stream));
+    }
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_ILLUMINATION, true, pl);
     if (s != FWI_OK) return s;

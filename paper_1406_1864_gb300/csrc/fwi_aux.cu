@@ -66,6 +66,57 @@ __global__ void k_prep_c2(const Lay2D L, const float *__restrict__ v, float *__r
     if (bad) atomicOr(status, bad);
 }
 
+// 3-D: c2 and the sponge factor of every padded cell (edge-replicated
+// velocity; eta dt sums the three axes' parts, as the 2-D kernel does two)
+__global__ void k_prep3d(const Lay3D L, const float *__restrict__ v, float *__restrict__ c2,
+                         float *__restrict__ damp, float cfl_limit, int *status)
+{
+    const long long n = (long long)L.nzp * L.nyp * L.nxp;
+    int bad = 0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ((long long)L.nyp * L.nxp));
+        const long long r = e - (long long)i * L.nyp * L.nxp;
+        const int k = (int)(r / L.nxp), j = (int)(r - (long long)k * L.nxp);
+        const int iz = clampi(i - L.P, 0, L.nz - 1), iy = clampi(k - L.P, 0, L.ny - 1),
+                  ix = clampi(j - L.P, 0, L.nx - 1);
+        const float vv = v[((long long)iz * L.ny + iy) * L.nx + ix];
+        const float rr = vv * L.dt / L.dx;
+        if (!(vv > 0.f) || !isfinite(vv)) bad |= ST_BAD_VELOCITY;
+        else if (rr > cfl_limit) bad |= ST_CFL;
+        const long long o = fidx3(L, i, k, j);
+        c2[o] = rr * rr;
+        const int dz = sponge_depth(i, L.P, L.nz), dy = sponge_depth(k, L.P, L.ny), dxs = sponge_depth(j, L.P, L.nx);
+        const float ez = L.etamax_dt * (float)(dz * dz) * L.inv_p2;
+        const float ey = L.etamax_dt * (float)(dy * dy) * L.inv_p2;
+        const float ex = L.etamax_dt * (float)(dxs * dxs) * L.inv_p2;
+        damp[o] = 1.0f / (1.0f + ((ez + ey) + ex));
+    }
+    if (bad) atomicOr(status, bad);
+}
+
+// 3-D fold of the padded-grid imaging sum into the model cells (each edge
+// cell collects the sponge cells that replicate it), times 2/(v dx^2)
+__global__ void k_fold_grad3d(const Lay3D L, const float *__restrict__ acc, const float *__restrict__ v,
+                              float *__restrict__ grad)
+{
+    const long long n = (long long)L.nz * L.ny * L.nx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int iz = (int)(e / ((long long)L.ny * L.nx));
+        const long long r = e - (long long)iz * L.ny * L.nx;
+        const int iy = (int)(r / L.nx), ix = (int)(r - (long long)iy * L.nx);
+        const int ia = iz == 0 ? 0 : iz + L.P, ib = iz == L.nz - 1 ? L.nzp - 1 : iz + L.P;
+        const int ka = iy == 0 ? 0 : iy + L.P, kb = iy == L.ny - 1 ? L.nyp - 1 : iy + L.P;
+        const int ja = ix == 0 ? 0 : ix + L.P, jb = ix == L.nx - 1 ? L.nxp - 1 : ix + L.P;
+        float sum = 0.f;
+        for (int i = ia; i <= ib; ++i)
+            for (int k = ka; k <= kb; ++k)
+                for (int j = ja; j <= jb; ++j) sum += acc[((long long)i * L.nyp + k) * L.nxp + j];
+        grad[e] = sum * (2.0f / (v[e] * L.dx * L.dx));
+    }
+}
+
 // r = syn - obs (in place in syn), misfit += 1/2 sum r^2 (misfit may be NULL)
 __global__ void k_residual_ols(float *__restrict__ syn, const float *__restrict__ obs, long long n,
                                double *misfit)
@@ -298,6 +349,19 @@ cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float *dam
     return cudaGetLastError();
 }
 
+cudaError_t launch_prep3d(const Lay3D &L, const float *v, float *c2, float *damp, float cfl_limit, int *status,
+                          cudaStream_t st)
+{
+    k_prep3d<<<grid_for((long long)L.nzp * L.nyp * L.nxp), NT1, 0, st>>>(L, v, c2, damp, cfl_limit, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_grad3d(const Lay3D &L, const float *acc, const float *v, float *grad, cudaStream_t st)
+{
+    k_fold_grad3d<<<grid_for((long long)L.nz * L.ny * L.nx), NT1, 0, st>>>(L, acc, v, grad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_residual_ols(float *syn, const float *obs, long long n, double *misfit,
                                 cudaStream_t st)
 {
@@ -321,18 +385,28 @@ cudaError_t launch_fold_grad(const Lay2D &L, const float *acc, int groups, const
     return cudaGetLastError();
 }
 
+cudaError_t launch_finish_accum_n(long long nphys, const float *acc, int groups, int planes, float scale,
+                                  float *out, cudaStream_t st)
+{
+    k_finish_accum<<<grid_for(nphys * planes), NT1, 0, st>>>(nphys, acc, groups, planes, scale, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finish_accum(const Lay2D &L, const float *acc, int groups, int planes,
                                 float scale, float *out, cudaStream_t st)
 {
-    const long long nphys = (long long)L.nz * L.nx;
-    k_finish_accum<<<grid_for(nphys * planes), NT1, 0, st>>>(nphys, acc, groups, planes, scale, out);
-    return cudaGetLastError();
+    return launch_finish_accum_n((long long)L.nz * L.nx, acc, groups, planes, scale, out, st);
 }
 
 cudaError_t launch_precond(const Lay2D &L, const float *grad, const float *scale, int kind,
                            int hmax, float eps, float *out, unsigned *pmax, cudaStream_t st)
 {
-    const long long nphys = (long long)L.nz * L.nx;
+    return launch_precond_n((long long)L.nz * L.nx, grad, scale, kind, hmax, eps, out, pmax, st);
+}
+
+cudaError_t launch_precond_n(long long nphys, const float *grad, const float *scale, int kind, int hmax, float eps,
+                             float *out, unsigned *pmax, cudaStream_t st)
+{
     cudaError_t e = cudaMemsetAsync(pmax, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     k_precond_max<<<grid_for(nphys), NT1, 0, st>>>(nphys, scale, kind, hmax, pmax);

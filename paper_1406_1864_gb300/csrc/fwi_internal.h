@@ -145,6 +145,95 @@ struct Batch {
     int *sched; // the launch's chunk counter (zero at launch)
 };
 
+// ------------------------------------------------------------------- 3-D
+// Padded 3-D field [planes][rows][pitch]: z planes (GZ ghost planes above and
+// below), y rows (GY ghost rows on both sides), x as in 2-D (GXL / GXR ghost
+// columns, pitch a multiple of 32 floats). Shots are stacked by fstride.
+constexpr int GY = 4;
+constexpr int TY3 = 8; // 3-D tiles: 64 (x) x 8 (y) columns, marched along z
+
+struct Lay3D {
+    int nz, ny, nx, P;
+    int nzp, nyp, nxp;
+    int pitch, rows, planes; // floats per row, rows per plane, planes per field
+    long long plane;         // floats per plane
+    long long fstride;       // floats per field (aligned)
+    float dt, dx;
+    float etamax_dt, inv_p2;
+};
+
+__host__ __device__ inline long long fidx3(const Lay3D &L, int i, int k, int j)
+{
+    return (long long)(i + GZ) * L.plane + (long long)(k + GY) * L.pitch + GXL + j;
+}
+
+struct Step3Common {
+    Lay3D L;
+    const float *c2;    // (v dt / dx)^2, field layout
+    const float *damp;  // 1 / (1 + eta dt), field layout
+    const int4 *src;    // [ns] padded (z, y, x) of each source
+    const float *wav;   // [ns][nt]
+    float src_scale;    // dx^(2 - ndim) = 1/dx
+    int ns, nt, nrec;
+    int nty, ntx;       // tiles along y and x
+    int *status;        // device status flags
+    int *sched;         // this launch's item counter (zero at launch)
+};
+
+// receivers of each (tile, shot): ptr[tile * ns + s] .. ptr[... + 1] into ent
+// = (padded plane, y * 64 + x within the tile, receiver, 0), sorted by plane;
+// zr[tile * ns + s] = (first, last) plane with receivers (last < first: none)
+struct Rec3Table {
+    const int *ptr;
+    const int4 *ent;
+    const int2 *zr;
+};
+
+struct Fwd3Args {
+    CUtensorMap tm_u;    // u^n, halo box (TX+8) x (TY3+8) of one plane
+    CUtensorMap tm_upt;  // u^n, point box TX x TY3
+    CUtensorMap tm_prev; // u^{n-1}, point box
+    CUtensorMap tm_c2;   // c2, point box (one field)
+    CUtensorMap tm_damp; // damping factor, point box (one field)
+    Step3Common c;
+    float *uout;         // u^{n+1} written here
+    float *seis;         // [ns][nt][nrec] or null
+    float *acc_illum;    // [nz][ny][nx] or null (red.add)
+    Rec3Table rt;
+    int n, last, illum_utt;
+};
+
+struct Bwd3Args {
+    CUtensorMap tm_u, tm_upt; // u^{m-1}: halo, point boxes
+    CUtensorMap tm_p, tm_ppt; // psi^{m+1}: halo, point boxes
+    CUtensorMap tm_pb;        // psi^{m+2}: point box
+    CUtensorMap tm_c2, tm_damp;
+    Step3Common c;
+    float *pb;                // psi^m written here (the psi^{m+2} buffer)
+    const float *adj;         // [ns][nt][nrec] adjoint source or null
+    float *acc_grad;          // [nzp][nyp][nxp] (red.add)
+    Rec3Table rt;
+    float adj_scale;          // dx^2
+    int m;
+};
+
+struct Tiling3 {
+    int nty, ntx, ctas;
+};
+Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward);
+// tensor map over nfields 3-D fields with a box of bx x by cells of one plane
+bool encode_field_map3(CUtensorMap *map, const float *base, const Lay3D &L, int nfields, int bx, int by);
+cudaError_t launch_fwd3d(const Fwd3Args &a, const Tiling3 &t, cudaStream_t st);
+cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, cudaStream_t st);
+cudaError_t launch_prep3d(const Lay3D &L, const float *v, float *c2, float *damp, float cfl_limit, int *status,
+                          cudaStream_t st);
+cudaError_t launch_fold_grad3d(const Lay3D &L, const float *acc, const float *v, float *grad, cudaStream_t st);
+// finish / precondition over nphys model cells (any dimension)
+cudaError_t launch_finish_accum_n(long long nphys, const float *acc, int groups, int planes, float scale,
+                                  float *out, cudaStream_t st);
+cudaError_t launch_precond_n(long long nphys, const float *grad, const float *scale, int kind, int hmax, float eps,
+                             float *out, unsigned *pmax, cudaStream_t st);
+
 // status bits written by kernels
 enum : int {
     ST_NONFINITE = 1,

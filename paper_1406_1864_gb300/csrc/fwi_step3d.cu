@@ -1,0 +1,533 @@
+// fwi_step3d.cu -- time-step kernels of the 3-D FWI gradient (sm_103a).
+//
+// The same discrete scheme as in 2-D [Sec. 2]: damped leapfrog with the
+// 8th-order Laplacian, now over three axes (25 points),
+//   u^{n+1} = u^n + fma(c2 ia, Lhat u^n + f delta_s / dx, (2 ia - 1)(u^n - u^{n-1})),
+// ia = 1/(1 + eta dt) per cell (1 in the model, where the update is exactly
+// the plain leapfrog), traces d^n = R u^n, the illumination of Eq. 1, and
+// in the backward step the adjoint psi^m of the same update with the
+// residuals injected at the receivers (dx^2 R^T a^m) and the zero-lag
+// imaging sum psi^m (Lhat u^{m-1} + f delta_s / dx).
+//
+// Work decomposition (GB300-first): a CTA of 128 threads owns one column of
+// 64 (x) x 8 (y) cells of one shot and marches it down z. Each thread keeps
+// its 4 x-points' values of the nine planes i-4 .. i+4 in registers (the z
+// part of the stencil); for the x and y parts, plane i with its 4-cell halo is
+// brought into shared memory by a 4-D TMA copy (x, y, z, shot), together with
+// the point tile of plane i+4 that enters the register window and the point
+// tiles of u^{n-1}, c2 and the damping factor of plane i: one ring stage per
+// plane, STAGES-1 planes ahead of the compute, on mbarriers with bounded
+// waits. Items (column, shot) are handed out by an atomic counter, shot-major,
+// so neighbouring columns of one shot are in flight together and their halo
+// re-reads hit L2. Accumulations (illumination, gradient) are red.add per
+// point and plane: a column's planes do not fit in registers.
+#include "fwi_device.cuh"
+
+#include <mutex>
+
+namespace fwi {
+namespace {
+
+constexpr int TXS3 = TX + 2 * RADIUS;             // halo row length
+constexpr int HALO3 = (TY3 + 2 * RADIUS) * TXS3;  // floats of one halo plane tile
+constexpr int PT3 = TY3 * TX;                     // floats of one point tile
+
+struct Item3 {
+    int tile, s; // tile < 0: no more work
+};
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                            uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+                 : "memory");
+}
+
+// Lhat in second-difference form over three axes for two adjacent points:
+// sum_k W_k ((x_{-k}+x_{+k}-2c) + (y_{-k}+y_{+k}-2c) + (z_{-k}+z_{+k}-2c))
+__device__ __forceinline__ float2 lap3x2(float2 c, const float2 (&xs)[4], const float2 (&ys)[4],
+                                         const float2 (&zs)[4])
+{
+    const float2 m2 = make_float2(-2.f, -2.f);
+    float2 q = mul2(make_float2(W4, W4),
+                    add2(add2(fma2(c, m2, xs[3]), fma2(c, m2, ys[3])), fma2(c, m2, zs[3])));
+    q = fma2(make_float2(W3, W3), add2(add2(fma2(c, m2, xs[2]), fma2(c, m2, ys[2])), fma2(c, m2, zs[2])), q);
+    q = fma2(make_float2(W2, W2), add2(add2(fma2(c, m2, xs[1]), fma2(c, m2, ys[1])), fma2(c, m2, zs[1])), q);
+    q = fma2(make_float2(W1, W1), add2(add2(fma2(c, m2, xs[0]), fma2(c, m2, ys[0])), fma2(c, m2, zs[0])), q);
+    return q;
+}
+
+// Lhat of the thread's 4 points at the plane whose halo tile is `sh` (the
+// thread's row at ty + RADIUS) with the z window zw (zw[4] = this plane)
+__device__ __forceinline__ void lap3_4(float2 (&q)[2], const float *sh, const float4 (&zw)[9], int tx, int ty)
+{
+    const float *row = &sh[(ty + RADIUS) * TXS3 + RADIUS + 4 * tx];
+    const float4 a0 = lds4(row - 4), a1 = lds4(row), a2 = lds4(row + 4);
+    const float w[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+    float4 yv[8];
+#pragma unroll
+    for (int k = 1; k <= RADIUS; ++k) {
+        yv[k - 1] = lds4(row - k * TXS3);
+        yv[k + 3] = lds4(row + k * TXS3);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int p = 4 + 2 * h;
+        float2 xs[4], ys[4], zs[4];
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) {
+            xs[k - 1] = f2(w[p - k] + w[p + k], w[p + 1 - k] + w[p + 1 + k]);
+            ys[k - 1] = add2(half2of(yv[k - 1], h), half2of(yv[k + 3], h));
+            zs[k - 1] = add2(half2of(zw[4 - k], h), half2of(zw[4 + k], h));
+        }
+        q[h] = lap3x2(f2(w[p], w[p + 1]), xs, ys, zs);
+    }
+}
+
+// next item of this CTA (thread 0): column-major within a shot, shot-major
+__device__ __forceinline__ Item3 grab_item(int *counter, int ntiles, int nitems)
+{
+    const int q = atomicAdd(counter, 1);
+    if (q >= nitems) return Item3{-1, 0};
+    const int s = q / ntiles;
+    return Item3{q - s * ntiles, s};
+}
+
+// ------------------------------------------------------------ forward step
+// stage: [halo u(i)] [u(i+4)] [u_prev(i)] [c2(i)] [damp(i)]
+constexpr int FWD3_STAGE_F = HALO3 + 4 * PT3;
+
+template <int STAGES, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd3Args a)
+{
+    constexpr int D = STAGES - 1;
+    static_assert(D >= 1, "at least two stages");
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_abort;
+    __shared__ Item3 s_item[4];
+    unsigned char *smem = align_smem(smem_raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    float *ring = reinterpret_cast<float *>(smem + 128);
+
+    const Step3Common &c = a.c;
+    const Lay3D &L = c.L;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int NS = L.nzp + RADIUS; // steps per item: planes -4 .. nzp-1
+    const int ntiles = c.nty * c.ntx, nitems = ntiles * c.ns;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < STAGES; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    // thread 0: copies of global step t (item t / NS, plane t % NS - 4)
+    Item3 iss{-1, 0};
+    auto issue = [&](int t) {
+        const int slot = t / NS, ls = t - slot * NS;
+        if (ls == 0) {
+            iss = grab_item(c.sched, ntiles, nitems);
+            s_item[slot & 3] = iss;
+        }
+        if (iss.tile < 0) return;
+        const int i = ls - RADIUS;
+        const int bk = (iss.tile / c.ntx) * TY3, bj = (iss.tile % c.ntx) * TX;
+        const int st = t % STAGES;
+        float *sg = ring + st * FWD3_STAGE_F;
+        const uint32_t bar = smem_u32(&bars[st]);
+        fence_proxy_async_smem();
+        mbar_expect_tx(bar, (i >= 0 ? HALO3 + 4 * PT3 : PT3) * 4);
+        tma_load_4d(smem_u32(sg + HALO3), &a.tm_upt, GXL + bj, bk + GY, i + RADIUS + GZ, iss.s, bar);
+        if (i >= 0) {
+            tma_load_4d(smem_u32(sg), &a.tm_u, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
+            tma_load_4d(smem_u32(sg + HALO3 + PT3), &a.tm_prev, GXL + bj, bk + GY, i + GZ, iss.s, bar);
+            tma_load_4d(smem_u32(sg + HALO3 + 2 * PT3), &a.tm_c2, GXL + bj, bk + GY, i + GZ, 0, bar);
+            tma_load_4d(smem_u32(sg + HALO3 + 3 * PT3), &a.tm_damp, GXL + bj, bk + GY, i + GZ, 0, bar);
+        }
+    };
+    if (threadIdx.x == 0)
+        for (int t = 0; t < D; ++t) issue(t);
+    __syncthreads();
+
+    float4 zw[9];
+    int slot = 0, ls = 0;
+    Item3 it{-1, 0};
+    int k0 = 0, j0 = 0, my_e = 0, re = 0, my_plane = 0x7fffffff;
+    int4 src = make_int4(-1, -1, -1, 0);
+    float amp = 0.f;
+    bool rowok = false;
+    for (int t = 0;; ++t) {
+        if (threadIdx.x == 0) issue(t + D);
+        if (ls == 0) {
+            it = s_item[slot & 3];
+            if (it.tile < 0) break;
+            const int bk = (it.tile / c.ntx) * TY3, bj = (it.tile % c.ntx) * TX;
+            k0 = bk + ty;
+            j0 = bj + 4 * tx;
+            rowok = k0 < L.nyp;
+#pragma unroll
+            for (int z = 0; z < 9; ++z) zw[z] = make_float4(0.f, 0.f, 0.f, 0.f);
+            src = c.src[it.s];
+            amp = a.last ? 0.f : c.wav[(long long)it.s * c.nt + a.n] * c.src_scale;
+            re = 0;
+            my_plane = 0x7fffffff;
+            if (a.seis != nullptr) {
+                const int e0 = a.rt.ptr[it.tile * c.ns + it.s];
+                re = a.rt.ptr[it.tile * c.ns + it.s + 1];
+                my_e = e0 + (int)threadIdx.x;
+                if (my_e < re) my_plane = a.rt.ent[my_e].x;
+            }
+        }
+        const int st = t % STAGES;
+        const bool ok = stage_ready<STAGES>(bars, t, &s_abort);
+        if (ok) {
+            const float *sg = ring + st * FWD3_STAGE_F;
+            zw[8] = lds4(&sg[HALO3 + ty * TX + 4 * tx]);
+            const int i = ls - RADIUS;
+            if (i >= 0) {
+                const float4 cu = zw[4];
+                const float2 u0[2] = {lo2(cu), hi2(cu)};
+                float2 out[2] = {u0[0], u0[1]};
+                const long long so = (long long)it.s * L.fstride;
+                if (!a.last) {
+                    float2 q[2];
+                    lap3_4(q, sg, zw, tx, ty);
+                    if (i == src.x && k0 == src.y) {
+                        const int d = src.z - j0;
+                        if (d == 0) q[0].x += amp;
+                        if (d == 1) q[0].y += amp;
+                        if (d == 2) q[1].x += amp;
+                        if (d == 3) q[1].y += amp;
+                    }
+                    const float4 um4 = lds4(&sg[HALO3 + PT3 + ty * TX + 4 * tx]);
+                    const float4 c24 = lds4(&sg[HALO3 + 2 * PT3 + ty * TX + 4 * tx]);
+                    const float4 ia4 = lds4(&sg[HALO3 + 3 * PT3 + ty * TX + 4 * tx]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 ia2 = half2of(ia4, h);
+                        const float2 kb = fma2(ia2, make_float2(2.f, 2.f), make_float2(-1.f, -1.f));
+                        out[h] = add2(u0[h], fma2(mul2(half2of(c24, h), ia2), q[h],
+                                                  mul2(kb, sub2(u0[h], half2of(um4, h)))));
+                    }
+                    if (rowok && j0 < L.nxp) {
+                        const float o[4] = {out[0].x, out[0].y, out[1].x, out[1].y};
+                        store4(a.uout + so + fidx3(L, i, k0, j0), j0, L.nxp, o);
+                    }
+                    if (a.illum_utt && a.acc_illum != nullptr) {
+                        // (u^{n+1} - 2u^n + u^{n-1})^2 replaces u^2
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            out[h] = add2(fma2(u0[h], make_float2(-2.f, -2.f), out[h]), half2of(um4, h));
+                    }
+                }
+                // receiver extraction d^n = R u^n at this plane
+                while (my_plane == i) {
+                    const int4 en = a.rt.ent[my_e];
+                    const int ly = en.y >> 6, lx = en.y & 63;
+                    a.seis[((long long)it.s * c.nt + a.n) * c.nrec + en.z] =
+                        sg[(ly + RADIUS) * TXS3 + RADIUS + lx];
+                    my_e += TPB;
+                    my_plane = my_e < re ? a.rt.ent[my_e].x : 0x7fffffff;
+                }
+                // illumination of Eq. 1 (physical cells)
+                if (a.acc_illum != nullptr && rowok && i >= L.P && i < L.P + L.nz && k0 >= L.P &&
+                    k0 < L.P + L.ny) {
+                    const bool utt = a.illum_utt && !a.last;
+                    const float2 e0 = utt ? out[0] : u0[0], e1 = utt ? out[1] : u0[1];
+                    const float ev[4] = {e0.x, e0.y, e1.x, e1.y};
+                    const long long rowb = ((long long)(i - L.P) * L.ny + (k0 - L.P)) * L.nx;
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const int ix = j0 + p - L.P;
+                        if (ix >= 0 && ix < L.nx) atomicAdd(a.acc_illum + rowb + ix, ev[p] * ev[p]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int z = 0; z < 8; ++z) zw[z] = zw[z + 1];
+        __syncthreads();
+        if (s_abort) {
+            if (threadIdx.x == 0) {
+                atomicOr(c.status, ST_TIMEOUT);
+                for (int j = t; j < t + STAGES; ++j) mbar_wait(smem_u32(&bars[j % STAGES]), (j / STAGES) & 1, 200000000ull);
+            }
+            return;
+        }
+        if (++ls == NS) {
+            ls = 0;
+            ++slot;
+        }
+    }
+}
+
+// ----------------------------------------------------------- backward step
+// stage: [halo u(i)] [halo psi(i)] [u(i+4)] [psi(i+4)] [psi_b(i)] [c2(i)] [damp(i)]
+constexpr int BWD3_STAGE_F = 2 * HALO3 + 5 * PT3;
+
+template <int STAGES, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd3Args a)
+{
+    constexpr int D = STAGES - 1;
+    static_assert(D >= 1, "at least two stages");
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_abort;
+    __shared__ Item3 s_item[4];
+    __shared__ float sinj[PT3]; // adjoint source of the current plane
+    unsigned char *smem = align_smem(smem_raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    float *ring = reinterpret_cast<float *>(smem + 128);
+
+    const Step3Common &c = a.c;
+    const Lay3D &L = c.L;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int NS = L.nzp + RADIUS;
+    const int ntiles = c.nty * c.ntx, nitems = ntiles * c.ns;
+    const int m = a.m;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < STAGES; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    for (int e = threadIdx.x; e < PT3; e += TPB) sinj[e] = 0.f;
+    __syncthreads();
+
+    Item3 iss{-1, 0};
+    auto issue = [&](int t) {
+        const int slot = t / NS, ls = t - slot * NS;
+        if (ls == 0) {
+            iss = grab_item(c.sched, ntiles, nitems);
+            s_item[slot & 3] = iss;
+        }
+        if (iss.tile < 0) return;
+        const int i = ls - RADIUS;
+        const int bk = (iss.tile / c.ntx) * TY3, bj = (iss.tile % c.ntx) * TX;
+        const int st = t % STAGES;
+        float *sg = ring + st * BWD3_STAGE_F;
+        const uint32_t bar = smem_u32(&bars[st]);
+        fence_proxy_async_smem();
+        mbar_expect_tx(bar, (i >= 0 ? 2 * HALO3 + 5 * PT3 : 2 * PT3) * 4);
+        tma_load_4d(smem_u32(sg + 2 * HALO3), &a.tm_upt, GXL + bj, bk + GY, i + RADIUS + GZ, iss.s, bar);
+        tma_load_4d(smem_u32(sg + 2 * HALO3 + PT3), &a.tm_ppt, GXL + bj, bk + GY, i + RADIUS + GZ, iss.s, bar);
+        if (i >= 0) {
+            tma_load_4d(smem_u32(sg), &a.tm_u, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
+            tma_load_4d(smem_u32(sg + HALO3), &a.tm_p, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
+            tma_load_4d(smem_u32(sg + 2 * HALO3 + 2 * PT3), &a.tm_pb, GXL + bj, bk + GY, i + GZ, iss.s, bar);
+            tma_load_4d(smem_u32(sg + 2 * HALO3 + 3 * PT3), &a.tm_c2, GXL + bj, bk + GY, i + GZ, 0, bar);
+            tma_load_4d(smem_u32(sg + 2 * HALO3 + 4 * PT3), &a.tm_damp, GXL + bj, bk + GY, i + GZ, 0, bar);
+        }
+    };
+    if (threadIdx.x == 0)
+        for (int t = 0; t < D; ++t) issue(t);
+    __syncthreads();
+
+    float4 zu[9], zp[9];
+    int slot = 0, ls = 0;
+    Item3 it{-1, 0};
+    int k0 = 0, j0 = 0, my_e = 0, re = 0, my_plane = 0x7fffffff;
+    int2 zr = make_int2(1, 0);
+    int4 src = make_int4(-1, -1, -1, 0);
+    float amp = 0.f;
+    bool rowok = false;
+    for (int t = 0;; ++t) {
+        if (threadIdx.x == 0) issue(t + D);
+        if (ls == 0) {
+            it = s_item[slot & 3];
+            if (it.tile < 0) break;
+            const int bk = (it.tile / c.ntx) * TY3, bj = (it.tile % c.ntx) * TX;
+            k0 = bk + ty;
+            j0 = bj + 4 * tx;
+            rowok = k0 < L.nyp;
+#pragma unroll
+            for (int z = 0; z < 9; ++z) zu[z] = zp[z] = make_float4(0.f, 0.f, 0.f, 0.f);
+            src = c.src[it.s];
+            amp = c.wav[(long long)it.s * c.nt + (m - 1)] * c.src_scale;
+            re = 0;
+            my_plane = 0x7fffffff;
+            zr = make_int2(1, 0);
+            if (a.adj != nullptr) {
+                const int e0 = a.rt.ptr[it.tile * c.ns + it.s];
+                re = a.rt.ptr[it.tile * c.ns + it.s + 1];
+                zr = a.rt.zr[it.tile * c.ns + it.s];
+                my_e = e0 + (int)threadIdx.x;
+                if (my_e < re) my_plane = a.rt.ent[my_e].x;
+            }
+        }
+        const int st = t % STAGES;
+        const int i = ls - RADIUS;
+        // adjoint source of this plane into shared memory (uniform test)
+        const bool inj = i >= zr.x && i <= zr.y;
+        if (inj) {
+            while (my_plane == i) {
+                const int4 en = a.rt.ent[my_e];
+                atomicAdd(&sinj[en.y], a.adj[((long long)it.s * c.nt + m) * c.nrec + en.z] * a.adj_scale);
+                my_e += TPB;
+                my_plane = my_e < re ? a.rt.ent[my_e].x : 0x7fffffff;
+            }
+            __syncthreads();
+        }
+        const bool ok = stage_ready<STAGES>(bars, t, &s_abort);
+        if (ok) {
+            const float *sg = ring + st * BWD3_STAGE_F;
+            zu[8] = lds4(&sg[2 * HALO3 + ty * TX + 4 * tx]);
+            zp[8] = lds4(&sg[2 * HALO3 + PT3 + ty * TX + 4 * tx]);
+            if (i >= 0) {
+                float2 qu[2], qp[2];
+                lap3_4(qu, sg, zu, tx, ty);
+                lap3_4(qp, sg + HALO3, zp, tx, ty);
+                if (i == src.x && k0 == src.y) {
+                    const int d = src.z - j0;
+                    if (d == 0) qu[0].x += amp;
+                    if (d == 1) qu[0].y += amp;
+                    if (d == 2) qu[1].x += amp;
+                    if (d == 3) qu[1].y += amp;
+                }
+                if (inj) {
+                    // each thread reads and clears its own four entries; the
+                    // end-of-iteration barrier orders the clear before the
+                    // next plane's additions
+                    float4 *s4p = reinterpret_cast<float4 *>(&sinj[ty * TX + 4 * tx]);
+                    const float4 s4 = *s4p;
+                    *s4p = make_float4(0.f, 0.f, 0.f, 0.f);
+                    qp[0] = add2(qp[0], lo2(s4));
+                    qp[1] = add2(qp[1], hi2(s4));
+                }
+                const float4 p1 = zp[4];
+                const float4 pb4 = lds4(&sg[2 * HALO3 + 2 * PT3 + ty * TX + 4 * tx]);
+                const float4 c24 = lds4(&sg[2 * HALO3 + 3 * PT3 + ty * TX + 4 * tx]);
+                const float4 ia4 = lds4(&sg[2 * HALO3 + 4 * PT3 + ty * TX + 4 * tx]);
+                float2 pn[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 ia2 = half2of(ia4, h);
+                    const float2 kb = fma2(ia2, make_float2(2.f, 2.f), make_float2(-1.f, -1.f));
+                    const float2 p1h = half2of(p1, h);
+                    pn[h] = add2(p1h, fma2(mul2(half2of(c24, h), ia2), qp[h], mul2(kb, sub2(p1h, half2of(pb4, h)))));
+                }
+                if (rowok && j0 < L.nxp) {
+                    const long long so = (long long)it.s * L.fstride;
+                    const float o[4] = {pn[0].x, pn[0].y, pn[1].x, pn[1].y};
+                    store4(a.pb + so + fidx3(L, i, k0, j0), j0, L.nxp, o);
+                    // imaging: G += psi^m (Lhat u^{m-1} + f delta_s / dx), padded grid
+                    const float g[4] = {pn[0].x * qu[0].x, pn[0].y * qu[0].y, pn[1].x * qu[1].x, pn[1].y * qu[1].y};
+                    const long long rowb = ((long long)i * L.nyp + k0) * L.nxp;
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+                        if (j0 + p < L.nxp) atomicAdd(a.acc_grad + rowb + j0 + p, g[p]);
+                }
+            }
+        }
+#pragma unroll
+        for (int z = 0; z < 8; ++z) {
+            zu[z] = zu[z + 1];
+            zp[z] = zp[z + 1];
+        }
+        __syncthreads();
+        if (s_abort) {
+            if (threadIdx.x == 0) {
+                atomicOr(c.status, ST_TIMEOUT);
+                for (int j = t; j < t + STAGES; ++j) mbar_wait(smem_u32(&bars[j % STAGES]), (j / STAGES) & 1, 200000000ull);
+            }
+            return;
+        }
+        if (++ls == NS) {
+            ls = 0;
+            ++slot;
+        }
+    }
+}
+
+constexpr int F3_ST = 3, F3_MINB = 4, B3_ST = 3, B3_MINB = 3;
+#define K_FWD3 k_fwd3d<F3_ST, F3_MINB>
+#define K_BWD3 k_bwd3d<B3_ST, B3_MINB>
+constexpr int SMEM_FWD3 = 128 + 128 + F3_ST * FWD3_STAGE_F * 4;
+constexpr int SMEM_BWD3 = 128 + 128 + B3_ST * BWD3_STAGE_F * 4;
+
+int g_occ3[2] = {0, 0};
+std::once_flag g_prep3_once;
+
+void prepare_kernels3()
+{
+    std::call_once(g_prep3_once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            cudaFuncSetAttribute(K_FWD3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FWD3);
+            cudaFuncSetAttribute(K_BWD3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BWD3);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ3[0], K_FWD3, TPB, SMEM_FWD3) != cudaSuccess)
+                g_occ3[0] = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ3[1], K_BWD3, TPB, SMEM_BWD3) != cudaSuccess)
+                g_occ3[1] = 0;
+        }
+        cudaGetLastError();
+        for (int k = 0; k < 2; ++k)
+            if (g_occ3[k] < 1) g_occ3[k] = 2;
+    });
+}
+
+int sm_count3()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        v > 0)
+        return v;
+    cudaGetLastError();
+    return 152;
+}
+} // namespace
+
+Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward)
+{
+    prepare_kernels3();
+    Tiling3 t;
+    t.nty = (L.nyp + TY3 - 1) / TY3;
+    t.ntx = (L.nxp + TX - 1) / TX;
+    const long long items = (long long)t.nty * t.ntx * ns;
+    const long long slots = (long long)sm_count3() * g_occ3[backward ? 1 : 0];
+    t.ctas = (int)(items < slots ? items : slots);
+    return t;
+}
+
+cudaError_t launch_fwd3d(const Fwd3Args &a, const Tiling3 &t, cudaStream_t st)
+{
+    if (t.ctas <= 0) return cudaSuccess;
+    K_FWD3<<<t.ctas, TPB, SMEM_FWD3, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, cudaStream_t st)
+{
+    if (t.ctas <= 0) return cudaSuccess;
+    K_BWD3<<<t.ctas, TPB, SMEM_BWD3, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Tensor map over `nfields` stored 3-D fields [nfields][planes][rows][pitch]
+// with a box of bx x by cells of one plane; out-of-range cells read as zero.
+bool encode_field_map3(CUtensorMap *map, const float *base, const Lay3D &L, int nfields, int bx, int by)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)L.planes, (cuuint64_t)nfields};
+    const cuuint64_t strides[3] = {(cuuint64_t)L.pitch * sizeof(float), (cuuint64_t)L.plane * sizeof(float),
+                                   (cuuint64_t)L.fstride * sizeof(float)};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+} // namespace fwi

@@ -23,7 +23,8 @@ OPS = {"forward": L.FWI_OP_FORWARD, "forward_save": L.FWI_OP_FORWARD_SAVE,
 
 @dataclass
 class Grid:
-    """fwi_grid: physical nz x nx model, spacing dx (m), step dt (s), nt levels."""
+    """fwi_grid: physical nz x nx (2-D) or nz x ny x nx (ndim = 3) model,
+    spacing dx (m), step dt (s), nt levels."""
     nz: int
     nx: int
     dx: float
@@ -32,14 +33,16 @@ class Grid:
     sponge: int = 20
     vref: float = 3000.0
     refl: float = 0.05
+    ny: int = 1
+    ndim: int = 2
 
     def c(self) -> L.FwiGrid:
-        return L.FwiGrid(2, self.nz, 1, self.nx, self.dx, self.dt, self.nt, self.sponge, self.vref,
-                         self.refl)
+        return L.FwiGrid(self.ndim, self.nz, self.ny, self.nx, self.dx, self.dt, self.nt, self.sponge,
+                         self.vref, self.refl)
 
     @property
     def shape(self):
-        return (self.nz, self.nx)
+        return (self.nz, self.ny, self.nx) if self.ndim == 3 else (self.nz, self.nx)
 
 
 class Geometry:
@@ -85,6 +88,7 @@ class Options:
     ckpt: str = "sponge"
     snap: str = "f32"
     snap_interval: int = 0
+    shot_group: int = 0
 
     def c(self) -> L.FwiOptions:
         m = {"ols": L.FWI_MISFIT_OLS, "integral": L.FWI_MISFIT_TIME_INTEGRAL}[self.misfit]
@@ -93,7 +97,8 @@ class Options:
              "offset": L.FWI_PRECOND_OFFSET}[self.precond]
         k = {"sponge": L.FWI_CKPT_SPONGE, "snapshot": L.FWI_CKPT_SNAPSHOT}[self.ckpt]
         sp = {"f32": L.FWI_SNAP_F32, "bf16": L.FWI_SNAP_BF16, "f16s": L.FWI_SNAP_F16S}[self.snap]
-        return L.FwiOptions(m, i, int(self.hmax), p, float(self.eps), k, sp, int(self.snap_interval))
+        return L.FwiOptions(m, i, int(self.hmax), p, float(self.eps), k, sp, int(self.snap_interval),
+                            int(self.shot_group))
 
 
 def _ptr(t):
@@ -396,6 +401,6 @@ def last_phase_times() -> dict:
 def from_problem(prob, device="cuda"):
     """(Grid, Geometry) of a workloads.Problem, the wavelet uploaded to the GPU."""
     grid = Grid(prob.nz, prob.nx, float(prob.dx), float(prob.dt), int(prob.nt), int(prob.sponge),
-                float(prob.vref), float(prob.refl))
+                float(prob.vref), float(prob.refl), ny=int(prob.ny), ndim=int(prob.ndim))
     wav = torch.as_tensor(np.ascontiguousarray(prob.wavelet, dtype=np.float32), device=device)
     return grid, Geometry(prob.src, prob.rec, wav)

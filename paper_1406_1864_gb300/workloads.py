@@ -180,6 +180,54 @@ def smooth_perturbation(shape, seed, sigma_cells=5.0, amplitude=1.0):
 
 # ------------------------------------------------------------------ named workloads
 
+def dipping_layers_model3d(nz, ny, nx, dx, seed=0, vels=(1500, 2100, 2700, 3300, 3900, 4500),
+                           max_dip_deg=8.0, body_sigma_m=200.0, body_dv=600.0):
+    """3-D counterpart of dipping_layers_model: planar interfaces dipping in x
+    and y (dips from U(-max_dip, max_dip) each) at evenly spaced mean depths,
+    plus a Gaussian body centred in the middle third of each axis."""
+    rng = np.random.default_rng(seed)
+    nl = len(vels)
+    z = np.arange(nz)[:, None, None].astype(np.float64)
+    y = np.arange(ny)[None, :, None].astype(np.float64)
+    x = np.arange(nx)[None, None, :].astype(np.float64)
+    dips = np.deg2rad(rng.uniform(-max_dip_deg, max_dip_deg, (nl - 1, 2)))
+    depths = np.arange(1, nl) * nz / nl
+    layer = np.zeros((nz, ny, nx), np.int64)
+    for d, (ax, ay) in zip(depths, dips):
+        layer += (z >= d + np.tan(ax) * (x - nx / 2.0) + np.tan(ay) * (y - ny / 2.0)).astype(np.int64)
+    v = np.asarray(vels, np.float64)[layer]
+    c = [rng.uniform(n / 3.0, 2.0 * n / 3.0) for n in (nz, ny, nx)]
+    s = body_sigma_m / dx
+    v += body_dv * np.exp(-((z - c[0]) ** 2 + (y - c[1]) ** 2 + (x - c[2]) ** 2) / (2.0 * s * s))
+    return v
+
+
+def dipping3d(nz=200, ny=400, nx=400, dx=12.5, dt=1e-3, nt=3000, ns=8, rec_step=1, f0=8.0, seed=0,
+              sponge=20, smooth_m=300.0, name="dipping3d") -> Problem:
+    """3-D layered model with a Gaussian body; starting model smoothed over
+    smooth_m; ns shots at depth 2 cells on a regular (y, x) grid; receivers on
+    the top model row every rec_step cells in y and x (400 x 400 by default)."""
+    v_true = dipping_layers_model3d(nz, ny, nx, dx, seed=seed)
+    v_init = smooth(v_true, smooth_m / dx)
+    gy = int(np.floor(np.sqrt(ns)))
+    while ns % gy:
+        gy -= 1
+    gx = ns // gy
+    sy = np.floor((np.arange(gy) + 0.5) * ny / gy).astype(np.int32)
+    sx = np.floor((np.arange(gx) + 0.5) * nx / gx).astype(np.int32)
+    src = np.zeros((ns, 3), np.int32)
+    src[:, 0] = min(2, nz - 1)
+    src[:, 1] = np.repeat(sy, gx)
+    src[:, 2] = np.tile(sx, gy)
+    ry, rx = np.meshgrid(np.arange(0, ny, rec_step), np.arange(0, nx, rec_step), indexing="ij")
+    one = np.stack([np.zeros(ry.size, np.int32), ry.ravel().astype(np.int32), rx.ravel().astype(np.int32)], 1)
+    rec = np.repeat(one[None], ns, axis=0)
+    w = np.repeat(ricker(nt, dt, f0)[None, :], ns, axis=0)
+    vref = float(max(v_true.max(), v_init.max()))
+    return Problem(name, 3, nz, ny, nx, dx, dt, nt, src, rec, w.astype(np.float32), v_true.astype(np.float32),
+                   v_init.astype(np.float32), sponge=sponge, vref=vref, meta={"f0": f0, "seed": seed})
+
+
 def uneven_batch(nt=4000, ns=32, sizes=((200, 400), (350, 900), (500, 1500)), seed=1) -> list:
     """Independent models of uneven sizes sharing nt: the dipping-layer
     generator at each size (its own seed), ns shots and nx / 2 receivers each."""
@@ -193,6 +241,8 @@ def workload(name: str) -> Problem:
         return two_layer()
     if name == "dipping_300x1000_96shots":
         return dipping()
+    if name == "dipping3d_200x400x400_8shots":
+        return dipping3d()
     if name == "dipping_400x1200_64shots":
         return dipping(nz=400, nx=1200, nt=5000, ns=64, nrec=600, name="dipping_400x1200_64shots")
     raise KeyError(name)

@@ -86,7 +86,7 @@ def test_workspace_sizes(lib):
 
 
 @pytest.mark.parametrize("field,value,code", [
-    ("ndim", 3, 1), ("ny", 2, 1), ("nz", 0, 1), ("nt", 1, 1), ("sponge", 0, 1), ("dx", 0.0, 1),
+    ("ndim", 4, 1), ("ny", 2, 1), ("nz", 0, 1), ("nt", 1, 1), ("sponge", 0, 1), ("dx", 0.0, 1),
     ("dt", -1.0, 1), ("refl", 1.0, 1), ("vref", 0.0, 1)])
 def test_bad_grid_rejected(lib, field, value, code):
     g, ge, o, keep = _structs()
@@ -213,3 +213,41 @@ def test_batch_workspace_and_errors(lib):
     G[1].nz = 0
     assert lib.fwi_batch_workspace_bytes(2, G, GE, ctypes.byref(o), ctypes.byref(n)) == L.FWI_ERR_INVALID_ARG
     assert b"model 1" in lib.fwi_last_error()
+
+
+def test_3d_workspace_and_options(lib):
+    """3-D plans: snapshot checkpoints required for gradients, no offset
+    Hessian; shot groups bound the workspace (one group's fields and
+    snapshots); forward modelling needs no checkpoints."""
+    from paper_1406_1864_gb300 import _lib as L
+    g = L.FwiGrid(3, 20, 24, 28, 10.0, 1e-3, 100, 8, 3000.0, 0.05)
+    ns, nrec = 4, 6
+    src = np.zeros((ns, 3), np.int32)
+    src[:, 1] = 12
+    src[:, 2] = [3, 9, 15, 21]
+    rec = np.zeros((ns, nrec, 3), np.int32)
+    rec[:, :, 1] = 12
+    rec[:, :, 2] = np.arange(nrec) * 4
+    ge = L.FwiGeometry(ns, nrec, src.ctypes.data, rec.ctypes.data, 1)
+    o = L.FwiOptions(0, 0, -1, 1, 1e-3)
+    st, _ = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
+    assert st == L.FWI_ERR_INVALID_ARG and b"SNAPSHOT" in lib.fwi_last_error()
+    o.ckpt = L.FWI_CKPT_SNAPSHOT
+    st, full = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
+    assert st == L.FWI_OK, lib.fwi_last_error()
+    o.shot_group = 1
+    st, one = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
+    assert st == L.FWI_OK and one < full / 2
+    o.snap_prec = L.FWI_SNAP_BF16
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[1] < one
+    st, fw = ws_bytes(lib, g, ge, o, L.FWI_OP_FORWARD)
+    assert st == L.FWI_OK and fw < one
+    o.hmax = 2
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[0] == L.FWI_ERR_INVALID_ARG
+    o.hmax, o.precond = -1, L.FWI_PRECOND_OFFSET
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[0] == L.FWI_ERR_INVALID_ARG
+    o.precond = L.FWI_PRECOND_ILLUM
+    for op in (L.FWI_OP_FORWARD_SAVE, L.FWI_OP_OFFSET_HESSIAN):
+        assert ws_bytes(lib, g, ge, o, op)[0] == L.FWI_ERR_INVALID_ARG
+    o.shot_group = -1
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[0] == L.FWI_ERR_INVALID_ARG

@@ -1,0 +1,115 @@
+"""3-D modelling and gradients (25-point 8th-order stencil) against the FP64
+oracle, which runs the same scheme in 3-D.
+
+Small ragged grid (padded 30 x 33 x 38: not a multiple of the 64 x 8
+columns), receivers on the surface grid plus some at depth, on edges and in
+corners. Tolerances as in 2-D: traces 1e-5, gradient / illumination /
+preconditioned gradient 1e-4 with F32 snapshots, 1e-2 with bfloat16 ones;
+shot groups (opts.shot_group) give the all-at-once result.
+"""
+import numpy as np
+import pytest
+
+from paper_1406_1864_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    torch.cuda.set_device(0)
+    return torch
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def problem3(nt=150, ns=3):
+    p = W.dipping3d(nz=18, ny=21, nx=26, dx=10.0, dt=8e-4, nt=nt, ns=ns, rec_step=3, f0=15.0, seed=3, sponge=6)
+    rec = p.rec.copy()
+    extra = np.array([[5, 4, 7], [17, 20, 25], [17, 0, 0], [0, 20, 25], [9, 10, 0], [12, 0, 13]], np.int32)
+    rec[:, :len(extra)] = extra[None]
+    p.rec = rec
+    src = p.src.copy()
+    src[-1] = [17, 20, 25]  # a source in the bottom corner
+    p.src = src
+    return p
+
+
+@pytest.fixture(scope="module")
+def case(torch_cuda, oracle_mod):
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import fwi
+    p = problem3()
+    g = oracle_mod.Grid.of(p)
+    w64 = p.wavelet.astype(np.float64)
+    d_true = oracle_mod.forward(g, p.v_true, p.src, p.rec, w64)["seis"]
+    ref = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w64, d_true.astype(np.float32).astype(np.float64))
+    grid, geom = fwi.from_problem(p)
+    v = torch.as_tensor(np.ascontiguousarray(p.v_init), device="cuda")
+    d = torch.as_tensor(d_true.astype(np.float32), device="cuda")
+    return p, g, grid, geom, v, d, d_true, ref
+
+
+def test_3d_forward_traces(torch_cuda, case):
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import fwi
+    p, g, grid, geom, v, d, d_true, ref = case
+    seis = fwi.forward(grid, geom, torch.as_tensor(np.ascontiguousarray(p.v_true), device="cuda")).cpu().numpy()
+    for s in range(p.nshots):
+        assert rel(seis[s], d_true[s]) <= 1e-5, (s, rel(seis[s], d_true[s]))
+
+
+def test_3d_gradient_f32_snapshots(torch_cuda, case):
+    from paper_1406_1864_gb300 import fwi
+    p, g, grid, geom, v, d, d_true, ref = case
+    r = fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot", snap="f32"))
+    assert rel(r["grad"].cpu(), ref["grad"]) <= 1e-4
+    assert rel(r["illum"].cpu(), ref["illum"]) <= 1e-4
+    assert rel(r["grad_pre"].cpu(), ref["grad_pre_illum"]) <= 1e-4
+    assert abs(float(r["misfit"]) - ref["J"]) <= 1e-5 * ref["J"]
+
+
+def test_3d_gradient_16bit_snapshots_and_groups(torch_cuda, case):
+    from paper_1406_1864_gb300 import fwi
+    p, g, grid, geom, v, d, d_true, ref = case
+    bf = fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot", snap="bf16"))
+    assert rel(bf["grad"].cpu(), ref["grad"]) <= 1e-2
+    whole = fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot", snap="f32", snap_interval=7))
+    for grp in (1, 2):
+        part = fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot", snap="f32", snap_interval=7,
+                                                                  shot_group=grp))
+        assert rel(part["grad"].cpu(), whole["grad"].cpu()) <= 1e-6, grp
+        assert rel(part["illum"].cpu(), whole["illum"].cpu()) <= 1e-6, grp
+        assert abs(float(part["misfit"]) - float(whole["misfit"])) <= 1e-12 * float(whole["misfit"])
+    assert rel(whole["grad"].cpu(), ref["grad"]) <= 1e-4
+
+
+def test_3d_illumination_entry_point(torch_cuda, case):
+    from paper_1406_1864_gb300 import fwi
+    p, g, grid, geom, v, d, d_true, ref = case
+    il = fwi.illumination(grid, geom, v, fwi.Options(shot_group=2))
+    assert rel(il.cpu(), ref["illum"]) <= 1e-4
+
+
+def test_3d_errors(torch_cuda, case):
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import fwi, _lib
+    p, g, grid, geom, v, d, d_true, ref = case
+    with pytest.raises(_lib.FwiError):  # sponge checkpoints are 2-D only
+        fwi.adjoint_gradient(grid, geom, v, d, fwi.Options())
+    with pytest.raises(_lib.FwiError):  # the offset Hessian is 2-D only
+        fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot", hmax=2, precond="illum"))
+    fast = v.clone()
+    fast[3, 4, 5] = 9000.0
+    with pytest.raises(_lib.FwiError) as e:
+        fwi.adjoint_gradient(grid, geom, fast, d, fwi.Options(ckpt="snapshot"))
+    assert e.value.status == _lib.FWI_ERR_CFL
+    again = fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot"))
+    assert np.isfinite(again["grad"].cpu().numpy()).all()
