@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_abort;
     __shared__ Item3 s_item[4];
-    __shared__ float sinj[PT3]; // adjoint source of the current plane
+    __shared__ __align__(16) float sinj[PT3]; // adjoint source of the current plane (read as float4)
     unsigned char *smem = align_smem(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *ring = reinterpret_cast<float *>(smem + 128);
