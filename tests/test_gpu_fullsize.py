@@ -172,3 +172,4 @@ def test_c4_autograd_finite_differences_8_directions(torch_cuda, c4):
         an = float(np.sum(g * dv))
         errs.append(abs(fd - an) / max(abs(an), 0.05 * np.linalg.norm(g) * np.linalg.norm(dv)))
     assert max(errs) <= 1e-2, errs
+
