@@ -472,8 +472,8 @@ fwi_status run_forward_models(int nm, const Plan *pl, const fwi_geometry *const 
         til[k] = p.tf;
         U[k] = {at<float>(w, p.u[0]), at<float>(w, p.u[1])};
         for (int b = 0; b < 2; ++b)
-            if (!encode_field_map(&mh[k][b], U[k][b], p.L, p.ns, hx, hy) ||
-                !encode_field_map(&mp[k][b], U[k][b], p.L, p.ns, px, py))
+            if (!encode_field_map(&mh[k][b], U[k][b], p.L, p.ns, hx, hy, p.tf.spi) ||
+                !encode_field_map(&mp[k][b], U[k][b], p.L, p.ns, px, py, p.tf.spi))
                 return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
     }
     const bool capture = nm == 1 && save && pl[0].snap;
@@ -541,8 +541,8 @@ fwi_status run_backward_segments(const Plan &pl, const fwi_geometry *ge, void *w
     step_boxes(STEP_BWD, pl.tb, bhx, bhy, bpx, bpy);
     std::vector<CUtensorMap> fh(K + 1), fp(K + 1), bh(K + 1);
     for (int i = 0; i <= K; ++i)
-        if (!encode_field_map(&fh[i], S[i], pl.L, pl.ns, fhx, fhy) ||
-            !encode_field_map(&fp[i], S[i], pl.L, pl.ns, fpx, fpy) ||
+        if (!encode_field_map(&fh[i], S[i], pl.L, pl.ns, fhx, fhy, pl.tr.spi) ||
+            !encode_field_map(&fp[i], S[i], pl.L, pl.ns, fpx, fpy, pl.tr.spi) ||
             !encode_field_map(&bh[i], S[i], pl.L, pl.ns, bhx, bhy))
             return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the segment buffers");
     FwdArgs f{};

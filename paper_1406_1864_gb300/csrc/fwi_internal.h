@@ -247,6 +247,7 @@ enum : int {
 // shots of one tile from an atomic counter.
 struct Tiling {
     int variant;   // compiled tile variant of the kind (0 = default)
+    int spi;       // shots per item (the depth of the step's tensor-map boxes)
     int tz;        // tile height
     int ntx, ntz;  // tiles
     int ctas;      // CTAs of one launch
@@ -268,7 +269,8 @@ void step_tuned_store(StepKind kind, const Lay2D &L, int ns, int variant, int ch
 bool step_tuned_lookup(StepKind kind, const Lay2D &L, int ns, int &variant, int &chunk);
 void step_tuned_clear();
 
-bool encode_field_map(CUtensorMap *map, const float *base, const Lay2D &L, int nfields, int bx, int by);
+bool encode_field_map(CUtensorMap *map, const float *base, const Lay2D &L, int nfields, int bx, int by,
+                      int bz = 1);
 cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st);
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st);
 // one launch over the (tile, shot) pairs of nm <= BATCH_MAX models at the

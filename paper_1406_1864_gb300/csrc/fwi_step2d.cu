@@ -56,11 +56,16 @@ namespace fwi {
 // costs, and at any moment all CTAs work on nearby chunks: neighbouring tiles
 // of the same shots, whose halo re-reads then hit L2.
 struct alignas(16) ItemDesc {
-    int tile, s;   // tile and shot of the item; tile < 0: no more work
+    int tile, s;   // tile and (first) shot of the item; tile < 0: no more work
     int rb, re;    // receiver-table range of (tile, shot)
     int si, sj;    // padded cell of the shot's source (8-byte aligned pair)
     float amp;     // source amplitude at this time level
     int model;     // model of the item in a batched launch
+    int nsh;       // shots in the item (items of two shots: shots s, s + 1)
+    float amp1;    // the second shot's amplitude, source cell and receivers
+    int si1, sj1;
+    int rb1, re1;
+    int pad[2];
 };
 
 // State of the staging lane that walks the CTA's chunks.
@@ -109,9 +114,10 @@ __device__ __forceinline__ void cursor_init(Cursor &cu, const BT &B)
     }
 }
 
-// next (model, tile, shot) of this CTA; false when the launch's work is exhausted
+// next (model, tile, shots s .. s + cnt - 1 with cnt <= spi) of this CTA;
+// false when the launch's work is exhausted
 template <class BT>
-__device__ __forceinline__ bool cursor_next(Cursor &cu, const BT &B, int &model, int &tile, int &s)
+__device__ __forceinline__ bool cursor_next(Cursor &cu, const BT &B, int &model, int &tile, int &s, int spi, int &cnt)
 {
     if (cu.done) return false;
     if (cu.s >= cu.s_end) {
@@ -124,7 +130,9 @@ __device__ __forceinline__ bool cursor_next(Cursor &cu, const BT &B, int &model,
     }
     model = cu.model;
     tile = cu.tile;
-    s = cu.s++;
+    s = cu.s;
+    cnt = min(spi, cu.s_end - cu.s);
+    cu.s += cnt;
     return true;
 }
 
@@ -148,14 +156,15 @@ __device__ __forceinline__ bool has_rec(const BwdArgs &a) { return a.adj != null
 // are in flight. The copies complete at cp_async_wait_all(), which the
 // staging thread calls before the barrier that publishes the slot. The
 // amplitude is stored unscaled (times src_scale at use).
-template <class BT>
+template <int SPI, class BT>
 __device__ __forceinline__ void stage_desc_async(ItemDesc *slot, Cursor &cu, const BT &B, int n_src, bool use_src)
 {
-    int mdl = 0, t = -1, s = 0;
-    if (!cursor_next(cu, B, mdl, t, s)) t = -1;
+    int mdl = 0, t = -1, s = 0, cnt = 0;
+    if (!cursor_next(cu, B, mdl, t, s, SPI, cnt)) t = -1;
     slot->tile = t;
     slot->s = s;
     slot->model = mdl;
+    slot->nsh = cnt;
     if (t < 0) {
         slot->rb = slot->re = slot->si = slot->sj = 0;
         slot->amp = 0.f;
@@ -173,6 +182,25 @@ __device__ __forceinline__ void stage_desc_async(ItemDesc *slot, Cursor &cu, con
         cp_async4(&slot->re, &a.rt.ptr[t * c.ns + s + 1]);
     } else {
         slot->rb = slot->re = 0;
+    }
+    if (SPI > 1) {
+        if (cnt > 1) {
+            cp_async8(&slot->si1, &c.src_ij[s + 1]);
+            if (use_src)
+                cp_async4(&slot->amp1, &c.wav[(long long)(s + 1) * c.nt + n_src]);
+            else
+                slot->amp1 = 0.f;
+            if (has_rec(a)) {
+                cp_async4(&slot->rb1, &a.rt.ptr[t * c.ns + s + 1]);
+                cp_async4(&slot->re1, &a.rt.ptr[t * c.ns + s + 2]);
+            } else {
+                slot->rb1 = slot->re1 = 0;
+            }
+        } else {
+            slot->si1 = slot->sj1 = -1000000;
+            slot->amp1 = 0.f;
+            slot->rb1 = slot->re1 = 0;
+        }
     }
 }
 
@@ -226,10 +254,15 @@ __device__ __forceinline__ bool in_band(const Lay2D &L, int i, int j)
 
 // index (row * 4 + column) of the thread's point that holds the source, or -1
 template <int RZ>
+__device__ __forceinline__ int source_slot(int si, int sj, int i0, int j0)
+{
+    const int dr = si - i0, dc = sj - j0;
+    return (dr >= 0 && dr < RZ && dc >= 0 && dc < 4) ? dr * 4 + dc : -1;
+}
+template <int RZ>
 __device__ __forceinline__ int source_slot(const ItemDesc &v, int i0, int j0)
 {
-    const int dr = v.si - i0, dc = v.sj - j0;
-    return (dr >= 0 && dr < RZ && dc >= 0 && dc < 4) ? dr * 4 + dc : -1;
+    return source_slot<RZ>(v.si, v.sj, i0, j0);
 }
 
 // load a TZ x TX tile of a field-layout coefficient array (c2, damping) into
@@ -247,13 +280,17 @@ __device__ __forceinline__ void load_c2_tile(float *dst, const float *c2, const 
 }
 
 // ------------------------------------------------------------ forward step
-template <int RZ, int HX, bool WITH_H, int STAGES>
-using FwdRing = Ring<8 * RZ, HX, 1, 1, STAGES, 2 * 8 * RZ * TX * 4>; // + c2 and damping tiles
+// a stage holds SPI consecutive shots' halo tiles and point tiles (one TMA
+// box of depth SPI in the shot dimension each; the tile sizes are multiples
+// of 128 bytes, so the shots' tiles are contiguous)
+template <int RZ, int HX, bool WITH_H, int STAGES, int SPI = 1>
+using FwdRing = Ring<8 * RZ, HX, SPI, SPI, STAGES, 2 * 8 * RZ * TX * 4>; // + c2 and damping tiles
 
-template <int RZ, int HX, bool WITH_H, int STAGES, int MINB, int NM>
+template <int RZ, int HX, bool WITH_H, int STAGES, int MINB, int NM, int SPI = 1>
 __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ Batch<FwdArgs, NM> B)
 {
-    using R = FwdRing<RZ, HX, WITH_H, STAGES>;
+    using R = FwdRing<RZ, HX, WITH_H, STAGES, SPI>;
+    static_assert(SPI == 1 || R::HALO_B == R::HALO * 4, "contiguous shot tiles");
     constexpr int TZ = 8 * RZ;
     constexpr int TXS = R::TXS;
     constexpr int NH = WITH_H ? HMAX_LIMIT + 1 : 1;
@@ -288,14 +325,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
     // lane 0 of warp 1 walks the chunks (cursor in shared memory) and stages
     // descriptors D + 1 items ahead
     __shared__ Cursor s_cu;
-    auto stage = [&](int slot) { stage_desc_async(&s_desc[slot % DESC_RING], s_cu, B, a0.n, !a0.last); };
+    auto stage = [&](int slot) { stage_desc_async<SPI>(&s_desc[slot % DESC_RING], s_cu, B, a0.n, !a0.last); };
     auto issue = [&](const ItemDesc &d, int k) {
         const FwdArgs &ad = B.m[NM == 1 ? 0 : d.model];
         const int bz = d.tile / ad.c.ntx, bx = d.tile - bz * ad.c.ntx;
         const int st = k % STAGES;
         const uint32_t bar = smem_u32(&bars[st]);
         fence_proxy_async_smem();
-        mbar_expect_tx(bar, (R::HALO + (a0.last ? 0 : R::PT)) * 4);
+        mbar_expect_tx(bar, SPI * (R::HALO + (a0.last ? 0 : R::PT)) * 4);
         tma_load_3d(smem_u32(R::halo(smem, st, 0)), &ad.tm_cur, GXL + bx * TX - HX, bz * TZ, d.s, bar);
         if (!a0.last)
             tma_load_3d(smem_u32(R::point(smem, st, 0)), &ad.tm_prev, GXL + bx * TX, bz * TZ + GZ, d.s, bar);
@@ -397,23 +434,30 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
             __syncthreads();
         }
         const int st = k % STAGES;
-        if (stage_ready<STAGES>(bars, k, &s_abort)) {
-            const float *sm = R::halo(smem, st, 0);
-            const float *pm = R::point(smem, st, 0);
-            float *up = a.uout + (long long)s * L.fstride;
+        const bool ready = stage_ready<STAGES>(bars, k, &s_abort);
+        // the item's shots, one after the other (accumulators are shared)
+#pragma unroll 1
+        for (int sh = 0; sh < SPI && ready; ++sh) {
+            if (sh >= now.nsh) break; // uniform
+            const int ss = s + sh;
+            const float *sm = R::halo(smem, st, sh);
+            const float *pm = R::point(smem, st, sh);
+            float *up = a.uout + (long long)ss * L.fstride;
 
             // receiver extraction d^n = R u^n
-            float *seis_s = a.seis + ((long long)s * c.nt + a.n) * c.nrec;
-            if (now_en.x >= 0) {
+            float *seis_s = a.seis + ((long long)ss * c.nt + a.n) * c.nrec;
+            if (sh == 0 && now_en.x >= 0) {
                 const int zl = now_en.x / TX, xl = now_en.x - zl * TX;
                 seis_s[now_en.y] = sm[(zl + RADIUS) * TXS + HX + xl];
             }
-            for (int e = now.rb + TPB + (int)threadIdx.x; e < now.re; e += TPB) {
+            const int rb = sh == 0 ? now.rb + TPB : now.rb1, re = sh == 0 ? now.re : now.re1;
+            for (int e = rb + (int)threadIdx.x; e < re; e += TPB) {
                 const int2 en = a.rt.ent[e];
                 const int zl = en.x / TX, xl = en.x - zl * TX;
                 seis_s[en.y] = sm[(zl + RADIUS) * TXS + HX + xl];
             }
-            const int sslot = source_slot<RZ>(now, i0, j0);
+            const int sslot = sh == 0 ? source_slot<RZ>(now.si, now.sj, i0, j0)
+                                      : source_slot<RZ>(now.si1, now.sj1, i0, j0);
 
             float4 zc[RZ + 2 * RADIUS];
 #pragma unroll
@@ -432,7 +476,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                 if (!a.last) {
                     float2 q[2];
                     lap4<WL>(q, w, zc, r);
-                    const float amp = now.amp * c.src_scale;
+                    const float amp = (sh == 0 ? now.amp : now.amp1) * c.src_scale;
                     if (sslot == r * 4 + 0) q[0].x += amp;
                     if (sslot == r * 4 + 1) q[0].y += amp;
                     if (sslot == r * 4 + 2) q[1].x += amp;
@@ -460,7 +504,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                         const float o[4] = {out[0].x, out[0].y, out[1].x, out[1].y};
                         if (colok && i < L.nzp) store4(up + fidx(L, i, j0), j0, L.nxp, o);
                         if (a.band != nullptr && sg.brow[r] != -1) {
-                            float *bb = a.band + ((long long)s * c.nt + a.n + 1) * L.nbandp;
+                            float *bb = a.band + ((long long)ss * c.nt + a.n + 1) * L.nbandp;
                             if (sg.brow[r] >= 0) {
                                 *reinterpret_cast<float4 *>(bb + sg.brow[r]) = make_float4(o[0], o[1], o[2], o[3]);
                             } else {
@@ -555,7 +599,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     __syncthreads();
 
     __shared__ Cursor s_cu;
-    auto stage = [&](int slot) { stage_desc_async(&s_desc[slot % DESC_RING], s_cu, B, m - 1, true); };
+    auto stage = [&](int slot) { stage_desc_async<1>(&s_desc[slot % DESC_RING], s_cu, B, m - 1, true); };
     auto issue = [&](const ItemDesc &d, int k) {
         const BwdArgs &a = B.m[NM == 1 ? 0 : d.model];
         const int bz = d.tile / a.c.ntx, bx = d.tile - bz * a.c.ntx;
@@ -819,31 +863,34 @@ namespace {
 // autotuner may pick another per problem shape): tile height 8 RZ rows,
 // ring stages, minimum resident CTAs per SM (the register cap).
 struct Variant {
-    int rz, smem;
+    int rz, spi, smem; // tile rows / 8, shots per item, dynamic shared memory
     const void *fn[2]; // one model per launch, batch of up to BATCH_MAX models
     int occ[2];        // resident CTAs per SM (from the occupancy calculator)
 };
 
-#define FWD_VARIANT(RZ, ST, MINB)                                                          \
-    {RZ, FwdRing<RZ, RADIUS, false, ST>::SMEM,                                             \
-     {(const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, 1>,                            \
-      (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, BATCH_MAX>},                   \
+#define FWD_VARIANT(RZ, ST, MINB, SPI)                                                     \
+    {RZ, SPI, FwdRing<RZ, RADIUS, false, ST, SPI>::SMEM,                                   \
+     {(const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, 1, SPI>,                       \
+      (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, BATCH_MAX, SPI>},              \
      {0, 0}}
-#define FWDH_VARIANT(ST, MINB)                                                             \
-    {1, FwdRing<1, HMAX_LIMIT, true, ST>::SMEM,                                            \
-     {(const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, 1>,                          \
-      (const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, BATCH_MAX>},                 \
+#define FWDH_VARIANT(ST, MINB, SPI)                                                        \
+    {1, SPI, FwdRing<1, HMAX_LIMIT, true, ST, SPI>::SMEM,                                  \
+     {(const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, 1, SPI>,                     \
+      (const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, BATCH_MAX, SPI>},            \
      {0, 0}}
 #define BWD_VARIANT(RZ, ST, MINB)                                                          \
-    {RZ, BwdRing<RZ, ST>::SMEM,                                                            \
+    {RZ, 1, BwdRing<RZ, ST>::SMEM,                                                         \
      {(const void *)k_bwd_step<RZ, ST, MINB, 1>, (const void *)k_bwd_step<RZ, ST, MINB, BATCH_MAX>}, \
      {0, 0}}
 
-// forward: 64 x 16 tiles (3 stages, 4 CTAs/SM), 64 x 32 (2 stages), 64 x 8 (6 CTAs/SM)
-Variant g_var_f[] = {FWD_VARIANT(2, 3, 4), FWD_VARIANT(4, 2, 4), FWD_VARIANT(1, 3, 6)};
+// forward: 64 x 16 tiles (3 stages, 4 CTAs/SM), 64 x 32 (2 stages), 64 x 8
+// (6 CTAs/SM), 64 x 16 with two shots per item (2 stages)
+Variant g_var_f[] = {FWD_VARIANT(2, 3, 4, 1), FWD_VARIANT(4, 2, 4, 1), FWD_VARIANT(1, 3, 6, 1),
+                     FWD_VARIANT(2, 2, 4, 2)};
 // forward with the offset Hessian: 64 x 8 tiles, halo 12 (its 44 register
-// accumulators rule out taller tiles)
-Variant g_var_h[] = {FWDH_VARIANT(3, 4)};
+// accumulators rule out taller tiles), one or two shots per item (the
+// accumulators serve both shots of an item)
+Variant g_var_h[] = {FWDH_VARIANT(3, 4, 1), FWDH_VARIANT(3, 4, 2)};
 // backward: 64 x 16 tiles (2 stages, 4 CTAs/SM), 64 x 8 (5 CTAs/SM)
 Variant g_var_b[] = {BWD_VARIANT(2, 2, 4), BWD_VARIANT(1, 2, 5)};
 
@@ -1008,6 +1055,7 @@ Tiling make_tiling(const Lay2D &L, int ns, StepKind kind, int variant, int chunk
     if (chunk <= 0) chunk = kind == STEP_FWD_OFFH ? CHUNKS_H[0] : CHUNKS_F[0];
     Tiling t;
     t.variant = variant;
+    t.spi = vs[variant].spi;
     t.tz = 8 * vs[variant].rz;
     t.ntx = (L.nxp + TX - 1) / TX;
     t.ntz = (L.nzp + t.tz - 1) / t.tz;
@@ -1055,7 +1103,7 @@ cudaError_t launch_bwd_batch(const BwdArgs *a, const Tiling *t, int nm, cudaStre
 
 // Tensor map over `nfields` stored fields [nfields][rows][pitch] (float32)
 // with a box of bx x by cells; out-of-range cells read as zero.
-bool encode_field_map(CUtensorMap *map, const float *base, const Lay2D &L, int nfields, int bx, int by)
+bool encode_field_map(CUtensorMap *map, const float *base, const Lay2D &L, int nfields, int bx, int by, int bz)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -1069,7 +1117,7 @@ bool encode_field_map(CUtensorMap *map, const float *base, const Lay2D &L, int n
     }
     const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)nfields};
     const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * sizeof(float), (cuuint64_t)L.fstride * sizeof(float)};
-    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
