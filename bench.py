@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default tile variants (no fwi_autotune)")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="cudaProfilerStart/Stop around the timed steps (ncu --profile-from-start off)")
     ap.add_argument("--no-graph", action="store_true",
                     help="call fwi_adjoint_gradient directly instead of replaying the recorded gradient")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
@@ -308,12 +310,16 @@ def run_ours(args):
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        if args.profile_region:
+            torch.cuda.profiler.start()
         e0.record()
         for _ in range(args.steps):
             step()
             phases.append(phase_box[-1])
         e1.record()
         barrier()
+        if args.profile_region:
+            torch.cuda.profiler.stop()
     fwi.profile(False)
     ms = e0.elapsed_time(e1) / args.steps
     if dist is not None:

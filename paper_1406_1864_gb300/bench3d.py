@@ -1,0 +1,59 @@
+"""Timing of the 3-D path: python -m paper_1406_1864_gb300.bench3d [options].
+
+Models the seeded 3-D dipping-layer workload (workloads.dipping3d: surface
+receivers every cell, shots on a grid at depth 2), times forward modelling
+(per-level step time and algorithmic bandwidth at 16 B per padded
+point-step per shot) and one snapshot-checkpointed gradient per snapshot
+precision, with CUDA events on the library's stream. Prints one JSON line.
+Defaults: the 200 x 400 x 400, 8-shot, nt 3000 workload in shot groups of 4.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+
+def main():
+    import torch
+
+    from . import fwi, workloads as W
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nz", type=int, default=200)
+    ap.add_argument("--ny", type=int, default=400)
+    ap.add_argument("--nx", type=int, default=400)
+    ap.add_argument("--shots", type=int, default=8)
+    ap.add_argument("--nt", type=int, default=3000)
+    ap.add_argument("--shot-group", type=int, default=4)
+    ap.add_argument("--snap", default="f32,bf16")
+    args = ap.parse_args()
+    p = W.dipping3d(nz=args.nz, ny=args.ny, nx=args.nx, nt=args.nt, ns=args.shots)
+    grid, geom = fwi.from_problem(p)
+    ws = fwi.Workspace()
+    grp = fwi.Options(shot_group=args.shot_group)
+    npad = (p.nz + 2 * p.sponge) * (p.ny + 2 * p.sponge) * (p.nx + 2 * p.sponge)
+    g = min(p.nshots, args.shot_group or p.nshots)
+    fwi.profile(True)
+    torch.cuda.synchronize()
+    d_obs = fwi.forward(grid, geom, torch.as_tensor(p.v_true, device="cuda"), ws=ws, opts=grp)
+    ph = fwi.last_phase_times()
+    us = 1e3 * ph["forward_ms"] / max(1, ph["forward_launches"])
+    out = {"workload": f"dipping3d {p.nz}x{p.ny}x{p.nx}, {p.nshots} shots, nt {p.nt}, {p.nrec} receivers",
+           "shot_group": g, "forward_us_per_level": us,
+           "forward_alg_GBps": 16 * npad * g / (us * 1e-6) / 1e9, "gradients": {}}
+    v = torch.as_tensor(p.v_init, device="cuda")
+    for snap in args.snap.split(","):
+        o = fwi.Options(ckpt="snapshot", snap=snap, shot_group=args.shot_group)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fwi.adjoint_gradient(grid, geom, v, d_obs, o, ws=ws)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out["gradients"][snap] = {"seconds": dt, "Gpts_per_s": p.phys_points * p.nt * p.nshots / dt / 1e9,
+                                  "workspace_GB": fwi.workspace_bytes(grid, geom, o, "gradient") / 1e9}
+    fwi.profile(False)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
