@@ -202,7 +202,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         return fail(FWI_ERR_INVALID_ARG, "offset Hessian needs hmax >= 0");
     pl.need_bwd = need_bwd;
     pl.need_seis_tab = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE);
-    pl.tf = make_tiling(L, pl.ns, pl.with_offh ? STEP_FWD_OFFH : STEP_FWD);
+    pl.tf = make_tiling(L, pl.ns, pl.with_offh ? STEP_FWD_OFFH : STEP_FWD, -1, 0, pl.hmax);
     pl.tb = make_tiling(L, pl.ns, STEP_BWD);
     const size_t fbytes = (size_t)L.fstride * sizeof(float);
     const size_t nphys = (size_t)L.nz * L.nx;
@@ -1361,7 +1361,7 @@ fwi_status make_batch(int nm, const fwi_grid *grids, const fwi_geometry *geoms, 
                         grids[0].nt);
         if (k > 0) { // a launch runs one kernel: model 0's tile variants for all
             const StepKind fk = pl[k].with_offh ? STEP_FWD_OFFH : STEP_FWD;
-            pl[k].tf = make_tiling(pl[k].L, pl[k].ns, fk, pl[0].tf.variant, pl[0].tf.chunk);
+            pl[k].tf = make_tiling(pl[k].L, pl[k].ns, fk, pl[0].tf.variant, pl[0].tf.chunk, pl[k].hmax);
             pl[k].tb = make_tiling(pl[k].L, pl[k].ns, STEP_BWD, pl[0].tb.variant, pl[0].tb.chunk);
         }
         base[k] = total;
@@ -1598,9 +1598,10 @@ fwi_status fwi_autotune(const fwi_grid *grid, const fwi_geometry *geom, const fw
         float best_ms = 1e30f;
         for (int vi = 0; vi < nv; ++vi)
             for (int ci = 0; ci < nc; ++ci) {
+                if (!step_variant_valid(kind, vi, pl.hmax)) continue;
                 Plan p = pl;
                 if (kk == 0)
-                    p.tf = make_tiling(p.L, p.ns, kind, vi, chunks[ci]);
+                    p.tf = make_tiling(p.L, p.ns, kind, vi, chunks[ci], pl.hmax);
                 else
                     p.tb = make_tiling(p.L, p.ns, kind, vi, chunks[ci]);
                 if ((s = upload_tables(p, geom, ws, st)) != FWI_OK) break;
@@ -1658,9 +1659,9 @@ fwi_status fwi_autotune_set(const fwi_grid *grid, const fwi_geometry *geom, cons
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_GRADIENT, false, pl);
     if (s != FWI_OK) return s;
     const StepKind fk = pl.with_offh ? STEP_FWD_OFFH : STEP_FWD;
-    if (choice[0] < 0 || choice[0] >= step_variants(fk) || choice[2] < 0 || choice[2] >= step_variants(STEP_BWD))
-        return fail(FWI_ERR_INVALID_ARG, "variant outside the compiled ones (%d forward, %d backward)",
-                    step_variants(fk), step_variants(STEP_BWD));
+    if (!step_variant_valid(fk, choice[0], pl.hmax) || !step_variant_valid(STEP_BWD, choice[2], pl.hmax))
+        return fail(FWI_ERR_INVALID_ARG, "variant outside the compiled ones (%d forward, %d backward) or not "
+                    "covering hmax=%d", step_variants(fk), step_variants(STEP_BWD), pl.hmax);
     if (choice[1] < 1 || choice[3] < 1) return fail(FWI_ERR_INVALID_ARG, "chunk must be >= 1");
     step_tuned_store(fk, pl.L, pl.ns, choice[0], choice[1]);
     step_tuned_store(STEP_BWD, pl.L, pl.ns, choice[2], choice[3]);

@@ -256,7 +256,10 @@ struct Tiling {
 enum StepKind { STEP_FWD = 0, STEP_FWD_OFFH = 1, STEP_BWD = 2 };
 // tiling of a kind of step: the given variant / chunk, or (variant < 0,
 // chunk <= 0) the autotuned ones of this problem shape, else the defaults
-Tiling make_tiling(const Lay2D &L, int ns, StepKind kind, int variant = -1, int chunk = 0);
+// (hmax: the offset Hessian's largest offset, for the variants of
+// STEP_FWD_OFFH, which cover hmax up to a compiled count)
+Tiling make_tiling(const Lay2D &L, int ns, StepKind kind, int variant = -1, int chunk = 0, int hmax = HMAX_LIMIT);
+bool step_variant_valid(StepKind kind, int variant, int hmax);
 // box sizes (x, y) of the halo and point tiles of a step kernel
 void step_boxes(StepKind kind, const Tiling &t, int &hx, int &hy, int &px, int &py);
 // most tiles of any variant (receiver tables are sized for it)

@@ -286,14 +286,17 @@ __device__ __forceinline__ void load_c2_tile(float *dst, const float *c2, const 
 template <int RZ, int HX, bool WITH_H, int STAGES, int SPI = 1>
 using FwdRing = Ring<8 * RZ, HX, SPI, SPI, STAGES, 2 * 8 * RZ * TX * 4>; // + c2 and damping tiles
 
-template <int RZ, int HX, bool WITH_H, int STAGES, int MINB, int NM, int SPI = 1>
+// NHC: offsets h = 0 .. NHC-1 of the offset Hessian are accumulated (any
+// hmax <= NHC-1; offsets above hmax are computed and not stored)
+template <int RZ, int HX, bool WITH_H, int STAGES, int MINB, int NM, int SPI = 1, int NHC = HMAX_LIMIT + 1>
 __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ Batch<FwdArgs, NM> B)
 {
     using R = FwdRing<RZ, HX, WITH_H, STAGES, SPI>;
     static_assert(SPI == 1 || R::HALO_B == R::HALO * 4, "contiguous shot tiles");
     constexpr int TZ = 8 * RZ;
     constexpr int TXS = R::TXS;
-    constexpr int NH = WITH_H ? HMAX_LIMIT + 1 : 1;
+    constexpr int NH = WITH_H ? NHC : 1;
+    static_assert(NHC >= 1 && NHC <= HMAX_LIMIT + 1, "offset count");
     constexpr int WL = WITH_H ? HMAX_LIMIT : RADIUS; // x-window left extent
     constexpr int NW = (2 * WL + 4) / 4;             // float4s in the x-window
     constexpr int D = STAGES - 1;                    // items in flight ahead of the compute
@@ -529,21 +532,20 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                 if (WITH_H) {
                     // u(x+h) u(x-h); even h on aligned lane pairs
 #pragma unroll
-                    for (int h = 0; h < NH; ++h)
-                        if (h <= a.hmax) {
-                            if ((h & 1) == 0) {
+                    for (int h = 0; h < NH; ++h) {
+                        if ((h & 1) == 0) {
 #pragma unroll
-                                for (int q = 0; q < 2; ++q)
-                                    acc_h[h][q] = fma2(f2(w[WL + 2 * q + h], w[WL + 2 * q + 1 + h]),
-                                                       f2(w[WL + 2 * q - h], w[WL + 2 * q + 1 - h]), acc_h[h][q]);
-                            } else {
+                            for (int q = 0; q < 2; ++q)
+                                acc_h[h][q] = fma2(f2(w[WL + 2 * q + h], w[WL + 2 * q + 1 + h]),
+                                                   f2(w[WL + 2 * q - h], w[WL + 2 * q + 1 - h]), acc_h[h][q]);
+                        } else {
 #pragma unroll
-                                for (int q = 0; q < 2; ++q) {
-                                    acc_h[h][q].x = fmaf(w[WL + 2 * q + h], w[WL + 2 * q - h], acc_h[h][q].x);
-                                    acc_h[h][q].y = fmaf(w[WL + 2 * q + 1 + h], w[WL + 2 * q + 1 - h], acc_h[h][q].y);
-                                }
+                            for (int q = 0; q < 2; ++q) {
+                                acc_h[h][q].x = fmaf(w[WL + 2 * q + h], w[WL + 2 * q - h], acc_h[h][q].x);
+                                acc_h[h][q].y = fmaf(w[WL + 2 * q + 1 + h], w[WL + 2 * q + 1 - h], acc_h[h][q].y);
                             }
                         }
+                    }
                 }
             }
         }
@@ -864,22 +866,23 @@ namespace {
 // ring stages, minimum resident CTAs per SM (the register cap).
 struct Variant {
     int rz, spi, smem; // tile rows / 8, shots per item, dynamic shared memory
+    int nh;            // offsets of the offset Hessian it accumulates (valid for hmax <= nh - 1)
     const void *fn[2]; // one model per launch, batch of up to BATCH_MAX models
     int occ[2];        // resident CTAs per SM (from the occupancy calculator)
 };
 
 #define FWD_VARIANT(RZ, ST, MINB, SPI)                                                     \
-    {RZ, SPI, FwdRing<RZ, RADIUS, false, ST, SPI>::SMEM,                                   \
+    {RZ, SPI, FwdRing<RZ, RADIUS, false, ST, SPI>::SMEM, 0,                                \
      {(const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, 1, SPI>,                       \
       (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, BATCH_MAX, SPI>},              \
      {0, 0}}
-#define FWDH_VARIANT(ST, MINB, SPI)                                                        \
-    {1, SPI, FwdRing<1, HMAX_LIMIT, true, ST, SPI>::SMEM,                                  \
-     {(const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, 1, SPI>,                     \
-      (const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, BATCH_MAX, SPI>},            \
+#define FWDH_VARIANT(ST, MINB, SPI, NHC)                                                   \
+    {1, SPI, FwdRing<1, HMAX_LIMIT, true, ST, SPI>::SMEM, NHC,                             \
+     {(const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, 1, SPI, NHC>,                \
+      (const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, BATCH_MAX, SPI, NHC>},       \
      {0, 0}}
 #define BWD_VARIANT(RZ, ST, MINB)                                                          \
-    {RZ, 1, BwdRing<RZ, ST>::SMEM,                                                         \
+    {RZ, 1, BwdRing<RZ, ST>::SMEM, 0,                                                      \
      {(const void *)k_bwd_step<RZ, ST, MINB, 1>, (const void *)k_bwd_step<RZ, ST, MINB, BATCH_MAX>}, \
      {0, 0}}
 
@@ -890,7 +893,8 @@ Variant g_var_f[] = {FWD_VARIANT(2, 3, 4, 1), FWD_VARIANT(4, 2, 4, 1), FWD_VARIA
 // forward with the offset Hessian: 64 x 8 tiles, halo 12 (its 44 register
 // accumulators rule out taller tiles), one or two shots per item (the
 // accumulators serve both shots of an item)
-Variant g_var_h[] = {FWDH_VARIANT(3, 4, 1), FWDH_VARIANT(3, 4, 2)};
+// and the offset count compiled for hmax <= 12 or <= 10
+Variant g_var_h[] = {FWDH_VARIANT(3, 4, 1, 13), FWDH_VARIANT(3, 4, 2, 13), FWDH_VARIANT(3, 4, 2, 11)};
 // backward: 64 x 16 tiles (2 stages, 4 CTAs/SM), 64 x 8 (5 CTAs/SM)
 Variant g_var_b[] = {BWD_VARIANT(2, 2, 4), BWD_VARIANT(1, 2, 5)};
 
@@ -1038,18 +1042,33 @@ void step_boxes(StepKind kind, const Tiling &t, int &hx, int &hy, int &px, int &
 
 int max_tiles(const Lay2D &L) { return ((L.nxp + TX - 1) / TX) * ((L.nzp + 7) / 8); }
 
-Tiling make_tiling(const Lay2D &L, int ns, StepKind kind, int variant, int chunk)
+bool step_variant_valid(StepKind kind, int variant, int hmax)
+{
+    int n = 0;
+    Variant *vs = variants(kind, n);
+    if (variant < 0 || variant >= n) return false;
+    return kind != STEP_FWD_OFFH || hmax <= vs[variant].nh - 1;
+}
+
+Tiling make_tiling(const Lay2D &L, int ns, StepKind kind, int variant, int chunk, int hmax)
 {
     prepare_kernels();
     int n = 0;
     Variant *vs = variants(kind, n);
-    if (variant < 0 || variant >= n) {
+    if (!step_variant_valid(kind, variant, hmax)) {
         int tv = 0, tc = 0;
-        if (step_tuned_lookup(kind, L, ns, tv, tc) && tv >= 0 && tv < n) {
+        if (step_tuned_lookup(kind, L, ns, tv, tc) && step_variant_valid(kind, tv, hmax)) {
             variant = tv;
             if (chunk <= 0) chunk = tc;
         } else {
+            // default: the first variant, or for the offset Hessian the one
+            // with the fewest offsets that covers hmax, two shots per item
             variant = 0;
+            if (kind == STEP_FWD_OFFH)
+                for (int i = 0; i < n; ++i)
+                    if (vs[i].spi == 2 && hmax <= vs[i].nh - 1 &&
+                        (!step_variant_valid(kind, variant, hmax) || vs[variant].spi != 2 || vs[i].nh < vs[variant].nh))
+                        variant = i;
         }
     }
     if (chunk <= 0) chunk = kind == STEP_FWD_OFFH ? CHUNKS_H[0] : CHUNKS_F[0];

@@ -14,7 +14,7 @@ from paper_1406_1864_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-N_FWD, N_FWDH, N_BWD = 4, 2, 2  # compiled variants of each kind
+N_FWD, N_FWDH, N_BWD = 4, 3, 2  # compiled variants of each kind
 
 
 @pytest.fixture(scope="module")
