@@ -74,7 +74,9 @@ enum {
     FWI_OP_GRADIENT = 2,       /* fwi_adjoint_gradient                      */
     FWI_OP_ILLUMINATION = 3,   /* fwi_illumination                          */
     FWI_OP_OFFSET_HESSIAN = 4, /* fwi_offset_hessian_diag                   */
-    FWI_OP_PRECONDITION = 5    /* fwi_precondition                          */
+    FWI_OP_PRECONDITION = 5,   /* fwi_precondition                          */
+    FWI_OP_BORN = 6,           /* fwi_born                                  */
+    FWI_OP_GN_HVP = 7          /* fwi_gauss_newton_hvp                      */
 };
 
 #define FWI_HMAX_LIMIT 12 /* largest offset (cells) of the offset Hessian */
@@ -200,6 +202,24 @@ fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geom
                               const fwi_options *opts, const float *const *v, const float *const *d_obs,
                               float *const *grad, float *const *grad_pre, double *misfit, float *const *illum,
                               float *const *offh, void *ws, size_t ws_bytes, void *stream);
+
+/* Born modelling [Eq. 4, as the exact derivative of fwi_forward's discrete
+   traces]: dseis = J dv, the change of the traces along the velocity change
+   dv, by the tangent-linear scheme (u and du = J dv advanced together).
+   v, dv DEVICE [nz][nx]; dseis DEVICE [nshots][nt][nrec] output. Workspace
+   of FWI_OP_BORN. 2-D, sponge checkpoints (opts may be NULL). */
+fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
+                    const float *dv, float *dseis, void *ws, size_t ws_bytes, void *stream);
+
+/* Gauss-Newton Hessian-vector product [Sec. 3, the Hessian of the
+   linearised problem]: hv = J^T J dv, Born modelling of dv followed by the
+   adjoint pass with the Born traces as adjoint source (the gradient's
+   imaging and fold: hv has the units of fwi_adjoint_gradient's grad).
+   v, dv DEVICE [nz][nx]; hv DEVICE [nz][nx] output. Workspace of
+   FWI_OP_GN_HVP. 2-D, sponge checkpoints. */
+fwi_status fwi_gauss_newton_hvp(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                                const float *v, const float *dv, float *hv, void *ws, size_t ws_bytes,
+                                void *stream);
 
 /* Tile autotuning: times every compiled tile variant and shot-chunk size of
    the gradient's forward step (with the offset Hessian if opts->hmax >= 0)

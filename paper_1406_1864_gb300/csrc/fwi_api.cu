@@ -68,8 +68,9 @@ struct Plan {
     bool with_offh = false; // forward kernel accumulates the offset Hessian
     bool need_bwd = false;  // adjoint pass (gradient / forward_save)
     bool need_seis_tab = false;
+    bool born = false;      // Born modelling (u and du = J dv together)
     Tiling tf{}, tb{};
-    Part scal, c2, damp, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab, sched;
+    Part scal, c2, damp, dc2, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab, sched;
     size_t tab_src = 0, tab_srcij = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0, tab_bshot = 0;
     Part adj_t; // adjoint source in backward-table order [nt][ns*nrec]
     // snapshot checkpoints (FWI_CKPT_SNAPSHOT): snapshot j holds level j*K
@@ -124,7 +125,9 @@ fwi_status check_geom(const fwi_grid *g, const fwi_geometry *ge, bool coords)
 fwi_status check_opts(const fwi_options *o, int op)
 {
     if (!o) {
-        if (op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_PRECONDITION) return FWI_OK;
+        if (op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_PRECONDITION || op == FWI_OP_BORN ||
+            op == FWI_OP_GN_HVP)
+            return FWI_OK;
         return fail(FWI_ERR_INVALID_ARG, "options are NULL");
     }
     if (o->misfit != FWI_MISFIT_OLS && o->misfit != FWI_MISFIT_TIME_INTEGRAL)
@@ -186,7 +189,10 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         off = align_up(off + bytes);
     };
     take(pl.scal, 256);
-    const bool need_bwd = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE);
+    const bool need_bwd = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_GN_HVP);
+    const bool born = (op == FWI_OP_BORN || op == FWI_OP_GN_HVP);
+    if (born && o && o->ckpt != FWI_CKPT_SPONGE)
+        return fail(FWI_ERR_INVALID_ARG, "Born modelling and Hessian-vector products use sponge checkpoints");
     pl.snap = need_bwd && o && o->ckpt == FWI_CKPT_SNAPSHOT;
     // scheduler counters: forward, backward, and (snapshots) re-propagation
     if (op != FWI_OP_PRECONDITION) take(pl.sched, (size_t)(pl.snap ? 3 : 2) * g->nt * sizeof(int));
@@ -202,12 +208,21 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         return fail(FWI_ERR_INVALID_ARG, "offset Hessian needs hmax >= 0");
     pl.need_bwd = need_bwd;
     pl.need_seis_tab = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE);
+    pl.born = born;
     pl.tf = make_tiling(L, pl.ns, pl.with_offh ? STEP_FWD_OFFH : STEP_FWD, -1, 0, pl.hmax);
-    pl.tb = make_tiling(L, pl.ns, STEP_BWD);
+    // the Born step runs on the backward step's default 64 x 16 tiles
+    pl.tb = born ? make_tiling(L, pl.ns, STEP_BWD, 0) : make_tiling(L, pl.ns, STEP_BWD);
     const size_t fbytes = (size_t)L.fstride * sizeof(float);
     const size_t nphys = (size_t)L.nz * L.nx;
     take(pl.c2, fbytes);
     take(pl.damp, fbytes);
+    if (born) {
+        take(pl.dc2, fbytes);
+        if (!pl.need_bwd) { // du^n, du^{n-1}
+            take(pl.p[0], fbytes * pl.ns);
+            take(pl.p[1], fbytes * pl.ns);
+        }
+    }
     take(pl.u[0], fbytes * pl.ns);
     take(pl.u[1], fbytes * pl.ns);
     if (pl.need_bwd) {
@@ -232,7 +247,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         }
         take(pl.acc_g, (size_t)L.nzp * L.nxp * sizeof(float));
     }
-    if (op == FWI_OP_GRADIENT) take(pl.syn, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
+    if (op == FWI_OP_GRADIENT || op == FWI_OP_GN_HVP) take(pl.syn, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
     if (pl.need_bwd) take(pl.adj_t, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
     if (op == FWI_OP_GRADIENT || op == FWI_OP_ILLUMINATION)
         take(pl.acc_i, nphys * sizeof(float));
@@ -250,7 +265,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
     const size_t mt = (size_t)max_tiles(L);
     tk(pl.tab_fptr, (mt * pl.ns + 1) * sizeof(int));
     tk(pl.tab_fent, std::max<size_t>(nent, 1) * sizeof(int2));
-    if (pl.need_bwd) {
+    if (pl.need_bwd || born) {
         tk(pl.tab_bptr, (mt * pl.ns + 1) * sizeof(int));
         tk(pl.tab_bent, std::max<size_t>(nent, 1) * sizeof(int2));
         tk(pl.tab_bshot, std::max<size_t>(nent, 1) * sizeof(int));
@@ -312,7 +327,7 @@ fwi_status upload_tables(const Plan &pl, const fwi_geometry *ge, void *ws, cudaS
     }
     if (pl.nrec > 0) {
         build_csr(pl, pl.tf, ge->rec, buf, pl.tab_fptr, pl.tab_fent);
-        if (pl.need_bwd) build_csr(pl, pl.tb, ge->rec, buf, pl.tab_bptr, pl.tab_bent, pl.tab_bshot);
+        if (pl.need_bwd || pl.born) build_csr(pl, pl.tb, ge->rec, buf, pl.tab_bptr, pl.tab_bent, pl.tab_bshot);
     }
     cudaError_t e = cudaMemcpyAsync(at<char>(ws, pl.tab), buf.data(), buf.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "upload of geometry tables");
@@ -436,6 +451,52 @@ fwi_status restore_snapshot(const Plan &pl, void *ws, int j, float *u, float *up
 // nm > 1: one batched launch per time level, sponge checkpoints only). Model
 // k's plan, geometry, workspace and outputs are pl[k], ge[k], ws[k], seis[k],
 // acc_i[k], acc_h[k] (outputs may be null).
+// Born time loop n = 0..nt-1: u and du = J dv advanced together (the du
+// buffers are the adjoint-state buffers p), Born traces into dseis; with
+// `save` the sponge checkpoint of u for a following adjoint pass
+fwi_status run_born(const Plan &pl, const fwi_geometry *ge, void *ws, float *dseis, bool save, cudaStream_t st)
+{
+    cudaError_t e;
+    BornArgs a{};
+    a.c = make_common(pl, ge, ws, pl.tb);
+    a.dc2 = at<float>(ws, pl.dc2);
+    a.band = save ? at<float>(ws, pl.band) : nullptr;
+    a.dseis = (dseis && pl.nrec > 0) ? dseis : nullptr;
+    a.rt.ptr = at<int>(ws, pl.tab, pl.tab_bptr);
+    a.rt.ent = at<int2>(ws, pl.tab, pl.tab_bent);
+    float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
+    float *DU[2] = {at<float>(ws, pl.p[0]), at<float>(ws, pl.p[1])};
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaMemsetAsync(DU[b], 0, pl.p[b].bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    int hx, hy, px, py;
+    step_boxes(STEP_BWD, pl.tb, hx, hy, px, py);
+    CUtensorMap uh[2], up[2], dh[2], dp[2];
+    for (int b = 0; b < 2; ++b)
+        if (!encode_field_map(&uh[b], U[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&up[b], U[b], pl.L, pl.ns, px, py) ||
+            !encode_field_map(&dh[b], DU[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&dp[b], DU[b], pl.L, pl.ns, px, py))
+            return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the wavefield buffers");
+    for (int n = 0; n < pl.nt; ++n) {
+        a.n = n;
+        a.last = n == pl.nt - 1;
+        a.tm_u = uh[n & 1];
+        a.tm_du = dh[n & 1];
+        a.tm_up = up[(n + 1) & 1];
+        a.tm_dup = dp[(n + 1) & 1];
+        a.uout = U[(n + 1) & 1];
+        a.duout = DU[(n + 1) & 1];
+        a.c.sched = at<int>(ws, pl.sched) + n;
+        if ((e = launch_born_step(a, pl.tb, st)) != cudaSuccess) return cuda_fail(e, "Born step");
+        t_launch[0]++;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if ((e = launch_check_finite(U[b], (long long)pl.ns * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess ||
+            (e = launch_check_finite(DU[b], (long long)pl.ns * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
+            return cuda_fail(e, "finite check");
+        t_launch[2] += 2;
+    }
+    return FWI_OK;
+}
+
 // (levels [n0, n1) only, and events around the step launches, when timing
 // tile variants)
 fwi_status run_forward_models(int nm, const Plan *pl, const fwi_geometry *const *ge, void *const *ws,
@@ -1397,7 +1458,7 @@ fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, c
                                int op, size_t *bytes)
 {
     if (!bytes) return fail(FWI_ERR_INVALID_ARG, "bytes is NULL");
-    if (op < FWI_OP_FORWARD || op > FWI_OP_PRECONDITION) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
+    if (op < FWI_OP_FORWARD || op > FWI_OP_GN_HVP) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
     if (grid && grid->ndim == 3) {
         Plan3 p3;
         fwi_status s3 = make_plan3(grid, geom, opts, op, false, p3);
@@ -1557,6 +1618,57 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
     if ((e = launch_precond(pl.L, grad, scale, kind, hmax, eps, out, at<unsigned>(ws, pl.scal, 12), st)) != cudaSuccess)
         return cuda_fail(e, "precondition kernel");
     t_launch[2] += 2;
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
+                    const float *dv, float *dseis, void *ws, size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_BORN, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || !dv || (!dseis && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v, dv or dseis is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.dc2), 0, pl.dc2.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_prep_dc2(pl.L, v, dv, at<float>(ws, pl.c2), at<float>(ws, pl.dc2), st)) != cudaSuccess)
+        return cuda_fail(e, "prep kernel");
+    t_launch[2]++;
+    if ((s = run_born(pl, geom, ws, dseis, false, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    prof_record(2, st);
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_gauss_newton_hvp(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                                const float *v, const float *dv, float *hv, void *ws, size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_GN_HVP, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || !dv || !hv) return fail(FWI_ERR_INVALID_ARG, "v, dv or hv is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.dc2), 0, pl.dc2.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_prep_dc2(pl.L, v, dv, at<float>(ws, pl.c2), at<float>(ws, pl.dc2), st)) != cudaSuccess)
+        return cuda_fail(e, "prep kernel");
+    t_launch[2]++;
+    float *dseis = at<float>(ws, pl.syn);
+    if ((s = run_born(pl, geom, ws, dseis, true, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    if ((s = run_backward(pl, geom, ws, dseis, st)) != FWI_OK) return s;
+    prof_record(2, st);
+    if ((e = launch_fold_grad(pl.L, at<float>(ws, pl.acc_g), 1, v, hv, st)) != cudaSuccess)
+        return cuda_fail(e, "fold kernel");
+    t_launch[2]++;
     prof_record(3, st);
     return finish(pl, ws, st);
 }

@@ -66,6 +66,23 @@ __global__ void k_prep_c2(const Lay2D L, const float *__restrict__ v, float *__r
     if (bad) atomicOr(status, bad);
 }
 
+// dc2 = 2 c2 dv / v on the padded grid (dv edge-replicated like v): the
+// derivative of c2 = (v dt/dx)^2 along dv
+__global__ void k_prep_dc2(const Lay2D L, const float *__restrict__ v, const float *__restrict__ dv,
+                           const float *__restrict__ c2, float *__restrict__ dc2)
+{
+    const long long n = (long long)L.nzp * L.nxp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / L.nxp), j = (int)(e - (long long)i * L.nxp);
+        const long long m = (long long)clampi(i - L.P, 0, L.nz - 1) * L.nx + clampi(j - L.P, 0, L.nx - 1);
+        const long long o = fidx(L, i, j);
+        // dv times a factor that does not depend on dv (correctly rounded
+        // quotient), so that dc2 scales exactly with dv
+        dc2[o] = dv[m] * __fdiv_rn(2.0f * c2[o], v[m]);
+    }
+}
+
 // 3-D: c2 and the sponge factor of every padded cell (edge-replicated
 // velocity; eta dt sums the three axes' parts, as the 2-D kernel does two)
 __global__ void k_prep3d(const Lay3D L, const float *__restrict__ v, float *__restrict__ c2,
@@ -346,6 +363,13 @@ cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float *dam
                            int *status, cudaStream_t st)
 {
     k_prep_c2<<<grid_for((long long)L.nzp * L.nxp), NT1, 0, st>>>(L, v, c2, damp, cfl_limit, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_dc2(const Lay2D &L, const float *v, const float *dv, const float *c2, float *dc2,
+                            cudaStream_t st)
+{
+    k_prep_dc2<<<grid_for((long long)L.nzp * L.nxp), NT1, 0, st>>>(L, v, dv, c2, dc2);
     return cudaGetLastError();
 }
 

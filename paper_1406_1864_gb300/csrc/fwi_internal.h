@@ -234,6 +234,21 @@ cudaError_t launch_finish_accum_n(long long nphys, const float *acc, int groups,
 cudaError_t launch_precond_n(long long nphys, const float *grad, const float *scale, int kind, int hmax, float eps,
                              float *out, unsigned *pmax, cudaStream_t st);
 
+// Born (tangent-linear) step: u and du = J dv advanced together
+struct BornArgs {
+    CUtensorMap tm_u;      // u^n, halo box
+    CUtensorMap tm_du;     // du^n, halo box
+    CUtensorMap tm_up;     // u^{n-1}, point box
+    CUtensorMap tm_dup;    // du^{n-1}, point box
+    StepCommon c;
+    const float *dc2;      // 2 c2 dv / v, field layout
+    float *uout, *duout;   // u^{n+1} and du^{n+1} written here
+    float *band;           // sponge checkpoint of u^{n+1} (for an adjoint pass) or null
+    float *dseis;          // [ns][nt][nrec] Born traces du^n at the receivers, or null
+    RecTable rt;
+    int n, last;
+};
+
 // status bits written by kernels
 enum : int {
     ST_NONFINITE = 1,
@@ -280,6 +295,11 @@ cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st);
 // same time level (per-model arguments and tilings of the same kind)
 cudaError_t launch_fwd_batch(const FwdArgs *a, const Tiling *t, int nm, bool with_offh, cudaStream_t st);
 cudaError_t launch_bwd_batch(const BwdArgs *a, const Tiling *t, int nm, cudaStream_t st);
+// Born step over all shots (the backward step's tiling: two halo fields)
+cudaError_t launch_born_step(const BornArgs &a, const Tiling &t, cudaStream_t st);
+// dc2 = 2 c2 dv / v on the padded grid (edge-replicated dv)
+cudaError_t launch_prep_dc2(const Lay2D &L, const float *v, const float *dv, const float *c2, float *dc2,
+                            cudaStream_t st);
 
 // auxiliary kernels (fwi_aux.cu)
 cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float *damp, float cfl_limit,

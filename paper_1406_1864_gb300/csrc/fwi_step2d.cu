@@ -148,6 +148,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __device__ __forceinline__ bool has_rec(const FwdArgs &a) { return a.seis != nullptr; }
 __device__ __forceinline__ bool has_rec(const BwdArgs &a) { return a.adj != nullptr; }
+__device__ __forceinline__ bool has_rec(const BornArgs &a) { return a.dseis != nullptr; }
 
 // Stage the descriptor of the CTA's next item into a ring slot (lane 0 of
 // warp 1 only): model, tile and shot from the chunk cursor (shared memory),
@@ -859,6 +860,205 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     if (cur_tile >= 0) flush();
 }
 
+// -------------------------------------------------------------- Born step
+// The tangent-linear of the forward step along dv (Born modelling, Eq. 4, in
+// the discrete form whose adjoint is the backward step):
+//   u^{n+1}  = u^n  + fma(c2 ia, q^n, kb (u^n - u^{n-1})),      q^n = Lhat u^n + f delta_s
+//   du^{n+1} = du^n + ia (c2 Lhat du^n + dc2 q^n) + kb (du^n - du^{n-1}),
+// dc2 = 2 c2 dv / v, ia = 1 / (1 + eta dt), kb = 2 ia - 1; Born traces du^n at
+// the receivers. Same tiles, ring and scheduling as the backward step (two
+// halo fields and two point fields per item).
+template <int RZ, int STAGES>
+using BornRing = Ring<8 * RZ, RADIUS, 2, 2, STAGES, 3 * 8 * RZ * TX * 4>; // + c2, dc2, damping tiles
+
+template <int RZ, int STAGES, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__ Batch<BornArgs, 1> B)
+{
+    using R = BornRing<RZ, STAGES>;
+    constexpr int TZ = 8 * RZ;
+    constexpr int HX = RADIUS;
+    constexpr int TXS = R::TXS;
+    constexpr int D = STAGES - 1;
+    static_assert(D >= 1 && D + 2 <= DESC_RING, "needs 2 <= STAGES <= 7");
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_abort;
+    __shared__ ItemDesc s_desc[DESC_RING];
+    __shared__ Cursor s_cu;
+    unsigned char *smem = align_smem(smem_raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    float *c2s = reinterpret_cast<float *>(R::extra(smem));
+    float *dcs = c2s + TZ * TX;  // dc2 tile
+    float *dms = dcs + TZ * TX;  // damping tile (sponge tiles)
+
+    const BornArgs &a = B.m[0];
+    const StepCommon &c = a.c;
+    const Lay2D &L = c.L;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < STAGES; ++k) mbar_init(smem_u32(&bars[k]), 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    auto stage = [&](int slot) { stage_desc_async<1>(&s_desc[slot % DESC_RING], s_cu, B, a.n, !a.last); };
+    auto issue = [&](const ItemDesc &d, int k) {
+        const int bz = d.tile / c.ntx, bx = d.tile - bz * c.ntx;
+        const int bi = bz * TZ, bj = bx * TX;
+        const int st = k % STAGES;
+        const uint32_t bar = smem_u32(&bars[st]);
+        fence_proxy_async_smem();
+        mbar_expect_tx(bar, (2 * R::HALO + (a.last ? 0 : 2 * R::PT)) * 4);
+        tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_u, GXL + bj - HX, bi, d.s, bar);
+        tma_load_3d(smem_u32(R::halo(smem, st, 1)), &a.tm_du, GXL + bj - HX, bi, d.s, bar);
+        if (!a.last) {
+            tma_load_3d(smem_u32(R::point(smem, st, 0)), &a.tm_up, GXL + bj, bi + GZ, d.s, bar);
+            tma_load_3d(smem_u32(R::point(smem, st, 1)), &a.tm_dup, GXL + bj, bi + GZ, d.s, bar);
+        }
+    };
+    if (threadIdx.x == 32) {
+        cursor_init(s_cu, B);
+        for (int k = 0; k <= D; ++k) stage(k);
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < D; ++k)
+            if (s_desc[k].tile >= 0) issue(s_desc[k], k);
+
+    int cur_tile = -1, bi = 0, bj = 0, i0 = 0, j0 = 0;
+    bool tile_sponge = false, colok = false;
+    SpongeInfo<RZ> sg;
+    for (int k = 0;; ++k) {
+        if (threadIdx.x == 0) {
+            const ItemDesc d = s_desc[(k + D) % DESC_RING];
+            if (d.tile >= 0) issue(d, k + D);
+        } else if (threadIdx.x == 32) {
+            stage(k + D + 1);
+        }
+        const ItemDesc now = s_desc[k % DESC_RING];
+        if (now.tile < 0) {
+            if (threadIdx.x == 32) cp_async_wait_all();
+            break;
+        }
+        const int s = now.s;
+        if (now.tile != cur_tile) {
+            cur_tile = now.tile;
+            const int bz = cur_tile / c.ntx, bx = cur_tile - bz * c.ntx;
+            bi = bz * TZ;
+            bj = bx * TX;
+            i0 = bi + ty * RZ;
+            j0 = bj + 4 * tx;
+            tile_sponge = bi < L.P || bi + TZ > L.P + L.nz || bj < L.P || bj + TX > L.P + L.nx;
+            colok = j0 < L.nxp;
+            if (tile_sponge) sg.init(L, i0, j0);
+            load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
+            load_c2_tile<TZ>(dcs, a.dc2, L, bi, bj);
+            if (tile_sponge) load_c2_tile<TZ>(dms, c.damp, L, bi, bj);
+            __syncthreads();
+        }
+        const int st = k % STAGES;
+        if (stage_ready<STAGES>(bars, k, &s_abort)) {
+            const float *su = R::halo(smem, st, 0);
+            const float *sd = R::halo(smem, st, 1);
+            // Born traces du^n = R du^n
+            if (a.dseis != nullptr) {
+                float *ds = a.dseis + ((long long)s * c.nt + a.n) * c.nrec;
+                for (int e = now.rb + (int)threadIdx.x; e < now.re; e += TPB) {
+                    const int2 en = a.rt.ent[e];
+                    const int zl = en.x / TX, xl = en.x - zl * TX;
+                    ds[en.y] = sd[(zl + RADIUS) * TXS + HX + xl];
+                }
+            }
+            if (!a.last) {
+                const float *pu = R::point(smem, st, 0);
+                const float *pd = R::point(smem, st, 1);
+                const long long so = (long long)s * L.fstride;
+                const int sslot = source_slot<RZ>(now, i0, j0);
+                float2 qu[RZ][2], qd[RZ][2];
+#pragma unroll
+                for (int fld = 0; fld < 2; ++fld) {
+                    const float *sf = fld == 0 ? su : sd;
+                    float4 zc[RZ + 2 * RADIUS];
+#pragma unroll
+                    for (int kk = 0; kk < RZ + 2 * RADIUS; ++kk) zc[kk] = lds4(&sf[(ty * RZ + kk) * TXS + HX + 4 * tx]);
+#pragma unroll
+                    for (int r = 0; r < RZ; ++r) {
+                        const float *rw = &sf[(ty * RZ + r + RADIUS) * TXS + HX + 4 * tx];
+                        const float4 a0 = lds4(rw - 4), a2 = lds4(rw + 4);
+                        const float4 a1 = zc[r + RADIUS];
+                        const float w[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+                        if (fld == 0)
+                            lap4<4, RZ + 2 * RADIUS, false>(qu[r], w, zc, r);
+                        else
+                            lap4<4, RZ + 2 * RADIUS, false>(qd[r], w, zc, r);
+                    }
+                }
+                const float amp = now.amp * c.src_scale;
+#pragma unroll
+                for (int r = 0; r < RZ; ++r) {
+                    if (sslot == r * 4 + 0) qu[r][0].x += amp;
+                    if (sslot == r * 4 + 1) qu[r][0].y += amp;
+                    if (sslot == r * 4 + 2) qu[r][1].x += amp;
+                    if (sslot == r * 4 + 3) qu[r][1].y += amp;
+                    const int sr = ty * RZ + r + RADIUS;
+                    const float4 uc = lds4(&su[sr * TXS + HX + 4 * tx]);
+                    const float4 dc = lds4(&sd[sr * TXS + HX + 4 * tx]);
+                    const float4 up4 = lds4(&pu[(ty * RZ + r) * TX + 4 * tx]);
+                    const float4 dp4 = lds4(&pd[(ty * RZ + r) * TX + 4 * tx]);
+                    const float4 c24 = lds4(&c2s[(ty * RZ + r) * TX + 4 * tx]);
+                    const float4 dc24 = lds4(&dcs[(ty * RZ + r) * TX + 4 * tx]);
+                    float2 un[2], dn[2];
+                    if (!tile_sponge) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float2 u1 = half2of(uc, h), d1 = half2of(dc, h);
+                            un[h] = add2(u1, fma2(half2of(c24, h), qu[r][h], sub2(u1, half2of(up4, h))));
+                            dn[h] = add2(d1, fma2(half2of(c24, h), qd[r][h],
+                                                  fma2(half2of(dc24, h), qu[r][h], sub2(d1, half2of(dp4, h)))));
+                        }
+                    } else {
+                        const float4 ia4 = lds4(&dms[(ty * RZ + r) * TX + 4 * tx]);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float2 ia2 = half2of(ia4, h);
+                            const float2 kb = fma2(ia2, make_float2(2.f, 2.f), make_float2(-1.f, -1.f));
+                            const float2 u1 = half2of(uc, h), d1 = half2of(dc, h);
+                            un[h] = add2(u1, fma2(mul2(half2of(c24, h), ia2), qu[r][h], mul2(kb, sub2(u1, half2of(up4, h)))));
+                            const float2 src2 = fma2(half2of(c24, h), qd[r][h], mul2(half2of(dc24, h), qu[r][h]));
+                            dn[h] = add2(d1, fma2(ia2, src2, mul2(kb, sub2(d1, half2of(dp4, h)))));
+                        }
+                    }
+                    const int i = i0 + r;
+                    if (colok && i < L.nzp) {
+                        const float uo[4] = {un[0].x, un[0].y, un[1].x, un[1].y};
+                        const float dox[4] = {dn[0].x, dn[0].y, dn[1].x, dn[1].y};
+                        store4(a.uout + so + fidx(L, i, j0), j0, L.nxp, uo);
+                        store4(a.duout + so + fidx(L, i, j0), j0, L.nxp, dox);
+                        if (tile_sponge && a.band != nullptr && sg.brow[r] != -1) {
+                            float *bb = a.band + ((long long)s * c.nt + a.n + 1) * L.nbandp;
+                            if (sg.brow[r] >= 0) {
+                                *reinterpret_cast<float4 *>(bb + sg.brow[r]) = make_float4(uo[0], uo[1], uo[2], uo[3]);
+                            } else {
+#pragma unroll
+                                for (int p = 0; p < 4; ++p)
+                                    if (in_band(L, i, j0 + p)) bb[band_index(L, i, j0 + p)] = uo[p];
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (threadIdx.x == 32) cp_async_wait_all();
+        __syncthreads();
+        if (s_abort) {
+            abort_drain_ring<STAGES>(bars, s_desc, k, c.status);
+            return;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 namespace {
 // Compiled tile variants of each kind of step (index 0 is the default; the
@@ -1118,6 +1318,31 @@ cudaError_t launch_bwd_batch(const BwdArgs *a, const Tiling *t, int nm, cudaStre
     const Variant &v = variants(STEP_BWD, n)[t[0].variant];
     Batch<BwdArgs, BATCH_MAX> b;
     return launch_variant(v, 1, b, batch_fill(b, a, t, nm, v.occ[1]), st);
+}
+
+namespace {
+constexpr int BORN_RZ = 2, BORN_ST = 2, BORN_MINB = 3;
+#define K_BORN k_born_step<BORN_RZ, BORN_ST, BORN_MINB>
+constexpr int SMEM_BORN = BornRing<BORN_RZ, BORN_ST>::SMEM;
+std::once_flag g_born_once;
+int g_occ_born = 2;
+} // namespace
+
+cudaError_t launch_born_step(const BornArgs &a, const Tiling &t, cudaStream_t st)
+{
+    std::call_once(g_born_once, [] {
+        cudaFuncSetAttribute(K_BORN, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BORN);
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, K_BORN, TPB, SMEM_BORN) == cudaSuccess && occ > 0)
+            g_occ_born = occ;
+        cudaGetLastError();
+    });
+    if (t.tz != 8 * BORN_RZ) return cudaErrorInvalidValue;
+    Batch<BornArgs, 1> b;
+    const int ctas = batch_fill(b, &a, &t, 1, g_occ_born);
+    if (ctas <= 0) return cudaSuccess;
+    K_BORN<<<ctas, TPB, SMEM_BORN, st>>>(b);
+    return cudaGetLastError();
 }
 
 // Tensor map over `nfields` stored fields [nfields][rows][pitch] (float32)

@@ -18,7 +18,8 @@ from ._lib import FwiError  # noqa: F401  (re-export)
 
 OPS = {"forward": L.FWI_OP_FORWARD, "forward_save": L.FWI_OP_FORWARD_SAVE,
        "gradient": L.FWI_OP_GRADIENT, "illumination": L.FWI_OP_ILLUMINATION,
-       "offset_hessian": L.FWI_OP_OFFSET_HESSIAN, "precondition": L.FWI_OP_PRECONDITION}
+       "offset_hessian": L.FWI_OP_OFFSET_HESSIAN, "precondition": L.FWI_OP_PRECONDITION,
+       "born": L.FWI_OP_BORN, "gn_hvp": L.FWI_OP_GN_HVP}
 
 
 @dataclass
@@ -324,6 +325,36 @@ def illumination(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options | No
     L.check(L.load().fwi_illumination(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(oc), _ptr(v),
                                       _ptr(out), _ptr(buf), nb, _stream(stream)), "fwi_illumination")
     return out
+
+
+def born(grid: Grid, geom: Geometry, v: torch.Tensor, dv: torch.Tensor, *, ws=None, out=None,
+         stream=None) -> torch.Tensor:
+    """fwi_born: Born traces J dv [ns, nt, nrec], the derivative of the
+    traces along the velocity change dv (Eq. 4)."""
+    _dev(v, "v", grid.shape)
+    _dev(dv, "dv", grid.shape)
+    d = out if out is not None else torch.empty((geom.nshots, grid.nt, geom.nrec), dtype=torch.float32,
+                                                device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, None, "born"))
+    g, ge = grid.c(), geom.c()
+    L.check(L.load().fwi_born(ctypes.byref(g), ctypes.byref(ge), None, _ptr(v), _ptr(dv), _ptr(d), _ptr(buf),
+                              nb, _stream(stream)), "fwi_born")
+    return d
+
+
+def gauss_newton_hvp(grid: Grid, geom: Geometry, v: torch.Tensor, dv: torch.Tensor, *, ws=None, out=None,
+                     stream=None) -> torch.Tensor:
+    """fwi_gauss_newton_hvp: J^T J dv [nz, nx], the Gauss-Newton Hessian of
+    the OLS misfit applied to dv (Born modelling, then adjoint imaging of the
+    Born traces)."""
+    _dev(v, "v", grid.shape)
+    _dev(dv, "dv", grid.shape)
+    hv = out if out is not None else torch.empty(grid.shape, dtype=torch.float32, device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, None, "gn_hvp"))
+    g, ge = grid.c(), geom.c()
+    L.check(L.load().fwi_gauss_newton_hvp(ctypes.byref(g), ctypes.byref(ge), None, _ptr(v), _ptr(dv), _ptr(hv),
+                                          _ptr(buf), nb, _stream(stream)), "fwi_gauss_newton_hvp")
+    return hv
 
 
 def offset_hessian_diag(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options, *, ws=None,

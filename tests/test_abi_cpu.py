@@ -33,7 +33,8 @@ def test_header_declares_the_boundary():
     for must in ["fwi_forward", "fwi_adjoint_gradient", "fwi_illumination", "fwi_offset_hessian_diag",
                  "fwi_adjoint_apply", "fwi_workspace_bytes", "fwi_last_error", "fwi_batch_gradient",
                  "fwi_batch_workspace_bytes", "fwi_exec_gradient_create", "fwi_exec_run", "fwi_exec_destroy",
-                 "fwi_autotune", "fwi_autotune_reset", "fwi_autotune_set"]:
+                 "fwi_autotune", "fwi_autotune_reset", "fwi_autotune_set", "fwi_born",
+                 "fwi_gauss_newton_hvp"]:
         assert must in names
 
 
@@ -170,6 +171,35 @@ def test_call_argument_errors_before_any_device_work(lib):
     st = lib.fwi_forward(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1),
                          ctypes.c_void_p(1), 0, ctypes.c_void_p(256), 1 << 40, None)
     assert st == L.FWI_ERR_INVALID_ARG
+
+
+def test_born_workspace_and_errors(lib):
+    """Born modelling keeps u and du (four wavefield buffers); the
+    Gauss-Newton product adds the Born traces and the backward pass's
+    state, the same as a gradient without the illumination. Both take only
+    sponge checkpoints and reject NULL inputs before any device work."""
+    from paper_1406_1864_gb300 import _lib as L
+    g, ge, o, keep = _structs()
+    st, fwd = ws_bytes(lib, g, ge, None, L.FWI_OP_FORWARD)
+    st1, born = ws_bytes(lib, g, ge, None, L.FWI_OP_BORN)
+    st2, hvp = ws_bytes(lib, g, ge, None, L.FWI_OP_GN_HVP)
+    st3, grad = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
+    assert st == st1 == st2 == st3 == L.FWI_OK, lib.fwi_last_error()
+    nzp, nxp = 30 + 20, 40 + 20
+    assert born >= fwd + 2 * 2 * nzp * nxp * 4   # du^n, du^{n-1} for 2 shots
+    assert born < hvp and hvp >= grad - 30 * 40 * 4 * 2
+    o.ckpt = L.FWI_CKPT_SNAPSHOT
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_GN_HVP)[0] == L.FWI_ERR_INVALID_ARG
+    assert ws_bytes(lib, g, ge, None, 8)[0] == L.FWI_ERR_INVALID_ARG
+    st = lib.fwi_born(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1), None, ctypes.c_void_p(1),
+                      ctypes.c_void_p(256), 1 << 40, None)
+    assert st == L.FWI_ERR_INVALID_ARG
+    st = lib.fwi_gauss_newton_hvp(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1), ctypes.c_void_p(1),
+                                  None, ctypes.c_void_p(256), 1 << 40, None)
+    assert st == L.FWI_ERR_INVALID_ARG
+    st = lib.fwi_born(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1), ctypes.c_void_p(1),
+                      ctypes.c_void_p(1), ctypes.c_void_p(256), 16, None)
+    assert st == L.FWI_ERR_NOMEM
 
 
 def test_product_path_does_not_import_the_oracle():
