@@ -63,6 +63,12 @@ typedef enum {
     FWI_ERR_UNSTABLE = 6     /* a wavefield became non-finite                 */
 } fwi_status;
 
+/* Stability limits of the leapfrog schemes: every cell needs
+   v dt / dx <= FWI_CFL_LIMIT_2D (2-D, 17-point Laplacian) or
+   FWI_CFL_LIMIT_3D (3-D, 25-point); calls over it return FWI_ERR_CFL. */
+#define FWI_CFL_LIMIT_2D 0.5546f
+#define FWI_CFL_LIMIT_3D 0.4529f
+
 enum { FWI_MISFIT_OLS = 0, FWI_MISFIT_TIME_INTEGRAL = 1 };
 enum { FWI_ILLUM_U2 = 0, FWI_ILLUM_UTT2 = 1 };
 enum { FWI_PRECOND_NONE = 0, FWI_PRECOND_ILLUM = 1, FWI_PRECOND_OFFSET = 2 };
@@ -76,7 +82,8 @@ enum {
     FWI_OP_OFFSET_HESSIAN = 4, /* fwi_offset_hessian_diag                   */
     FWI_OP_PRECONDITION = 5,   /* fwi_precondition                          */
     FWI_OP_BORN = 6,           /* fwi_born                                  */
-    FWI_OP_GN_HVP = 7          /* fwi_gauss_newton_hvp                      */
+    FWI_OP_GN_HVP = 7,         /* fwi_gauss_newton_hvp                      */
+    FWI_OP_MISFIT = 8          /* fwi_misfit                                */
 };
 
 #define FWI_HMAX_LIMIT 12 /* largest offset (cells) of the offset Hessian */
@@ -203,6 +210,15 @@ fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geom
                               float *const *grad, float *const *grad_pre, double *misfit, float *const *illum,
                               float *const *offh, void *ws, size_t ws_bytes, void *stream);
 
+/* Misfit only [Sec. 2 OLS misfit, or Eq. 2 with misfit =
+   FWI_MISFIT_TIME_INTEGRAL]: forward modelling of every shot, the residual
+   against d_obs and J in FP64, without checkpoints or the adjoint pass (the
+   trial steps of a line search). v DEVICE [nz][nx]; d_obs DEVICE
+   [nshots][nt][nrec]; misfit DEVICE double, written. opts may be NULL (OLS).
+   Workspace of FWI_OP_MISFIT. 2-D. */
+fwi_status fwi_misfit(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
+                      const float *d_obs, double *misfit, void *ws, size_t ws_bytes, void *stream);
+
 /* Born modelling [Eq. 4, as the exact derivative of fwi_forward's discrete
    traces]: dseis = J dv, the change of the traces along the velocity change
    dv, by the tangent-linear scheme (u and du = J dv advanced together).
@@ -212,11 +228,13 @@ fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_op
                     const float *dv, float *dseis, void *ws, size_t ws_bytes, void *stream);
 
 /* Gauss-Newton Hessian-vector product [Sec. 3, the Hessian of the
-   linearised problem]: hv = J^T J dv, Born modelling of dv followed by the
-   adjoint pass with the Born traces as adjoint source (the gradient's
-   imaging and fold: hv has the units of fwi_adjoint_gradient's grad).
-   v, dv DEVICE [nz][nx]; hv DEVICE [nz][nx] output. Workspace of
-   FWI_OP_GN_HVP. 2-D, sponge checkpoints. */
+   linearised problem]: hv = J^T W^T W J dv, Born modelling of dv followed by
+   the adjoint pass with the weighted Born traces as adjoint source (the
+   gradient's imaging and fold: hv has the units of fwi_adjoint_gradient's
+   grad). W is the misfit's data weighting: the identity for the OLS misfit
+   (opts NULL or misfit = FWI_MISFIT_OLS), the time integral C of Eq. 2 for
+   misfit = FWI_MISFIT_TIME_INTEGRAL. v, dv DEVICE [nz][nx]; hv DEVICE
+   [nz][nx] output. Workspace of FWI_OP_GN_HVP. 2-D, sponge checkpoints. */
 fwi_status fwi_gauss_newton_hvp(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
                                 const float *v, const float *dv, float *hv, void *ws, size_t ws_bytes,
                                 void *stream);

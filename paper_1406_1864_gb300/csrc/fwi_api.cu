@@ -53,7 +53,7 @@ fwi_status cuda_fail(cudaError_t e, const char *where)
 
 // Stability limit of v dt / dx for the 8th-order / leapfrog pair in 2-D:
 // (v dt/dx)^2 * 2 * max|symbol| <= 4, max|symbol| = 205/72 + 2(8/5 + 1/5 + 8/315 + 1/560).
-constexpr float CFL_2D = 0.5546f;
+constexpr float CFL_2D = FWI_CFL_LIMIT_2D;
 
 constexpr size_t ALIGN = 256;
 inline size_t align_up(size_t x, size_t a = ALIGN) { return (x + a - 1) / a * a; }
@@ -126,7 +126,7 @@ fwi_status check_opts(const fwi_options *o, int op)
 {
     if (!o) {
         if (op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_PRECONDITION || op == FWI_OP_BORN ||
-            op == FWI_OP_GN_HVP)
+            op == FWI_OP_GN_HVP || op == FWI_OP_MISFIT)
             return FWI_OK;
         return fail(FWI_ERR_INVALID_ARG, "options are NULL");
     }
@@ -207,7 +207,8 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
     if (op == FWI_OP_OFFSET_HESSIAN && pl.hmax < 0)
         return fail(FWI_ERR_INVALID_ARG, "offset Hessian needs hmax >= 0");
     pl.need_bwd = need_bwd;
-    pl.need_seis_tab = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE);
+    pl.need_seis_tab = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE ||
+                        op == FWI_OP_MISFIT);
     pl.born = born;
     pl.tf = make_tiling(L, pl.ns, pl.with_offh ? STEP_FWD_OFFH : STEP_FWD, -1, 0, pl.hmax);
     // the Born step runs on the backward step's default 64 x 16 tiles
@@ -247,7 +248,7 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         }
         take(pl.acc_g, (size_t)L.nzp * L.nxp * sizeof(float));
     }
-    if (op == FWI_OP_GRADIENT || op == FWI_OP_GN_HVP) take(pl.syn, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
+    if (op == FWI_OP_GRADIENT || op == FWI_OP_GN_HVP || op == FWI_OP_MISFIT) take(pl.syn, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
     if (pl.need_bwd) take(pl.adj_t, (size_t)pl.ns * pl.nt * pl.nrec * sizeof(float));
     if (op == FWI_OP_GRADIENT || op == FWI_OP_ILLUMINATION)
         take(pl.acc_i, nphys * sizeof(float));
@@ -866,7 +867,7 @@ fwi_status gradient_models(int nm, const Plan *pl, const fwi_geometry *const *ge
 // ---------------------------------------------------------------------- 3-D
 // Stability limit of v dt / dx in 3-D: (v dt/dx)^2 * 3 * max|symbol| <= 4
 // with the 1-D max|symbol| of the 2-D limit above.
-constexpr float CFL_3D = 0.4529f;
+constexpr float CFL_3D = FWI_CFL_LIMIT_3D;
 
 fwi_status check_grid3(const fwi_grid *g)
 {
@@ -1458,7 +1459,7 @@ fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, c
                                int op, size_t *bytes)
 {
     if (!bytes) return fail(FWI_ERR_INVALID_ARG, "bytes is NULL");
-    if (op < FWI_OP_FORWARD || op > FWI_OP_GN_HVP) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
+    if (op < FWI_OP_FORWARD || op > FWI_OP_MISFIT) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
     if (grid && grid->ndim == 3) {
         Plan3 p3;
         fwi_status s3 = make_plan3(grid, geom, opts, op, false, p3);
@@ -1622,6 +1623,41 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
     return finish(pl, ws, st);
 }
 
+fwi_status fwi_misfit(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
+                      const float *d_obs, double *misfit, void *ws, size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_MISFIT, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || !misfit || (!d_obs && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v, d_obs or misfit is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    float *syn = at<float>(ws, pl.syn);
+    if ((s = run_forward(pl, geom, ws, syn, false, nullptr, nullptr, 0, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    cudaError_t e;
+    double *J = at<double>(ws, pl.scal, 0);
+    const long long nsamp = (long long)pl.ns * pl.nt * pl.nrec;
+    const bool integral = opts && opts->misfit == FWI_MISFIT_TIME_INTEGRAL;
+    if (nsamp > 0) {
+        if ((e = launch_residual_ols(syn, d_obs, nsamp, integral ? nullptr : J, st)) != cudaSuccess)
+            return cuda_fail(e, "residual kernel");
+        t_launch[2]++;
+        if (integral) {
+            if ((e = launch_time_integral(syn, pl.ns, pl.nt, pl.nrec, pl.L.dt, J, st)) != cudaSuccess)
+                return cuda_fail(e, "time-integral kernel");
+            t_launch[2]++;
+        }
+    }
+    if ((e = cudaMemcpyAsync(misfit, J, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    prof_record(2, st);
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
 fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                     const float *dv, float *dseis, void *ws, size_t ws_bytes, void *stream)
 {
@@ -1664,6 +1700,14 @@ fwi_status fwi_gauss_newton_hvp(const fwi_grid *grid, const fwi_geometry *geom, 
     float *dseis = at<float>(ws, pl.syn);
     if ((s = run_born(pl, geom, ws, dseis, true, st)) != FWI_OK) return s;
     prof_record(1, st);
+    if (opts && opts->misfit == FWI_MISFIT_TIME_INTEGRAL && (long long)pl.ns * pl.nrec > 0) {
+        // W^T W = C^T C of Eq. 2 on the Born traces (the misfit of the Born
+        // traces goes to the call's scratch word)
+        if ((e = launch_time_integral(dseis, pl.ns, pl.nt, pl.nrec, pl.L.dt, at<double>(ws, pl.scal, 0), st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "time-integral kernel");
+        t_launch[2]++;
+    }
     if ((s = run_backward(pl, geom, ws, dseis, st)) != FWI_OK) return s;
     prof_record(2, st);
     if ((e = launch_fold_grad(pl.L, at<float>(ws, pl.acc_g), 1, v, hv, st)) != cudaSuccess)

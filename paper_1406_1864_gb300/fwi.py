@@ -19,7 +19,7 @@ from ._lib import FwiError  # noqa: F401  (re-export)
 OPS = {"forward": L.FWI_OP_FORWARD, "forward_save": L.FWI_OP_FORWARD_SAVE,
        "gradient": L.FWI_OP_GRADIENT, "illumination": L.FWI_OP_ILLUMINATION,
        "offset_hessian": L.FWI_OP_OFFSET_HESSIAN, "precondition": L.FWI_OP_PRECONDITION,
-       "born": L.FWI_OP_BORN, "gn_hvp": L.FWI_OP_GN_HVP}
+       "born": L.FWI_OP_BORN, "gn_hvp": L.FWI_OP_GN_HVP, "misfit": L.FWI_OP_MISFIT}
 
 
 @dataclass
@@ -327,6 +327,21 @@ def illumination(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options | No
     return out
 
 
+def misfit(grid: Grid, geom: Geometry, v: torch.Tensor, d_obs: torch.Tensor, opts: Options | None = None, *,
+           ws=None, out=None, stream=None) -> torch.Tensor:
+    """fwi_misfit: the misfit J (0-d float64 CUDA tensor) of v against d_obs,
+    forward modelling only (OLS, or Eq. 2 with misfit="integral")."""
+    _dev(v, "v", grid.shape)
+    _dev(d_obs, "d_obs", (geom.nshots, grid.nt, geom.nrec))
+    J = out if out is not None else torch.zeros((), dtype=torch.float64, device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "misfit"))
+    g, ge = grid.c(), geom.c()
+    o = opts.c() if opts is not None else None
+    L.check(L.load().fwi_misfit(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o) if o is not None else None,
+                                _ptr(v), _ptr(d_obs), _ptr(J), _ptr(buf), nb, _stream(stream)), "fwi_misfit")
+    return J
+
+
 def born(grid: Grid, geom: Geometry, v: torch.Tensor, dv: torch.Tensor, *, ws=None, out=None,
          stream=None) -> torch.Tensor:
     """fwi_born: Born traces J dv [ns, nt, nrec], the derivative of the
@@ -342,18 +357,21 @@ def born(grid: Grid, geom: Geometry, v: torch.Tensor, dv: torch.Tensor, *, ws=No
     return d
 
 
-def gauss_newton_hvp(grid: Grid, geom: Geometry, v: torch.Tensor, dv: torch.Tensor, *, ws=None, out=None,
-                     stream=None) -> torch.Tensor:
-    """fwi_gauss_newton_hvp: J^T J dv [nz, nx], the Gauss-Newton Hessian of
-    the OLS misfit applied to dv (Born modelling, then adjoint imaging of the
-    Born traces)."""
+def gauss_newton_hvp(grid: Grid, geom: Geometry, v: torch.Tensor, dv: torch.Tensor, opts: Options | None = None,
+                     *, ws=None, out=None, stream=None) -> torch.Tensor:
+    """fwi_gauss_newton_hvp: J^T W^T W J dv [nz, nx], the Gauss-Newton
+    Hessian of the misfit applied to dv (Born modelling, then adjoint imaging
+    of the weighted Born traces; W = I for the OLS misfit, the time integral
+    for misfit="integral")."""
     _dev(v, "v", grid.shape)
     _dev(dv, "dv", grid.shape)
     hv = out if out is not None else torch.empty(grid.shape, dtype=torch.float32, device=v.device)
-    buf, nb = _ws(ws, workspace_bytes(grid, geom, None, "gn_hvp"))
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "gn_hvp"))
     g, ge = grid.c(), geom.c()
-    L.check(L.load().fwi_gauss_newton_hvp(ctypes.byref(g), ctypes.byref(ge), None, _ptr(v), _ptr(dv), _ptr(hv),
-                                          _ptr(buf), nb, _stream(stream)), "fwi_gauss_newton_hvp")
+    o = opts.c() if opts is not None else None
+    L.check(L.load().fwi_gauss_newton_hvp(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o) if o is not None else None,
+                                          _ptr(v), _ptr(dv), _ptr(hv), _ptr(buf), nb, _stream(stream)),
+            "fwi_gauss_newton_hvp")
     return hv
 
 

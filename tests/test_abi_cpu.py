@@ -34,7 +34,7 @@ def test_header_declares_the_boundary():
                  "fwi_adjoint_apply", "fwi_workspace_bytes", "fwi_last_error", "fwi_batch_gradient",
                  "fwi_batch_workspace_bytes", "fwi_exec_gradient_create", "fwi_exec_run", "fwi_exec_destroy",
                  "fwi_autotune", "fwi_autotune_reset", "fwi_autotune_set", "fwi_born",
-                 "fwi_gauss_newton_hvp"]:
+                 "fwi_gauss_newton_hvp", "fwi_misfit"]:
         assert must in names
 
 
@@ -190,7 +190,7 @@ def test_born_workspace_and_errors(lib):
     assert born < hvp and hvp >= grad - 30 * 40 * 4 * 2
     o.ckpt = L.FWI_CKPT_SNAPSHOT
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GN_HVP)[0] == L.FWI_ERR_INVALID_ARG
-    assert ws_bytes(lib, g, ge, None, 8)[0] == L.FWI_ERR_INVALID_ARG
+    assert ws_bytes(lib, g, ge, None, L.FWI_OP_MISFIT + 1)[0] == L.FWI_ERR_INVALID_ARG
     st = lib.fwi_born(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1), None, ctypes.c_void_p(1),
                       ctypes.c_void_p(256), 1 << 40, None)
     assert st == L.FWI_ERR_INVALID_ARG
@@ -200,6 +200,27 @@ def test_born_workspace_and_errors(lib):
     st = lib.fwi_born(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1), ctypes.c_void_p(1),
                       ctypes.c_void_p(1), ctypes.c_void_p(256), 16, None)
     assert st == L.FWI_ERR_NOMEM
+
+
+def test_misfit_workspace_and_header_constants(lib):
+    """fwi_misfit keeps the forward fields and the residual traces (no
+    checkpoints); the Python constants mirror the header's."""
+    from paper_1406_1864_gb300 import _lib as L
+    g, ge, o, keep = _structs()
+    _, fwd = ws_bytes(lib, g, ge, None, L.FWI_OP_FORWARD)
+    st, mis = ws_bytes(lib, g, ge, None, L.FWI_OP_MISFIT)
+    _, grad = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
+    assert st == L.FWI_OK
+    assert mis >= fwd + 2 * 100 * 5 * 4 and mis < grad
+    st = lib.fwi_misfit(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1), ctypes.c_void_p(1), None,
+                        ctypes.c_void_p(256), 1 << 40, None)
+    assert st == L.FWI_ERR_INVALID_ARG
+    text = open(os.path.join(ROOT, "include", "fwi.h")).read()
+    for name in ("FWI_CFL_LIMIT_2D", "FWI_CFL_LIMIT_3D"):
+        m = re.search(r"#define\s+%s\s+([0-9.]+)f" % name, text)
+        assert m and float(m.group(1)) == getattr(L, name), name
+    m = re.search(r"FWI_OP_MISFIT\s*=\s*(\d+)", text)
+    assert int(m.group(1)) == L.FWI_OP_MISFIT
 
 
 def test_product_path_does_not_import_the_oracle():

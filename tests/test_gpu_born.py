@@ -6,7 +6,8 @@
   v_true - v_init and for white noise that reaches the model edges (edge
   replication into the sponge).
 * J^T J dv against the oracle's adjoint imaging of the oracle's Born traces
-  (<= 1e-4), and against the library's own adjoint_apply of its Born traces
+  (<= 1e-4), J^T C^T C J dv (time-integral misfit, Eq. 2) likewise, and
+  against the library's own adjoint_apply of its Born traces
   after forward(save=True): the Born pass must leave the same sponge
   checkpoint as the forward pass.
 * Properties that hold at any size: linearity (J (2 dv) = 2 J dv to FP32
@@ -98,6 +99,20 @@ def test_gauss_newton_hvp_against_oracle(torch_cuda, oracle_mod, small, kind):
     ref = oracle_mod.gradient_for_adjoint_source(g, p.v_init, p.src, p.rec, w64, jdv)["grad"][:, 0, :]
     got = fwi.gauss_newton_hvp(grid, geom, v, torch_cuda.as_tensor(dv, device="cuda")).cpu().numpy()
     assert rel(got, ref) <= 1e-4, (kind, rel(got, ref))
+
+
+def test_gauss_newton_hvp_time_integral_misfit(torch_cuda, oracle_mod, small):
+    """H dv of the Eq. 2 misfit: J^T C^T C J dv."""
+    from paper_1406_1864_gb300 import fwi
+    p, g, grid, geom, v = small
+    dv = perturbations(p)["reflectivity"]
+    w64 = p.wavelet.astype(np.float64)
+    jdv = oracle_mod.born(g, p.v_init, dv, p.src, p.rec, w64)
+    adj = oracle_mod.time_integral_adjoint(oracle_mod.time_integral(jdv, p.dt), p.dt)
+    ref = oracle_mod.gradient_for_adjoint_source(g, p.v_init, p.src, p.rec, w64, adj)["grad"][:, 0, :]
+    got = fwi.gauss_newton_hvp(grid, geom, v, torch_cuda.as_tensor(dv, device="cuda"),
+                               fwi.Options(misfit="integral")).cpu().numpy()
+    assert rel(got, ref) <= 1e-4, rel(got, ref)
 
 
 def test_hvp_equals_adjoint_apply_of_born_traces(torch_cuda, small):
