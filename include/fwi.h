@@ -83,7 +83,10 @@ enum {
     FWI_OP_PRECONDITION = 5,   /* fwi_precondition                          */
     FWI_OP_BORN = 6,           /* fwi_born                                  */
     FWI_OP_GN_HVP = 7,         /* fwi_gauss_newton_hvp                      */
-    FWI_OP_MISFIT = 8          /* fwi_misfit                                */
+    FWI_OP_MISFIT = 8,         /* fwi_misfit                                */
+    FWI_OP_RECEIVER_FACTOR = 9, /* fwi_receiver_factor (kind from opts.precond
+                                   is not used: see fwi_receiver_factor)     */
+    FWI_OP_PRECONDITION_RECEIVER = 10 /* fwi_precondition_receiver         */
 };
 
 #define FWI_HMAX_LIMIT 12 /* largest offset (cells) of the offset Hessian */
@@ -218,6 +221,37 @@ fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geom
    Workspace of FWI_OP_MISFIT. 2-D. */
 fwi_status fwi_misfit(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                       const float *d_obs, double *misfit, void *ws, size_t ws_bytes, void *stream);
+
+/* Receiver-side factor R of the diagonal Hessian for a fixed receiver spread
+   (every shot records at the same cells) [Sec. 1 and Sec. 3: H_a's sum over
+   receivers of G(x, x_r) G(y, x_r), which Eq. 1 drops]. The source-side
+   preconditioners (illumination, offset-Hessian diagonal) times R give the
+   receiver-inclusive diagonal Hessian (fwi_precondition_receiver).
+   kind = FWI_RECV_PLESSIX_MULDER: Plessix and Mulder's analytic factor,
+     R(x) = asinh((x_max - x) / z) - asinh((x_min - x) / z), x_min, x_max the
+     spread's extent along x (m), z the depth below the receivers' mean row
+     (m), floored at dx / 2; out [nz][nx]; v may be NULL; no workspace.
+   kind = FWI_RECV_GREEN: receiver Green's-function correlations,
+     R(x, h) = sum_r sum_n G_r^n(x + h e_x) G_r^n(x - h e_x) dt, h = 0 ..
+     max(hmax, 0) (opts->hmax; opts NULL: 0), G_r the wavefield of a source
+     at receiver r with shot 0's wavelet, modelled in v; out
+     [max(hmax, 0) + 1][nz][nx]; workspace of FWI_OP_RECEIVER_FACTOR (the
+     receivers are modelled as nrec simultaneous independent sources).
+   A geometry whose shots do not share one receiver spread is refused
+   (FWI_ERR_INVALID_ARG). 2-D. */
+enum { FWI_RECV_PLESSIX_MULDER = 0, FWI_RECV_GREEN = 1 };
+fwi_status fwi_receiver_factor(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int kind,
+                               const float *v, float *out, void *ws, size_t ws_bytes, void *stream);
+
+/* Preconditioning by a source-side scale times a receiver factor
+   [Sec. 3.1 with the receiver term]: fwi_precondition with the scale
+   P(x, h) = scale(x, h) * recv(x, min(h, recv_planes - 1)), recv_planes = 1
+   (one factor for every offset, e.g. Plessix-Mulder's) or hmax + 1.
+   kind FWI_PRECOND_ILLUM (scale [nz][nx], h = 0 only) or FWI_PRECOND_OFFSET
+   (scale [hmax+1][nz][nx]). Workspace of FWI_OP_PRECONDITION_RECEIVER. */
+fwi_status fwi_precondition_receiver(const fwi_grid *grid, const float *grad, const float *scale, int kind,
+                                     int hmax, const float *recv, int recv_planes, float eps, float *out, void *ws,
+                                     size_t ws_bytes, void *stream);
 
 /* Born modelling [Eq. 4, as the exact derivative of fwi_forward's discrete
    traces]: dseis = J dv, the change of the traces along the velocity change

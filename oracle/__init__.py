@@ -16,7 +16,11 @@ parts that are clearest in numpy, each following the paper:
   the integral read as the inclusive rectangle rule dt * sum_{k<=n}, and its
   adjoint source C^T C r (reverse cumulative sum);
 * the gradient preconditioning of Sec. 3 / Fig. 5: g / (P + eps max P) with P the
-  shot illumination (Eq. 1) or the offset-Hessian diagonal summed over offsets.
+  shot illumination (Eq. 1) or the offset-Hessian diagonal summed over offsets;
+* the receiver side of the diagonal Hessian for a fixed spread (Sec. 1):
+  Plessix and Mulder's factor asinh((x_max - x)/z) - asinh((x_min - x)/z),
+  and the receiver Green's-function correlations sum_r sum_t G_r(x+h)
+  G_r(x-h) dt (the offset-Hessian pass with sources at the receivers).
 
 Parity pins: none of these functions is trusted on its own; tests/test_oracle_*
 check them against closed forms (2-D Green's function), adjoint dot products,
@@ -190,6 +194,33 @@ def eta(grid: Grid):
                         float(grid.vref), float(grid.refl), _ptr(out))
     _check(rc, "oracle_eta")
     return out
+
+
+# ------------------------------------------ receiver side of the Hessian (Sec. 1)
+
+def plessix_mulder_factor(nz, nx, dx, rec):
+    """Plessix and Mulder's receiver factor of the diagonal Hessian for one
+    receiver spread (Sec. 1): asinh((x_max - x)/z) - asinh((x_min - x)/z) at
+    every model cell, x = j dx, x_min / x_max the spread's extent (m), z the
+    depth (m) below the receivers' mean row, floored at dx / 2. rec: [nrec, 3]
+    (z, y, x) cells of the spread. Returns [nz, nx] float64."""
+    rec = np.asarray(rec).reshape(-1, 3)
+    x_min, x_max = rec[:, 2].min() * dx, rec[:, 2].max() * dx
+    zr = rec[:, 0].mean()
+    z = np.maximum(np.abs(np.arange(nz, dtype=np.float64) - zr) * dx, 0.5 * dx)[:, None]
+    x = np.arange(nx, dtype=np.float64)[None, :] * dx
+    return np.arcsinh((x_max - x) / z) - np.arcsinh((x_min - x) / z)
+
+
+def receiver_green_factor(grid: Grid, v, rec, wav0, hmax=0, nthreads=0):
+    """Receiver Green's-function correlations of a fixed spread (the
+    receiver sum of H_a, Sec. 1 / Sec. 3): sum_r sum_n G_r(x + h) G_r(x - h) dt,
+    h = 0..hmax, G_r the wavefield of a source at receiver r with the wavelet
+    wav0 [nt]. Returns [hmax + 1, nz, ny, nx]."""
+    rec = np.asarray(rec).reshape(-1, 3)
+    wav = np.repeat(np.asarray(wav0, np.float64).reshape(1, -1), rec.shape[0], axis=0)
+    none = np.zeros((rec.shape[0], 0, 3), np.int32)
+    return forward(grid, v, rec, none, wav, hmax=hmax, nthreads=nthreads)["offh"]
 
 
 # ---------------------------------------------------------------- misfits (Sec. 2)

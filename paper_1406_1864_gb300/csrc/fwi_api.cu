@@ -73,6 +73,7 @@ struct Plan {
     Part scal, c2, damp, dc2, u[2], p[2], band, syn, acc_i, acc_h, acc_g, tab, sched;
     size_t tab_src = 0, tab_srcij = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0, tab_bshot = 0;
     Part adj_t; // adjoint source in backward-table order [nt][ns*nrec]
+    Part prod;  // scale x receiver factor (fwi_precondition_receiver)
     // snapshot checkpoints (FWI_CKPT_SNAPSHOT): snapshot j holds level j*K
     bool snap = false;
     int snap_prec = FWI_SNAP_F32, K = 0, nck = 0;
@@ -126,7 +127,8 @@ fwi_status check_opts(const fwi_options *o, int op)
 {
     if (!o) {
         if (op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_PRECONDITION || op == FWI_OP_BORN ||
-            op == FWI_OP_GN_HVP || op == FWI_OP_MISFIT)
+            op == FWI_OP_GN_HVP || op == FWI_OP_MISFIT || op == FWI_OP_RECEIVER_FACTOR ||
+            op == FWI_OP_PRECONDITION_RECEIVER)
             return FWI_OK;
         return fail(FWI_ERR_INVALID_ARG, "options are NULL");
     }
@@ -176,7 +178,8 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
 {
     fwi_status st;
     if ((st = check_grid(g)) != FWI_OK) return st;
-    if (op != FWI_OP_PRECONDITION && (st = check_geom(g, ge, coords)) != FWI_OK) return st;
+    const bool no_geom = op == FWI_OP_PRECONDITION || op == FWI_OP_PRECONDITION_RECEIVER;
+    if (!no_geom && (st = check_geom(g, ge, coords)) != FWI_OK) return st;
     if ((st = check_opts(o, op)) != FWI_OK) return st;
     pl.L = make_layout(g);
     pl.op = op;
@@ -195,8 +198,10 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         return fail(FWI_ERR_INVALID_ARG, "Born modelling and Hessian-vector products use sponge checkpoints");
     pl.snap = need_bwd && o && o->ckpt == FWI_CKPT_SNAPSHOT;
     // scheduler counters: forward, backward, and (snapshots) re-propagation
-    if (op != FWI_OP_PRECONDITION) take(pl.sched, (size_t)(pl.snap ? 3 : 2) * g->nt * sizeof(int));
-    if (op == FWI_OP_PRECONDITION) {
+    if (!no_geom) take(pl.sched, (size_t)(pl.snap ? 3 : 2) * g->nt * sizeof(int));
+    if (no_geom) {
+        if (op == FWI_OP_PRECONDITION_RECEIVER)
+            take(pl.prod, (size_t)(FWI_HMAX_LIMIT + 1) * L.nz * L.nx * sizeof(float));
         pl.total = off;
         return FWI_OK;
     }
@@ -1404,6 +1409,55 @@ fwi_status gradient3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_o
 // Plans of a batch of models in one workspace: model k's parts start at
 // base[k]. Every model is checked as in fwi_adjoint_gradient; the models
 // share opts and nt.
+// The receivers of a fixed spread as nrec sources without receivers (the
+// receiver Green's functions), planned as an offset-Hessian pass, followed in
+// the workspace by the sources' wavelets (shot 0's, replicated).
+struct RecvPlan {
+    Plan pl;
+    fwi_geometry g2{};
+    std::vector<int> src;
+    fwi_options o2{};
+    int hmax = 0;
+    size_t wav_off = 0, total = 0;
+};
+
+// every shot records at the same cells (coords: the coordinates are read)
+fwi_status check_fixed_spread(const fwi_geometry *ge)
+{
+    if (ge->nrec < 1) return fail(FWI_ERR_INVALID_ARG, "the receiver factor needs receivers");
+    for (int s = 1; s < ge->nshots; ++s)
+        if (std::memcmp(ge->rec, ge->rec + 3 * (size_t)s * ge->nrec, 3 * (size_t)ge->nrec * sizeof(int)) != 0)
+            return fail(FWI_ERR_INVALID_ARG, "the receiver factor needs a fixed spread (shot %d records elsewhere)", s);
+    return FWI_OK;
+}
+
+fwi_status make_recv_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_options *o, bool coords, RecvPlan &rp)
+{
+    fwi_status s;
+    if ((s = check_grid(g)) != FWI_OK) return s;
+    if ((s = check_geom(g, ge, coords)) != FWI_OK) return s;
+    if ((s = check_opts(o, FWI_OP_RECEIVER_FACTOR)) != FWI_OK) return s;
+    if (coords && (s = check_fixed_spread(ge)) != FWI_OK) return s;
+    if (ge->nrec < 1) return fail(FWI_ERR_INVALID_ARG, "the receiver factor needs receivers");
+    rp.hmax = o ? std::max(o->hmax, 0) : 0;
+    rp.o2 = o ? *o : fwi_options{FWI_MISFIT_OLS, FWI_ILLUM_U2, 0, FWI_PRECOND_NONE, 1e-3f, FWI_CKPT_SPONGE,
+                                 FWI_SNAP_F32, 0, 0};
+    rp.o2.hmax = rp.hmax;
+    rp.o2.precond = FWI_PRECOND_NONE;
+    rp.g2.nshots = ge->nrec;
+    rp.g2.nrec = 0;
+    rp.g2.rec = nullptr;
+    rp.g2.wavelet = ge->wavelet; // replaced by the replicated wavelets at the call
+    if (coords) {
+        rp.src.assign(ge->rec, ge->rec + 3 * (size_t)ge->nrec);
+        rp.g2.src = rp.src.data();
+    }
+    if ((s = make_plan(g, &rp.g2, &rp.o2, FWI_OP_OFFSET_HESSIAN, coords, rp.pl)) != FWI_OK) return s;
+    rp.wav_off = align_up(rp.pl.total);
+    rp.total = rp.wav_off + (size_t)ge->nrec * g->nt * sizeof(float);
+    return FWI_OK;
+}
+
 fwi_status make_batch(int nm, const fwi_grid *grids, const fwi_geometry *geoms, const fwi_options *opts,
                       bool coords, std::vector<Plan> &pl, std::vector<size_t> &base, size_t &total)
 {
@@ -1459,12 +1513,21 @@ fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, c
                                int op, size_t *bytes)
 {
     if (!bytes) return fail(FWI_ERR_INVALID_ARG, "bytes is NULL");
-    if (op < FWI_OP_FORWARD || op > FWI_OP_MISFIT) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
+    if (op < FWI_OP_FORWARD || op > FWI_OP_PRECONDITION_RECEIVER)
+        return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
     if (grid && grid->ndim == 3) {
         Plan3 p3;
         fwi_status s3 = make_plan3(grid, geom, opts, op, false, p3);
         if (s3 != FWI_OK) return s3;
         *bytes = p3.total;
+        t_err.clear();
+        return FWI_OK;
+    }
+    if (op == FWI_OP_RECEIVER_FACTOR) {
+        RecvPlan rp;
+        fwi_status s = make_recv_plan(grid, geom, opts, false, rp);
+        if (s != FWI_OK) return s;
+        *bytes = rp.total;
         t_err.clear();
         return FWI_OK;
     }
@@ -1654,6 +1717,91 @@ fwi_status fwi_misfit(const fwi_grid *grid, const fwi_geometry *geom, const fwi_
     if ((e = cudaMemcpyAsync(misfit, J, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "copy");
     prof_record(2, st);
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_receiver_factor(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int kind,
+                               const float *v, float *out, void *ws, size_t ws_bytes, void *stream)
+{
+    fwi_status s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (kind == FWI_RECV_PLESSIX_MULDER) {
+        if ((s = check_grid(grid)) != FWI_OK) return s;
+        if ((s = check_geom(grid, geom, true)) != FWI_OK) return s;
+        if ((s = check_fixed_spread(geom)) != FWI_OK) return s;
+        if (!out) return fail(FWI_ERR_INVALID_ARG, "out is NULL");
+        int xmin = grid->nx, xmax = -1;
+        double zsum = 0;
+        for (int r = 0; r < geom->nrec; ++r) {
+            const int *q = geom->rec + 3 * r;
+            xmin = std::min(xmin, q[2]);
+            xmax = std::max(xmax, q[2]);
+            zsum += q[0];
+        }
+        cudaError_t e = launch_pm_factor(grid->nz, grid->nx, grid->dx, (float)xmin * grid->dx,
+                                         (float)xmax * grid->dx, (float)(zsum / geom->nrec), out, st);
+        if (e != cudaSuccess) return cuda_fail(e, "receiver-factor kernel");
+        t_err.clear();
+        return FWI_OK;
+    }
+    if (kind != FWI_RECV_GREEN) return fail(FWI_ERR_INVALID_ARG, "kind=%d unknown", kind);
+    RecvPlan rp;
+    if ((s = make_recv_plan(grid, geom, opts, true, rp)) != FWI_OK) return s;
+    if (!v || !out) return fail(FWI_ERR_INVALID_ARG, "v or out is NULL");
+    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
+        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
+    if (ws_bytes < rp.total) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, rp.total);
+    const Plan &pl = rp.pl;
+    begin_call(st);
+    cudaError_t e;
+    float *wav = reinterpret_cast<float *>(static_cast<char *>(ws) + rp.wav_off);
+    if ((e = launch_replicate_row(geom->wavelet, grid->nt, geom->nrec, wav, st)) != cudaSuccess)
+        return cuda_fail(e, "wavelet copy");
+    t_launch[2]++;
+    rp.g2.wavelet = wav;
+    if ((s = setup(pl, &rp.g2, v, ws, st)) != FWI_OK) return s;
+    float *acc_h = at<float>(ws, pl.acc_h);
+    if ((s = run_forward(pl, &rp.g2, ws, nullptr, false, nullptr, acc_h, 0, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    prof_record(2, st);
+    if ((e = launch_finish_accum(pl.L, acc_h, 1, rp.hmax + 1, pl.L.dt, out, st)) != cudaSuccess)
+        return cuda_fail(e, "receiver-factor output");
+    t_launch[2]++;
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_precondition_receiver(const fwi_grid *grid, const float *grad, const float *scale, int kind,
+                                     int hmax, const float *recv, int recv_planes, float eps, float *out, void *ws,
+                                     size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, nullptr, nullptr, FWI_OP_PRECONDITION_RECEIVER, false, pl);
+    if (s != FWI_OK) return s;
+    if (!grad || !scale || !recv || !out) return fail(FWI_ERR_INVALID_ARG, "grad, scale, recv or out is NULL");
+    if (kind != FWI_PRECOND_ILLUM && kind != FWI_PRECOND_OFFSET) return fail(FWI_ERR_INVALID_ARG, "kind=%d", kind);
+    if (kind == FWI_PRECOND_OFFSET && (hmax < 0 || hmax > FWI_HMAX_LIMIT))
+        return fail(FWI_ERR_INVALID_ARG, "hmax=%d outside 0..%d", hmax, FWI_HMAX_LIMIT);
+    const int planes = kind == FWI_PRECOND_OFFSET ? hmax + 1 : 1;
+    if (recv_planes != 1 && recv_planes < planes)
+        return fail(FWI_ERR_INVALID_ARG, "recv_planes=%d: 1 or >= %d", recv_planes, planes);
+    if (!(eps > 0.f)) return fail(FWI_ERR_INVALID_ARG, "eps must be > 0");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    prof_record(1, st);
+    prof_record(2, st);
+    cudaError_t e;
+    const long long nphys = (long long)pl.L.nz * pl.L.nx;
+    float *prod = at<float>(ws, pl.prod);
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.scal), 0, pl.scal.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_scale_product(nphys, planes, scale, recv, recv_planes, prod, st)) != cudaSuccess)
+        return cuda_fail(e, "scale product");
+    if ((e = launch_precond(pl.L, grad, prod, kind, hmax, eps, out, at<unsigned>(ws, pl.scal, 12), st)) != cudaSuccess)
+        return cuda_fail(e, "precondition kernel");
+    t_launch[2] += 3;
     prof_record(3, st);
     return finish(pl, ws, st);
 }

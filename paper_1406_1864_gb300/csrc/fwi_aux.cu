@@ -83,6 +83,43 @@ __global__ void k_prep_dc2(const Lay2D L, const float *__restrict__ v, const flo
     }
 }
 
+// Plessix-Mulder receiver factor of a fixed spread: the integral over the
+// receiver line of 1 / distance, asinh((xmax - x)/z) - asinh((xmin - x)/z),
+// x = j dx, z = |i - zr| dx floored at dx / 2 (the receiver row itself)
+__global__ void k_pm_factor(int nz, int nx, float dx, float xmin, float xmax, float zr, float *__restrict__ out)
+{
+    const long long n = (long long)nz * nx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+        const float z = fmaxf(fabsf((float)i - zr) * dx, 0.5f * dx);
+        const float x = (float)j * dx;
+        out[e] = asinhf((xmax - x) / z) - asinhf((xmin - x) / z);
+    }
+}
+
+// rows of a [rows][n] array all equal to src[0 .. n-1]
+__global__ void k_replicate_row(const float *__restrict__ src, int n, int rows, float *__restrict__ dst)
+{
+    const long long tot = (long long)rows * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x)
+        dst[e] = src[e % n];
+}
+
+// out[h][x] = scale[h][x] * recv[min(h, rn - 1)][x], h < planes
+__global__ void k_scale_product(long long nphys, int planes, const float *__restrict__ scale,
+                                const float *__restrict__ recv, int rn, float *__restrict__ out)
+{
+    const long long n = nphys * planes;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(e / nphys);
+        const long long x = e - (long long)h * nphys;
+        out[e] = scale[e] * recv[(long long)min(h, rn - 1) * nphys + x];
+    }
+}
+
 // 3-D: c2 and the sponge factor of every padded cell (edge-replicated
 // velocity; eta dt sums the three axes' parts, as the 2-D kernel does two)
 __global__ void k_prep3d(const Lay3D L, const float *__restrict__ v, float *__restrict__ c2,
@@ -370,6 +407,26 @@ cudaError_t launch_prep_dc2(const Lay2D &L, const float *v, const float *dv, con
                             cudaStream_t st)
 {
     k_prep_dc2<<<grid_for((long long)L.nzp * L.nxp), NT1, 0, st>>>(L, v, dv, c2, dc2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pm_factor(int nz, int nx, float dx, float xmin, float xmax, float zr, float *out,
+                             cudaStream_t st)
+{
+    k_pm_factor<<<grid_for((long long)nz * nx), NT1, 0, st>>>(nz, nx, dx, xmin, xmax, zr, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_replicate_row(const float *src, int n, int rows, float *dst, cudaStream_t st)
+{
+    k_replicate_row<<<grid_for((long long)n * rows), NT1, 0, st>>>(src, n, rows, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_product(long long nphys, int planes, const float *scale, const float *recv, int rn,
+                                 float *out, cudaStream_t st)
+{
+    k_scale_product<<<grid_for(nphys * planes), NT1, 0, st>>>(nphys, planes, scale, recv, rn, out);
     return cudaGetLastError();
 }
 

@@ -302,6 +302,12 @@ cudaError_t launch_prep_dc2(const Lay2D &L, const float *v, const float *dv, con
                             cudaStream_t st);
 
 // auxiliary kernels (fwi_aux.cu)
+// receiver factor of the diagonal Hessian and its product with a scale
+cudaError_t launch_pm_factor(int nz, int nx, float dx, float xmin, float xmax, float zr, float *out,
+                             cudaStream_t st);
+cudaError_t launch_replicate_row(const float *src, int n, int rows, float *dst, cudaStream_t st);
+cudaError_t launch_scale_product(long long nphys, int planes, const float *scale, const float *recv, int rn,
+                                 float *out, cudaStream_t st);
 cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float *damp, float cfl_limit,
                            int *status, cudaStream_t st);
 cudaError_t launch_residual_ols(float *syn, const float *obs, long long n, double *misfit,

@@ -19,7 +19,8 @@ from ._lib import FwiError  # noqa: F401  (re-export)
 OPS = {"forward": L.FWI_OP_FORWARD, "forward_save": L.FWI_OP_FORWARD_SAVE,
        "gradient": L.FWI_OP_GRADIENT, "illumination": L.FWI_OP_ILLUMINATION,
        "offset_hessian": L.FWI_OP_OFFSET_HESSIAN, "precondition": L.FWI_OP_PRECONDITION,
-       "born": L.FWI_OP_BORN, "gn_hvp": L.FWI_OP_GN_HVP, "misfit": L.FWI_OP_MISFIT}
+       "born": L.FWI_OP_BORN, "gn_hvp": L.FWI_OP_GN_HVP, "misfit": L.FWI_OP_MISFIT,
+       "receiver_factor": L.FWI_OP_RECEIVER_FACTOR, "precondition_receiver": L.FWI_OP_PRECONDITION_RECEIVER}
 
 
 @dataclass
@@ -403,6 +404,56 @@ def precondition(grid: Grid, grad: torch.Tensor, scale: torch.Tensor, kind: str,
     buf, nb = _ws(ws, int(nbytes.value))
     L.check(L.load().fwi_precondition(ctypes.byref(g), _ptr(grad), _ptr(scale), k, hmax, float(eps),
                                       _ptr(out), _ptr(buf), nb, _stream(stream)), "fwi_precondition")
+    return out
+
+
+def receiver_factor(grid: Grid, geom: Geometry, kind: str = "pm", v: torch.Tensor | None = None,
+                    opts: Options | None = None, *, ws=None, stream=None) -> torch.Tensor:
+    """fwi_receiver_factor for a fixed receiver spread: kind "pm" (Plessix
+    and Mulder's asinh factor, [nz, nx]) or "green" (receiver Green's-function
+    correlations in v, [max(hmax, 0) + 1, nz, nx] with hmax = opts.hmax)."""
+    g, ge = grid.c(), geom.c()
+    o = opts.c() if opts is not None else None
+    lib = L.load()
+    if kind == "pm":
+        out = torch.empty(grid.shape, dtype=torch.float32, device=geom.wavelet.device)
+        L.check(lib.fwi_receiver_factor(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o) if o is not None else None,
+                                        L.FWI_RECV_PLESSIX_MULDER, None, _ptr(out), None, 0, _stream(stream)),
+                "fwi_receiver_factor")
+        return out
+    if kind != "green":
+        raise ValueError(kind)
+    _dev(v, "v", grid.shape)
+    h = max(opts.hmax, 0) if opts is not None else 0
+    out = torch.empty((h + 1,) + grid.shape, dtype=torch.float32, device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "receiver_factor"))
+    L.check(lib.fwi_receiver_factor(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o) if o is not None else None,
+                                    L.FWI_RECV_GREEN, _ptr(v), _ptr(out), _ptr(buf), nb, _stream(stream)),
+            "fwi_receiver_factor")
+    return out
+
+
+def precondition_receiver(grid: Grid, grad: torch.Tensor, scale: torch.Tensor, kind: str, recv: torch.Tensor,
+                          eps=1e-3, *, ws=None, stream=None) -> torch.Tensor:
+    """fwi_precondition_receiver: grad / (P + eps max P) with P = scale x recv
+    (kind 'illum': [nz, nx] scale; 'offset': [hmax+1, nz, nx], summed over
+    offsets as fwi_precondition does). recv: [nz, nx] (one factor for every
+    offset) or [k, nz, nx], k = 1 or >= hmax + 1."""
+    _dev(grad, "grad", grid.shape)
+    k = {"illum": L.FWI_PRECOND_ILLUM, "offset": L.FWI_PRECOND_OFFSET}[kind]
+    hmax = scale.shape[0] - 1 if kind == "offset" else 0
+    _dev(scale, "scale", grid.shape if kind == "illum" else (hmax + 1,) + grid.shape)
+    rp = 1 if recv.dim() == 2 else recv.shape[0]
+    _dev(recv, "recv", grid.shape if recv.dim() == 2 else (rp,) + grid.shape)
+    out = torch.empty_like(grad)
+    g = grid.c()
+    nbytes = ctypes.c_size_t(0)
+    L.check(L.load().fwi_workspace_bytes(ctypes.byref(g), None, None, L.FWI_OP_PRECONDITION_RECEIVER,
+                                         ctypes.byref(nbytes)), "fwi_workspace_bytes")
+    buf, nb = _ws(ws, int(nbytes.value))
+    L.check(L.load().fwi_precondition_receiver(ctypes.byref(g), _ptr(grad), _ptr(scale), k, hmax, _ptr(recv), rp,
+                                               float(eps), _ptr(out), _ptr(buf), nb, _stream(stream)),
+            "fwi_precondition_receiver")
     return out
 
 

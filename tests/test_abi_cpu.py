@@ -34,7 +34,7 @@ def test_header_declares_the_boundary():
                  "fwi_adjoint_apply", "fwi_workspace_bytes", "fwi_last_error", "fwi_batch_gradient",
                  "fwi_batch_workspace_bytes", "fwi_exec_gradient_create", "fwi_exec_run", "fwi_exec_destroy",
                  "fwi_autotune", "fwi_autotune_reset", "fwi_autotune_set", "fwi_born",
-                 "fwi_gauss_newton_hvp", "fwi_misfit"]:
+                 "fwi_gauss_newton_hvp", "fwi_misfit", "fwi_receiver_factor", "fwi_precondition_receiver"]:
         assert must in names
 
 
@@ -190,7 +190,7 @@ def test_born_workspace_and_errors(lib):
     assert born < hvp and hvp >= grad - 30 * 40 * 4 * 2
     o.ckpt = L.FWI_CKPT_SNAPSHOT
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GN_HVP)[0] == L.FWI_ERR_INVALID_ARG
-    assert ws_bytes(lib, g, ge, None, L.FWI_OP_MISFIT + 1)[0] == L.FWI_ERR_INVALID_ARG
+    assert ws_bytes(lib, g, ge, None, L.FWI_OP_PRECONDITION_RECEIVER + 1)[0] == L.FWI_ERR_INVALID_ARG
     st = lib.fwi_born(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1), None, ctypes.c_void_p(1),
                       ctypes.c_void_p(256), 1 << 40, None)
     assert st == L.FWI_ERR_INVALID_ARG
@@ -221,6 +221,38 @@ def test_misfit_workspace_and_header_constants(lib):
         assert m and float(m.group(1)) == getattr(L, name), name
     m = re.search(r"FWI_OP_MISFIT\s*=\s*(\d+)", text)
     assert int(m.group(1)) == L.FWI_OP_MISFIT
+
+
+def test_receiver_factor_workspace_and_errors(lib):
+    """The Green's-function factor models the nrec receivers as sources
+    without receivers (an offset-Hessian pass) plus their wavelets; the
+    receiver preconditioning holds the product of scale and factor. Moving
+    spreads and NULL outputs are refused before any device work."""
+    from paper_1406_1864_gb300 import _lib as L
+    g, ge, o, (src, rec) = _structs(ns=2, nrec=5)
+    o.hmax = 2
+    st, rf = ws_bytes(lib, g, ge, o, L.FWI_OP_RECEIVER_FACTOR)
+    assert st == L.FWI_OK, lib.fwi_last_error()
+    nzp, nxp = 30 + 20, 40 + 20
+    assert rf >= 2 * 5 * nzp * nxp * 4 + 5 * 100 * 4   # u^n, u^{n-1} of 5 sources, their wavelets
+    st, pr = ws_bytes(lib, g, None, None, L.FWI_OP_PRECONDITION_RECEIVER)
+    assert st == L.FWI_OK and pr >= 13 * 30 * 40 * 4
+    out = ctypes.c_void_p(256)
+    st = lib.fwi_receiver_factor(ctypes.byref(g), ctypes.byref(ge), None, L.FWI_RECV_PLESSIX_MULDER, None, None,
+                                 None, 0, None)
+    assert st == L.FWI_ERR_INVALID_ARG
+    rec[1, 0, 2] += 1  # shot 1 records elsewhere
+    for kind in (L.FWI_RECV_PLESSIX_MULDER, L.FWI_RECV_GREEN):
+        st = lib.fwi_receiver_factor(ctypes.byref(g), ctypes.byref(ge), None, kind, ctypes.c_void_p(1), out,
+                                     ctypes.c_void_p(256), 1 << 40, None)
+        assert st == L.FWI_ERR_INVALID_ARG and b"fixed spread" in lib.fwi_last_error()
+    rec[1, 0, 2] -= 1
+    st = lib.fwi_receiver_factor(ctypes.byref(g), ctypes.byref(ge), None, 7, None, out, None, 0, None)
+    assert st == L.FWI_ERR_INVALID_ARG
+    st = lib.fwi_precondition_receiver(ctypes.byref(g), ctypes.c_void_p(1), ctypes.c_void_p(1), L.FWI_PRECOND_OFFSET,
+                                       4, ctypes.c_void_p(1), 3, ctypes.c_float(1e-3), ctypes.c_void_p(1),
+                                       ctypes.c_void_p(256), 1 << 40, None)
+    assert st == L.FWI_ERR_INVALID_ARG  # 3 factor planes for 5 offsets
 
 
 def test_product_path_does_not_import_the_oracle():
