@@ -17,6 +17,8 @@ parts that are clearest in numpy, each following the paper:
   adjoint source C^T C r (reverse cumulative sum);
 * the gradient preconditioning of Sec. 3 / Fig. 5: g / (P + eps max P) with P the
   shot illumination (Eq. 1) or the offset-Hessian diagonal summed over offsets;
+* (in C) extended Born modelling and extended migration with horizontal
+  subsurface offsets (Eq. 5, Eq. 6);
 * the receiver side of the diagonal Hessian for a fixed spread (Sec. 1):
   Plessix and Mulder's factor asinh((x_max - x)/z) - asinh((x_min - x)/z),
   and the receiver Green's-function correlations sum_r sum_t G_r(x+h)
@@ -65,7 +67,10 @@ def _load():
         lib.oracle_gradient.argtypes = grid + [p, i, p, p, i, p, p, p, p, p, i]
         lib.oracle_born.argtypes = grid + [p, p, i, p, p, i, p, p, i]
         lib.oracle_eta.argtypes = [i, i, i, i, i, d, d, d, p]
-        for f in (lib.oracle_forward, lib.oracle_gradient, lib.oracle_born, lib.oracle_eta):
+        lib.oracle_ext_born.argtypes = grid + [p, p, i, i, p, p, i, p, p, i]
+        lib.oracle_ext_migration.argtypes = grid + [p, i, p, p, i, p, p, i, p, i]
+        for f in (lib.oracle_forward, lib.oracle_gradient, lib.oracle_born, lib.oracle_eta, lib.oracle_ext_born,
+                  lib.oracle_ext_migration):
             f.restype = i
         _lib = lib
     return _lib
@@ -184,6 +189,35 @@ def born(grid: Grid, v, dv, src, rec, wav, nthreads=0):
                          _ptr(rec), _ptr(dseis), int(nthreads))
     _check(rc, "oracle_born")
     return dseis
+
+
+def extended_born(grid: Grid, v, dv_ext, src, rec, wav, he, nthreads=0):
+    """Extended Born modelling, Eq. 5: traces [ns, nt, nrec] of the extended
+    perturbation dv_ext [2 he + 1, nz, ny, nx] (horizontal subsurface offsets
+    h = -he..he): the incident field at x + h scatters from x - h."""
+    lib = _load()
+    src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    dv_ext = np.ascontiguousarray(dv_ext, dtype=np.float64).reshape(2 * he + 1, grid.nz, grid.ny, grid.nx)
+    dseis = np.zeros((ns, grid.nt, nrec))
+    rc = lib.oracle_ext_born(*grid.args(), _ptr(v), _ptr(dv_ext), int(he), ns, _ptr(src), _ptr(wav), nrec,
+                             _ptr(rec), _ptr(dseis), int(nthreads))
+    _check(rc, "oracle_ext_born")
+    return dseis
+
+
+def extended_migration(grid: Grid, v, src, rec, wav, adj, he, nthreads=0):
+    """Extended migration, Eq. 6, the adjoint of extended_born: the image
+    [2 he + 1, nz, ny, nx] of the adjoint source adj [ns, nt, nrec]."""
+    lib = _load()
+    src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    adj = np.ascontiguousarray(adj, dtype=np.float64).reshape(ns, grid.nt, nrec)
+    image = np.zeros((2 * he + 1, grid.nz, grid.ny, grid.nx))
+    rc = lib.oracle_ext_migration(*grid.args(), _ptr(v), ns, _ptr(src), _ptr(wav), nrec, _ptr(rec), _ptr(adj),
+                                  int(he), _ptr(image), int(nthreads))
+    _check(rc, "oracle_ext_migration")
+    return image
 
 
 def eta(grid: Grid):

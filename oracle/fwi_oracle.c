@@ -24,7 +24,12 @@
  *   - the diagonal of the localized subsurface-offset Hessian [Sec. 3, the
  *     Hessian obtained by substituting Eq. 5 into Eq. 6, diagonal part] as
  *     sum_s sum_n u_s^n(x + h e_x) u_s^n(x - h e_x) dt for h = 0..hmax;
- *   - the Born (tangent-linear) operator [Eq. 4] for the Jacobian dot test.
+ *   - the Born (tangent-linear) operator [Eq. 4] for the Jacobian dot test;
+ *   - extended Born modelling [Eq. 5]: the velocity perturbation dv(x, h)
+ *     carries a horizontal subsurface offset h; the incident field at x + h
+ *     scatters from x - h, and extended migration [Eq. 6] is its exact
+ *     adjoint, the correlation of the adjoint field at x - h with the
+ *     incident field at x + h.
  * The misfits (OLS and the time-integral misfit of Eq. 2), their adjoint
  * sources and the preconditioning division are done in oracle/__init__.py.
  *
@@ -275,6 +280,106 @@ static void born_shot(const grid_t *g, const double *vp, const double *dvp, cons
     for (int a = 0; a < 3; ++a) { free(u[a]); free(du[a]); }
 }
 
+/* Extended Born modelling of one shot [Eq. 5]: as born_shot, with the
+   scattering source at padded point y
+     S^n(y) = sum_{h=-he..he} 2 v(y + h e_x) dv(y + h e_x, h) dt^2 q^n(y + 2h e_x),
+   q^n = L u^n + s^n, zero where y + h or y + 2h leaves the padded grid.
+   dvp [2he+1][npad] holds dv(., h) for h = -he..he, edge-replicated. */
+static void ext_born_shot(const grid_t *g, const double *vp, const double *dvp, int he, const double *eta,
+                          long src, const double *wav, int nrec, const long *rec, double *dseis)
+{
+    const long N = g->npad;
+    const double dt = g->dt;
+    const double sscale = 1.0 / pow(g->dx, g->ndim);
+    double *u[3], *du[3];
+    for (int a = 0; a < 3; ++a) { u[a] = calloc(N, sizeof(double)); du[a] = calloc(N, sizeof(double)); }
+    double *q = calloc(N, sizeof(double));
+    double *um1 = u[0], *u0 = u[1], *up1 = u[2];
+    double *dum1 = du[0], *du0 = du[1], *dup1 = du[2];
+    for (int n = 0; n < g->nt; ++n) {
+        for (int r = 0; r < nrec; ++r) dseis[(long)n * nrec + r] = du0[rec[r]];
+        if (n == g->nt - 1) break;
+        for (int i = 0; i < g->nzp; ++i)
+            for (int k = 0; k < g->nyp; ++k)
+                for (int j = 0; j < g->nxp; ++j) {
+                    long p = ID(g, i, k, j);
+                    q[p] = lap(g, u0, i, k, j) + (p == src ? wav[n] * sscale : 0.0);
+                }
+        for (int i = 0; i < g->nzp; ++i)
+            for (int k = 0; k < g->nyp; ++k)
+                for (int j = 0; j < g->nxp; ++j) {
+                    long p = ID(g, i, k, j);
+                    double S = 0.0;
+                    for (int h = -he; h <= he; ++h) {
+                        int jx = j + h, jq = j + 2 * h;
+                        if (jx < 0 || jx >= g->nxp || jq < 0 || jq >= g->nxp) continue;
+                        long x = ID(g, i, k, jx);
+                        S += 2.0 * vp[x] * dvp[(long)(h + he) * N + x] * dt * dt * q[ID(g, i, k, jq)];
+                    }
+                    double c2 = vp[p] * vp[p] * dt * dt;
+                    double a = 1.0 + eta[p] * dt, b = 1.0 - eta[p] * dt;
+                    up1[p] = (2.0 * u0[p] - b * um1[p] + c2 * q[p]) / a;
+                    dup1[p] = (2.0 * du0[p] - b * dum1[p] + c2 * lap(g, du0, i, k, j) + S) / a;
+                }
+        double *t = um1; um1 = u0; u0 = up1; up1 = t;
+        t = dum1; dum1 = du0; du0 = dup1; dup1 = t;
+    }
+    for (int a = 0; a < 3; ++a) { free(u[a]); free(du[a]); }
+    free(q);
+}
+
+/* Extended migration of one shot [Eq. 6], the adjoint of ext_born_shot: the
+   adjoint field psi of adjoint_shot correlated across offsets,
+     gext[h][x] += psi^m(x - h e_x) q^{m-1}(x + h e_x) 2 v(x) / v(x - h e_x)^2,
+   for padded x with x - h and x + h inside the padded grid (at h = 0 the
+   gradient's imaging term). */
+static void ext_migration_shot(const grid_t *g, const double *vp, const double *eta, long src,
+                               const double *wav, int nrec, const long *rec, const double *adj, int he,
+                               double *gext)
+{
+    const long N = g->npad;
+    const double dt = g->dt;
+    const double sscale = 1.0 / pow(g->dx, g->ndim);
+    double *hist = malloc((size_t)g->nt * N * sizeof(double));
+    forward_shot(g, vp, eta, src, wav, 0, NULL, NULL, NULL, 0, 0, NULL, hist);
+    double *p2 = calloc(N, sizeof(double));
+    double *p1 = calloc(N, sizeof(double));
+    double *p0 = calloc(N, sizeof(double));
+    double *inj = calloc(N, sizeof(double));
+    double *q = calloc(N, sizeof(double));
+    for (int m = g->nt - 1; m >= 1; --m) {
+        memset(inj, 0, N * sizeof(double));
+        for (int r = 0; r < nrec; ++r) inj[rec[r]] += adj[(long)m * nrec + r];
+        for (int i = 0; i < g->nzp; ++i)
+            for (int k = 0; k < g->nyp; ++k)
+                for (int j = 0; j < g->nxp; ++j) {
+                    long p = ID(g, i, k, j);
+                    double c2 = vp[p] * vp[p] * dt * dt;
+                    p0[p] = (2.0 * p1[p] - (1.0 - eta[p] * dt) * p2[p] +
+                             c2 * (lap(g, p1, i, k, j) + inj[p])) /
+                            (1.0 + eta[p] * dt);
+                }
+        const double *um = hist + (long)(m - 1) * N;
+        for (int i = 0; i < g->nzp; ++i)
+            for (int k = 0; k < g->nyp; ++k)
+                for (int j = 0; j < g->nxp; ++j) {
+                    long p = ID(g, i, k, j);
+                    q[p] = lap(g, um, i, k, j) + (p == src ? wav[m - 1] * sscale : 0.0);
+                }
+        for (int h = -he; h <= he; ++h)
+            for (int i = 0; i < g->nzp; ++i)
+                for (int k = 0; k < g->nyp; ++k)
+                    for (int j = 0; j < g->nxp; ++j) {
+                        int jm = j - h, jp = j + h;
+                        if (jm < 0 || jm >= g->nxp || jp < 0 || jp >= g->nxp) continue;
+                        long x = ID(g, i, k, j), y = ID(g, i, k, jm);
+                        gext[(long)(h + he) * N + x] += p0[y] * q[ID(g, i, k, jp)] * 2.0 * vp[x] / (vp[y] * vp[y]);
+                    }
+        double *t = p2; p2 = p1; p1 = p0; p0 = t;
+    }
+    free(p2); free(p1); free(p0); free(inj); free(q); free(hist);
+}
+
 /* shared argument checks; fills padded source/receiver indices */
 static int prepare(grid_t *g, int ndim, int nz, int ny, int nx, int P, double dx, double dt,
                    int nt, double vref, double R, int ns, const int *src, int nrec, const int *rec,
@@ -423,6 +528,74 @@ int oracle_born(int ndim, int nz, int ny, int nx, int P, double dx, double dt, i
         born_shot(&g, vp, dvp, eta, src_p[s], wav + (long)s * nt, nrec, rec_p + (long)s * nrec,
                   dseis + (long)s * nt * nrec);
     free(vp); free(dvp); free(eta); free(src_p); free(rec_p);
+    return 0;
+}
+
+/* Extended Born modelling [Eq. 5]: dseis [ns][nt][nrec] from the extended
+   perturbation dv_ext [2he+1][nz][ny][nx] (offsets h = -he..he along x). */
+int oracle_ext_born(int ndim, int nz, int ny, int nx, int P, double dx, double dt, int nt,
+                    double vref, double R, const double *v, const double *dv_ext, int he, int ns,
+                    const int *src, const double *wav, int nrec, const int *rec, double *dseis, int nthreads)
+{
+    grid_t g;
+    long *src_p = NULL, *rec_p = NULL;
+    int rc = prepare(&g, ndim, nz, ny, nx, P, dx, dt, nt, vref, R, ns, src, nrec, rec, &src_p, &rec_p);
+    if (rc || he < 0) { free(src_p); free(rec_p); return rc ? rc : -1; }
+    const long nphys = (long)nz * ny * nx;
+    double *vp = malloc(g.npad * sizeof(double));
+    double *eta = malloc(g.npad * sizeof(double));
+    double *dvp = malloc((size_t)(2 * he + 1) * g.npad * sizeof(double));
+    pad_model(&g, v, vp, eta);
+    for (int h = 0; h <= 2 * he; ++h) pad_model(&g, dv_ext + h * nphys, dvp + h * g.npad, eta);
+    int T = nthreads_used(nthreads);
+#pragma omp parallel for schedule(static) num_threads(T)
+    for (int s = 0; s < ns; ++s)
+        ext_born_shot(&g, vp, dvp, he, eta, src_p[s], wav + (long)s * nt, nrec, rec_p + (long)s * nrec,
+                      dseis + (long)s * nt * nrec);
+    free(vp); free(dvp); free(eta); free(src_p); free(rec_p);
+    return 0;
+}
+
+/* Extended migration [Eq. 6] of the adjoint source adj [ns][nt][nrec]: the
+   image [2he+1][nz][ny][nx], the padded image of each sponge cell added to the
+   physical edge cell it replicates (the adjoint of the edge replication of
+   oracle_ext_born's dv_ext). */
+int oracle_ext_migration(int ndim, int nz, int ny, int nx, int P, double dx, double dt, int nt,
+                         double vref, double R, const double *v, int ns, const int *src, const double *wav,
+                         int nrec, const int *rec, const double *adj, int he, double *image, int nthreads)
+{
+    grid_t g;
+    long *src_p = NULL, *rec_p = NULL;
+    int rc = prepare(&g, ndim, nz, ny, nx, P, dx, dt, nt, vref, R, ns, src, nrec, rec, &src_p, &rec_p);
+    if (rc || he < 0) { free(src_p); free(rec_p); return rc ? rc : -1; }
+    const long nphys = (long)nz * ny * nx;
+    const long NE = (long)(2 * he + 1) * g.npad;
+    double *vp = malloc(g.npad * sizeof(double));
+    double *eta = malloc(g.npad * sizeof(double));
+    pad_model(&g, v, vp, eta);
+    int T = nthreads_used(nthreads);
+    double *g_t = calloc((size_t)T * NE, sizeof(double));
+#pragma omp parallel for schedule(static) num_threads(T)
+    for (int s = 0; s < ns; ++s) {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        ext_migration_shot(&g, vp, eta, src_p[s], wav + (long)s * nt, nrec, rec_p + (long)s * nrec,
+                           adj + (long)s * nt * nrec, he, g_t + t * NE);
+    }
+    memset(image, 0, (size_t)(2 * he + 1) * nphys * sizeof(double));
+    for (int t = 0; t < T; ++t)
+        for (int h = 0; h <= 2 * he; ++h)
+            for (int i = 0; i < g.nzp; ++i)
+                for (int k = 0; k < g.nyp; ++k)
+                    for (int j = 0; j < g.nxp; ++j) {
+                        int iz = clampi(i - P, 0, nz - 1);
+                        int iy = (ndim == 3) ? clampi(k - P, 0, ny - 1) : 0;
+                        int ix = clampi(j - P, 0, nx - 1);
+                        image[h * nphys + ((long)iz * ny + iy) * nx + ix] += g_t[t * NE + h * g.npad + ID(&g, i, k, j)];
+                    }
+    free(g_t); free(vp); free(eta); free(src_p); free(rec_p);
     return 0;
 }
 

@@ -41,6 +41,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 from typing import Callable
 
+import numpy as np
 import torch
 
 
@@ -246,13 +247,24 @@ class FwiObjective:
     (misfit, gradient and the chosen preconditioner's scale in one call),
     value(v) runs fwi_misfit. The inverse preconditioner divides by the
     call's scale as fwi_precondition does (precond "illum": the illumination
-    of Eq. 1; "offset": the offset-Hessian diagonal of Sec. 3; "none")."""
+    of Eq. 1; "offset": the offset-Hessian diagonal of Sec. 3; "none").
+    receiver = "pm" or "green" multiplies the scale by the receiver side of
+    the diagonal Hessian of a fixed spread (fwi_receiver_factor: Plessix and
+    Mulder's factor, computed once; or the receiver Green's-function
+    correlations in the current model, recomputed every receiver_every
+    gradients)."""
 
-    def __init__(self, grid, geom, d_obs, opts, ws=None, mute_top=0):
+    def __init__(self, grid, geom, d_obs, opts, ws=None, mute_top=0, receiver=None, receiver_every=1):
         from . import fwi
         self.fwi = fwi
         self.grid, self.geom, self.d_obs, self.opts = grid, geom, d_obs, opts
         self.ws = ws if ws is not None else fwi.Workspace()
+        if receiver not in (None, "pm", "green"):
+            raise ValueError(receiver)
+        if receiver is not None and opts.precond == "none":
+            raise ValueError("a receiver factor needs precond 'illum' or 'offset'")
+        self.receiver, self.receiver_every = receiver, max(1, int(receiver_every))
+        self.recv = fwi.receiver_factor(grid, geom, "pm") if receiver == "pm" else None
         self.mask = None
         if mute_top > 0:
             self.mask = torch.ones(grid.shape, dtype=torch.float32, device=d_obs.device)
@@ -278,10 +290,16 @@ class FwiObjective:
         else:
             scale, kind = None, None
 
+        if self.receiver == "green" and (self.recv is None or (self.n_gradients - 1) % self.receiver_every == 0):
+            self.recv = fwi.receiver_factor(grid, self.geom, "green", v.contiguous(), o, ws=self.ws)
+        recv = self.recv
+
         def minv(q):
             if mask is not None:
                 q = q * mask
-            if kind is not None:
+            if kind is not None and recv is not None:
+                q = fwi.precondition_receiver(grid, q.contiguous(), scale, kind, recv, eps=o.eps, ws=self.ws)
+            elif kind is not None:
                 q = fwi.precondition(grid, q.contiguous(), scale, kind, eps=o.eps, ws=self.ws)
             return q * mask if mask is not None else q
         return Evaluation(float(r["misfit"]), r["grad"], minv)
@@ -297,7 +315,13 @@ def velocity_bounds(grid, v0, vmin=None, vmax=None, cfl_margin=0.98):
     cap = min(cfl_margin * lim * grid.dx / grid.dt, float(grid.vref))
     lo = 0.5 * float(v0.min()) if vmin is None else float(vmin)
     hi = min(1.5 * float(v0.max()), cap) if vmax is None else min(float(vmax), cap)
-    return lo, hi
+    # float32 values inside [lo, hi]: a float32 clamp to them stays within
+    lo32, hi32 = np.float32(lo), np.float32(hi)
+    if float(lo32) < lo:
+        lo32 = np.nextafter(lo32, np.float32(np.inf))
+    if float(hi32) > hi:
+        hi32 = np.nextafter(hi32, np.float32(0))
+    return float(lo32), float(hi32)
 
 
 def default_mute(geom):
@@ -310,13 +334,14 @@ def default_mute(geom):
 
 
 def invert(grid, geom, d_obs, v0, opts, *, method="lbfgs", iters=10, max_update=50.0, memory=5, vmin=None,
-           vmax=None, v_true=None, mute_top=None, ws=None):
+           vmax=None, v_true=None, mute_top=None, receiver=None, receiver_every=1, ws=None):
     """Run `iters` iterations of L-BFGS or PRCG from v0 with the library's
     gradient and preconditioner (opts.precond), the rows above mute_top fixed
     (None: default_mute(geom); 0: none). Returns (v, History); with v_true,
     History.model_error holds ||v_k - v_true|| / ||v_0 - v_true||."""
     mute = default_mute(geom) if mute_top is None else int(mute_top)
-    obj = FwiObjective(grid, geom, d_obs, opts, ws=ws, mute_top=mute)
+    obj = FwiObjective(grid, geom, d_obs, opts, ws=ws, mute_top=mute, receiver=receiver,
+                       receiver_every=receiver_every)
     lo, hi = velocity_bounds(grid, v0, vmin, vmax)
     hist = History()
     e0 = float(torch.linalg.vector_norm((v0 - v_true).double())) if v_true is not None else None

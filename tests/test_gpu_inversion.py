@@ -7,7 +7,9 @@ same loops driven by the FP64 oracle.
   against the same loops over the oracle's (relative L2 of the model update
   <= 1e-3: the line searches take the same branches, the steps then agree to
   the gradients' FP32 rounding).
-* Ten iterations of each on a dipping-layer model: the misfit decreases at
+* Ten iterations of each (also with the receiver factors of a fixed spread:
+  Plessix-Mulder's, the receiver Green's functions) on a dipping-layer
+  model: the misfit decreases at
   every iteration and by a quarter at least over the ten, the velocities stay
   within the projection bounds, the muted rows stay fixed, and fwi_misfit
   agrees with the gradient call's misfit. (The model error is reported, not
@@ -89,9 +91,11 @@ def test_first_iterates_against_oracle_loop(torch_cuda, oracle_mod, method, misf
         assert err <= 1e-3, (k, err)
 
 
-@pytest.mark.parametrize("method,misfit,precond,hmax", [("lbfgs", "ols", "illum", -1),
-                                                        ("prcg", "integral", "offset", 4)])
-def test_ten_iterations_decrease_misfit(torch_cuda, method, misfit, precond, hmax):
+@pytest.mark.parametrize("method,misfit,precond,hmax,recv", [("lbfgs", "ols", "illum", -1, None),
+                                                             ("prcg", "integral", "offset", 4, None),
+                                                             ("prcg", "ols", "illum", -1, "pm"),
+                                                             ("lbfgs", "ols", "offset", 2, "green")])
+def test_ten_iterations_decrease_misfit(torch_cuda, method, misfit, precond, hmax, recv):
     torch = torch_cuda
     from paper_1406_1864_gb300 import fwi, inversion as I
     p = problem()
@@ -100,7 +104,8 @@ def test_ten_iterations_decrease_misfit(torch_cuda, method, misfit, precond, hma
     d_obs = fwi.forward(grid, geom, v_true)
     opts = fwi.Options(misfit=misfit, precond=precond, hmax=hmax)
     v0 = torch.as_tensor(p.v_init, device="cuda")
-    v, h = I.invert(grid, geom, d_obs, v0, opts, method=method, iters=10, max_update=40.0, v_true=v_true)
+    v, h = I.invert(grid, geom, d_obs, v0, opts, method=method, iters=10, max_update=40.0, v_true=v_true,
+                    receiver=recv, receiver_every=3)
     m = np.array(h.misfit)
     assert len(m) == 11 and (np.diff(m) < 0).all(), m
     assert m[-1] < 0.75 * m[0], m
