@@ -86,7 +86,9 @@ enum {
     FWI_OP_MISFIT = 8,         /* fwi_misfit                                */
     FWI_OP_RECEIVER_FACTOR = 9, /* fwi_receiver_factor (kind from opts.precond
                                    is not used: see fwi_receiver_factor)     */
-    FWI_OP_PRECONDITION_RECEIVER = 10 /* fwi_precondition_receiver         */
+    FWI_OP_PRECONDITION_RECEIVER = 10, /* fwi_precondition_receiver        */
+    FWI_OP_EXT_BORN = 11,      /* fwi_extended_born (any hext)              */
+    FWI_OP_EXT_MIGRATION = 12  /* fwi_extended_migration (any hext)         */
 };
 
 #define FWI_HMAX_LIMIT 12 /* largest offset (cells) of the offset Hessian */
@@ -252,6 +254,32 @@ fwi_status fwi_receiver_factor(const fwi_grid *grid, const fwi_geometry *geom, c
 fwi_status fwi_precondition_receiver(const fwi_grid *grid, const float *grad, const float *scale, int kind,
                                      int hmax, const float *recv, int recv_planes, float eps, float *out, void *ws,
                                      size_t ws_bytes, void *stream);
+
+/* Extended Born modelling [Eq. 5]: traces of an extended velocity
+   perturbation dv_ext(x, h) with horizontal subsurface offsets
+   h = -hext..hext: the incident field at x + h scatters from x - h, with the
+   scattering strength 2 c2(x) dv_ext(x, h) / v(x) of fwi_born (at hext = 0
+   exactly fwi_born's operator up to rounding). dv_ext is edge-replicated into
+   the sponge for every h. v DEVICE [nz][nx]; dv_ext DEVICE [2 hext + 1][nz][nx]
+   (plane k is h = k - hext); dseis DEVICE [nshots][nt][nrec] output.
+   0 <= hext <= FWI_HEXT_LIMIT. Workspace of FWI_OP_EXT_BORN. 2-D, sponge
+   checkpoints (opts may be NULL). */
+#define FWI_HEXT_LIMIT 6
+fwi_status fwi_extended_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int hext,
+                             const float *v, const float *dv_ext, float *dseis, void *ws, size_t ws_bytes,
+                             void *stream);
+
+/* Extended migration [Eq. 6], the adjoint of fwi_extended_born: the image
+   [2 hext + 1][nz][nx] of the adjoint source adj_src [nshots][nt][nrec]
+   (the generalized imaging condition: the back-propagated field at x - h
+   correlated with the incident field at x + h; with the residual as adj_src,
+   the subsurface-offset extended gradient, whose h = 0 plane is
+   fwi_adjoint_gradient's grad). Forward modelling with sponge checkpoints,
+   then the adjoint pass with the extended imaging. Workspace of
+   FWI_OP_EXT_MIGRATION. 2-D (opts may be NULL). */
+fwi_status fwi_extended_migration(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int hext,
+                                  const float *v, const float *adj_src, float *image, void *ws, size_t ws_bytes,
+                                  void *stream);
 
 /* Born modelling [Eq. 4, as the exact derivative of fwi_forward's discrete
    traces]: dseis = J dv, the change of the traces along the velocity change

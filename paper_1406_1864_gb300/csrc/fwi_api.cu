@@ -74,6 +74,9 @@ struct Plan {
     size_t tab_src = 0, tab_srcij = 0, tab_fptr = 0, tab_fent = 0, tab_bptr = 0, tab_bent = 0, tab_bshot = 0;
     Part adj_t; // adjoint source in backward-table order [nt][ns*nrec]
     Part prod;  // scale x receiver factor (fwi_precondition_receiver)
+    Part dext;  // extended Born: planes D~(y, h), h = -HEXT_MAX..HEXT_MAX
+    Part acc_ext; // extended migration: [2 HEXT_MAX + 1][nzp][nxp] image sums
+    bool ext = false; // extended operators (64 x 8 tiles)
     // snapshot checkpoints (FWI_CKPT_SNAPSHOT): snapshot j holds level j*K
     bool snap = false;
     int snap_prec = FWI_SNAP_F32, K = 0, nck = 0;
@@ -128,7 +131,7 @@ fwi_status check_opts(const fwi_options *o, int op)
     if (!o) {
         if (op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_PRECONDITION || op == FWI_OP_BORN ||
             op == FWI_OP_GN_HVP || op == FWI_OP_MISFIT || op == FWI_OP_RECEIVER_FACTOR ||
-            op == FWI_OP_PRECONDITION_RECEIVER)
+            op == FWI_OP_PRECONDITION_RECEIVER || op == FWI_OP_EXT_BORN || op == FWI_OP_EXT_MIGRATION)
             return FWI_OK;
         return fail(FWI_ERR_INVALID_ARG, "options are NULL");
     }
@@ -192,10 +195,13 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
         off = align_up(off + bytes);
     };
     take(pl.scal, 256);
-    const bool need_bwd = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_GN_HVP);
-    const bool born = (op == FWI_OP_BORN || op == FWI_OP_GN_HVP);
-    if (born && o && o->ckpt != FWI_CKPT_SPONGE)
-        return fail(FWI_ERR_INVALID_ARG, "Born modelling and Hessian-vector products use sponge checkpoints");
+    const bool need_bwd = (op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_GN_HVP ||
+                           op == FWI_OP_EXT_MIGRATION);
+    const bool born = (op == FWI_OP_BORN || op == FWI_OP_GN_HVP || op == FWI_OP_EXT_BORN);
+    pl.ext = (op == FWI_OP_EXT_BORN || op == FWI_OP_EXT_MIGRATION);
+    if ((born || pl.ext) && o && o->ckpt != FWI_CKPT_SPONGE)
+        return fail(FWI_ERR_INVALID_ARG, "Born modelling, Hessian-vector products and the extended operators use "
+                                         "sponge checkpoints");
     pl.snap = need_bwd && o && o->ckpt == FWI_CKPT_SNAPSHOT;
     // scheduler counters: forward, backward, and (snapshots) re-propagation
     if (!no_geom) take(pl.sched, (size_t)(pl.snap ? 3 : 2) * g->nt * sizeof(int));
@@ -216,12 +222,17 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
                         op == FWI_OP_MISFIT);
     pl.born = born;
     pl.tf = make_tiling(L, pl.ns, pl.with_offh ? STEP_FWD_OFFH : STEP_FWD, -1, 0, pl.hmax);
-    // the Born step runs on the backward step's default 64 x 16 tiles
-    pl.tb = born ? make_tiling(L, pl.ns, STEP_BWD, 0) : make_tiling(L, pl.ns, STEP_BWD);
+    // the Born step runs on the backward step's default 64 x 16 tiles, the
+    // extended operators on its 64 x 8 tiles
+    pl.tb = pl.ext ? make_tiling(L, pl.ns, STEP_BWD, 1)
+                   : (born ? make_tiling(L, pl.ns, STEP_BWD, 0) : make_tiling(L, pl.ns, STEP_BWD));
     const size_t fbytes = (size_t)L.fstride * sizeof(float);
     const size_t nphys = (size_t)L.nz * L.nx;
     take(pl.c2, fbytes);
     take(pl.damp, fbytes);
+    if (op == FWI_OP_EXT_BORN) take(pl.dext, fbytes * (2 * HEXT_MAX + 1));
+    if (op == FWI_OP_EXT_MIGRATION)
+        take(pl.acc_ext, (size_t)(2 * HEXT_MAX + 1) * L.nzp * L.nxp * sizeof(float));
     if (born) {
         take(pl.dc2, fbytes);
         if (!pl.need_bwd) { // du^n, du^{n-1}
@@ -460,12 +471,14 @@ fwi_status restore_snapshot(const Plan &pl, void *ws, int j, float *u, float *up
 // Born time loop n = 0..nt-1: u and du = J dv advanced together (the du
 // buffers are the adjoint-state buffers p), Born traces into dseis; with
 // `save` the sponge checkpoint of u for a following adjoint pass
-fwi_status run_born(const Plan &pl, const fwi_geometry *ge, void *ws, float *dseis, bool save, cudaStream_t st)
+fwi_status run_born(const Plan &pl, const fwi_geometry *ge, void *ws, float *dseis, bool save, cudaStream_t st,
+                    int he = 0)
 {
     cudaError_t e;
     BornArgs a{};
     a.c = make_common(pl, ge, ws, pl.tb);
-    a.dc2 = at<float>(ws, pl.dc2);
+    a.dc2 = he > 0 ? nullptr : at<float>(ws, pl.dc2);
+    a.dext = he > 0 ? at<float>(ws, pl.dext) : nullptr;
     a.band = save ? at<float>(ws, pl.band) : nullptr;
     a.dseis = (dseis && pl.nrec > 0) ? dseis : nullptr;
     a.rt.ptr = at<int>(ws, pl.tab, pl.tab_bptr);
@@ -475,7 +488,10 @@ fwi_status run_born(const Plan &pl, const fwi_geometry *ge, void *ws, float *dse
     for (int b = 0; b < 2; ++b)
         if ((e = cudaMemsetAsync(DU[b], 0, pl.p[b].bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
     int hx, hy, px, py;
-    step_boxes(STEP_BWD, pl.tb, hx, hy, px, py);
+    if (he > 0)
+        ext_boxes(he, pl.tb, hx, hy, px, py);
+    else
+        step_boxes(STEP_BWD, pl.tb, hx, hy, px, py);
     CUtensorMap uh[2], up[2], dh[2], dp[2];
     for (int b = 0; b < 2; ++b)
         if (!encode_field_map(&uh[b], U[b], pl.L, pl.ns, hx, hy) || !encode_field_map(&up[b], U[b], pl.L, pl.ns, px, py) ||
@@ -491,7 +507,8 @@ fwi_status run_born(const Plan &pl, const fwi_geometry *ge, void *ws, float *dse
         a.uout = U[(n + 1) & 1];
         a.duout = DU[(n + 1) & 1];
         a.c.sched = at<int>(ws, pl.sched) + n;
-        if ((e = launch_born_step(a, pl.tb, st)) != cudaSuccess) return cuda_fail(e, "Born step");
+        e = he > 0 ? launch_born_ext_step(a, pl.tb, he, st) : launch_born_step(a, pl.tb, st);
+        if (e != cudaSuccess) return cuda_fail(e, "Born step");
         t_launch[0]++;
     }
     for (int b = 0; b < 2; ++b) {
@@ -654,7 +671,8 @@ fwi_status run_backward_segments(const Plan &pl, const fwi_geometry *ge, void *w
 // [ns][nt][nrec] of model k
 fwi_status run_backward_models(int nm, const Plan *pl, const fwi_geometry *const *ge, void *const *ws,
                                const float *const *adj, cudaStream_t st, int m_hi = -1, int m_lo = 1,
-                               cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
+                               cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, int he = 0,
+                               float *acc_ext = nullptr)
 {
     cudaError_t e;
     std::vector<BwdArgs> a(nm);
@@ -664,7 +682,10 @@ fwi_status run_backward_models(int nm, const Plan *pl, const fwi_geometry *const
     for (int k = 0; k < nm; ++k) {
         const Plan &p = pl[k];
         int hx, hy, px, py;
-        step_boxes(STEP_BWD, p.tb, hx, hy, px, py);
+        if (he > 0)
+            ext_boxes(he, p.tb, hx, hy, px, py);
+        else
+            step_boxes(STEP_BWD, p.tb, hx, hy, px, py);
         void *w = ws[k];
         for (int b = 0; b < 2; ++b)
             if ((e = cudaMemsetAsync(at<char>(w, p.p[b]), 0, p.p[b].bytes, st)) != cudaSuccess)
@@ -691,6 +712,7 @@ fwi_status run_backward_models(int nm, const Plan *pl, const fwi_geometry *const
         a[k].rt.ent = at<int2>(w, p.tab, p.tab_bent);
         a[k].adj_scale = p.L.dx * p.L.dx;
         a[k].recon = p.snap ? 0 : 1;
+        a[k].acc_ext = acc_ext;
         til[k] = p.tb;
         U[k] = {at<float>(w, p.u[0]), at<float>(w, p.u[1])};
         Pp[k] = {at<float>(w, p.p[0]), at<float>(w, p.p[1])};
@@ -720,7 +742,8 @@ fwi_status run_backward_models(int nm, const Plan *pl, const fwi_geometry *const
             a[k].ua = U[k][m & 1];
             a[k].pb = Pp[k][m & 1];
         }
-        e = nm == 1 ? launch_bwd_step(a[0], til[0], st) : launch_bwd_batch(a.data(), til.data(), nm, st);
+        e = he > 0 ? launch_bwd_ext_step(a[0], til[0], he, st)
+                   : (nm == 1 ? launch_bwd_step(a[0], til[0], st) : launch_bwd_batch(a.data(), til.data(), nm, st));
         if (e != cudaSuccess) return cuda_fail(e, "backward step");
         t_launch[1]++;
     }
@@ -1513,8 +1536,7 @@ fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, c
                                int op, size_t *bytes)
 {
     if (!bytes) return fail(FWI_ERR_INVALID_ARG, "bytes is NULL");
-    if (op < FWI_OP_FORWARD || op > FWI_OP_PRECONDITION_RECEIVER)
-        return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
+    if (op < FWI_OP_FORWARD || op > FWI_OP_EXT_MIGRATION) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
     if (grid && grid->ndim == 3) {
         Plan3 p3;
         fwi_status s3 = make_plan3(grid, geom, opts, op, false, p3);
@@ -1802,6 +1824,62 @@ fwi_status fwi_precondition_receiver(const fwi_grid *grid, const float *grad, co
     if ((e = launch_precond(pl.L, grad, prod, kind, hmax, eps, out, at<unsigned>(ws, pl.scal, 12), st)) != cudaSuccess)
         return cuda_fail(e, "precondition kernel");
     t_launch[2] += 3;
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_extended_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int hext,
+                             const float *v, const float *dv_ext, float *dseis, void *ws, size_t ws_bytes, void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_EXT_BORN, true, pl);
+    if (s != FWI_OK) return s;
+    if (hext < 0 || hext > FWI_HEXT_LIMIT) return fail(FWI_ERR_INVALID_ARG, "hext=%d outside 0..%d", hext, FWI_HEXT_LIMIT);
+    if (!v || !dv_ext || (!dseis && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v, dv_ext or dseis is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    const int he = ext_kernel_he(hext);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.dext), 0, pl.dext.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_prep_dext(pl.L, v, dv_ext, at<float>(ws, pl.c2), hext, he, at<float>(ws, pl.dext), st)) !=
+        cudaSuccess)
+        return cuda_fail(e, "prep kernel");
+    t_launch[2]++;
+    if ((s = run_born(pl, geom, ws, dseis, false, st, he)) != FWI_OK) return s;
+    prof_record(1, st);
+    prof_record(2, st);
+    prof_record(3, st);
+    return finish(pl, ws, st);
+}
+
+fwi_status fwi_extended_migration(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int hext,
+                                  const float *v, const float *adj_src, float *image, void *ws, size_t ws_bytes,
+                                  void *stream)
+{
+    Plan pl;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_EXT_MIGRATION, true, pl);
+    if (s != FWI_OK) return s;
+    if (hext < 0 || hext > FWI_HEXT_LIMIT) return fail(FWI_ERR_INVALID_ARG, "hext=%d outside 0..%d", hext, FWI_HEXT_LIMIT);
+    if (!v || !image || (!adj_src && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v, adj_src or image is NULL");
+    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    begin_call(st);
+    if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
+    if ((s = run_forward(pl, geom, ws, nullptr, true, nullptr, nullptr, 0, st)) != FWI_OK) return s;
+    prof_record(1, st);
+    const int he = ext_kernel_he(hext);
+    float *acc = at<float>(ws, pl.acc_ext);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(acc, 0, pl.acc_ext.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    const fwi_geometry *gp = geom;
+    void *wp = ws;
+    if ((s = run_backward_models(1, &pl, &gp, &wp, &adj_src, st, -1, 1, nullptr, nullptr, he, acc)) != FWI_OK)
+        return s;
+    prof_record(2, st);
+    if ((e = launch_fold_ext(pl.L, acc, he, hext, v, image, st)) != cudaSuccess) return cuda_fail(e, "fold kernel");
+    t_launch[2]++;
     prof_record(3, st);
     return finish(pl, ws, st);
 }

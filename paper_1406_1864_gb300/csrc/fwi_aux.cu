@@ -83,6 +83,58 @@ __global__ void k_prep_dc2(const Lay2D L, const float *__restrict__ v, const flo
     }
 }
 
+// D~(y, h) = 2 c2(y + h) dv(y + h, h) / v(y + h) for padded y, |h| <= hext
+// (dv_ext edge-replicated into the sponge, like v), zero where y + h leaves
+// the padded grid and for hext < |h| <= he; planes h = -he..he
+__global__ void k_prep_dext(const Lay2D L, const float *__restrict__ v, const float *__restrict__ dv_ext,
+                            const float *__restrict__ c2, int hext, int he, float *__restrict__ dext)
+{
+    const long long npl = (long long)L.nzp * L.nxp;
+    const long long n = npl * (2 * he + 1);
+    const long long nphys = (long long)L.nz * L.nx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int pl = (int)(e / npl);
+        const long long r = e - (long long)pl * npl;
+        const int i = (int)(r / L.nxp), j = (int)(r - (long long)i * L.nxp);
+        const int h = pl - he, jx = j + h;
+        float d = 0.f;
+        if (h >= -hext && h <= hext && jx >= 0 && jx < L.nxp) {
+            const long long m = (long long)clampi(i - L.P, 0, L.nz - 1) * L.nx + clampi(jx - L.P, 0, L.nx - 1);
+            d = dv_ext[(long long)(h + hext) * nphys + m] * __fdiv_rn(2.0f * c2[fidx(L, i, jx)], v[m]);
+        }
+        dext[(long long)pl * L.fstride + fidx(L, i, j)] = d;
+    }
+}
+
+// image(x, h) = sum over the padded cells x' folding into physical x of
+// 2 v(x') / (v(x' - h)^2 dx^2) acc(x' - h, h), |h| <= hext
+__global__ void k_fold_ext(const Lay2D L, const float *__restrict__ acc, int he, int hext,
+                           const float *__restrict__ v, float *__restrict__ image)
+{
+    const long long nphys = (long long)L.nz * L.nx;
+    const long long n = nphys * (2 * hext + 1);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int pl = (int)(e / nphys);
+        const long long o = e - (long long)pl * nphys;
+        const int h = pl - hext;
+        const int iz = (int)(o / L.nx), ix = (int)(o - (long long)iz * L.nx);
+        const int ia = iz == 0 ? 0 : iz + L.P, ib = iz == L.nz - 1 ? L.nzp - 1 : iz + L.P;
+        const int ja = ix == 0 ? 0 : ix + L.P, jb = ix == L.nx - 1 ? L.nxp - 1 : ix + L.P;
+        const float *ap = acc + (long long)(h + he) * L.nzp * L.nxp;
+        float sum = 0.f;
+        for (int i = ia; i <= ib; ++i)
+            for (int j = ja; j <= jb; ++j) {
+                const int jy = j - h;
+                if (jy < 0 || jy >= L.nxp) continue;
+                const float vy = v[(long long)clampi(i - L.P, 0, L.nz - 1) * L.nx + clampi(jy - L.P, 0, L.nx - 1)];
+                sum += ap[(long long)i * L.nxp + jy] / (vy * vy);
+            }
+        image[e] = sum * (2.0f * v[o] / (L.dx * L.dx));
+    }
+}
+
 // Plessix-Mulder receiver factor of a fixed spread: the integral over the
 // receiver line of 1 / distance, asinh((xmax - x)/z) - asinh((xmin - x)/z),
 // x = j dx, z = |i - zr| dx floored at dx / 2 (the receiver row itself)
@@ -407,6 +459,20 @@ cudaError_t launch_prep_dc2(const Lay2D &L, const float *v, const float *dv, con
                             cudaStream_t st)
 {
     k_prep_dc2<<<grid_for((long long)L.nzp * L.nxp), NT1, 0, st>>>(L, v, dv, c2, dc2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_dext(const Lay2D &L, const float *v, const float *dv_ext, const float *c2, int hext, int he,
+                             float *dext, cudaStream_t st)
+{
+    k_prep_dext<<<grid_for((long long)L.nzp * L.nxp * (2 * he + 1)), NT1, 0, st>>>(L, v, dv_ext, c2, hext, he, dext);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_ext(const Lay2D &L, const float *acc, int he, int hext, const float *v, float *image,
+                            cudaStream_t st)
+{
+    k_fold_ext<<<grid_for((long long)L.nz * L.nx * (2 * hext + 1)), NT1, 0, st>>>(L, acc, he, hext, v, image);
     return cudaGetLastError();
 }
 

@@ -122,6 +122,8 @@ struct BwdArgs {
     const float *adj;      // [nt][nent] adjoint source in receiver-table order, or null
     int nent;              // ns * nrec
     float *acc_grad;       // [nzp][nxp] sum psi^m * (Lhat u^{m-1} + f delta_s) (red.add)
+    float *acc_ext;        // extended imaging: [2 HE + 1][nzp][nxp] sums psi^m(y) q^{m-1}(y + 2h)
+                           // at (h + HE, y) (red.add), or null
     RecTable rt;
     float adj_scale;       // dx^2
     int m;
@@ -242,6 +244,8 @@ struct BornArgs {
     CUtensorMap tm_dup;    // du^{n-1}, point box
     StepCommon c;
     const float *dc2;      // 2 c2 dv / v, field layout
+    const float *dext;     // extended Born: planes h = -HE..HE (field layout, fstride apart) of
+                           // D~(y, h) = 2 c2 dv(y + h, h) / v at y + h, or null
     float *uout, *duout;   // u^{n+1} and du^{n+1} written here
     float *band;           // sponge checkpoint of u^{n+1} (for an adjoint pass) or null
     float *dseis;          // [ns][nt][nrec] Born traces du^n at the receivers, or null
@@ -297,6 +301,22 @@ cudaError_t launch_fwd_batch(const FwdArgs *a, const Tiling *t, int nm, bool wit
 cudaError_t launch_bwd_batch(const BwdArgs *a, const Tiling *t, int nm, cudaStream_t st);
 // Born step over all shots (the backward step's tiling: two halo fields)
 cudaError_t launch_born_step(const BornArgs &a, const Tiling &t, cudaStream_t st);
+// extended operators (Eq. 5, Eq. 6), offsets h = -he..he, he in {2, 4, 6};
+// tiles of 64 x 8 (t.tz == 8); the halo boxes are TX + 2 (RADIUS + 2 he) wide
+constexpr int HEXT_MAX = 6;
+int ext_kernel_he(int hext); // the compiled offset count that covers |h| <= hext
+void ext_boxes(int he, const Tiling &t, int &hx, int &hy, int &px, int &py);
+cudaError_t launch_bwd_ext_step(const BwdArgs &a, const Tiling &t, int he, cudaStream_t st);
+cudaError_t launch_born_ext_step(const BornArgs &a, const Tiling &t, int he, cudaStream_t st);
+// D~(y, h) = 2 c2(y + h) dv(y + h, h) / v(y + h) on the padded grid for |h| <= hext (edge-replicated
+// dv_ext [2 hext + 1][nz][nx]), zero where y + h leaves the padded grid or |h| > hext; planes
+// h = -he..he, fstride apart
+cudaError_t launch_prep_dext(const Lay2D &L, const float *v, const float *dv_ext, const float *c2, int hext, int he,
+                             float *dext, cudaStream_t st);
+// image(x, h) = sum over the padded cells x' folding into x of 2 v(x') / (v(x' - h)^2 dx^2) acc(x' - h, h),
+// |h| <= hext, image [2 hext + 1][nz][nx]; acc [2 he + 1][nzp][nxp]
+cudaError_t launch_fold_ext(const Lay2D &L, const float *acc, int he, int hext, const float *v, float *image,
+                            cudaStream_t st);
 // dc2 = 2 c2 dv / v on the padded grid (edge-replicated dv)
 cudaError_t launch_prep_dc2(const Lay2D &L, const float *v, const float *dv, const float *c2, float *dc2,
                             cudaStream_t st);

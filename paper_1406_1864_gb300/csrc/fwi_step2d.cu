@@ -564,12 +564,68 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
 template <int RZ, int STAGES>
 using BwdRing = Ring<8 * RZ, RADIUS, 2, 2, STAGES, 3 * 8 * RZ * TX * 4>; // + c2, injection, damping tiles
 
-template <int RZ, int STAGES, int MINB, int NM>
+// q = Lhat u + f delta_s of one halo tile on the TZ x (TX + 4 HE) columns
+// bj - 2 HE .. bj + TX + 2 HE - 1 (the x-extension of the extended operators'
+// offsets 2h, |h| <= HE), zero where a column leaves the padded grid or a row
+// its padded rows. Scalar points, the same second-difference arithmetic as
+// lap4 (lap8x2 on a duplicated lane).
+template <int RZ, int HE, int TXS, int HX>
+__device__ __forceinline__ void bwd_q_ext(float *qs, const float *su, const ItemDesc &d, int bi, int bj,
+                                          const Lay2D &L, float src_scale)
+{
+    constexpr int TZ = 8 * RZ, QW = TX + 4 * HE;
+    for (int e = threadIdx.x; e < TZ * QW; e += TPB) {
+        const int r = e / QW, cq = e - r * QW;
+        const int col = cq - 2 * HE;               // column in the tile, -2HE .. TX+2HE-1
+        const int gi = bi + r, gj = bj + col;
+        float q = 0.f;
+        if (gi < L.nzp && gj >= 0 && gj < L.nxp) {
+            const float *ctr = su + (r + RADIUS) * TXS + HX + col;
+            const float cv = ctr[0];
+            float2 xs[4], zs[4];
+#pragma unroll
+            for (int k = 1; k <= 4; ++k) {
+                const float xsum = ctr[-k] + ctr[k];
+                const float zsum = ctr[-k * TXS] + ctr[k * TXS];
+                xs[k - 1] = make_float2(xsum, xsum);
+                zs[k - 1] = make_float2(zsum, zsum);
+            }
+            q = lap8x2(make_float2(cv, cv), xs, zs).x;
+            if (gi == d.si && gj == d.sj) q += d.amp * src_scale;
+        }
+        qs[e] = q;
+    }
+}
+
+// acc[p][h + HE] += psi(y_p) q(y_p + 2h) for the two lanes (points 2 lane,
+// 2 lane + 1 of the thread's four) of one row; qrow is the q tile's row
+template <int HE, int QW>
+__device__ __forceinline__ void ext_accumulate(float (&acc)[4][2 * HE + 1], float2 psi, int lane, const float *qrow,
+                                               int tx)
+{
+#pragma unroll
+    for (int hh = 0; hh < 2 * HE + 1; ++hh) {
+        const int c0 = 4 * tx + 2 * lane + 2 * (hh - HE) + 2 * HE;   // column of y + 2h in the q tile
+        acc[2 * lane][hh] = fmaf(psi.x, qrow[c0], acc[2 * lane][hh]);
+        acc[2 * lane + 1][hh] = fmaf(psi.y, qrow[c0 + 1], acc[2 * lane + 1][hh]);
+    }
+}
+
+// With extended imaging over offsets h = -HE..HE (Eq. 6): halo tiles wide
+// enough for q^{m-1} on TX + 4 HE columns (x +- 2 HE), and that q row tile.
+template <int RZ, int STAGES, int HE>
+using BwdRingE = Ring<8 * RZ, RADIUS + 2 * HE, 2, 2, STAGES,
+                      3 * 8 * RZ * TX * 4 + (HE > 0 ? 8 * RZ * (TX + 4 * HE) * 4 : 0)>;
+
+template <int RZ, int STAGES, int MINB, int NM, int HE = 0>
 __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ Batch<BwdArgs, NM> B)
 {
-    using R = BwdRing<RZ, STAGES>;
+    static_assert(HE == 0 || (HE % 2 == 0 && NM == 1), "extended imaging: even HE, one model");
+    using R = BwdRingE<RZ, STAGES, HE>;
     constexpr int TZ = 8 * RZ;
-    constexpr int HX = RADIUS;
+    constexpr int HX = RADIUS + 2 * HE;   // a multiple of 4: TMA x offsets stay 16-byte aligned
+    constexpr int NE = 2 * HE + 1;        // extended offsets
+    constexpr int QW = TX + 4 * HE;       // columns of the q tile
     constexpr int TXS = R::TXS;
     constexpr int D = STAGES - 1;
     // item j's descriptor is staged (lane 0 of warp 1) in iteration j-D-1
@@ -585,6 +641,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
     float *c2s = reinterpret_cast<float *>(R::extra(smem));
     float *sinj = c2s + TZ * TX;
     float *dms = sinj + TZ * TX; // damping tile (sponge tiles)
+    float *qs = dms + TZ * TX;   // q^{m-1} on columns bj - 2 HE .. bj + TX + 2 HE - 1 (HE > 0)
+    (void)qs;
 
     // launch-wide values (time level, mode) are those of model 0
     const BwdArgs &a0 = B.m[0];
@@ -630,6 +688,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             if (s_desc[k].tile >= 0) issue(s_desc[k], k);
 
     float2 acc_g[RZ][2];
+    float acc_e[RZ][4][NE]; // extended image at (own point y, h): sum psi^m(y) q^{m-1}(y + 2h)
     int cur_tile = -1, cur_model = 0, bi = 0, bj = 0, i0 = 0, j0 = 0;
     bool tile_sponge = false, colok = false;
     SpongeInfo<RZ> sg;
@@ -646,6 +705,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                 const int j = j0 + p;
                 const float v = p < 2 ? (p == 0 ? acc_g[r][0].x : acc_g[r][0].y) : (p == 2 ? acc_g[r][1].x : acc_g[r][1].y);
                 if (i < L.nzp && j < L.nxp) atomicAdd(a.acc_grad + (long long)i * L.nxp + j, v);
+                if constexpr (HE > 0) {
+                    if (i < L.nzp && j < L.nxp)
+#pragma unroll
+                        for (int e = 0; e < NE; ++e)
+                            atomicAdd(a.acc_ext + ((long long)e * L.nzp + i) * L.nxp + j, acc_e[r][p][e]);
+                }
             }
         }
     };
@@ -725,6 +790,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             if (tile_sponge) sg.init(L, i0, j0);
 #pragma unroll
             for (int r = 0; r < RZ; ++r) acc_g[r][0] = acc_g[r][1] = make_float2(0.f, 0.f);
+            if constexpr (HE > 0) {
+#pragma unroll
+                for (int r = 0; r < RZ; ++r)
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int e = 0; e < NE; ++e) acc_e[r][p][e] = 0.f;
+            }
             load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
             if (tile_sponge) load_c2_tile<TZ>(dms, c.damp, L, bi, bj);
             bval_ok = false;
@@ -750,9 +823,19 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         if (bval_ok) fetch_band(nx.s, bval);
         if (has_rec) __syncthreads();
         const int st = k % STAGES;
-        if (stage_ready<STAGES>(bars, k, &s_abort)) {
-            const float *su = R::halo(smem, st, 0);
-            const float *sp = R::halo(smem, st, 1);
+        const bool ready = stage_ready<STAGES>(bars, k, &s_abort);
+        const float *su = R::halo(smem, st, 0);
+        const float *sp = R::halo(smem, st, 1);
+        float2 qu[RZ][2], qp[RZ][2];
+        if constexpr (HE > 0) {
+            // q^{m-1} on the tile and 2 HE columns on each side (zero outside
+            // the padded grid), for the extended image
+            if (ready) {
+                bwd_q_ext<RZ, HE, TXS, HX>(qs, su, now, bi, bj, L, c.src_scale);
+            }
+            __syncthreads();
+        }
+        if (ready) {
             const float *pua = R::point(smem, st, 0);
             const float *ppb = R::point(smem, st, 1);
             const long long so = (long long)s * L.fstride;
@@ -760,7 +843,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 
             // q^{m-1} = Lhat u^{m-1} + f(t_{m-1}) delta_s (as in the forward
             // step m-1), then Lhat psi^{m+1}; one column window live at a time
-            float2 qu[RZ][2], qp[RZ][2];
 #pragma unroll
             for (int fld = 0; fld < 2; ++fld) {
                 const float *sf = fld == 0 ? su : sp;
@@ -806,6 +888,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                         const float2 c2v = half2of(c24, h);
                         pn[h] = add2(p1[h], fma2(c2v, qp[r][h], sub2(p1[h], half2of(pb4, h))));
                         acc_g[r][h] = fma2(pn[h], qu[r][h], acc_g[r][h]);
+                        if constexpr (HE > 0) ext_accumulate<HE, QW>(acc_e[r], pn[h], h, qs + (ty * RZ + r) * QW, tx);
                         // leap_back on two lanes: u1 - (-(c2 q) + (u^m - u1))
                         un[h] = sub2(u1[h], fma2(make_float2(-c2v.x, -c2v.y), qu[r][h], sub2(half2of(ua4, h), u1[h])));
                     }
@@ -827,6 +910,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                         const float2 kb = fma2(ia2, make_float2(2.f, 2.f), make_float2(-1.f, -1.f));
                         pn[h] = add2(p1[h], fma2(mul2(c2v, ia2), qp[r][h], mul2(kb, sub2(p1[h], half2of(pb4, h)))));
                         acc_g[r][h] = fma2(pn[h], qu[r][h], acc_g[r][h]);
+                        if constexpr (HE > 0) ext_accumulate<HE, QW>(acc_e[r], pn[h], h, qs + (ty * RZ + r) * QW, tx);
                         un[h] = sub2(u1[h], fma2(make_float2(-c2v.x, -c2v.y), qu[r][h], sub2(half2of(ua4, h), u1[h])));
                     }
                     float pnew[4] = {pn[0].x, pn[0].y, pn[1].x, pn[1].y};
@@ -871,12 +955,21 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 template <int RZ, int STAGES>
 using BornRing = Ring<8 * RZ, RADIUS, 2, 2, STAGES, 3 * 8 * RZ * TX * 4>; // + c2, dc2, damping tiles
 
-template <int RZ, int STAGES, int MINB>
+// Extended Born (Eq. 5, offsets h = -HE..HE): wider halo tiles for q on
+// TX + 4 HE columns, plus the 2 HE + 1 planes of D~(y, h) and the q tile.
+template <int RZ, int STAGES, int HE>
+using BornRingE = Ring<8 * RZ, RADIUS + 2 * HE, 2, 2, STAGES,
+                       3 * 8 * RZ * TX * 4 + (HE > 0 ? (2 * HE + 1) * 8 * RZ * TX * 4 + 8 * RZ * (TX + 4 * HE) * 4 : 0)>;
+
+template <int RZ, int STAGES, int MINB, int HE = 0>
 __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__ Batch<BornArgs, 1> B)
 {
-    using R = BornRing<RZ, STAGES>;
+    static_assert(HE % 2 == 0, "extended Born: even HE (16-byte aligned TMA x offsets)");
+    using R = BornRingE<RZ, STAGES, HE>;
     constexpr int TZ = 8 * RZ;
-    constexpr int HX = RADIUS;
+    constexpr int HX = RADIUS + 2 * HE;
+    constexpr int NE = 2 * HE + 1;
+    constexpr int QW = TX + 4 * HE;
     constexpr int TXS = R::TXS;
     constexpr int D = STAGES - 1;
     static_assert(D >= 1 && D + 2 <= DESC_RING, "needs 2 <= STAGES <= 7");
@@ -889,6 +982,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
     float *c2s = reinterpret_cast<float *>(R::extra(smem));
     float *dcs = c2s + TZ * TX;  // dc2 tile
     float *dms = dcs + TZ * TX;  // damping tile (sponge tiles)
+    float *des = dms + TZ * TX;  // HE > 0: planes D~(y, h), h = -HE..HE
+    float *qs = des + NE * TZ * TX; // HE > 0: q^n on columns bj - 2 HE .. bj + TX + 2 HE - 1
+    (void)qs;
+    (void)QW;
 
     const BornArgs &a = B.m[0];
     const StepCommon &c = a.c;
@@ -954,12 +1051,21 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
             colok = j0 < L.nxp;
             if (tile_sponge) sg.init(L, i0, j0);
             load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
-            load_c2_tile<TZ>(dcs, a.dc2, L, bi, bj);
+            if constexpr (HE > 0) {
+                for (int e = 0; e < NE; ++e) load_c2_tile<TZ>(des + e * TZ * TX, a.dext + e * L.fstride, L, bi, bj);
+            } else {
+                load_c2_tile<TZ>(dcs, a.dc2, L, bi, bj);
+            }
             if (tile_sponge) load_c2_tile<TZ>(dms, c.damp, L, bi, bj);
             __syncthreads();
         }
         const int st = k % STAGES;
-        if (stage_ready<STAGES>(bars, k, &s_abort)) {
+        const bool ready = stage_ready<STAGES>(bars, k, &s_abort);
+        if constexpr (HE > 0) {
+            if (ready && !a.last) bwd_q_ext<RZ, HE, TXS, HX>(qs, R::halo(smem, st, 0), now, bi, bj, L, c.src_scale);
+            __syncthreads();
+        }
+        if (ready) {
             const float *su = R::halo(smem, st, 0);
             const float *sd = R::halo(smem, st, 1);
             // Born traces du^n = R du^n
@@ -1008,15 +1114,30 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
                     const float4 up4 = lds4(&pu[(ty * RZ + r) * TX + 4 * tx]);
                     const float4 dp4 = lds4(&pd[(ty * RZ + r) * TX + 4 * tx]);
                     const float4 c24 = lds4(&c2s[(ty * RZ + r) * TX + 4 * tx]);
-                    const float4 dc24 = lds4(&dcs[(ty * RZ + r) * TX + 4 * tx]);
+                    const float4 dc24 = HE > 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : lds4(&dcs[(ty * RZ + r) * TX + 4 * tx]);
+                    // extended scattering source S(y) = sum_h D~(y, h) q(y + 2h)
+                    float2 sx[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    if constexpr (HE > 0) {
+                        const float *qrow = qs + (ty * RZ + r) * QW;
+#pragma unroll
+                        for (int hh = 0; hh < NE; ++hh) {
+                            const float4 d4 = lds4(&des[(hh * TZ + ty * RZ + r) * TX + 4 * tx]);
+                            const int c0 = 4 * tx + 2 * hh;   // column of y + 2h for the first point
+                            sx[0] = fma2(lo2(d4), make_float2(qrow[c0], qrow[c0 + 1]), sx[0]);
+                            sx[1] = fma2(hi2(d4), make_float2(qrow[c0 + 2], qrow[c0 + 3]), sx[1]);
+                        }
+                    }
                     float2 un[2], dn[2];
                     if (!tile_sponge) {
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const float2 u1 = half2of(uc, h), d1 = half2of(dc, h);
                             un[h] = add2(u1, fma2(half2of(c24, h), qu[r][h], sub2(u1, half2of(up4, h))));
-                            dn[h] = add2(d1, fma2(half2of(c24, h), qd[r][h],
-                                                  fma2(half2of(dc24, h), qu[r][h], sub2(d1, half2of(dp4, h)))));
+                            if constexpr (HE > 0)
+                                dn[h] = add2(d1, fma2(half2of(c24, h), qd[r][h], add2(sx[h], sub2(d1, half2of(dp4, h)))));
+                            else
+                                dn[h] = add2(d1, fma2(half2of(c24, h), qd[r][h],
+                                                      fma2(half2of(dc24, h), qu[r][h], sub2(d1, half2of(dp4, h)))));
                         }
                     } else {
                         const float4 ia4 = lds4(&dms[(ty * RZ + r) * TX + 4 * tx]);
@@ -1026,7 +1147,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
                             const float2 kb = fma2(ia2, make_float2(2.f, 2.f), make_float2(-1.f, -1.f));
                             const float2 u1 = half2of(uc, h), d1 = half2of(dc, h);
                             un[h] = add2(u1, fma2(mul2(half2of(c24, h), ia2), qu[r][h], mul2(kb, sub2(u1, half2of(up4, h)))));
-                            const float2 src2 = fma2(half2of(c24, h), qd[r][h], mul2(half2of(dc24, h), qu[r][h]));
+                            const float2 src2 = HE > 0 ? fma2(half2of(c24, h), qd[r][h], sx[h])
+                                                       : fma2(half2of(c24, h), qd[r][h], mul2(half2of(dc24, h), qu[r][h]));
                             dn[h] = add2(d1, fma2(ia2, src2, mul2(kb, sub2(d1, half2of(dp4, h)))));
                         }
                     }
@@ -1327,6 +1449,82 @@ constexpr int SMEM_BORN = BornRing<BORN_RZ, BORN_ST>::SMEM;
 std::once_flag g_born_once;
 int g_occ_born = 2;
 } // namespace
+
+// ---------------------------------------------------- extended operators
+namespace {
+template <int HE> struct ExtKernels {
+    static constexpr int SMEM_B = BwdRingE<1, 2, HE>::SMEM;
+    static constexpr int SMEM_O = BornRingE<1, 2, HE>::SMEM;
+    static std::once_flag once;
+    static int occ_b, occ_o;
+    static void prepare()
+    {
+        std::call_once(once, [] {
+            auto kb = k_bwd_step<1, 2, 2, 1, HE>;
+            auto ko = k_born_step<1, 2, 2, HE>;
+            cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B);
+            cudaFuncSetAttribute(ko, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_O);
+            int o = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kb, TPB, SMEM_B) == cudaSuccess && o > 0) occ_b = o;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, ko, TPB, SMEM_O) == cudaSuccess && o > 0) occ_o = o;
+            cudaGetLastError();
+        });
+    }
+    static cudaError_t bwd(const BwdArgs &a, const Tiling &t, cudaStream_t st)
+    {
+        prepare();
+        Batch<BwdArgs, 1> b;
+        const int ctas = batch_fill(b, &a, &t, 1, occ_b);
+        if (ctas <= 0) return cudaSuccess;
+        k_bwd_step<1, 2, 2, 1, HE><<<ctas, TPB, SMEM_B, st>>>(b);
+        return cudaGetLastError();
+    }
+    static cudaError_t born(const BornArgs &a, const Tiling &t, cudaStream_t st)
+    {
+        prepare();
+        Batch<BornArgs, 1> b;
+        const int ctas = batch_fill(b, &a, &t, 1, occ_o);
+        if (ctas <= 0) return cudaSuccess;
+        k_born_step<1, 2, 2, HE><<<ctas, TPB, SMEM_O, st>>>(b);
+        return cudaGetLastError();
+    }
+};
+template <int HE> std::once_flag ExtKernels<HE>::once;
+template <int HE> int ExtKernels<HE>::occ_b = 1;
+template <int HE> int ExtKernels<HE>::occ_o = 1;
+} // namespace
+
+int ext_kernel_he(int hext) { return hext <= 2 ? 2 : (hext <= 4 ? 4 : 6); }
+
+void ext_boxes(int he, const Tiling &t, int &hx, int &hy, int &px, int &py)
+{
+    hx = TX + 2 * (RADIUS + 2 * he);
+    hy = t.tz + 2 * RADIUS;
+    px = TX;
+    py = t.tz;
+}
+
+cudaError_t launch_bwd_ext_step(const BwdArgs &a, const Tiling &t, int he, cudaStream_t st)
+{
+    if (t.tz != 8) return cudaErrorInvalidValue;
+    switch (he) {
+    case 2: return ExtKernels<2>::bwd(a, t, st);
+    case 4: return ExtKernels<4>::bwd(a, t, st);
+    case 6: return ExtKernels<6>::bwd(a, t, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_born_ext_step(const BornArgs &a, const Tiling &t, int he, cudaStream_t st)
+{
+    if (t.tz != 8) return cudaErrorInvalidValue;
+    switch (he) {
+    case 2: return ExtKernels<2>::born(a, t, st);
+    case 4: return ExtKernels<4>::born(a, t, st);
+    case 6: return ExtKernels<6>::born(a, t, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_born_step(const BornArgs &a, const Tiling &t, cudaStream_t st)
 {

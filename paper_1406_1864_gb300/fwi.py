@@ -20,7 +20,8 @@ OPS = {"forward": L.FWI_OP_FORWARD, "forward_save": L.FWI_OP_FORWARD_SAVE,
        "gradient": L.FWI_OP_GRADIENT, "illumination": L.FWI_OP_ILLUMINATION,
        "offset_hessian": L.FWI_OP_OFFSET_HESSIAN, "precondition": L.FWI_OP_PRECONDITION,
        "born": L.FWI_OP_BORN, "gn_hvp": L.FWI_OP_GN_HVP, "misfit": L.FWI_OP_MISFIT,
-       "receiver_factor": L.FWI_OP_RECEIVER_FACTOR, "precondition_receiver": L.FWI_OP_PRECONDITION_RECEIVER}
+       "receiver_factor": L.FWI_OP_RECEIVER_FACTOR, "precondition_receiver": L.FWI_OP_PRECONDITION_RECEIVER,
+       "extended_born": L.FWI_OP_EXT_BORN, "extended_migration": L.FWI_OP_EXT_MIGRATION}
 
 
 @dataclass
@@ -341,6 +342,38 @@ def misfit(grid: Grid, geom: Geometry, v: torch.Tensor, d_obs: torch.Tensor, opt
     L.check(L.load().fwi_misfit(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o) if o is not None else None,
                                 _ptr(v), _ptr(d_obs), _ptr(J), _ptr(buf), nb, _stream(stream)), "fwi_misfit")
     return J
+
+
+def extended_born(grid: Grid, geom: Geometry, v: torch.Tensor, dv_ext: torch.Tensor, *, ws=None, out=None,
+                  stream=None) -> torch.Tensor:
+    """fwi_extended_born (Eq. 5): traces [ns, nt, nrec] of the extended
+    perturbation dv_ext [2 hext + 1, nz, nx] (plane k: offset k - hext)."""
+    _dev(v, "v", grid.shape)
+    hext = (dv_ext.shape[0] - 1) // 2
+    _dev(dv_ext, "dv_ext", (2 * hext + 1,) + grid.shape)
+    d = out if out is not None else torch.empty((geom.nshots, grid.nt, geom.nrec), dtype=torch.float32,
+                                                device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, None, "extended_born"))
+    g, ge = grid.c(), geom.c()
+    L.check(L.load().fwi_extended_born(ctypes.byref(g), ctypes.byref(ge), None, int(hext), _ptr(v), _ptr(dv_ext),
+                                       _ptr(d), _ptr(buf), nb, _stream(stream)), "fwi_extended_born")
+    return d
+
+
+def extended_migration(grid: Grid, geom: Geometry, v: torch.Tensor, adj_src: torch.Tensor, hext: int, *, ws=None,
+                       out=None, stream=None) -> torch.Tensor:
+    """fwi_extended_migration (Eq. 6): the image [2 hext + 1, nz, nx] of the
+    adjoint source adj_src [ns, nt, nrec] (plane k: offset k - hext)."""
+    _dev(v, "v", grid.shape)
+    _dev(adj_src, "adj_src", (geom.nshots, grid.nt, geom.nrec))
+    img = out if out is not None else torch.empty((2 * hext + 1,) + grid.shape, dtype=torch.float32,
+                                                  device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, None, "extended_migration"))
+    g, ge = grid.c(), geom.c()
+    L.check(L.load().fwi_extended_migration(ctypes.byref(g), ctypes.byref(ge), None, int(hext), _ptr(v),
+                                            _ptr(adj_src), _ptr(img), _ptr(buf), nb, _stream(stream)),
+            "fwi_extended_migration")
+    return img
 
 
 def born(grid: Grid, geom: Geometry, v: torch.Tensor, dv: torch.Tensor, *, ws=None, out=None,

@@ -34,7 +34,8 @@ def test_header_declares_the_boundary():
                  "fwi_adjoint_apply", "fwi_workspace_bytes", "fwi_last_error", "fwi_batch_gradient",
                  "fwi_batch_workspace_bytes", "fwi_exec_gradient_create", "fwi_exec_run", "fwi_exec_destroy",
                  "fwi_autotune", "fwi_autotune_reset", "fwi_autotune_set", "fwi_born",
-                 "fwi_gauss_newton_hvp", "fwi_misfit", "fwi_receiver_factor", "fwi_precondition_receiver"]:
+                 "fwi_gauss_newton_hvp", "fwi_misfit", "fwi_receiver_factor", "fwi_precondition_receiver",
+                 "fwi_extended_born", "fwi_extended_migration"]:
         assert must in names
 
 
@@ -190,7 +191,7 @@ def test_born_workspace_and_errors(lib):
     assert born < hvp and hvp >= grad - 30 * 40 * 4 * 2
     o.ckpt = L.FWI_CKPT_SNAPSHOT
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GN_HVP)[0] == L.FWI_ERR_INVALID_ARG
-    assert ws_bytes(lib, g, ge, None, L.FWI_OP_PRECONDITION_RECEIVER + 1)[0] == L.FWI_ERR_INVALID_ARG
+    assert ws_bytes(lib, g, ge, None, L.FWI_OP_EXT_MIGRATION + 1)[0] == L.FWI_ERR_INVALID_ARG
     st = lib.fwi_born(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1), None, ctypes.c_void_p(1),
                       ctypes.c_void_p(256), 1 << 40, None)
     assert st == L.FWI_ERR_INVALID_ARG
@@ -253,6 +254,33 @@ def test_receiver_factor_workspace_and_errors(lib):
                                        4, ctypes.c_void_p(1), 3, ctypes.c_float(1e-3), ctypes.c_void_p(1),
                                        ctypes.c_void_p(256), 1 << 40, None)
     assert st == L.FWI_ERR_INVALID_ARG  # 3 factor planes for 5 offsets
+
+
+def test_extended_operator_workspace_and_errors(lib):
+    """The extended Born pass holds u, du and the 13 planes of its scattering
+    strengths; extended migration the gradient's state plus 13 image planes.
+    Both refuse hext outside 0..6, snapshot checkpoints and NULL inputs."""
+    from paper_1406_1864_gb300 import _lib as L
+    g, ge, o, keep = _structs()
+    _, born = ws_bytes(lib, g, ge, None, L.FWI_OP_BORN)
+    st, eb = ws_bytes(lib, g, ge, None, L.FWI_OP_EXT_BORN)
+    assert st == L.FWI_OK and eb >= born + 13 * 50 * 60 * 4
+    _, fs = ws_bytes(lib, g, ge, None, L.FWI_OP_FORWARD_SAVE)
+    st, em = ws_bytes(lib, g, ge, None, L.FWI_OP_EXT_MIGRATION)
+    assert st == L.FWI_OK and em >= fs + 13 * 50 * 60 * 4
+    o.ckpt = L.FWI_CKPT_SNAPSHOT
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_EXT_MIGRATION)[0] == L.FWI_ERR_INVALID_ARG
+    p1 = ctypes.c_void_p(1)
+    for hext in (-1, 7):
+        st = lib.fwi_extended_born(ctypes.byref(g), ctypes.byref(ge), None, hext, p1, p1, p1, ctypes.c_void_p(256),
+                                   1 << 40, None)
+        assert st == L.FWI_ERR_INVALID_ARG
+        st = lib.fwi_extended_migration(ctypes.byref(g), ctypes.byref(ge), None, hext, p1, p1, p1,
+                                        ctypes.c_void_p(256), 1 << 40, None)
+        assert st == L.FWI_ERR_INVALID_ARG
+    st = lib.fwi_extended_migration(ctypes.byref(g), ctypes.byref(ge), None, 2, p1, p1, None, ctypes.c_void_p(256),
+                                    1 << 40, None)
+    assert st == L.FWI_ERR_INVALID_ARG
 
 
 def test_product_path_does_not_import_the_oracle():
