@@ -1,5 +1,5 @@
-"""Timing of Born modelling and Gauss-Newton Hessian-vector products:
-python -m paper_1406_1864_gb300.bench_born [options].
+"""Timing of Born modelling, Gauss-Newton Hessian-vector products and the
+extended operators: python -m paper_1406_1864_gb300.bench_born [options].
 
 On the seeded dipping-layer workload (workloads.dipping, default 300 x 1000,
 96 shots, nt 4000, dv = v_true - v_init; --shots and --nt give smaller cases
@@ -8,7 +8,11 @@ fwi_gauss_newton_hvp with CUDA events on the library's stream (phase times of
 the library's profiler: the Born pass, the backward pass). The Born step
 moves 24 B per padded point-step per shot at the least: u^n and du^n read
 once (halo tiles), u^{n-1} and du^{n-1} read, u^{n+1} and du^{n+1} written;
-the backward step 28 B (its own figure). Prints one JSON line with the
+the backward step 28 B (its own figure). With --hext H (> 0) also
+fwi_extended_born and fwi_extended_migration with offsets -H..H (a random
+dv_ext and a random adjoint source): the same 24 B / 28 B
+per point-step (the 2 H + 1 planes of D~ and of the image are read or added
+once per tile and chunk of shots). Prints one JSON line with the
 per-level step times, the algorithmic bandwidth and its fraction of the
 measured copy bandwidth (MEASURED_PEAKS.json at the repository root, burst
 figure), and the whole-call throughput in physical point-steps per second.
@@ -41,6 +45,7 @@ def main():
     ap.add_argument("--nt", type=int, default=4000)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--hext", type=int, default=4)
     args = ap.parse_args()
     p = W.dipping(ns=args.shots, nt=args.nt)
     grid, geom = fwi.from_problem(p)
@@ -51,21 +56,30 @@ def main():
     peak, kind = hbm_peak()
     fwi.profile(True)
     res = {}
-    for name, fn in (("born", fwi.born), ("gn_hvp", fwi.gauss_newton_hvp)):
+    calls = [("born", lambda: fwi.born(grid, geom, v, dv, ws=ws)),
+             ("gn_hvp", lambda: fwi.gauss_newton_hvp(grid, geom, v, dv, ws=ws))]
+    if args.hext > 0:
+        gen = torch.Generator(device="cuda").manual_seed(3)
+        dve = 20.0 * torch.randn((2 * args.hext + 1,) + tuple(v.shape), device="cuda", generator=gen)
+        adj = torch.randn((p.nshots, p.nt, p.nrec), device="cuda", generator=gen)
+        calls += [("extended_born", lambda: fwi.extended_born(grid, geom, v, dve, ws=ws)),
+                  ("extended_migration", lambda: fwi.extended_migration(grid, geom, v, adj, args.hext, ws=ws))]
+    for name, fn in calls:
         for _ in range(args.warmup):
-            fn(grid, geom, v, dv, ws=ws)
+            fn()
         best = None
         for _ in range(args.reps):
             torch.cuda.synchronize()
-            fn(grid, geom, v, dv, ws=ws)
+            fn()
             ph = fwi.last_phase_times()
             if best is None or ph["forward_ms"] + ph["adjoint_ms"] + ph["other_ms"] < best["total"]:
                 best = dict(ph, total=ph["forward_ms"] + ph["adjoint_ms"] + ph["other_ms"])
         us_b = 1e3 * best["forward_ms"] / max(1, best["forward_launches"])
-        r = {"call_ms": best["total"], "born_us_per_level": us_b,
-             "born_alg_GBps": BORN_BYTES * npad * p.nshots / (us_b * 1e-6) / 1e9,
+        fb = 16 if name == "extended_migration" else BORN_BYTES   # its forward pass is the plain step
+        r = {"call_ms": best["total"], "forward_us_per_level": us_b,
+             "forward_alg_GBps": fb * npad * p.nshots / (us_b * 1e-6) / 1e9,
              "Gpts_per_s": p.nz * p.nx * p.nt * p.nshots / (best["total"] * 1e-3) / 1e9}
-        r["born_frac"] = r["born_alg_GBps"] / peak
+        r["forward_frac"] = r["forward_alg_GBps"] / peak
         if best["adjoint_launches"]:
             us_a = 1e3 * best["adjoint_ms"] / best["adjoint_launches"]
             r["bwd_us_per_level"] = us_a

@@ -564,19 +564,21 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
 template <int RZ, int STAGES>
 using BwdRing = Ring<8 * RZ, RADIUS, 2, 2, STAGES, 3 * 8 * RZ * TX * 4>; // + c2, injection, damping tiles
 
-// q = Lhat u + f delta_s of one halo tile on the TZ x (TX + 4 HE) columns
-// bj - 2 HE .. bj + TX + 2 HE - 1 (the x-extension of the extended operators'
-// offsets 2h, |h| <= HE), zero where a column leaves the padded grid or a row
-// its padded rows. Scalar points, the same second-difference arithmetic as
-// lap4 (lap8x2 on a duplicated lane).
+// The q tile of the extended operators: q = Lhat u + f delta_s of one halo
+// tile on the TZ x (TX + 4 HE) columns bj - 2 HE .. bj + TX + 2 HE - 1 (the
+// x-extension of the offsets 2h, |h| <= HE), zero where a column leaves the
+// padded grid or a row its padded rows. The thread's own columns come from
+// its registers (q_own_to_smem); the 2 HE columns on each side are scalar
+// points here, with lap4's second-difference arithmetic (lap8x2 on a
+// duplicated lane).
 template <int RZ, int HE, int TXS, int HX>
-__device__ __forceinline__ void bwd_q_ext(float *qs, const float *su, const ItemDesc &d, int bi, int bj,
-                                          const Lay2D &L, float src_scale)
+__device__ __forceinline__ void q_edges_to_smem(float *qs, const float *su, const ItemDesc &d, int bi, int bj,
+                                                const Lay2D &L, float src_scale)
 {
-    constexpr int TZ = 8 * RZ, QW = TX + 4 * HE;
-    for (int e = threadIdx.x; e < TZ * QW; e += TPB) {
-        const int r = e / QW, cq = e - r * QW;
-        const int col = cq - 2 * HE;               // column in the tile, -2HE .. TX+2HE-1
+    constexpr int TZ = 8 * RZ, QW = TX + 4 * HE, EW = 4 * HE;
+    for (int e = threadIdx.x; e < TZ * EW; e += TPB) {
+        const int r = e / EW, cc = e - r * EW;
+        const int col = cc < 2 * HE ? cc - 2 * HE : TX + cc - 2 * HE; // column in the tile
         const int gi = bi + r, gj = bj + col;
         float q = 0.f;
         if (gi < L.nzp && gj >= 0 && gj < L.nxp) {
@@ -593,7 +595,51 @@ __device__ __forceinline__ void bwd_q_ext(float *qs, const float *su, const Item
             q = lap8x2(make_float2(cv, cv), xs, zs).x;
             if (gi == d.si && gj == d.sj) q += d.amp * src_scale;
         }
-        qs[e] = q;
+        qs[r * QW + col + 2 * HE] = q;
+    }
+}
+
+template <int RZ, int HE>
+__device__ __forceinline__ void q_own_to_smem(float *qs, const float2 (&q)[RZ][2], int i0, int j0, const Lay2D &L,
+                                              int tx, int ty)
+{
+    constexpr int QW = TX + 4 * HE;
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const bool rowok = i0 + r < L.nzp;
+        const float v[4] = {q[r][0].x, q[r][0].y, q[r][1].x, q[r][1].y};
+        float *dst = qs + (ty * RZ + r) * QW + 2 * HE + 4 * tx;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) dst[p] = (rowok && j0 + p < L.nxp) ? v[p] : 0.f;
+    }
+}
+
+// Lhat of one halo tile at the thread's RZ x 4 points, in lane pairs
+template <int RZ, int TXS, int HX>
+__device__ __forceinline__ void tile_lap(float2 (&q)[RZ][2], const float *sf, int tx, int ty)
+{
+    float4 zc[RZ + 2 * RADIUS];
+#pragma unroll
+    for (int kk = 0; kk < RZ + 2 * RADIUS; ++kk) zc[kk] = lds4(&sf[(ty * RZ + kk) * TXS + HX + 4 * tx]);
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const float *rw = &sf[(ty * RZ + r + RADIUS) * TXS + HX + 4 * tx];
+        const float4 a0 = lds4(rw - 4), a2 = lds4(rw + 4);
+        const float4 a1 = zc[r + RADIUS];
+        const float w[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+        lap4<4, RZ + 2 * RADIUS, false>(q[r], w, zc, r);
+    }
+}
+
+template <int RZ>
+__device__ __forceinline__ void add_source(float2 (&q)[RZ][2], int sslot, float amp)
+{
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        if (sslot == r * 4 + 0) q[r][0].x += amp;
+        if (sslot == r * 4 + 1) q[r][0].y += amp;
+        if (sslot == r * 4 + 2) q[r][1].x += amp;
+        if (sslot == r * 4 + 3) q[r][1].y += amp;
     }
 }
 
@@ -605,9 +651,10 @@ __device__ __forceinline__ void ext_accumulate(float (&acc)[4][2 * HE + 1], floa
 {
 #pragma unroll
     for (int hh = 0; hh < 2 * HE + 1; ++hh) {
-        const int c0 = 4 * tx + 2 * lane + 2 * (hh - HE) + 2 * HE;   // column of y + 2h in the q tile
-        acc[2 * lane][hh] = fmaf(psi.x, qrow[c0], acc[2 * lane][hh]);
-        acc[2 * lane + 1][hh] = fmaf(psi.y, qrow[c0 + 1], acc[2 * lane + 1][hh]);
+        const int c0 = 4 * tx + 2 * lane + 2 * hh;   // column of y + 2h in the q tile (even: 8-byte aligned)
+        const float2 q2 = *reinterpret_cast<const float2 *>(qrow + c0);
+        acc[2 * lane][hh] = fmaf(psi.x, q2.x, acc[2 * lane][hh]);
+        acc[2 * lane + 1][hh] = fmaf(psi.y, q2.y, acc[2 * lane + 1][hh]);
     }
 }
 
@@ -831,7 +878,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             // q^{m-1} on the tile and 2 HE columns on each side (zero outside
             // the padded grid), for the extended image
             if (ready) {
-                bwd_q_ext<RZ, HE, TXS, HX>(qs, su, now, bi, bj, L, c.src_scale);
+                tile_lap<RZ, TXS, HX>(qu, su, tx, ty);
+                add_source<RZ>(qu, source_slot<RZ>(now, i0, j0), now.amp * c.src_scale);
+                q_own_to_smem<RZ, HE>(qs, qu, i0, j0, L, tx, ty);
+                q_edges_to_smem<RZ, HE, TXS, HX>(qs, su, now, bi, bj, L, c.src_scale);
             }
             __syncthreads();
         }
@@ -842,9 +892,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             const int sslot = source_slot<RZ>(now, i0, j0);
 
             // q^{m-1} = Lhat u^{m-1} + f(t_{m-1}) delta_s (as in the forward
-            // step m-1), then Lhat psi^{m+1}; one column window live at a time
+            // step m-1; done above with the extended image), then Lhat psi^{m+1};
+            // one column window live at a time
 #pragma unroll
-            for (int fld = 0; fld < 2; ++fld) {
+            for (int fld = HE > 0 ? 1 : 0; fld < 2; ++fld) {
                 const float *sf = fld == 0 ? su : sp;
                 float4 zc[RZ + 2 * RADIUS];
 #pragma unroll
@@ -864,10 +915,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 #pragma unroll
             for (int r = 0; r < RZ; ++r) {
                 const float amp = now.amp * c.src_scale;
-                if (sslot == r * 4 + 0) qu[r][0].x += amp;
-                if (sslot == r * 4 + 1) qu[r][0].y += amp;
-                if (sslot == r * 4 + 2) qu[r][1].x += amp;
-                if (sslot == r * 4 + 3) qu[r][1].y += amp;
+                if constexpr (HE == 0) {
+                    if (sslot == r * 4 + 0) qu[r][0].x += amp;
+                    if (sslot == r * 4 + 1) qu[r][0].y += amp;
+                    if (sslot == r * 4 + 2) qu[r][1].x += amp;
+                    if (sslot == r * 4 + 3) qu[r][1].y += amp;
+                }
                 if (has_rec) {
                     const float4 inj = lds4(&sinj[(ty * RZ + r) * TX + 4 * tx]);
                     qp[r][0] = add2(qp[r][0], lo2(inj));
@@ -1061,8 +1114,17 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
         }
         const int st = k % STAGES;
         const bool ready = stage_ready<STAGES>(bars, k, &s_abort);
+        float2 qu[RZ][2];
         if constexpr (HE > 0) {
-            if (ready && !a.last) bwd_q_ext<RZ, HE, TXS, HX>(qs, R::halo(smem, st, 0), now, bi, bj, L, c.src_scale);
+            // q^n on the tile and 2 HE columns on each side, for the
+            // extended scattering source
+            if (ready && !a.last) {
+                const float *su = R::halo(smem, st, 0);
+                tile_lap<RZ, TXS, HX>(qu, su, tx, ty);
+                add_source<RZ>(qu, source_slot<RZ>(now, i0, j0), now.amp * c.src_scale);
+                q_own_to_smem<RZ, HE>(qs, qu, i0, j0, L, tx, ty);
+                q_edges_to_smem<RZ, HE, TXS, HX>(qs, su, now, bi, bj, L, c.src_scale);
+            }
             __syncthreads();
         }
         if (ready) {
@@ -1082,9 +1144,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
                 const float *pd = R::point(smem, st, 1);
                 const long long so = (long long)s * L.fstride;
                 const int sslot = source_slot<RZ>(now, i0, j0);
-                float2 qu[RZ][2], qd[RZ][2];
+                float2 qd[RZ][2];
 #pragma unroll
-                for (int fld = 0; fld < 2; ++fld) {
+                for (int fld = HE > 0 ? 1 : 0; fld < 2; ++fld) {
                     const float *sf = fld == 0 ? su : sd;
                     float4 zc[RZ + 2 * RADIUS];
 #pragma unroll
@@ -1104,10 +1166,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
                 const float amp = now.amp * c.src_scale;
 #pragma unroll
                 for (int r = 0; r < RZ; ++r) {
-                    if (sslot == r * 4 + 0) qu[r][0].x += amp;
-                    if (sslot == r * 4 + 1) qu[r][0].y += amp;
-                    if (sslot == r * 4 + 2) qu[r][1].x += amp;
-                    if (sslot == r * 4 + 3) qu[r][1].y += amp;
+                    if constexpr (HE == 0) {
+                        if (sslot == r * 4 + 0) qu[r][0].x += amp;
+                        if (sslot == r * 4 + 1) qu[r][0].y += amp;
+                        if (sslot == r * 4 + 2) qu[r][1].x += amp;
+                        if (sslot == r * 4 + 3) qu[r][1].y += amp;
+                    }
                     const int sr = ty * RZ + r + RADIUS;
                     const float4 uc = lds4(&su[sr * TXS + HX + 4 * tx]);
                     const float4 dc = lds4(&sd[sr * TXS + HX + 4 * tx]);
@@ -1122,9 +1186,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
 #pragma unroll
                         for (int hh = 0; hh < NE; ++hh) {
                             const float4 d4 = lds4(&des[(hh * TZ + ty * RZ + r) * TX + 4 * tx]);
-                            const int c0 = 4 * tx + 2 * hh;   // column of y + 2h for the first point
-                            sx[0] = fma2(lo2(d4), make_float2(qrow[c0], qrow[c0 + 1]), sx[0]);
-                            sx[1] = fma2(hi2(d4), make_float2(qrow[c0 + 2], qrow[c0 + 3]), sx[1]);
+                            const int c0 = 4 * tx + 2 * hh;   // column of y + 2h for the first point (even)
+                            sx[0] = fma2(lo2(d4), *reinterpret_cast<const float2 *>(qrow + c0), sx[0]);
+                            sx[1] = fma2(hi2(d4), *reinterpret_cast<const float2 *>(qrow + c0 + 2), sx[1]);
                         }
                     }
                     float2 un[2], dn[2];
@@ -1460,8 +1524,8 @@ template <int HE> struct ExtKernels {
     static void prepare()
     {
         std::call_once(once, [] {
-            auto kb = k_bwd_step<1, 2, 2, 1, HE>;
-            auto ko = k_born_step<1, 2, 2, HE>;
+            auto kb = k_bwd_step<1, 2, 3, 1, HE>;
+            auto ko = k_born_step<1, 2, 3, HE>;
             cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B);
             cudaFuncSetAttribute(ko, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_O);
             int o = 0;
@@ -1476,7 +1540,7 @@ template <int HE> struct ExtKernels {
         Batch<BwdArgs, 1> b;
         const int ctas = batch_fill(b, &a, &t, 1, occ_b);
         if (ctas <= 0) return cudaSuccess;
-        k_bwd_step<1, 2, 2, 1, HE><<<ctas, TPB, SMEM_B, st>>>(b);
+        k_bwd_step<1, 2, 3, 1, HE><<<ctas, TPB, SMEM_B, st>>>(b);
         return cudaGetLastError();
     }
     static cudaError_t born(const BornArgs &a, const Tiling &t, cudaStream_t st)
@@ -1485,7 +1549,7 @@ template <int HE> struct ExtKernels {
         Batch<BornArgs, 1> b;
         const int ctas = batch_fill(b, &a, &t, 1, occ_o);
         if (ctas <= 0) return cudaSuccess;
-        k_born_step<1, 2, 2, HE><<<ctas, TPB, SMEM_O, st>>>(b);
+        k_born_step<1, 2, 3, HE><<<ctas, TPB, SMEM_O, st>>>(b);
         return cudaGetLastError();
     }
 };
