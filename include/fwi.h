@@ -139,6 +139,10 @@ typedef struct {
     int shot_group; /* 3-D: shots modelled at a time (the workspace holds one
                        group; the sums over groups are the sums over shots);
                        0: all shots at once                                    */
+    int hess_v6;    /* 1: the illumination and offset-Hessian outputs, and the
+                       preconditioners built from them, carry the 4 / v(x)^6
+                       prefactor of H_a's diagonal [Sec. 3]; 0: without (Eq. 1
+                       as printed)                                             */
 } fwi_options;
 
 /* Per-phase device times of the last call on this host thread, when enabled

@@ -301,7 +301,7 @@ def precondition(grad, P, eps=1e-3):
 
 
 def fwi_gradient(grid: Grid, v, src, rec, wav, d_obs, *, misfit="ols", hmax=None,
-                 illum_utt=False, eps=1e-3, nthreads=0):
+                 illum_utt=False, eps=1e-3, hess_v6=False, nthreads=0):
     """The whole preconditioned gradient of one model: forward modelling,
     misfit, adjoint source, adjoint imaging, illumination / offset-Hessian
     preconditioners. Returns a dict of float64 arrays and the misfit J."""
@@ -314,9 +314,11 @@ def fwi_gradient(grid: Grid, v, src, rec, wav, d_obs, *, misfit="ols", hmax=None
     else:
         raise ValueError(misfit)
     g = gradient_for_adjoint_source(grid, v, src, rec, wav, adj, nthreads=nthreads)["grad"]
-    out = {"seis": fw["seis"], "J": J, "grad": g, "illum": fw["illum"],
-           "grad_pre_illum": precondition(g, fw["illum"], eps)}
+    # H_a's diagonal carries 4 omega^4 / (v^3(x) v^3(y)) (Sec. 3): at y = x, 4 / v(x)^6
+    w6 = 4.0 / np.asarray(v, np.float64).reshape(grid.nz, grid.ny, grid.nx) ** 6 if hess_v6 else 1.0
+    illum = fw["illum"] * w6
+    out = {"seis": fw["seis"], "J": J, "grad": g, "illum": illum, "grad_pre_illum": precondition(g, illum, eps)}
     if hmax is not None:
-        out["offh"] = fw["offh"]
-        out["grad_pre_offset"] = precondition(g, offset_scale(fw["offh"]), eps)
+        out["offh"] = fw["offh"] * w6
+        out["grad_pre_offset"] = precondition(g, offset_scale(out["offh"]), eps)
     return out

@@ -47,7 +47,7 @@ class FwiGeometry(ctypes.Structure):
 class FwiOptions(ctypes.Structure):
     _fields_ = [("misfit", c_int), ("illum_mode", c_int), ("hmax", c_int), ("precond", c_int),
                 ("eps", c_float), ("ckpt", c_int), ("snap_prec", c_int), ("snap_interval", c_int),
-                ("shot_group", c_int)]
+                ("shot_group", c_int), ("hess_v6", c_int)]
 
 
 class FwiPhaseTimes(ctypes.Structure):

@@ -152,6 +152,7 @@ fwi_status check_opts(const fwi_options *o, int op)
         return fail(FWI_ERR_INVALID_ARG, "snap_prec=%d unknown", o->snap_prec);
     if (o->snap_interval < 0) return fail(FWI_ERR_INVALID_ARG, "snap_interval=%d must be >= 0", o->snap_interval);
     if (o->shot_group < 0) return fail(FWI_ERR_INVALID_ARG, "shot_group=%d must be >= 0", o->shot_group);
+    if (o->hess_v6 != 0 && o->hess_v6 != 1) return fail(FWI_ERR_INVALID_ARG, "hess_v6=%d must be 0 or 1", o->hess_v6);
     return FWI_OK;
 }
 
@@ -860,13 +861,14 @@ fwi_status gradient_models(int nm, const Plan *pl, const fwi_geometry *const *ge
         // illumination: dt sum u^2, or (1/dt^3) sum (second difference)^2
         const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? p.L.dt : 1.0f / (p.L.dt * p.L.dt * p.L.dt);
         float *ill_out = o.illum ? o.illum : acc_i[k]; // in place into group 0 when not requested
-        if ((e = launch_finish_accum(p.L, acc_i[k], 1, 1, iscale, ill_out, st)) != cudaSuccess)
+        const float *v6 = opts->hess_v6 ? o.v : nullptr;
+        if ((e = launch_finish_accum(p.L, acc_i[k], 1, 1, iscale, ill_out, st, v6)) != cudaSuccess)
             return cuda_fail(e, "illumination output");
         t_launch[2]++;
         float *off_out = nullptr;
         if (acc_h[k]) {
             off_out = o.offh ? o.offh : acc_h[k];
-            if ((e = launch_finish_accum(p.L, acc_h[k], 1, p.hmax + 1, p.L.dt, off_out, st)) != cudaSuccess)
+            if ((e = launch_finish_accum(p.L, acc_h[k], 1, p.hmax + 1, p.L.dt, off_out, st, v6)) != cudaSuccess)
                 return cuda_fail(e, "offset-Hessian output");
             t_launch[2]++;
         }
@@ -1359,7 +1361,8 @@ fwi_status forward3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_op
     prof_record(2, st);
     if (illum) {
         const float iscale = utt == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
-        cudaError_t e = launch_finish_accum_n((long long)pl.L.nz * pl.L.ny * pl.L.nx, acc_i, 1, 1, iscale, illum, st);
+        cudaError_t e = launch_finish_accum_n((long long)pl.L.nz * pl.L.ny * pl.L.nx, acc_i, 1, 1, iscale, illum, st,
+                                              opts && opts->hess_v6 ? v : nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "illumination output");
         t_launch[2]++;
     }
@@ -1408,7 +1411,8 @@ fwi_status gradient3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_o
     const long long nphys = (long long)pl.L.nz * pl.L.ny * pl.L.nx;
     const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
     float *ill_out = illum ? illum : acc_i;
-    if ((e = launch_finish_accum_n(nphys, acc_i, 1, 1, iscale, ill_out, st)) != cudaSuccess)
+    if ((e = launch_finish_accum_n(nphys, acc_i, 1, 1, iscale, ill_out, st, opts->hess_v6 ? v : nullptr)) !=
+        cudaSuccess)
         return cuda_fail(e, "illumination output");
     t_launch[2]++;
     if (grad_pre) {
@@ -1464,7 +1468,7 @@ fwi_status make_recv_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_o
     if (ge->nrec < 1) return fail(FWI_ERR_INVALID_ARG, "the receiver factor needs receivers");
     rp.hmax = o ? std::max(o->hmax, 0) : 0;
     rp.o2 = o ? *o : fwi_options{FWI_MISFIT_OLS, FWI_ILLUM_U2, 0, FWI_PRECOND_NONE, 1e-3f, FWI_CKPT_SPONGE,
-                                 FWI_SNAP_F32, 0, 0};
+                                 FWI_SNAP_F32, 0, 0, 0};
     rp.o2.hmax = rp.hmax;
     rp.o2.precond = FWI_PRECOND_NONE;
     rp.g2.nshots = ge->nrec;
@@ -1653,7 +1657,7 @@ fwi_status fwi_illumination(const fwi_grid *grid, const fwi_geometry *geom, cons
     prof_record(2, st);
     const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
     cudaError_t e;
-    if ((e = launch_finish_accum(pl.L, acc_i, 1, 1, iscale, illum, st)) != cudaSuccess)
+    if ((e = launch_finish_accum(pl.L, acc_i, 1, 1, iscale, illum, st, opts->hess_v6 ? v : nullptr)) != cudaSuccess)
         return cuda_fail(e, "illumination output");
     t_launch[2]++;
     prof_record(3, st);
@@ -1676,7 +1680,8 @@ fwi_status fwi_offset_hessian_diag(const fwi_grid *grid, const fwi_geometry *geo
     prof_record(1, st);
     prof_record(2, st);
     cudaError_t e;
-    if ((e = launch_finish_accum(pl.L, acc_h, 1, pl.hmax + 1, pl.L.dt, offh, st)) != cudaSuccess)
+    if ((e = launch_finish_accum(pl.L, acc_h, 1, pl.hmax + 1, pl.L.dt, offh, st, opts->hess_v6 ? v : nullptr)) !=
+        cudaSuccess)
         return cuda_fail(e, "offset-Hessian output");
     t_launch[2]++;
     prof_record(3, st);

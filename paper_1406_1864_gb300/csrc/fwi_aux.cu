@@ -299,14 +299,20 @@ __global__ void k_fold_grad(const Lay2D L, const float *__restrict__ acc, int gr
 
 // out[plane][iz][ix] = scale * sum_g acc[g][plane][iz][ix]
 __global__ void k_finish_accum(long long nphys, const float *__restrict__ acc, int groups,
-                               int planes, float scale, float *__restrict__ out)
+                               int planes, float scale, const float *__restrict__ v6, float *__restrict__ out)
 {
     const long long n = nphys * planes;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         float sum = 0.f;
         for (int g = 0; g < groups; ++g) sum += acc[(long long)g * n + e];
-        out[e] = sum * scale;
+        float sc = scale;
+        if (v6 != nullptr) {
+            // H_a's diagonal prefactor 4 / v^6 at the cell
+            const float v = v6[e % nphys], v3 = v * v * v;
+            sc = sc * __fdiv_rn(4.0f, v3 * v3);
+        }
+        out[e] = sum * sc;
     }
 }
 
@@ -533,16 +539,16 @@ cudaError_t launch_fold_grad(const Lay2D &L, const float *acc, int groups, const
 }
 
 cudaError_t launch_finish_accum_n(long long nphys, const float *acc, int groups, int planes, float scale,
-                                  float *out, cudaStream_t st)
+                                  float *out, cudaStream_t st, const float *v6)
 {
-    k_finish_accum<<<grid_for(nphys * planes), NT1, 0, st>>>(nphys, acc, groups, planes, scale, out);
+    k_finish_accum<<<grid_for(nphys * planes), NT1, 0, st>>>(nphys, acc, groups, planes, scale, v6, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish_accum(const Lay2D &L, const float *acc, int groups, int planes,
-                                float scale, float *out, cudaStream_t st)
+                                float scale, float *out, cudaStream_t st, const float *v6)
 {
-    return launch_finish_accum_n((long long)L.nz * L.nx, acc, groups, planes, scale, out, st);
+    return launch_finish_accum_n((long long)L.nz * L.nx, acc, groups, planes, scale, out, st, v6);
 }
 
 cudaError_t launch_precond(const Lay2D &L, const float *grad, const float *scale, int kind,

@@ -232,7 +232,7 @@ cudaError_t launch_prep3d(const Lay3D &L, const float *v, float *c2, float *damp
 cudaError_t launch_fold_grad3d(const Lay3D &L, const float *acc, const float *v, float *grad, cudaStream_t st);
 // finish / precondition over nphys model cells (any dimension)
 cudaError_t launch_finish_accum_n(long long nphys, const float *acc, int groups, int planes, float scale,
-                                  float *out, cudaStream_t st);
+                                  float *out, cudaStream_t st, const float *v6 = nullptr);
 cudaError_t launch_precond_n(long long nphys, const float *grad, const float *scale, int kind, int hmax, float eps,
                              float *out, unsigned *pmax, cudaStream_t st);
 
@@ -336,8 +336,9 @@ cudaError_t launch_time_integral(float *r, int ns, int nt, int nrec, float dt, d
                                  cudaStream_t st);
 cudaError_t launch_fold_grad(const Lay2D &L, const float *acc, int groups, const float *v,
                              float *grad, cudaStream_t st);
+// (v6: multiply by 4 / v^6 at each cell, v the physical velocity, or null)
 cudaError_t launch_finish_accum(const Lay2D &L, const float *acc, int groups, int planes,
-                                float scale, float *out, cudaStream_t st);
+                                float scale, float *out, cudaStream_t st, const float *v6 = nullptr);
 cudaError_t launch_precond(const Lay2D &L, const float *grad, const float *scale, int kind,
                            int hmax, float eps, float *out, unsigned *pmax, cudaStream_t st);
 cudaError_t launch_check_finite(const float *x, long long n, int *status, cudaStream_t st);

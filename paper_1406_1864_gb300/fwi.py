@@ -92,6 +92,7 @@ class Options:
     snap: str = "f32"
     snap_interval: int = 0
     shot_group: int = 0
+    hess_v6: bool = False
 
     def c(self) -> L.FwiOptions:
         m = {"ols": L.FWI_MISFIT_OLS, "integral": L.FWI_MISFIT_TIME_INTEGRAL}[self.misfit]
@@ -101,7 +102,7 @@ class Options:
         k = {"sponge": L.FWI_CKPT_SPONGE, "snapshot": L.FWI_CKPT_SNAPSHOT}[self.ckpt]
         sp = {"f32": L.FWI_SNAP_F32, "bf16": L.FWI_SNAP_BF16, "f16s": L.FWI_SNAP_F16S}[self.snap]
         return L.FwiOptions(m, i, int(self.hmax), p, float(self.eps), k, sp, int(self.snap_interval),
-                            int(self.shot_group))
+                            int(self.shot_group), int(bool(self.hess_v6)))
 
 
 def _ptr(t):

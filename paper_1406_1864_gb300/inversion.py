@@ -15,6 +15,11 @@ objective that supplies the misfit, its gradient and the preconditioner:
   y = g_{k+1} - g_k (pairs with <s, y> <= 0 are skipped), with the diagonal
   preconditioner as the initial inverse Hessian, H_0 = gamma M^-1,
   gamma = <s, y> / <y, M^-1 y> of the newest pair.
+* Truncated Gauss-Newton: each outer step solves H dv = -g approximately,
+  H the Gauss-Newton Hessian J^T W^T W J (fwi_gauss_newton_hvp), by CG
+  preconditioned with M (at most cg_iters products, until the residual is
+  cg_tol of the gradient, stopping at non-positive curvature), then searches
+  along dv from the unit step.
 * Line search: projected backtracking on the Armijo condition
   f(x + a d) <= f(x) + c1 a <g, d>, with parabolic steps (the minimum of the
   parabola through f(x), its slope and the last trial, kept within [0.1, 0.5]
@@ -242,6 +247,73 @@ class LBFGS(_Base):
         return x, hist
 
 
+class GaussNewton(_Base):
+    """Truncated Gauss-Newton with a preconditioned CG inner solve. hvp(x, p)
+    applies the Gauss-Newton Hessian at x to p."""
+
+    def __init__(self, value_grad, value, hvp, *, max_update, cg_iters=5, cg_tol=0.1, **kw):
+        super().__init__(value_grad, value, max_update=max_update, **kw)
+        self.hvp = hvp
+        self.cg_iters = int(cg_iters)
+        self.cg_tol = float(cg_tol)
+
+    def solve(self, x, g, minv):
+        """Preconditioned CG on H d = -g from d = 0. Returns (d, products)."""
+        d = torch.zeros_like(g)
+        r = -g
+        z = minv(r)
+        p = z
+        rz = _dot(r, z)
+        gnorm = float(torch.linalg.vector_norm(g.double()))
+        n = 0
+        for _ in range(self.cg_iters):
+            Hp = self.hvp(x, p)
+            n += 1
+            pHp = _dot(p, Hp)
+            if pHp <= 0:
+                break
+            a = rz / pHp
+            d = d + a * p
+            r = r - a * Hp
+            if float(torch.linalg.vector_norm(r.double())) <= self.cg_tol * gnorm:
+                break
+            z = minv(r)
+            rz_new = _dot(r, z)
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+        if not bool(d.any()):
+            d = minv(-g)
+        return d, n
+
+    def run(self, x, iters, hist: History | None = None):
+        hist = hist or History()
+        ev = self.value_grad(x)
+        hist.misfit.append(ev.f)
+        hist.hvps = 0
+        for k in range(iters):
+            d, n = self.solve(x, ev.g, ev.minv)
+            hist.hvps += n
+            if _dot(ev.g, d) >= 0:
+                d = -ev.minv(ev.g)
+                hist.restarts += 1
+            alpha, x_new, f_new, trials = self._search(x, ev, d, min(1.0, 10.0 * self._first_alpha(d)))
+            if alpha == 0.0:
+                d = -ev.minv(ev.g)
+                hist.restarts += 1
+                alpha, x_new, f_new, t2 = self._search(x, ev, d, self._first_alpha(d))
+                trials += t2
+            hist.step.append(alpha)
+            hist.evals.append(trials)
+            if alpha == 0.0:
+                break
+            x = x_new
+            ev = self.value_grad(x)
+            hist.misfit.append(ev.f)
+            if self.callback:
+                self.callback(k, x, ev, hist)
+        return x, hist
+
+
 class FwiObjective:
     """The FWI misfit of the library: value_grad(v) runs fwi_adjoint_gradient
     (misfit, gradient and the chosen preconditioner's scale in one call),
@@ -264,6 +336,7 @@ class FwiObjective:
         if receiver is not None and opts.precond == "none":
             raise ValueError("a receiver factor needs precond 'illum' or 'offset'")
         self.receiver, self.receiver_every = receiver, max(1, int(receiver_every))
+        self.n_hvps = 0
         self.recv = fwi.receiver_factor(grid, geom, "pm") if receiver == "pm" else None
         self.mask = None
         if mute_top > 0:
@@ -271,6 +344,16 @@ class FwiObjective:
             self.mask[:mute_top] = 0.0
         self.n_gradients = 0
         self.n_misfits = 0
+
+    def hvp(self, v, p):
+        """The Gauss-Newton Hessian of the misfit at v applied to p
+        (fwi_gauss_newton_hvp), restricted to the unmuted rows."""
+        self.n_hvps += 1
+        fwi = self.fwi
+        q = p * self.mask if self.mask is not None else p
+        hv = fwi.gauss_newton_hvp(self.grid, self.geom, v.contiguous(), q.contiguous(),
+                                  fwi.Options(misfit=self.opts.misfit), ws=self.ws)
+        return hv * self.mask if self.mask is not None else hv
 
     def value(self, v):
         self.n_misfits += 1
@@ -334,8 +417,10 @@ def default_mute(geom):
 
 
 def invert(grid, geom, d_obs, v0, opts, *, method="lbfgs", iters=10, max_update=50.0, memory=5, vmin=None,
-           vmax=None, v_true=None, mute_top=None, receiver=None, receiver_every=1, ws=None):
-    """Run `iters` iterations of L-BFGS or PRCG from v0 with the library's
+           vmax=None, v_true=None, mute_top=None, receiver=None, receiver_every=1, cg_iters=5, cg_tol=0.1,
+           ws=None):
+    """Run `iters` iterations of L-BFGS, PRCG or truncated Gauss-Newton
+    (method "lbfgs", "prcg", "gauss_newton") from v0 with the library's
     gradient and preconditioner (opts.precond), the rows above mute_top fixed
     (None: default_mute(geom); 0: none). Returns (v, History); with v_true,
     History.model_error holds ||v_k - v_true|| / ||v_0 - v_true||."""
@@ -353,8 +438,14 @@ def invert(grid, geom, d_obs, v0, opts, *, method="lbfgs", iters=10, max_update=
             h.model_error.append(float(torch.linalg.vector_norm((x - v_true).double())) / e0)
 
     kw = dict(max_update=max_update, project=lambda x: x.clamp(lo, hi), callback=cb)
-    opt = LBFGS(obj.value_grad, obj.value, memory=memory, **kw) if method == "lbfgs" else \
-        PRCG(obj.value_grad, obj.value, **kw)
+    if method == "lbfgs":
+        opt = LBFGS(obj.value_grad, obj.value, memory=memory, **kw)
+    elif method == "prcg":
+        opt = PRCG(obj.value_grad, obj.value, **kw)
+    elif method == "gauss_newton":
+        opt = GaussNewton(obj.value_grad, obj.value, obj.hvp, cg_iters=cg_iters, cg_tol=cg_tol, **kw)
+    else:
+        raise ValueError(method)
     v, hist = opt.run(v0.clone(), iters, hist)
-    hist.n_gradients, hist.n_misfits = obj.n_gradients, obj.n_misfits
+    hist.n_gradients, hist.n_misfits, hist.n_hvps = obj.n_gradients, obj.n_misfits, obj.n_hvps
     return v, hist

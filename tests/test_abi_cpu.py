@@ -100,7 +100,7 @@ def test_bad_grid_rejected(lib, field, value, code):
 
 @pytest.mark.parametrize("field,value", [("misfit", 7), ("illum_mode", 3), ("hmax", 13),
                                          ("hmax", -2), ("precond", 5), ("eps", 0.0), ("ckpt", 2),
-                                         ("snap_prec", 3), ("snap_interval", -1)])
+                                         ("snap_prec", 3), ("snap_interval", -1), ("hess_v6", 2)])
 def test_bad_options_rejected(lib, field, value):
     from paper_1406_1864_gb300 import _lib as L
     g, ge, o, keep = _structs()

@@ -1,9 +1,9 @@
 """The outer inversion loops driven by the library (GPU) and, for parity, the
 same loops driven by the FP64 oracle.
 
-* The first two iterates of PRCG (illumination preconditioner, OLS misfit)
-  and of L-BFGS (offset-Hessian preconditioner, time-integral misfit of
-  Eq. 2, hmax 3) from the library's gradients, misfits and preconditioner
+* The first two iterates of PRCG (illumination preconditioner, OLS misfit),
+  of L-BFGS (offset-Hessian preconditioner, time-integral misfit of Eq. 2,
+  hmax 3) and of truncated Gauss-Newton (three CG products per step) from the library's gradients, misfits and preconditioner
   against the same loops over the oracle's (relative L2 of the model update
   <= 1e-3: the line searches take the same branches, the steps then agree to
   the gradients' FP32 rounding).
@@ -63,9 +63,19 @@ class OracleObjective:
         g = torch.as_tensor(r["grad"][:, 0, :])
         return I.Evaluation(r["J"], g, lambda q: torch.as_tensor(self.o.precondition(q.numpy(), P, self.eps)))
 
+    def hvp(self, v, q):
+        """J^T W^T W J q from the oracle's Born modelling and adjoint imaging."""
+        import torch
+        jq = self.o.born(self.g, v.numpy(), q.numpy(), self.p.src, self.p.rec, self.w)
+        if self.misfit == "integral":
+            jq = self.o.time_integral_adjoint(self.o.time_integral(jq, self.p.dt), self.p.dt)
+        hq = self.o.gradient_for_adjoint_source(self.g, v.numpy(), self.p.src, self.p.rec, self.w, jq)["grad"]
+        return torch.as_tensor(hq[:, 0, :])
+
 
 @pytest.mark.parametrize("method,misfit,precond,hmax", [("prcg", "ols", "illum", -1),
-                                                        ("lbfgs", "integral", "offset", 3)])
+                                                        ("lbfgs", "integral", "offset", 3),
+                                                        ("gauss_newton", "ols", "illum", -1)])
 def test_first_iterates_against_oracle_loop(torch_cuda, oracle_mod, method, misfit, precond, hmax):
     torch = torch_cuda
     from paper_1406_1864_gb300 import fwi, inversion as I
@@ -75,15 +85,17 @@ def test_first_iterates_against_oracle_loop(torch_cuda, oracle_mod, method, misf
     grid, geom = fwi.from_problem(p)
     opts = fwi.Options(misfit=misfit, precond=precond, hmax=hmax)
     lo, hi = I.velocity_bounds(grid, torch.as_tensor(p.v_init))
-    cls = I.LBFGS if method == "lbfgs" else I.PRCG
     seen_g, seen_o = [], []
+
+    def make(o, cb):
+        kw = dict(max_update=40.0, project=lambda x: x.clamp(lo, hi), callback=cb)
+        if method == "gauss_newton":
+            return I.GaussNewton(o.value_grad, o.value, o.hvp, cg_iters=3, **kw)
+        return (I.LBFGS if method == "lbfgs" else I.PRCG)(o.value_grad, o.value, **kw)
     obj = I.FwiObjective(grid, geom, torch.as_tensor(d_obs, device="cuda"), opts)
-    cls(obj.value_grad, obj.value, max_update=40.0, project=lambda x: x.clamp(lo, hi),
-        callback=lambda k, x, ev, h: seen_g.append(x.cpu().double())).run(
-        torch.as_tensor(p.v_init, device="cuda"), 2)
+    make(obj, lambda k, x, ev, h: seen_g.append(x.cpu().double())).run(torch.as_tensor(p.v_init, device="cuda"), 2)
     ob = OracleObjective(oracle_mod, p, d_obs.astype(np.float64), misfit, precond, hmax)
-    cls(ob.value_grad, ob.value, max_update=40.0, project=lambda x: x.clamp(lo, hi),
-        callback=lambda k, x, ev, h: seen_o.append(x.clone())).run(torch.as_tensor(p.v_init.astype(np.float64)), 2)
+    make(ob, lambda k, x, ev, h: seen_o.append(x.clone())).run(torch.as_tensor(p.v_init.astype(np.float64)), 2)
     v0 = torch.as_tensor(p.v_init.astype(np.float64))
     assert len(seen_g) == len(seen_o) == 2
     for k, (a, b) in enumerate(zip(seen_g, seen_o)):
@@ -94,7 +106,8 @@ def test_first_iterates_against_oracle_loop(torch_cuda, oracle_mod, method, misf
 @pytest.mark.parametrize("method,misfit,precond,hmax,recv", [("lbfgs", "ols", "illum", -1, None),
                                                              ("prcg", "integral", "offset", 4, None),
                                                              ("prcg", "ols", "illum", -1, "pm"),
-                                                             ("lbfgs", "ols", "offset", 2, "green")])
+                                                             ("lbfgs", "ols", "offset", 2, "green"),
+                                                             ("gauss_newton", "integral", "illum", -1, None)])
 def test_ten_iterations_decrease_misfit(torch_cuda, method, misfit, precond, hmax, recv):
     torch = torch_cuda
     from paper_1406_1864_gb300 import fwi, inversion as I

@@ -263,3 +263,24 @@ def test_sharded_gradient_one_rank(torch_cuda):
         for k in ("grad", "illum", "grad_pre") + (("offh",) if hmax >= 0 else ()):
             assert rel(got[k].cpu().numpy(), ref[k].cpu().numpy()) <= 1e-6, (precond, k)
         assert abs(float(got["misfit"]) - float(ref["misfit"])) <= 1e-12 * float(ref["misfit"])
+
+
+def test_hessian_v6_prefactor(torch_cuda, oracle_mod):
+    """hess_v6: the illumination, offset Hessian and preconditioned
+    gradients with H_a's diagonal prefactor 4 / v^6 (Sec. 3)."""
+    torch = torch_cuda
+    p = ragged_problem(ns=2)
+    g = oracle_mod.Grid.of(p)
+    d_obs = observed(oracle_mod, p)
+    ref = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, p.wavelet.astype(np.float64), d_obs.astype(np.float64),
+                                  hmax=4, hess_v6=True)
+    fwi, grid, geom, v = gpu_inputs(torch, p)
+    for precond, key in (("illum", "grad_pre_illum"), ("offset", "grad_pre_offset")):
+        r = fwi.adjoint_gradient(grid, geom, v, torch.as_tensor(d_obs, device="cuda"),
+                                 fwi.Options(hmax=4, precond=precond, hess_v6=True))
+        assert rel(r["illum"].cpu(), ref["illum"][:, 0, :]) <= TOL_GRAD
+        assert rel(r["offh"].cpu(), ref["offh"][:, :, 0, :]) <= TOL_GRAD
+        assert rel(r["grad_pre"].cpu(), ref[key][:, 0, :]) <= TOL_GRAD, precond
+    il = fwi.illumination(grid, geom, v, fwi.Options(hess_v6=True))
+    assert rel(il.cpu(), ref["illum"][:, 0, :]) <= TOL_GRAD
+

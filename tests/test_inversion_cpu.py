@@ -169,3 +169,36 @@ def test_failed_line_search_restarts_along_steepest_descent(cls):
     x, h = cls(vg, value, max_update=1.0, line_search=picky).run(torch.zeros(8, dtype=torch.float64), 300)
     assert h.restarts > 0 and len(h.misfit) > 10
     assert float(torch.linalg.vector_norm(x - xs)) <= 1e-3 * float(torch.linalg.vector_norm(xs))
+
+
+def test_gauss_newton_solves_linear_least_squares_in_one_step():
+    """f = 1/2 |A x - b|^2 has the exact Gauss-Newton Hessian A^T A: with CG
+    run to convergence the first step (unit step) lands on the minimiser."""
+    rng = np.random.default_rng(4)
+    A = torch.tensor(rng.standard_normal((20, 8)))
+    b = torch.tensor(rng.standard_normal(20))
+    xs = torch.linalg.lstsq(A, b).solution
+    value = lambda x: float(0.5 * torch.sum((A @ x - b) ** 2))  # noqa: E731
+    vg = lambda x: I.Evaluation(value(x), A.T @ (A @ x - b), lambda q: q)  # noqa: E731
+    hvp = lambda x, p: A.T @ (A @ p)  # noqa: E731
+    gn = I.GaussNewton(vg, value, hvp, max_update=10.0, cg_iters=8, cg_tol=0.0)
+    x, h = gn.run(torch.zeros(8, dtype=torch.float64), 1)
+    assert float(torch.linalg.vector_norm(x - xs)) <= 1e-8 * float(torch.linalg.vector_norm(xs))
+    assert h.step == [1.0] and h.hvps == 8
+
+
+def test_gauss_newton_on_rosenbrock_residuals():
+    """Rosenbrock as the least-squares problem r = (10 (x2 - x1^2), 1 - x1):
+    Gauss-Newton with J^T J products converges to (1, 1)."""
+    def res(x):
+        return torch.stack([10 * (x[1] - x[0] ** 2), 1 - x[0]])
+
+    def jac(x):
+        return torch.tensor([[-20 * float(x[0]), 10.0], [-1.0, 0.0]], dtype=torch.float64)
+    value = lambda x: float(0.5 * torch.sum(res(x) ** 2))  # noqa: E731
+    vg = lambda x: I.Evaluation(value(x), jac(x).T @ res(x), lambda q: q)  # noqa: E731
+    hvp = lambda x, p: jac(x).T @ (jac(x) @ p)  # noqa: E731
+    x, h = I.GaussNewton(vg, value, hvp, max_update=0.5, cg_iters=2, cg_tol=1e-12).run(
+        torch.tensor([-1.2, 1.0], dtype=torch.float64), 50)
+    assert float(torch.linalg.vector_norm(x - torch.ones(2, dtype=torch.float64))) <= 1e-6, x
+

@@ -11,6 +11,8 @@
   products, reduces to the illumination at h = 0, and obeys Cauchy-Schwarz.
 * The time-integral misfit's gradient is a low-passed version of the OLS
   gradient (Sec. 2, after Eq. 3): its wavenumber centroid is lower.
+* H_a's diagonal prefactor 4 / v^6 (Sec. 3) in a constant velocity is a
+  single number.
 """
 import numpy as np
 
@@ -107,3 +109,23 @@ def test_time_integral_gradient_is_low_passed(oracle_mod):
     # integral misfit's gradient carries lower wavenumbers (measured ~0.85x)
     assert _centroid(gi[6:, :]) < 0.95 * _centroid(go[6:, :])
     assert _centroid(gi[10:50, :]) < 0.95 * _centroid(go[10:50, :])
+
+
+def test_hessian_v6_prefactor_constant_velocity(oracle_mod):
+    """In a constant velocity v0 the 4 / v^6 prefactor (Sec. 3, H_a) is one
+    number k = 4 / v0^6: the scaled illumination and offset Hessian are the
+    plain ones times k, and the preconditioned gradients the plain ones
+    divided by k (the water level scales with the maximum)."""
+    p = W.homogeneous(nz=20, nx=30, v=2500.0, nt=150, src=[[3, 0, 15]],
+                      rec=[[1, 0, j] for j in range(0, 30, 3)], sponge=6)
+    g = oracle_mod.Grid.of(p)
+    w = p.wavelet.astype(np.float64)
+    d = np.random.default_rng(0).standard_normal((1, p.nt, p.nrec)) * 1e-3
+    a = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w, d, hmax=2)
+    b = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w, d, hmax=2, hess_v6=True)
+    k = 4.0 / 2500.0 ** 6
+    assert np.allclose(b["illum"], k * a["illum"], rtol=1e-14, atol=0)
+    assert np.allclose(b["offh"], k * a["offh"], rtol=1e-14, atol=0)
+    assert np.allclose(b["grad_pre_illum"] * k, a["grad_pre_illum"], rtol=1e-12)
+    assert np.allclose(b["grad_pre_offset"] * k, a["grad_pre_offset"], rtol=1e-12)
+
