@@ -224,8 +224,10 @@ fwi_status make_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_option
     pl.born = born;
     pl.tf = make_tiling(L, pl.ns, pl.with_offh ? STEP_FWD_OFFH : STEP_FWD, -1, 0, pl.hmax);
     // the Born step runs on the backward step's default 64 x 16 tiles, the
-    // extended operators on its 64 x 8 tiles
-    pl.tb = pl.ext ? make_tiling(L, pl.ns, STEP_BWD, 1)
+    // extended operators on its 64 x 8 tiles, in chunks of 32 shots (each
+    // chunk loads the tile's 2 HE + 1 coefficient planes or flushes its
+    // 2 HE + 1 image planes once)
+    pl.tb = pl.ext ? make_tiling(L, pl.ns, STEP_BWD, 1, 32)
                    : (born ? make_tiling(L, pl.ns, STEP_BWD, 0) : make_tiling(L, pl.ns, STEP_BWD));
     const size_t fbytes = (size_t)L.fstride * sizeof(float);
     const size_t nphys = (size_t)L.nz * L.nx;
