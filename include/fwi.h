@@ -339,6 +339,15 @@ fwi_status fwi_exec_gradient_create(int nmodels, const fwi_grid *grids, const fw
                                     void *stream, fwi_exec **out);
 fwi_status fwi_exec_run(fwi_exec *ex, void *stream);
 fwi_status fwi_exec_destroy(fwi_exec *ex);
+/* Overlap the upload of the observed traces with the forward pass: the
+   recorded gradient reads d_obs only after its forward time loop, and waits
+   there for the exec's input event. fwi_exec_input_ready() records that
+   event on `stream` (typically the stream copying d_obs from the host),
+   after the work already queued on it. Call it before fwi_exec_run(); runs
+   without a new call proceed once the last recording has completed (at
+   once if it was never recorded). The caller orders the next write of
+   d_obs after the run (e.g. `stream` waits for the run's stream). */
+fwi_status fwi_exec_input_ready(fwi_exec *ex, void *stream);
 
 /* Shot illumination, the pseudo-diagonal Hessian of Eq. 1:
    illum DEVICE [nz][nx] = sum_s sum_n u_s^n(x)^2 dt (FWI_ILLUM_U2) or

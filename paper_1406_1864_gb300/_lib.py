@@ -95,6 +95,7 @@ _SIGS = {
                                  P(c_void_p), P(c_void_p), P(c_void_p), c_void_p, P(c_void_p),
                                  P(c_void_p), c_void_p, c_size_t, c_void_p, P(c_void_p)],
     "fwi_exec_run": [c_void_p, c_void_p],
+    "fwi_exec_input_ready": [c_void_p, c_void_p],
     "fwi_autotune": [P(FwiGrid), P(FwiGeometry), P(FwiOptions), c_void_p, c_void_p, c_size_t, c_void_p,
                      P(c_int)],
     "fwi_autotune_reset": [],

@@ -820,7 +820,8 @@ struct GradientIO {
 // backward time loop, fold, illumination / offset-Hessian outputs and
 // preconditioning. The time loops of all models run as one launch per level.
 fwi_status gradient_models(int nm, const Plan *pl, const fwi_geometry *const *ge, const fwi_options *opts,
-                           void *const *ws, const GradientIO *io, cudaStream_t st, bool tables = true)
+                           void *const *ws, const GradientIO *io, cudaStream_t st, bool tables = true,
+                           cudaEvent_t input_ev = nullptr)
 {
     fwi_status s;
     cudaError_t e;
@@ -836,6 +837,11 @@ fwi_status gradient_models(int nm, const Plan *pl, const fwi_geometry *const *ge
         FWI_OK)
         return s;
     prof_record(1, st);
+    // the observed traces may still be arriving (uploaded on another stream
+    // during the forward pass): wait for them here, before their first use
+    if (input_ev != nullptr &&
+        (e = cudaStreamWaitEvent(st, input_ev, t_capturing ? cudaEventWaitExternal : 0)) != cudaSuccess)
+        return cuda_fail(e, "wait for the observed traces");
     for (int k = 0; k < nm; ++k) {
         double *J = at<double>(ws[k], pl[k].scal, 0);
         const long long nsamp = (long long)pl[k].ns * pl[k].nt * pl[k].nrec;
@@ -2126,6 +2132,7 @@ fwi_status batch_prepare(int nmodels, const fwi_grid *grids, const fwi_geometry 
 struct fwi_exec_s {
     std::vector<Plan> pl;
     std::vector<void *> wk;
+    cudaEvent_t input_ev = nullptr; // the misfit waits on it (fwi_exec_input_ready)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool prof = false;
@@ -2172,12 +2179,18 @@ fwi_status fwi_exec_gradient_create(int nmodels, const fwi_grid *grids, const fw
     ex->pl = bc.pl;
     ex->wk = bc.wk;
     ex->prof = t_prof;
+    if ((e = cudaEventCreateWithFlags(&ex->input_ev, cudaEventDisableTiming)) != cudaSuccess) {
+        delete ex;
+        return cuda_fail(e, "cudaEventCreate");
+    }
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        cudaEventDestroy(ex->input_ev);
         delete ex;
         return cuda_fail(e, "cudaStreamBeginCapture");
     }
     t_capturing = true;
-    s = gradient_models(nmodels, bc.pl.data(), bc.gp.data(), opts, bc.wk.data(), bc.io.data(), st, false);
+    s = gradient_models(nmodels, bc.pl.data(), bc.gp.data(), opts, bc.wk.data(), bc.io.data(), st, false,
+                        ex->input_ev);
     t_capturing = false;
     e = cudaStreamEndCapture(st, &ex->graph);
     if (s == FWI_OK && e != cudaSuccess) s = cuda_fail(e, "cudaStreamEndCapture");
@@ -2185,11 +2198,21 @@ fwi_status fwi_exec_gradient_create(int nmodels, const fwi_grid *grids, const fw
         s = cuda_fail(e, "cudaGraphInstantiate");
     if (s != FWI_OK) {
         if (ex->graph) cudaGraphDestroy(ex->graph);
+        cudaEventDestroy(ex->input_ev);
         delete ex;
         return s;
     }
     for (int i = 0; i < 3; ++i) ex->launches[i] = t_launch[i];
     *out = ex;
+    t_err.clear();
+    return FWI_OK;
+}
+
+fwi_status fwi_exec_input_ready(fwi_exec *ex, void *stream)
+{
+    if (!ex || !ex->exec) return fail(FWI_ERR_INVALID_ARG, "exec is NULL");
+    cudaError_t e = cudaEventRecord(ex->input_ev, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     t_err.clear();
     return FWI_OK;
 }
@@ -2210,6 +2233,7 @@ fwi_status fwi_exec_destroy(fwi_exec *ex)
     if (!ex) return FWI_OK;
     if (ex->exec) cudaGraphExecDestroy(ex->exec);
     if (ex->graph) cudaGraphDestroy(ex->graph);
+    if (ex->input_ev) cudaEventDestroy(ex->input_ev);
     delete ex;
     return FWI_OK;
 }

@@ -296,13 +296,22 @@ class GradientGraph:
                                                   ctypes.byref(h)), "fwi_exec_gradient_create")
         self._h = h
 
-    def run(self) -> list:
+    def run(self, d_obs_ready=None) -> list:
+        """Replay the gradient. d_obs_ready: a stream on which the observed
+        traces are being written (e.g. copied from the host): the forward pass
+        starts at once and the misfit waits for that stream's work queued so
+        far (fwi_exec_input_ready), so the upload overlaps the forward pass;
+        later work on that stream is ordered after this run."""
         if not self._h:
             raise RuntimeError("the graph was closed")
         cur = torch.cuda.current_stream()
         self.stream.wait_stream(cur)
+        if d_obs_ready is not None:
+            L.check(L.load().fwi_exec_input_ready(self._h, _stream(d_obs_ready)), "fwi_exec_input_ready")
         L.check(L.load().fwi_exec_run(self._h, _stream(self.stream)), "fwi_exec_run")
         cur.wait_stream(self.stream)
+        if d_obs_ready is not None:
+            d_obs_ready.wait_stream(self.stream)
         return self.results
 
     def close(self):

@@ -35,7 +35,7 @@ def test_header_declares_the_boundary():
                  "fwi_batch_workspace_bytes", "fwi_exec_gradient_create", "fwi_exec_run", "fwi_exec_destroy",
                  "fwi_autotune", "fwi_autotune_reset", "fwi_autotune_set", "fwi_born",
                  "fwi_gauss_newton_hvp", "fwi_misfit", "fwi_receiver_factor", "fwi_precondition_receiver",
-                 "fwi_extended_born", "fwi_extended_migration"]:
+                 "fwi_extended_born", "fwi_extended_migration", "fwi_exec_input_ready"]:
         assert must in names
 
 

@@ -150,3 +150,35 @@ def test_recorded_gradient_graph(torch_cuda):
     finally:
         g1.close()
         gb.close()
+
+
+def test_recorded_graph_overlapped_upload(torch_cuda):
+    """fwi_exec_input_ready: the observed traces are written on another stream
+    while the recorded gradient's forward pass runs (delayed there by a timed
+    spin longer than the forward pass); the misfit waits for them, so the run
+    gives the direct call's outputs, not those of the stale buffer."""
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import fwi
+    probs = small_models(nt=200)
+    grids, geoms, vs, dobs = gpu_case(torch, probs)
+    real = dobs[1].clone()
+    opts = fwi.Options(misfit="ols", precond="illum")
+    direct = fwi.adjoint_gradient(grids[1], geoms[1], vs[1], real, opts)
+    g1 = fwi.GradientGraph(grids[1:2], geoms[1:2], [vs[1]], [dobs[1]], opts)
+    try:
+        for rep in range(2):
+            dobs[1].zero_()
+            up = torch.cuda.Stream()
+            up.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(up):
+                torch.cuda._sleep(50_000_000)  # ~25 ms of spinning, then the upload
+                dobs[1].copy_(real)
+            r = g1.run(d_obs_ready=up)[0]
+            torch.cuda.synchronize()
+            assert abs(float(r["misfit"]) - float(direct["misfit"])) <= 1e-12 * float(direct["misfit"]), rep
+            assert rel(r["grad"].cpu(), direct["grad"].cpu()) <= 1e-6, rep
+        # a run without a new recording proceeds (the last recording completed)
+        r = g1.run()[0]
+        assert abs(float(r["misfit"]) - float(direct["misfit"])) <= 1e-12 * float(direct["misfit"])
+    finally:
+        g1.close()
