@@ -1012,7 +1012,7 @@ using BornRing = Ring<8 * RZ, RADIUS, 2, 2, STAGES, 3 * 8 * RZ * TX * 4>; // + c
 // TX + 4 HE columns, plus the 2 HE + 1 planes of D~(y, h) and the q tile.
 template <int RZ, int STAGES, int HE>
 using BornRingE = Ring<8 * RZ, RADIUS + 2 * HE, 2, 2, STAGES,
-                       3 * 8 * RZ * TX * 4 + (HE > 0 ? (2 * HE + 1) * 8 * RZ * TX * 4 + 8 * RZ * (TX + 4 * HE) * 4 : 0)>;
+                       2 * 8 * RZ * TX * 4 + (HE > 0 ? (2 * HE + 1) * 8 * RZ * TX * 4 + 8 * RZ * (TX + 4 * HE) * 4 : 0)>;
 
 template <int RZ, int STAGES, int MINB, int HE = 0>
 __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__ Batch<BornArgs, 1> B)
@@ -1033,8 +1033,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
     unsigned char *smem = align_smem(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *c2s = reinterpret_cast<float *>(R::extra(smem));
-    float *dcs = c2s + TZ * TX;  // dc2 tile
-    float *dms = dcs + TZ * TX;  // damping tile (sponge tiles)
+    float *dms = c2s + TZ * TX;  // damping tile (sponge tiles); dc2 is read per point from L2
     float *des = dms + TZ * TX;  // HE > 0: planes D~(y, h), h = -HE..HE
     float *qs = des + NE * TZ * TX; // HE > 0: q^n on columns bj - 2 HE .. bj + TX + 2 HE - 1
     (void)qs;
@@ -1106,8 +1105,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
             load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
             if constexpr (HE > 0) {
                 for (int e = 0; e < NE; ++e) load_c2_tile<TZ>(des + e * TZ * TX, a.dext + e * L.fstride, L, bi, bj);
-            } else {
-                load_c2_tile<TZ>(dcs, a.dc2, L, bi, bj);
             }
             if (tile_sponge) load_c2_tile<TZ>(dms, c.damp, L, bi, bj);
             __syncthreads();
@@ -1144,6 +1141,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
                 const float *pd = R::point(smem, st, 1);
                 const long long so = (long long)s * L.fstride;
                 const int sslot = source_slot<RZ>(now, i0, j0);
+                // dc2 of the thread's points, one float4 per row from L2
+                // (the tile stays out of shared memory: four CTAs per SM)
+                float4 dcg[RZ];
+#pragma unroll
+                for (int r = 0; r < RZ; ++r)
+                    dcg[r] = (HE == 0 && i0 + r < L.nzp)
+                                 ? __ldg(reinterpret_cast<const float4 *>(a.dc2 + fidx(L, i0 + r, j0)))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
                 float2 qd[RZ][2];
 #pragma unroll
                 for (int fld = HE > 0 ? 1 : 0; fld < 2; ++fld) {
@@ -1178,7 +1183,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
                     const float4 up4 = lds4(&pu[(ty * RZ + r) * TX + 4 * tx]);
                     const float4 dp4 = lds4(&pd[(ty * RZ + r) * TX + 4 * tx]);
                     const float4 c24 = lds4(&c2s[(ty * RZ + r) * TX + 4 * tx]);
-                    const float4 dc24 = HE > 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : lds4(&dcs[(ty * RZ + r) * TX + 4 * tx]);
+                    const float4 dc24 = dcg[r];
                     // extended scattering source S(y) = sum_h D~(y, h) q(y + 2h)
                     float2 sx[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
                     if constexpr (HE > 0) {
@@ -1507,7 +1512,7 @@ cudaError_t launch_bwd_batch(const BwdArgs *a, const Tiling *t, int nm, cudaStre
 }
 
 namespace {
-constexpr int BORN_RZ = 2, BORN_ST = 2, BORN_MINB = 3;
+constexpr int BORN_RZ = 2, BORN_ST = 2, BORN_MINB = 4;
 #define K_BORN k_born_step<BORN_RZ, BORN_ST, BORN_MINB>
 constexpr int SMEM_BORN = BornRing<BORN_RZ, BORN_ST>::SMEM;
 std::once_flag g_born_once;
