@@ -48,8 +48,6 @@ FALLBACK_HBM_GBS = 6800.0
 # write psi^m) and c2 shared by both.
 ALG_BYTES = {"forward": 16, "adjoint": 28}
 
-
-
 # the metric of both arms (this implementation and the reference arm)
 METRIC = "FWI gradient Gpts/s (fwd+adj+imaging, preconditioned)"
 
