@@ -61,11 +61,19 @@ class Evaluation:
 
 @dataclass
 class History:
+    """Per iteration: misfit (before the first and after every step), step
+    length, misfit evaluations of the line search, model error (when the
+    true model is known); totals: restarts, Hessian-vector products (Gauss-
+    Newton), gradient and misfit calls of the objective."""
     misfit: list = field(default_factory=list)
     step: list = field(default_factory=list)
     evals: list = field(default_factory=list)
     model_error: list = field(default_factory=list)
     restarts: int = 0
+    hvps: int = 0
+    n_gradients: int = 0
+    n_misfits: int = 0
+    n_hvps: int = 0
 
 
 def _dot(a, b) -> float:
@@ -289,7 +297,6 @@ class GaussNewton(_Base):
         hist = hist or History()
         ev = self.value_grad(x)
         hist.misfit.append(ev.f)
-        hist.hvps = 0
         for k in range(iters):
             d, n = self.solve(x, ev.g, ev.minv)
             hist.hvps += n
