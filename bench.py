@@ -396,6 +396,11 @@ def run_ours(args):
                          "other": statistics.median(p["other_ms"] for p in phases)},
             "launches_per_step": {"forward": nf, "adjoint": na,
                                   "other": phases[0]["other_launches"]}}
+    # the whole step against the method's minimum traffic: 44 B per padded
+    # point-step per shot (forward 16 + backward 28), at the same peak
+    t_min_ms = 44.0 * npad * prob.nt * prob.nshots / (peak * 1e9) * 1e3
+    step_roof = {"bytes_per_padded_point_step": 44, "t_min_ms": t_min_ms, "ms_per_step": ms,
+                 "frac": t_min_ms / ms}
     launches = sum(p["forward_launches"] + p["adjoint_launches"] + p["other_launches"] for p in phases)
 
     cpu = None
@@ -421,7 +426,8 @@ def run_ours(args):
                        "parallelism": "1 GPU" if world == 1 else
                        f"shots x{world} (each GPU {prob.nshots} shots; NCCL all-reduce of the sums)",
                        "l2": "inputs larger than L2 (wavefields of all shots ~0.6 GB per step)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "step_roofline": step_roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
