@@ -86,13 +86,16 @@ __device__ __forceinline__ void lap3_4(float2 (&q)[2], const float *sh, const fl
     }
 }
 
-// next item of this CTA (thread 0): column-major within a shot, shot-major
+// next item of this CTA (thread 0): the shots of one column consecutively
+// (CTAs running at the same time add into the same column of the imaging and
+// illumination sums, which then stay in L2), columns in order
 __device__ __forceinline__ Item3 grab_item(int *counter, int ntiles, int nitems)
 {
     const int q = atomicAdd(counter, 1);
     if (q >= nitems) return Item3{-1, 0};
-    const int s = q / ntiles;
-    return Item3{q - s * ntiles, s};
+    const int ns = nitems / ntiles;
+    const int tile = q / ns;
+    return Item3{tile, q - tile * ns};
 }
 
 // ------------------------------------------------------------ forward step
