@@ -88,7 +88,8 @@ enum {
                                    is not used: see fwi_receiver_factor)     */
     FWI_OP_PRECONDITION_RECEIVER = 10, /* fwi_precondition_receiver        */
     FWI_OP_EXT_BORN = 11,      /* fwi_extended_born (any hext)              */
-    FWI_OP_EXT_MIGRATION = 12  /* fwi_extended_migration (any hext)         */
+    FWI_OP_EXT_MIGRATION = 12, /* fwi_extended_migration (any hext)         */
+    FWI_OP_PM_HESSIAN = 13     /* fwi_plessix_mulder_hessian                */
 };
 
 #define FWI_HMAX_LIMIT 12 /* largest offset (cells) of the offset Hessian */
@@ -248,6 +249,20 @@ fwi_status fwi_misfit(const fwi_grid *grid, const fwi_geometry *geom, const fwi_
 enum { FWI_RECV_PLESSIX_MULDER = 0, FWI_RECV_GREEN = 1 };
 fwi_status fwi_receiver_factor(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int kind,
                                const float *v, float *out, void *ws, size_t ws_bytes, void *stream);
+
+/* Plessix and Mulder's approximate diagonal Hessian [Sec. 1], for any
+   acquisition: out(x) = sum_s W_s(x) I_s(x), I_s the illumination of shot s
+   (sum_n u^2 dt, or u_tt^2 dt with opts->illum_mode = FWI_ILLUM_UTT2; opts may
+   be NULL) and W_s(x) = asinh((x_max(s) - x)/z_s) - asinh((x_min(s) - x)/z_s)
+   from shot s's receiver extent along x and depth below its receivers' mean
+   row (floored at dx / 2), as in fwi_receiver_factor. Consecutive shots with
+   the same receiver cells share one illumination pass, so a fixed spread
+   costs one pass of all shots and a spread that moves with every shot one
+   pass per shot. v DEVICE [nz][nx]; out DEVICE [nz][nx]. Workspace of
+   FWI_OP_PM_HESSIAN. 2-D; needs receivers. As a preconditioner:
+   fwi_precondition(kind = FWI_PRECOND_ILLUM, scale = out). */
+fwi_status fwi_plessix_mulder_hessian(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                                      const float *v, float *out, void *ws, size_t ws_bytes, void *stream);
 
 /* Preconditioning by a source-side scale times a receiver factor
    [Sec. 3.1 with the receiver term]: fwi_precondition with the scale

@@ -246,6 +246,23 @@ def plessix_mulder_factor(nz, nx, dx, rec):
     return np.arcsinh((x_max - x) / z) - np.arcsinh((x_min - x) / z)
 
 
+def plessix_mulder_hessian(grid: Grid, v, src, rec, wav, illum_utt=False, nthreads=0):
+    """Plessix and Mulder's approximate diagonal Hessian (Sec. 1) for any
+    acquisition: sum over shots of the shot's illumination (Eq. 1's form,
+    sum_n u^2 dt or u_tt^2 dt) times the asinh factor of the shot's own
+    receiver spread. Returns [nz, ny, nx]."""
+    src = np.asarray(src).reshape(-1, 3)
+    ns = src.shape[0]
+    rec = np.asarray(rec).reshape(ns, -1, 3)
+    wav = np.asarray(wav, np.float64).reshape(ns, -1)
+    out = np.zeros((grid.nz, grid.ny, grid.nx))
+    for s in range(ns):
+        il = forward(grid, v, src[s:s + 1], rec[s:s + 1], wav[s:s + 1], illum=True, illum_utt=illum_utt,
+                     nthreads=nthreads)["illum"]
+        out += plessix_mulder_factor(grid.nz, grid.nx, grid.dx, rec[s])[:, None, :] * il
+    return out
+
+
 def receiver_green_factor(grid: Grid, v, rec, wav0, hmax=0, nthreads=0):
     """Receiver Green's-function correlations of a fixed spread (the
     receiver sum of H_a, Sec. 1 / Sec. 3): sum_r sum_n G_r(x + h) G_r(x - h) dt,

@@ -25,7 +25,8 @@ FWI_CKPT_SPONGE, FWI_CKPT_SNAPSHOT = 0, 1
 FWI_SNAP_F32, FWI_SNAP_BF16, FWI_SNAP_F16S = 0, 1, 2
 (FWI_OP_FORWARD, FWI_OP_FORWARD_SAVE, FWI_OP_GRADIENT, FWI_OP_ILLUMINATION,
  FWI_OP_OFFSET_HESSIAN, FWI_OP_PRECONDITION, FWI_OP_BORN, FWI_OP_GN_HVP, FWI_OP_MISFIT,
- FWI_OP_RECEIVER_FACTOR, FWI_OP_PRECONDITION_RECEIVER, FWI_OP_EXT_BORN, FWI_OP_EXT_MIGRATION) = range(13)
+ FWI_OP_RECEIVER_FACTOR, FWI_OP_PRECONDITION_RECEIVER, FWI_OP_EXT_BORN, FWI_OP_EXT_MIGRATION,
+ FWI_OP_PM_HESSIAN) = range(14)
 FWI_HEXT_LIMIT = 6
 FWI_RECV_PLESSIX_MULDER, FWI_RECV_GREEN = 0, 1
 FWI_CFL_LIMIT_2D, FWI_CFL_LIMIT_3D = 0.5546, 0.4529  # v dt / dx limits (include/fwi.h)
@@ -74,6 +75,8 @@ _SIGS = {
                    c_size_t, c_void_p],
     "fwi_receiver_factor": [P(FwiGrid), P(FwiGeometry), P(FwiOptions), c_int, c_void_p, c_void_p, c_void_p,
                             c_size_t, c_void_p],
+    "fwi_plessix_mulder_hessian": [P(FwiGrid), P(FwiGeometry), P(FwiOptions), c_void_p, c_void_p, c_void_p,
+                                   c_size_t, c_void_p],
     "fwi_precondition_receiver": [P(FwiGrid), c_void_p, c_void_p, c_int, c_int, c_void_p, c_int, c_float,
                                   c_void_p, c_void_p, c_size_t, c_void_p],
     "fwi_extended_born": [P(FwiGrid), P(FwiGeometry), P(FwiOptions), c_int, c_void_p, c_void_p, c_void_p,

@@ -131,7 +131,8 @@ fwi_status check_opts(const fwi_options *o, int op)
     if (!o) {
         if (op == FWI_OP_FORWARD || op == FWI_OP_FORWARD_SAVE || op == FWI_OP_PRECONDITION || op == FWI_OP_BORN ||
             op == FWI_OP_GN_HVP || op == FWI_OP_MISFIT || op == FWI_OP_RECEIVER_FACTOR ||
-            op == FWI_OP_PRECONDITION_RECEIVER || op == FWI_OP_EXT_BORN || op == FWI_OP_EXT_MIGRATION)
+            op == FWI_OP_PRECONDITION_RECEIVER || op == FWI_OP_EXT_BORN || op == FWI_OP_EXT_MIGRATION ||
+            op == FWI_OP_PM_HESSIAN)
             return FWI_OK;
         return fail(FWI_ERR_INVALID_ARG, "options are NULL");
     }
@@ -1493,6 +1494,19 @@ fwi_status make_recv_plan(const fwi_grid *g, const fwi_geometry *ge, const fwi_o
     return FWI_OK;
 }
 
+// workspace of fwi_plessix_mulder_hessian: the illumination plan of all
+// shots, then one illumination buffer
+size_t pm_workspace(const Plan &all) { return align_up(all.total) + (size_t)all.L.nz * all.L.nx * sizeof(float); }
+
+// options of a call that allows NULL ones: the defaults (OLS, u^2
+// illumination, no offset Hessian, sponge checkpoints)
+const fwi_options *or_defaults(const fwi_options *o, fwi_options &store)
+{
+    if (o) return o;
+    store = fwi_options{FWI_MISFIT_OLS, FWI_ILLUM_U2, -1, FWI_PRECOND_NONE, 1e-3f, FWI_CKPT_SPONGE, FWI_SNAP_F32, 0, 0, 0};
+    return &store;
+}
+
 fwi_status make_batch(int nm, const fwi_grid *grids, const fwi_geometry *geoms, const fwi_options *opts,
                       bool coords, std::vector<Plan> &pl, std::vector<size_t> &base, size_t &total)
 {
@@ -1548,7 +1562,16 @@ fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, c
                                int op, size_t *bytes)
 {
     if (!bytes) return fail(FWI_ERR_INVALID_ARG, "bytes is NULL");
-    if (op < FWI_OP_FORWARD || op > FWI_OP_EXT_MIGRATION) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
+    if (op < FWI_OP_FORWARD || op > FWI_OP_PM_HESSIAN) return fail(FWI_ERR_INVALID_ARG, "op=%d unknown", op);
+    if (op == FWI_OP_PM_HESSIAN) {
+        Plan pl;
+        fwi_options dflt;
+        fwi_status s = make_plan(grid, geom, or_defaults(opts, dflt), FWI_OP_ILLUMINATION, false, pl);
+        if (s != FWI_OK) return s;
+        *bytes = pm_workspace(pl);
+        t_err.clear();
+        return FWI_OK;
+    }
     if (grid && grid->ndim == 3) {
         Plan3 p3;
         fwi_status s3 = make_plan3(grid, geom, opts, op, false, p3);
@@ -1806,6 +1829,82 @@ fwi_status fwi_receiver_factor(const fwi_grid *grid, const fwi_geometry *geom, c
     t_launch[2]++;
     prof_record(3, st);
     return finish(pl, ws, st);
+}
+
+fwi_status fwi_plessix_mulder_hessian(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
+                                      const float *v, float *out, void *ws, size_t ws_bytes, void *stream)
+{
+    // the plan of all shots bounds every run's plan; the run's illumination
+    // goes to a buffer after it
+    fwi_options dflt;
+    opts = or_defaults(opts, dflt);
+    Plan all;
+    fwi_status s = make_plan(grid, geom, opts, FWI_OP_ILLUMINATION, true, all);
+    if (s != FWI_OK) return s;
+    if (geom->nrec < 1) return fail(FWI_ERR_INVALID_ARG, "the Plessix-Mulder Hessian needs receivers");
+    if (!v || !out) return fail(FWI_ERR_INVALID_ARG, "v or out is NULL");
+    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
+        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
+    const size_t need = pm_workspace(all);
+    if (ws_bytes < need) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, need);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int mode = opts->illum_mode;
+    const float iscale = mode == FWI_ILLUM_U2 ? all.L.dt : 1.0f / (all.L.dt * all.L.dt * all.L.dt);
+    float *tmp = reinterpret_cast<float *>(static_cast<char *>(ws) + align_up(all.total));
+    const size_t nrec3 = 3 * (size_t)geom->nrec;
+    begin_call(st);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(out, 0, (size_t)grid->nz * grid->nx * sizeof(float), st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    Plan pr;
+    for (int s0 = 0, run = 0; s0 < geom->nshots; ++run) {
+        int s1 = s0 + 1;
+        while (s1 < geom->nshots && std::memcmp(geom->rec + s1 * nrec3, geom->rec + s0 * nrec3, nrec3 * sizeof(int)) == 0)
+            ++s1;
+        fwi_geometry g{};
+        g.nshots = s1 - s0;
+        g.nrec = geom->nrec;
+        g.src = geom->src + 3 * (size_t)s0;
+        g.rec = geom->rec + s0 * nrec3;
+        g.wavelet = geom->wavelet + (size_t)s0 * grid->nt;
+        if ((s = make_plan(grid, &g, opts, FWI_OP_ILLUMINATION, true, pr)) != FWI_OK) return s;
+        if (run == 0) {
+            if ((s = setup(pr, &g, v, ws, st)) != FWI_OK) return s;
+        } else {
+            // c2 and the sponge factor stay (same v, same parts); the status
+            // word keeps the earlier runs' bits
+            if ((e = cudaMemsetAsync(at<char>(ws, pr.sched), 0, pr.sched.bytes, st)) != cudaSuccess)
+                return cuda_fail(e, "memset");
+            if ((s = upload_tables(pr, &g, ws, st)) != FWI_OK) return s;
+            for (int b = 0; b < 2; ++b)
+                if ((e = cudaMemsetAsync(at<char>(ws, pr.u[b]), 0, pr.u[b].bytes, st)) != cudaSuccess)
+                    return cuda_fail(e, "memset");
+        }
+        float *acc_i = at<float>(ws, pr.acc_i);
+        if ((e = cudaMemsetAsync(acc_i, 0, pr.acc_i.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+        if ((s = run_forward(pr, &g, ws, nullptr, false, acc_i, nullptr, mode, st)) != FWI_OK) return s;
+        if ((e = launch_finish_accum(pr.L, acc_i, 1, 1, iscale, tmp, st, opts->hess_v6 ? v : nullptr)) !=
+            cudaSuccess)
+            return cuda_fail(e, "illumination output");
+        int xmin = grid->nx, xmax = -1;
+        double zsum = 0;
+        for (int r = 0; r < geom->nrec; ++r) {
+            const int *q = g.rec + 3 * r;
+            xmin = std::min(xmin, q[2]);
+            xmax = std::max(xmax, q[2]);
+            zsum += q[0];
+        }
+        if ((e = launch_pm_accumulate(grid->nz, grid->nx, grid->dx, (float)xmin * grid->dx, (float)xmax * grid->dx,
+                                      (float)(zsum / geom->nrec), tmp, out, st)) != cudaSuccess)
+            return cuda_fail(e, "Plessix-Mulder accumulation");
+        t_launch[2] += 2;
+        s0 = s1;
+    }
+    prof_record(1, st);
+    prof_record(2, st);
+    prof_record(3, st);
+    return finish(pr, ws, st);
 }
 
 fwi_status fwi_precondition_receiver(const fwi_grid *grid, const float *grad, const float *scale, int kind,

@@ -150,6 +150,21 @@ __global__ void k_pm_factor(int nz, int nx, float dx, float xmin, float xmax, fl
     }
 }
 
+// out += W illum with W the Plessix-Mulder factor of one receiver spread
+// (as k_pm_factor)
+__global__ void k_pm_accumulate(int nz, int nx, float dx, float xmin, float xmax, float zr,
+                                const float *__restrict__ illum, float *__restrict__ out)
+{
+    const long long n = (long long)nz * nx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+        const float z = fmaxf(fabsf((float)i - zr) * dx, 0.5f * dx);
+        const float x = (float)j * dx;
+        out[e] = fmaf(asinhf((xmax - x) / z) - asinhf((xmin - x) / z), illum[e], out[e]);
+    }
+}
+
 // rows of a [rows][n] array all equal to src[0 .. n-1]
 __global__ void k_replicate_row(const float *__restrict__ src, int n, int rows, float *__restrict__ dst)
 {
@@ -486,6 +501,13 @@ cudaError_t launch_pm_factor(int nz, int nx, float dx, float xmin, float xmax, f
                              cudaStream_t st)
 {
     k_pm_factor<<<grid_for((long long)nz * nx), NT1, 0, st>>>(nz, nx, dx, xmin, xmax, zr, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pm_accumulate(int nz, int nx, float dx, float xmin, float xmax, float zr, const float *illum,
+                                 float *out, cudaStream_t st)
+{
+    k_pm_accumulate<<<grid_for((long long)nz * nx), NT1, 0, st>>>(nz, nx, dx, xmin, xmax, zr, illum, out);
     return cudaGetLastError();
 }
 

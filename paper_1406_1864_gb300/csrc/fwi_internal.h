@@ -326,6 +326,8 @@ cudaError_t launch_prep_dc2(const Lay2D &L, const float *v, const float *dv, con
 cudaError_t launch_pm_factor(int nz, int nx, float dx, float xmin, float xmax, float zr, float *out,
                              cudaStream_t st);
 cudaError_t launch_replicate_row(const float *src, int n, int rows, float *dst, cudaStream_t st);
+cudaError_t launch_pm_accumulate(int nz, int nx, float dx, float xmin, float xmax, float zr, const float *illum,
+                                 float *out, cudaStream_t st);
 cudaError_t launch_scale_product(long long nphys, int planes, const float *scale, const float *recv, int rn,
                                  float *out, cudaStream_t st);
 cudaError_t launch_prep_c2(const Lay2D &L, const float *v, float *c2, float *damp, float cfl_limit,

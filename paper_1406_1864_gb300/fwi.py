@@ -21,7 +21,8 @@ OPS = {"forward": L.FWI_OP_FORWARD, "forward_save": L.FWI_OP_FORWARD_SAVE,
        "offset_hessian": L.FWI_OP_OFFSET_HESSIAN, "precondition": L.FWI_OP_PRECONDITION,
        "born": L.FWI_OP_BORN, "gn_hvp": L.FWI_OP_GN_HVP, "misfit": L.FWI_OP_MISFIT,
        "receiver_factor": L.FWI_OP_RECEIVER_FACTOR, "precondition_receiver": L.FWI_OP_PRECONDITION_RECEIVER,
-       "extended_born": L.FWI_OP_EXT_BORN, "extended_migration": L.FWI_OP_EXT_MIGRATION}
+       "extended_born": L.FWI_OP_EXT_BORN, "extended_migration": L.FWI_OP_EXT_MIGRATION,
+       "pm_hessian": L.FWI_OP_PM_HESSIAN}
 
 
 @dataclass
@@ -473,6 +474,22 @@ def receiver_factor(grid: Grid, geom: Geometry, kind: str = "pm", v: torch.Tenso
     L.check(lib.fwi_receiver_factor(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o) if o is not None else None,
                                     L.FWI_RECV_GREEN, _ptr(v), _ptr(out), _ptr(buf), nb, _stream(stream)),
             "fwi_receiver_factor")
+    return out
+
+
+def plessix_mulder_hessian(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options | None = None, *,
+                           ws=None, stream=None) -> torch.Tensor:
+    """fwi_plessix_mulder_hessian: sum_s W_s(x) I_s(x) [nz, nx], each shot's
+    illumination weighted by the asinh factor of its own receiver spread
+    (any acquisition; runs of shots with one spread share a pass)."""
+    _dev(v, "v", grid.shape)
+    out = torch.empty(grid.shape, dtype=torch.float32, device=v.device)
+    buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "pm_hessian"))
+    g, ge = grid.c(), geom.c()
+    o = opts.c() if opts is not None else None
+    L.check(L.load().fwi_plessix_mulder_hessian(ctypes.byref(g), ctypes.byref(ge),
+                                                ctypes.byref(o) if o is not None else None, _ptr(v), _ptr(out),
+                                                _ptr(buf), nb, _stream(stream)), "fwi_plessix_mulder_hessian")
     return out
 
 

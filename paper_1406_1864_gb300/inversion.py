@@ -328,10 +328,12 @@ class FwiObjective:
     call's scale as fwi_precondition does (precond "illum": the illumination
     of Eq. 1; "offset": the offset-Hessian diagonal of Sec. 3; "none").
     receiver = "pm" or "green" multiplies the scale by the receiver side of
-    the diagonal Hessian of a fixed spread (fwi_receiver_factor: Plessix and
-    Mulder's factor, computed once; or the receiver Green's-function
-    correlations in the current model, recomputed every receiver_every
-    gradients)."""
+    the diagonal Hessian (fwi_receiver_factor): Plessix and Mulder's factor
+    (computed once for a fixed spread; for a spread that moves with the shots
+    the scale is fwi_plessix_mulder_hessian's per-shot sum instead, with
+    precond "illum"), or the receiver Green's-function correlations of a
+    fixed spread in the current model. Model-dependent receiver terms are
+    recomputed every receiver_every gradients."""
 
     def __init__(self, grid, geom, d_obs, opts, ws=None, mute_top=0, receiver=None, receiver_every=1):
         from . import fwi
@@ -344,7 +346,11 @@ class FwiObjective:
             raise ValueError("a receiver factor needs precond 'illum' or 'offset'")
         self.receiver, self.receiver_every = receiver, max(1, int(receiver_every))
         self.n_hvps = 0
-        self.recv = fwi.receiver_factor(grid, geom, "pm") if receiver == "pm" else None
+        self.fixed_spread = bool((geom.rec == geom.rec[:1]).all())
+        if receiver == "pm" and not self.fixed_spread and opts.precond != "illum":
+            raise ValueError("Plessix-Mulder with a moving spread needs precond 'illum'")
+        self.recv = fwi.receiver_factor(grid, geom, "pm") if receiver == "pm" and self.fixed_spread else None
+        self.pm_scale = None
         self.mask = None
         if mute_top > 0:
             self.mask = torch.ones(grid.shape, dtype=torch.float32, device=d_obs.device)
@@ -380,8 +386,13 @@ class FwiObjective:
         else:
             scale, kind = None, None
 
-        if self.receiver == "green" and (self.recv is None or (self.n_gradients - 1) % self.receiver_every == 0):
+        refresh = (self.n_gradients - 1) % self.receiver_every == 0
+        if self.receiver == "green" and (self.recv is None or refresh):
             self.recv = fwi.receiver_factor(grid, self.geom, "green", v.contiguous(), o, ws=self.ws)
+        if self.receiver == "pm" and not self.fixed_spread:
+            if self.pm_scale is None or refresh:
+                self.pm_scale = fwi.plessix_mulder_hessian(grid, self.geom, v.contiguous(), o, ws=self.ws)
+            scale = self.pm_scale
         recv = self.recv
 
         def minv(q):

@@ -35,7 +35,8 @@ def test_header_declares_the_boundary():
                  "fwi_batch_workspace_bytes", "fwi_exec_gradient_create", "fwi_exec_run", "fwi_exec_destroy",
                  "fwi_autotune", "fwi_autotune_reset", "fwi_autotune_set", "fwi_born",
                  "fwi_gauss_newton_hvp", "fwi_misfit", "fwi_receiver_factor", "fwi_precondition_receiver",
-                 "fwi_extended_born", "fwi_extended_migration", "fwi_exec_input_ready"]:
+                 "fwi_extended_born", "fwi_extended_migration", "fwi_exec_input_ready",
+                 "fwi_plessix_mulder_hessian"]:
         assert must in names
 
 
@@ -191,7 +192,7 @@ def test_born_workspace_and_errors(lib):
     assert born < hvp and hvp >= grad - 30 * 40 * 4 * 2
     o.ckpt = L.FWI_CKPT_SNAPSHOT
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GN_HVP)[0] == L.FWI_ERR_INVALID_ARG
-    assert ws_bytes(lib, g, ge, None, L.FWI_OP_EXT_MIGRATION + 1)[0] == L.FWI_ERR_INVALID_ARG
+    assert ws_bytes(lib, g, ge, None, L.FWI_OP_PM_HESSIAN + 1)[0] == L.FWI_ERR_INVALID_ARG
     st = lib.fwi_born(ctypes.byref(g), ctypes.byref(ge), None, ctypes.c_void_p(1), None, ctypes.c_void_p(1),
                       ctypes.c_void_p(256), 1 << 40, None)
     assert st == L.FWI_ERR_INVALID_ARG

@@ -128,3 +128,42 @@ def test_moving_spread_refused(torch_cuda, case):
     for kind in ("pm", "green"):
         with pytest.raises(_lib.FwiError):
             fwi.receiver_factor(grid2, geom2, kind, v)
+
+
+def moving_spread(nt=300, ns=4):
+    """An end-on spread that moves with the shot: receivers on the 12 cells
+    behind each source, two shots per spread position (runs of two)."""
+    p = W.dipping(nz=37, nx=83, dx=10.0, dt=1e-3, nt=nt, ns=ns, nrec=12, rec_step=1, f0=15.0, seed=2, sponge=7)
+    src = p.src.copy()
+    rec = np.zeros((ns, 12, 3), np.int32)
+    for s in range(ns):
+        x0 = 14 + 20 * (s // 2)
+        src[s] = [2, 0, x0 + 1 + (s % 2)]
+        rec[s, :, 0] = 1
+        rec[s, :, 2] = np.arange(x0 - 12, x0)
+    p.src, p.rec = src, rec
+    return p
+
+
+@pytest.mark.parametrize("utt", [False, True])
+def test_plessix_mulder_hessian_moving_spread(torch_cuda, oracle_mod, utt):
+    from paper_1406_1864_gb300 import fwi
+    p = moving_spread()
+    g = oracle_mod.Grid.of(p)
+    grid, geom = fwi.from_problem(p)
+    v = torch_cuda.as_tensor(np.ascontiguousarray(p.v_init), device="cuda")
+    got = fwi.plessix_mulder_hessian(grid, geom, v, fwi.Options(illum="utt2" if utt else "u2")).cpu().numpy()
+    ref = oracle_mod.plessix_mulder_hessian(g, p.v_init, p.src, p.rec, p.wavelet.astype(np.float64),
+                                            illum_utt=utt)[:, 0, :]
+    assert rel(got, ref) <= 1e-4, rel(got, ref)
+
+
+def test_plessix_mulder_hessian_fixed_spread(torch_cuda, case):
+    """One spread: the factor of fwi_receiver_factor times the illumination."""
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import fwi
+    p, g, grid, geom, v = case
+    H = fwi.plessix_mulder_hessian(grid, geom, v)
+    ref = fwi.receiver_factor(grid, geom, "pm") * fwi.illumination(grid, geom, v, fwi.Options())
+    assert rel(H.cpu(), ref.cpu()) <= 1e-5
+

@@ -10,6 +10,8 @@
   shifted products of the dumped wavefield of a source at the receiver, add
   up over receivers, and at h = 0 equal the illumination of sources at the
   receivers (Eq. 1's form on the receiver side).
+* Plessix and Mulder's per-shot Hessian reduces, for one spread shared by
+  all shots, to the factor times the illumination of all shots.
 A planted mistake (z not floored at the receiver row) must fail a pin.
 """
 import numpy as np
@@ -100,3 +102,16 @@ def test_receiver_green_factor_is_symmetric_positive_at_zero_offset(oracle_mod, 
         lhs = np.abs(R[h, :, 0, h:-h])
         rhs = np.sqrt(I[:, 2 * h:] * I[:, :-2 * h])
         assert (lhs <= rhs * (1 + 1e-12) + 1e-300).all()
+
+
+def test_plessix_mulder_hessian_fixed_spread_is_factor_times_illumination(oracle_mod):
+    """With one spread for all shots the per-shot sum factors: the asinh
+    factor times the illumination of all shots."""
+    p = W.dipping(nz=20, nx=30, dx=10.0, dt=1e-3, nt=120, ns=3, nrec=10, rec_step=3, f0=15.0, sponge=5, seed=2)
+    g = oracle_mod.Grid.of(p)
+    w = p.wavelet.astype(np.float64)
+    H = oracle_mod.plessix_mulder_hessian(g, p.v_init, p.src, p.rec, w)
+    il = oracle_mod.forward(g, p.v_init, p.src, p.rec, w, illum=True)["illum"]
+    F = oracle_mod.plessix_mulder_factor(p.nz, p.nx, p.dx, p.rec[0])
+    assert np.allclose(H[:, 0, :], F * il[:, 0, :], rtol=1e-12, atol=0)
+
