@@ -217,8 +217,10 @@ def read_peak():
 
 
 def kernel_source_hash():
+    """Hash of the sources the 2-D step kernels are compiled from (their file,
+    the device helpers and the argument blocks)."""
     h = hashlib.sha256()
-    for f in ("fwi_step2d.cu", "fwi_internal.h"):
+    for f in ("fwi_step2d.cu", "fwi_device.cuh", "fwi_args.h"):
         with open(os.path.join(ROOT, "paper_1406_1864_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
