@@ -300,6 +300,15 @@ fwi_status fwi_extended_migration(const fwi_grid *grid, const fwi_geometry *geom
                                   const float *v, const float *adj_src, float *image, void *ws, size_t ws_bytes,
                                   void *stream);
 
+/* Self-test of failure detection on the GPU: one warp waits on an mbarrier
+   that no thread arrives at, with the bounded wait every step kernel uses
+   (%globaltimer limit of limit_us microseconds, 1 .. 10,000,000). The wait
+   gives up, the kernel raises the timeout status and returns, and the call
+   returns FWI_ERR_TIMEOUT, as a step kernel's wait that ran out would; the
+   context stays usable. ws: DEVICE, >= 256 bytes, 256-byte aligned (the
+   status word). Any other return value is a failure of the mechanism. */
+fwi_status fwi_selftest_wait(unsigned limit_us, void *ws, size_t ws_bytes, void *stream);
+
 /* Born modelling [Eq. 4, as the exact derivative of fwi_forward's discrete
    traces]: dseis = J dv, the change of the traces along the velocity change
    dv, by the tangent-linear scheme (u and du = J dv advanced together).

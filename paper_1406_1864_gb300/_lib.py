@@ -83,6 +83,7 @@ _SIGS = {
                           c_void_p, c_size_t, c_void_p],
     "fwi_extended_migration": [P(FwiGrid), P(FwiGeometry), P(FwiOptions), c_int, c_void_p, c_void_p, c_void_p,
                                c_void_p, c_size_t, c_void_p],
+    "fwi_selftest_wait": [ctypes.c_uint, c_void_p, c_size_t, c_void_p],
     "fwi_born": [P(FwiGrid), P(FwiGeometry), P(FwiOptions), c_void_p, c_void_p, c_void_p, c_void_p,
                  c_size_t, c_void_p],
     "fwi_gauss_newton_hvp": [P(FwiGrid), P(FwiGeometry), P(FwiOptions), c_void_p, c_void_p, c_void_p,

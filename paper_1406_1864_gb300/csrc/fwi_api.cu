@@ -1996,6 +1996,27 @@ fwi_status fwi_extended_migration(const fwi_grid *grid, const fwi_geometry *geom
     return finish(pl, ws, st);
 }
 
+fwi_status fwi_selftest_wait(unsigned limit_us, void *ws, size_t ws_bytes, void *stream)
+{
+    if (limit_us < 1 || limit_us > 10000000u) return fail(FWI_ERR_INVALID_ARG, "limit_us=%u outside 1..10000000", limit_us);
+    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
+        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
+    if (ws_bytes < 256) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need 256", ws_bytes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *status = static_cast<int *>(ws);
+    int h = 0;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_wait_selftest((uint64_t)limit_us * 1000ull, status, st)) != cudaSuccess)
+        return cuda_fail(e, "self-test kernel");
+    if ((e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "status read-back");
+    if (h & ST_TIMEOUT) return fail(FWI_ERR_TIMEOUT, "the self-test wait gave up after %u us, as designed", limit_us);
+    return fail(FWI_ERR_CUDA, "the self-test wait did not report its timeout (status %d)", h);
+}
+
 fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                     const float *dv, float *dseis, void *ws, size_t ws_bytes, void *stream)
 {

@@ -3,6 +3,7 @@
 // time-integral misfit of Eq. 2), folding of the padded-grid gradient,
 // illumination / offset-Hessian outputs (Eq. 1, Sec. 3) and the diagonal
 // preconditioning g / (P + eps max P) of Sec. 3.1.
+#include "fwi_device.cuh"
 #include "fwi_internal.h"
 
 #include <cfloat>
@@ -163,6 +164,21 @@ __global__ void k_pm_accumulate(int nz, int nx, float dx, float xmin, float xmax
         const float x = (float)j * dx;
         out[e] = fmaf(asinhf((xmax - x) / z) - asinhf((xmin - x) / z), illum[e], out[e]);
     }
+}
+
+// The bounded wait of the step kernels on an mbarrier that no thread arrives
+// at: every lane gives up after limit_ns, and the block raises ST_TIMEOUT as
+// a step kernel does (then returns, leaving the context usable)
+__global__ void k_wait_selftest(uint64_t limit_ns, int *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool done = mbar_wait(smem_u32(&bar), 0, limit_ns);
+    if (!done && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
 }
 
 // rows of a [rows][n] array all equal to src[0 .. n-1]
@@ -508,6 +524,12 @@ cudaError_t launch_pm_accumulate(int nz, int nx, float dx, float xmin, float xma
                                  float *out, cudaStream_t st)
 {
     k_pm_accumulate<<<grid_for((long long)nz * nx), NT1, 0, st>>>(nz, nx, dx, xmin, xmax, zr, illum, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int *status, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, status);
     return cudaGetLastError();
 }
 

@@ -72,6 +72,8 @@ cudaError_t launch_prep_dc2(const Lay2D &L, const float *v, const float *dv, con
 cudaError_t launch_pm_factor(int nz, int nx, float dx, float xmin, float xmax, float zr, float *out,
                              cudaStream_t st);
 cudaError_t launch_replicate_row(const float *src, int n, int rows, float *dst, cudaStream_t st);
+// one warp waiting (bounded by limit_ns) on an mbarrier no thread arrives at
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int *status, cudaStream_t st);
 cudaError_t launch_pm_accumulate(int nz, int nx, float dx, float xmin, float xmax, float zr, const float *illum,
                                  float *out, cudaStream_t st);
 cudaError_t launch_scale_product(long long nphys, int planes, const float *scale, const float *recv, int rn,

@@ -387,6 +387,14 @@ def extended_migration(grid: Grid, geom: Geometry, v: torch.Tensor, adj_src: tor
     return img
 
 
+def selftest_wait(limit_us: int = 1000, stream=None) -> int:
+    """fwi_selftest_wait: one warp's bounded wait on an mbarrier nothing
+    arrives at. Returns the status code, FWI_ERR_TIMEOUT when the mechanism
+    works (the wait gave up, the kernel reported it, the context is usable)."""
+    buf = torch.empty(256, dtype=torch.uint8, device="cuda")
+    return int(L.load().fwi_selftest_wait(int(limit_us), _ptr(buf), 256, _stream(stream)))
+
+
 def born(grid: Grid, geom: Geometry, v: torch.Tensor, dv: torch.Tensor, *, ws=None, out=None,
          stream=None) -> torch.Tensor:
     """fwi_born: Born traces J dv [ns, nt, nrec], the derivative of the

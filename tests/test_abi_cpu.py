@@ -36,7 +36,7 @@ def test_header_declares_the_boundary():
                  "fwi_autotune", "fwi_autotune_reset", "fwi_autotune_set", "fwi_born",
                  "fwi_gauss_newton_hvp", "fwi_misfit", "fwi_receiver_factor", "fwi_precondition_receiver",
                  "fwi_extended_born", "fwi_extended_migration", "fwi_exec_input_ready",
-                 "fwi_plessix_mulder_hessian"]:
+                 "fwi_plessix_mulder_hessian", "fwi_selftest_wait"]:
         assert must in names
 
 
@@ -282,6 +282,16 @@ def test_extended_operator_workspace_and_errors(lib):
     st = lib.fwi_extended_migration(ctypes.byref(g), ctypes.byref(ge), None, 2, p1, p1, None, ctypes.c_void_p(256),
                                     1 << 40, None)
     assert st == L.FWI_ERR_INVALID_ARG
+
+
+def test_selftest_wait_argument_errors(lib):
+    """The bounded-wait self-test checks its arguments before any device work."""
+    from paper_1406_1864_gb300 import _lib as L
+    assert lib.fwi_selftest_wait(0, ctypes.c_void_p(256), 256, None) == L.FWI_ERR_INVALID_ARG
+    assert lib.fwi_selftest_wait(20000000, ctypes.c_void_p(256), 256, None) == L.FWI_ERR_INVALID_ARG
+    assert lib.fwi_selftest_wait(1000, None, 256, None) == L.FWI_ERR_INVALID_ARG
+    assert lib.fwi_selftest_wait(1000, ctypes.c_void_p(8), 256, None) == L.FWI_ERR_INVALID_ARG
+    assert lib.fwi_selftest_wait(1000, ctypes.c_void_p(256), 16, None) == L.FWI_ERR_NOMEM
 
 
 def test_product_path_does_not_import_the_oracle():
