@@ -355,14 +355,34 @@ fwi_status upload_tables(const Plan &pl, const fwi_geometry *ge, void *ws, cudaS
     return FWI_OK;
 }
 
-fwi_status check_ws(const Plan &pl, void *ws, size_t ws_bytes)
+// a caller's workspace: present, ALIGN-aligned, at least `need` bytes
+fwi_status check_ws_bytes(void *ws, size_t ws_bytes, size_t need)
 {
     if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
         return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
-    if (ws_bytes < pl.total)
-        return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, pl.total);
+    if (ws_bytes < need) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, need);
     return FWI_OK;
+}
+
+// the receivers' extent along x and mean row of one spread (nrec >= 1)
+void spread_extent(const int *rec, int nrec, int &xmin, int &xmax, float &zmean)
+{
+    xmin = rec[2];
+    xmax = rec[2];
+    double zsum = 0;
+    for (int r = 0; r < nrec; ++r) {
+        const int *q = rec + 3 * r;
+        xmin = std::min(xmin, q[2]);
+        xmax = std::max(xmax, q[2]);
+        zsum += q[0];
+    }
+    zmean = (float)(zsum / nrec);
+}
+
+fwi_status check_ws(const Plan &pl, void *ws, size_t ws_bytes)
+{
+    return check_ws_bytes(ws, ws_bytes, pl.total);
 }
 
 void prof_record(int k, cudaStream_t st)
@@ -1339,14 +1359,7 @@ fwi_status finish3(const Plan3 &pl, void *ws, cudaStream_t st)
     return FWI_OK;
 }
 
-fwi_status check_ws3(const Plan3 &pl, void *ws, size_t ws_bytes)
-{
-    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
-    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
-        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
-    if (ws_bytes < pl.total) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, pl.total);
-    return FWI_OK;
-}
+fwi_status check_ws3(const Plan3 &pl, void *ws, size_t ws_bytes) { return check_ws_bytes(ws, ws_bytes, pl.total); }
 
 // forward modelling (seis) and / or illumination (illum) of all shots
 fwi_status forward3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int op,
@@ -1789,16 +1802,11 @@ fwi_status fwi_receiver_factor(const fwi_grid *grid, const fwi_geometry *geom, c
         if ((s = check_geom(grid, geom, true)) != FWI_OK) return s;
         if ((s = check_fixed_spread(geom)) != FWI_OK) return s;
         if (!out) return fail(FWI_ERR_INVALID_ARG, "out is NULL");
-        int xmin = grid->nx, xmax = -1;
-        double zsum = 0;
-        for (int r = 0; r < geom->nrec; ++r) {
-            const int *q = geom->rec + 3 * r;
-            xmin = std::min(xmin, q[2]);
-            xmax = std::max(xmax, q[2]);
-            zsum += q[0];
-        }
+        int xmin, xmax;
+        float zr;
+        spread_extent(geom->rec, geom->nrec, xmin, xmax, zr);
         cudaError_t e = launch_pm_factor(grid->nz, grid->nx, grid->dx, (float)xmin * grid->dx,
-                                         (float)xmax * grid->dx, (float)(zsum / geom->nrec), out, st);
+                                         (float)xmax * grid->dx, zr, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "receiver-factor kernel");
         t_err.clear();
         return FWI_OK;
@@ -1807,10 +1815,7 @@ fwi_status fwi_receiver_factor(const fwi_grid *grid, const fwi_geometry *geom, c
     RecvPlan rp;
     if ((s = make_recv_plan(grid, geom, opts, true, rp)) != FWI_OK) return s;
     if (!v || !out) return fail(FWI_ERR_INVALID_ARG, "v or out is NULL");
-    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
-    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
-        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
-    if (ws_bytes < rp.total) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, rp.total);
+    if ((s = check_ws_bytes(ws, ws_bytes, rp.total)) != FWI_OK) return s;
     const Plan &pl = rp.pl;
     begin_call(st);
     cudaError_t e;
@@ -1843,11 +1848,7 @@ fwi_status fwi_plessix_mulder_hessian(const fwi_grid *grid, const fwi_geometry *
     if (s != FWI_OK) return s;
     if (geom->nrec < 1) return fail(FWI_ERR_INVALID_ARG, "the Plessix-Mulder Hessian needs receivers");
     if (!v || !out) return fail(FWI_ERR_INVALID_ARG, "v or out is NULL");
-    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
-    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
-        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
-    const size_t need = pm_workspace(all);
-    if (ws_bytes < need) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, need);
+    if ((s = check_ws_bytes(ws, ws_bytes, pm_workspace(all))) != FWI_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int mode = opts->illum_mode;
     const float iscale = mode == FWI_ILLUM_U2 ? all.L.dt : 1.0f / (all.L.dt * all.L.dt * all.L.dt);
@@ -1887,16 +1888,11 @@ fwi_status fwi_plessix_mulder_hessian(const fwi_grid *grid, const fwi_geometry *
         if ((e = launch_finish_accum(pr.L, acc_i, 1, 1, iscale, tmp, st, opts->hess_v6 ? v : nullptr)) !=
             cudaSuccess)
             return cuda_fail(e, "illumination output");
-        int xmin = grid->nx, xmax = -1;
-        double zsum = 0;
-        for (int r = 0; r < geom->nrec; ++r) {
-            const int *q = g.rec + 3 * r;
-            xmin = std::min(xmin, q[2]);
-            xmax = std::max(xmax, q[2]);
-            zsum += q[0];
-        }
+        int xmin, xmax;
+        float zr;
+        spread_extent(g.rec, g.nrec, xmin, xmax, zr);
         if ((e = launch_pm_accumulate(grid->nz, grid->nx, grid->dx, (float)xmin * grid->dx, (float)xmax * grid->dx,
-                                      (float)(zsum / geom->nrec), tmp, out, st)) != cudaSuccess)
+                                      zr, tmp, out, st)) != cudaSuccess)
             return cuda_fail(e, "Plessix-Mulder accumulation");
         t_launch[2] += 2;
         s0 = s1;
@@ -1999,10 +1995,8 @@ fwi_status fwi_extended_migration(const fwi_grid *grid, const fwi_geometry *geom
 fwi_status fwi_selftest_wait(unsigned limit_us, void *ws, size_t ws_bytes, void *stream)
 {
     if (limit_us < 1 || limit_us > 10000000u) return fail(FWI_ERR_INVALID_ARG, "limit_us=%u outside 1..10000000", limit_us);
-    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
-    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
-        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
-    if (ws_bytes < 256) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need 256", ws_bytes);
+    fwi_status s;
+    if ((s = check_ws_bytes(ws, ws_bytes, 256)) != FWI_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int *status = static_cast<int *>(ws);
     int h = 0;
@@ -2017,6 +2011,17 @@ fwi_status fwi_selftest_wait(unsigned limit_us, void *ws, size_t ws_bytes, void 
     return fail(FWI_ERR_CUDA, "the self-test wait did not report its timeout (status %d)", h);
 }
 
+// dc2 = 2 c2 dv / v of a Born call on its padded grid (after setup's c2)
+fwi_status prep_dc2(const Plan &pl, const float *v, const float *dv, void *ws, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.dc2), 0, pl.dc2.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_prep_dc2(pl.L, v, dv, at<float>(ws, pl.c2), at<float>(ws, pl.dc2), st)) != cudaSuccess)
+        return cuda_fail(e, "prep kernel");
+    t_launch[2]++;
+    return FWI_OK;
+}
+
 fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                     const float *dv, float *dseis, void *ws, size_t ws_bytes, void *stream)
 {
@@ -2029,10 +2034,7 @@ fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_op
     begin_call(st);
     if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(at<char>(ws, pl.dc2), 0, pl.dc2.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
-    if ((e = launch_prep_dc2(pl.L, v, dv, at<float>(ws, pl.c2), at<float>(ws, pl.dc2), st)) != cudaSuccess)
-        return cuda_fail(e, "prep kernel");
-    t_launch[2]++;
+    if ((s = prep_dc2(pl, v, dv, ws, st)) != FWI_OK) return s;
     if ((s = run_born(pl, geom, ws, dseis, false, st)) != FWI_OK) return s;
     prof_record(1, st);
     prof_record(2, st);
@@ -2052,10 +2054,7 @@ fwi_status fwi_gauss_newton_hvp(const fwi_grid *grid, const fwi_geometry *geom, 
     begin_call(st);
     if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(at<char>(ws, pl.dc2), 0, pl.dc2.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
-    if ((e = launch_prep_dc2(pl.L, v, dv, at<float>(ws, pl.c2), at<float>(ws, pl.dc2), st)) != cudaSuccess)
-        return cuda_fail(e, "prep kernel");
-    t_launch[2]++;
+    if ((s = prep_dc2(pl, v, dv, ws, st)) != FWI_OK) return s;
     float *dseis = at<float>(ws, pl.syn);
     if ((s = run_born(pl, geom, ws, dseis, true, st)) != FWI_OK) return s;
     prof_record(1, st);
@@ -2237,10 +2236,7 @@ fwi_status batch_prepare(int nmodels, const fwi_grid *grids, const fwi_geometry 
         if (io[k].offh && opts->hmax < 0) return fail(FWI_ERR_INVALID_ARG, "offh requested with hmax < 0");
         wk[k] = static_cast<char *>(ws) + base[k];
     }
-    if (!ws) return fail(FWI_ERR_INVALID_ARG, "workspace is NULL");
-    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0)
-        return fail(FWI_ERR_INVALID_ARG, "workspace must be %zu-byte aligned", ALIGN);
-    if (ws_bytes < total) return fail(FWI_ERR_NOMEM, "workspace of %zu bytes, need %zu", ws_bytes, total);
+    if ((s = check_ws_bytes(ws, ws_bytes, total)) != FWI_OK) return s;
     bc.gp.assign(nmodels, nullptr);
     for (int k = 0; k < nmodels; ++k) bc.gp[k] = &geoms[k];
     return FWI_OK;
