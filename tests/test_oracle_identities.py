@@ -11,6 +11,16 @@
   products, reduces to the illumination at h = 0, and obeys Cauchy-Schwarz.
 * The time-integral misfit's gradient is a low-passed version of the OLS
   gradient (Sec. 2, after Eq. 3): its wavenumber centroid is lower.
+* The same gradient is the OLS gradient of the integrated wavefield U
+  (modelled with the integrated wavelet) against the integrated data (Sec. 2):
+  exact for the discrete scheme, so the adjoint source C^T C r is pinned
+  against a route that uses no transpose.
+* Eq. 3: the gradient equals -sum_s int u_s v_s dt with v_s = (2/v^3) dLambda_s/dt,
+  Lambda_s the back-propagated time-integrated residual (obtained here by
+  forward modelling with time-reversed sources at the receivers). A
+  continuum identity (integration by parts in time of the Sec. 2 gradient
+  of U): the discrete forms agree to a few per cent and converge under
+  refinement of dx and dt.
 * H_a's diagonal prefactor 4 / v^6 (Sec. 3) in a constant velocity is a
   single number.
 """
@@ -129,3 +139,89 @@ def test_hessian_v6_prefactor_constant_velocity(oracle_mod):
     assert np.allclose(b["grad_pre_illum"] * k, a["grad_pre_illum"], rtol=1e-12)
     assert np.allclose(b["grad_pre_offset"] * k, a["grad_pre_offset"], rtol=1e-12)
 
+
+
+def test_integral_gradient_is_ols_gradient_of_integrated_wavefield(oracle_mod):
+    """J_int(v) = 1/2 |C (R u(v; f) - d)|^2 = 1/2 |R u(v; C f) - C d|^2
+    because the scheme is linear and time-invariant (Sec. 2's U), so the two
+    exact gradients are one function of v."""
+    p = W.dipping(nz=30, nx=40, dx=10.0, dt=1e-3, nt=300, ns=2, nrec=20, rec_step=2, f0=15.0,
+                  sponge=8, seed=1)
+    g = oracle_mod.Grid.of(p)
+    w = p.wavelet.astype(np.float64)
+    d = oracle_mod.forward(g, p.v_true, p.src, p.rec, w)["seis"]
+    gi = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w, d, misfit="integral")
+    go = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, p.dt * np.cumsum(w, axis=1),
+                                 p.dt * np.cumsum(d, axis=1), misfit="ols")
+    assert abs(gi["J"] - go["J"]) <= 1e-12 * go["J"]
+    assert np.linalg.norm(gi["grad"] - go["grad"]) <= 1e-12 * np.linalg.norm(go["grad"])
+
+
+def _eq3_problem(k, f0=15.0):
+    """Linear-gradient background plus a Gaussian anomaly, one shot, six
+    receivers; k refines dx, dt (and the cell counts, nt, sponge, source and
+    receiver cells) by k at fixed physical positions."""
+    nz, nx, dx, dt, nt = 30 * k, 50 * k, 10.0 / k, 1e-3 / k, 300 * k
+    z = np.arange(nz)[:, None] * dx + np.zeros((1, nx))
+    x = np.arange(nx)[None, :] * dx + np.zeros((nz, 1))
+    v0 = 2000.0 + 0.5 * z
+    v1 = v0 + 150.0 * np.exp(-((z - 200.0) ** 2 + (x - 250.0) ** 2) / (2 * 40.0 ** 2))
+    rec = [[k, 0, j * k] for j in (5, 13, 21, 29, 37, 45)]
+    p = W.homogeneous(nz, nx, dx=dx, dt=dt, nt=nt, src=[[2 * k, 0, 25 * k]], rec=rec, f0=f0, sponge=8 * k)
+    p.v_true, p.v_init = v1.astype(np.float32), v0.astype(np.float32)
+    p.vref = float(v1.max())
+    return p
+
+
+def _eq3_forms(oracle_mod, k):
+    """(exact gradient of the discrete integral misfit as a density,
+    Eq. 3's form) on the physical grid. The discrete misfit has no dt weight
+    and its gradient is per cell, so the density is grad * dt / dx^2."""
+    p = _eq3_problem(k)
+    g = oracle_mod.Grid.of(p)
+    w = p.wavelet.astype(np.float64)
+    d = oracle_mod.forward(g, p.v_true, p.src, p.rec, w)["seis"]
+    gi = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w, d, misfit="integral")
+    u = oracle_mod.forward(g, p.v_init, p.src, p.rec, w, dump_shot=0)["dump"][:, :, 0, :]
+    wint = oracle_mod.time_integral(gi["seis"] - d, p.dt)[0]          # [nt, nrec]
+    # Lambda(t) = V(T - t), V modelled with the sources w_r(T - t) at the receivers
+    lam = np.zeros_like(u)
+    for j in range(p.nrec):
+        vj = oracle_mod.forward(g, p.v_init, p.rec[0, j:j + 1], np.zeros((1, 0, 3), np.int32),
+                                wint[::-1, j][None, :], dump_shot=0)["dump"][:, :, 0, :]
+        lam += vj[::-1]
+    lam_t = np.zeros_like(lam)
+    lam_t[1:-1] = (lam[2:] - lam[:-2]) / (2 * p.dt)
+    P = p.sponge
+    v = p.v_init.astype(np.float64)
+    eq3 = -(2.0 / v ** 3) * np.sum(u * lam_t, axis=0)[P:P + p.nz, P:P + p.nx] * p.dt
+    # below the source and receivers, inside the model
+    zs, xs = slice(6 * k, 24 * k), slice(6 * k, 44 * k)
+    return (gi["grad"][:, 0, :] * p.dt / p.dx ** 2)[zs, xs], eq3[zs, xs]
+
+
+def test_eq3_form_of_the_integral_gradient(oracle_mod):
+    errs, scales = [], []
+    for k in (1, 2):
+        a, b = _eq3_forms(oracle_mod, k)
+        errs.append(np.linalg.norm(a - b) / np.linalg.norm(a))
+        scales.append(float(np.sum(a * b) / np.sum(b * b)))
+    # measured: 2.8e-2 and 1.4e-2 (first order: the rectangle-rule integral);
+    # least-squares scale 0.9975 and 0.9987
+    assert errs[0] < 0.05 and errs[1] < 0.6 * errs[0], errs
+    assert abs(scales[1] - 1.0) < 5e-3, scales
+
+
+def test_planted_adjoint_integral_fails(oracle_mod, monkeypatch):
+    """C in place of C^T in the oracle's adjoint source fails the
+    integrated-wavefield pin."""
+    p = W.dipping(nz=30, nx=40, dx=10.0, dt=1e-3, nt=300, ns=1, nrec=20, rec_step=2, f0=15.0,
+                  sponge=8, seed=1)
+    g = oracle_mod.Grid.of(p)
+    w = p.wavelet.astype(np.float64)
+    d = oracle_mod.forward(g, p.v_true, p.src, p.rec, w)["seis"]
+    go = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, p.dt * np.cumsum(w, axis=1),
+                                 p.dt * np.cumsum(d, axis=1), misfit="ols")
+    monkeypatch.setattr(oracle_mod, "time_integral_adjoint", oracle_mod.time_integral)
+    gi = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w, d, misfit="integral")
+    assert np.linalg.norm(gi["grad"] - go["grad"]) > 0.1 * np.linalg.norm(go["grad"])
