@@ -337,7 +337,11 @@ fwi_status fwi_gauss_newton_hvp(const fwi_grid *grid, const fwi_geometry *geom, 
    plans of the same shape use them (a batch uses model 0's). choice: NULL
    or int[4] = forward variant, forward chunk, backward variant, backward
    chunk. The timing leaves ws in an unspecified state (the next call's
-   set-up rewrites it). fwi_autotune_reset() forgets all choices. */
+   set-up rewrites it). fwi_autotune_reset() forgets all choices.
+   3-D grids (opts as for a 3-D gradient: ckpt = FWI_CKPT_SNAPSHOT): the
+   compiled ring-depth / CTAs-per-SM variants of the 3-D forward and backward
+   steps are timed on the first shot group, keyed by padded shape and group
+   size; the chunks are 1 (a 3-D item is one column of one shot). */
 fwi_status fwi_autotune(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                         void *ws, size_t ws_bytes, void *stream, int *choice);
 /* Keep a given choice (int[4] as above) for this problem's shape, as if

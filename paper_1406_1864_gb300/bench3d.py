@@ -4,7 +4,9 @@ Models the seeded 3-D dipping-layer workload (workloads.dipping3d: surface
 receivers every cell, shots on a grid at depth 2), times forward modelling
 (per-level step time and algorithmic bandwidth at 16 B per padded
 point-step per shot) and one snapshot-checkpointed gradient per snapshot
-precision, with CUDA events on the library's stream. Prints one JSON line.
+precision, with CUDA events on the library's stream, after fwi_autotune has
+picked the step variants (``--no-autotune``: the defaults). Prints one JSON
+line.
 Defaults: the 200 x 400 x 400, 8-shot, nt 3000 workload in shot groups of 4.
 """
 from __future__ import annotations
@@ -26,6 +28,7 @@ def main():
     ap.add_argument("--nt", type=int, default=3000)
     ap.add_argument("--shot-group", type=int, default=4)
     ap.add_argument("--snap", default="f32,bf16")
+    ap.add_argument("--no-autotune", action="store_true", help="default step variants (no fwi_autotune)")
     args = ap.parse_args()
     p = W.dipping3d(nz=args.nz, ny=args.ny, nx=args.nx, nt=args.nt, ns=args.shots)
     grid, geom = fwi.from_problem(p)
@@ -33,13 +36,17 @@ def main():
     grp = fwi.Options(shot_group=args.shot_group)
     npad = (p.nz + 2 * p.sponge) * (p.ny + 2 * p.sponge) * (p.nx + 2 * p.sponge)
     g = min(p.nshots, args.shot_group or p.nshots)
+    tiles = "default"
+    if not args.no_autotune:  # step variants timed on this problem (not timed)
+        tiles = fwi.autotune(grid, geom, torch.as_tensor(p.v_init, device="cuda"),
+                             fwi.Options(ckpt="snapshot", shot_group=args.shot_group), ws=ws)
     fwi.profile(True)
     torch.cuda.synchronize()
     d_obs = fwi.forward(grid, geom, torch.as_tensor(p.v_true, device="cuda"), ws=ws, opts=grp)
     ph = fwi.last_phase_times()
     us = 1e3 * ph["forward_ms"] / max(1, ph["forward_launches"])
     out = {"workload": f"dipping3d {p.nz}x{p.ny}x{p.nx}, {p.nshots} shots, nt {p.nt}, {p.nrec} receivers",
-           "shot_group": g, "forward_us_per_level": us,
+           "shot_group": g, "tiles": tiles, "forward_us_per_level": us,
            "forward_alg_GBps": 16 * npad * g / (us * 1e-6) / 1e9, "gradients": {}}
     v = torch.as_tensor(p.v_init, device="cuda")
     for snap in args.snap.split(","):

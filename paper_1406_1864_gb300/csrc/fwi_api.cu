@@ -999,6 +999,7 @@ struct Plan3 {
     int ns_all = 0, G = 0, nt = 0, nrec = 0, op = 0;
     bool need_bwd = false;
     Tiling3 tf{}, tb{};
+    int vf = 0, vb = 0; // step variants (autotuned per shape, else the defaults)
     Part scal, sched, c2, damp, u[2], p[2], syn, acc_i, acc_g, tab, snaps, snap_max, seg;
     size_t tab_src = 0, tab_ptr = 0, tab_ent = 0, tab_zr = 0;
     int snap_prec = FWI_SNAP_F32, K = 0, nck = 0;
@@ -1028,8 +1029,10 @@ fwi_status make_plan3(const fwi_grid *g, const fwi_geometry *ge, const fwi_optio
     pl.G = (o && o->shot_group > 0 && o->shot_group < ge->nshots) ? o->shot_group : ge->nshots;
     pl.need_bwd = op == FWI_OP_GRADIENT;
     const Lay3D &L = pl.L;
-    pl.tf = make_tiling3(L, pl.G, false);
-    pl.tb = make_tiling3(L, pl.G, true);
+    pl.vf = step3_variant_for(L, pl.G, false);
+    pl.vb = step3_variant_for(L, pl.G, true);
+    pl.tf = make_tiling3(L, pl.G, false, pl.vf);
+    pl.tb = make_tiling3(L, pl.G, true, pl.vb);
     size_t off = 0;
     auto take = [&](Part &p, size_t bytes) {
         p.off = off;
@@ -1195,9 +1198,12 @@ fwi_status snap3_restore(const Plan3 &pl, void *ws, int g, int j, float *u, floa
 }
 
 // forward time loop of one shot group [s0, s0 + g): traces into seis (the
-// group's rows) or null, illumination into acc_i or null, snapshots if `save`
+// group's rows) or null, illumination into acc_i or null, snapshots if `save`;
+// levels [n_begin, n_end) (n_end < 0: to nt), events ea / eb (if given)
+// recorded around the step launches
 fwi_status run_forward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, void *ws, float *seis,
-                        float *acc_i, int illum_utt, bool save, cudaStream_t st)
+                        float *acc_i, int illum_utt, bool save, cudaStream_t st, int n_begin = 0, int n_end = -1,
+                        cudaEvent_t ea = nullptr, cudaEvent_t eb = nullptr)
 {
     cudaError_t e;
     for (int b = 0; b < 2; ++b)
@@ -1219,7 +1225,9 @@ fwi_status run_forward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, 
         if ((s = maps3(pl, U[b], g, &mh[b], &mp[b])) != FWI_OK) return s;
     if ((s = maps3(pl, at<float>(ws, pl.c2), 1, nullptr, &a.tm_c2)) != FWI_OK) return s;
     if ((s = maps3(pl, at<float>(ws, pl.damp), 1, nullptr, &a.tm_damp)) != FWI_OK) return s;
-    for (int n = 0; n < pl.nt; ++n) {
+    if (n_end < 0) n_end = pl.nt;
+    if (ea && (e = cudaEventRecord(ea, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (int n = n_begin; n < n_end; ++n) {
         if (save && n % pl.K == 0 && n <= pl.nt - 2)
             if ((s = snap3_capture(pl, ws, g, n / pl.K, U[n & 1], U[(n + 1) & 1], st)) != FWI_OK) return s;
         a.n = n;
@@ -1229,9 +1237,10 @@ fwi_status run_forward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, 
         a.tm_prev = mp[(n + 1) & 1];
         a.uout = U[(n + 1) & 1];
         a.c.sched = at<int>(ws, pl.sched) + n;
-        if ((e = launch_fwd3d(a, pl.tf, st)) != cudaSuccess) return cuda_fail(e, "3-D forward step");
+        if ((e = launch_fwd3d(a, pl.tf, pl.vf, st)) != cudaSuccess) return cuda_fail(e, "3-D forward step");
         t_launch[0]++;
     }
+    if (eb && (e = cudaEventRecord(eb, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     for (int b = 0; b < 2; ++b) {
         if ((e = launch_check_finite(U[b], (long long)g * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
             return cuda_fail(e, "finite check");
@@ -1293,7 +1302,7 @@ fwi_status run_backward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g,
             f.tm_prev = sp[i == 0 ? K : i - 1];
             f.uout = S[i + 1];
             f.c.sched = at<int>(ws, pl.sched) + 2 * pl.nt + n;
-            if ((e = launch_fwd3d(f, pl.tf, st)) != cudaSuccess) return cuda_fail(e, "3-D segment step");
+            if ((e = launch_fwd3d(f, pl.tf, pl.vf, st)) != cudaSuccess) return cuda_fail(e, "3-D segment step");
             t_launch[1]++;
         }
         for (int m = n1 + 1; m >= n0 + 1; --m) {
@@ -1305,13 +1314,54 @@ fwi_status run_backward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g,
             a.tm_pb = pp[m & 1];
             a.pb = Pp[m & 1];
             a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
-            if ((e = launch_bwd3d(a, pl.tb, st)) != cudaSuccess) return cuda_fail(e, "3-D backward step");
+            if ((e = launch_bwd3d(a, pl.tb, pl.vb, st)) != cudaSuccess) return cuda_fail(e, "3-D backward step");
             t_launch[1]++;
         }
     }
     if ((e = launch_check_finite(Pp[0], (long long)g * pl.L.fstride, at<int>(ws, pl.scal, 8), st)) != cudaSuccess)
         return cuda_fail(e, "finite check");
     t_launch[2]++;
+    return FWI_OK;
+}
+
+// nlev backward steps of the first group, levels nt-1 downwards, on the
+// group's fields as they are (the autotuner's timing; events ea / eb around
+// the launches). The imaging sum is overwritten by the next call's set-up.
+fwi_status time_backward3(const Plan3 &pl, const fwi_geometry *ge, void *ws, int nlev, cudaStream_t st,
+                          cudaEvent_t ea, cudaEvent_t eb)
+{
+    cudaError_t e;
+    fwi_status s;
+    const int g = pl.G;
+    float *U[2] = {at<float>(ws, pl.u[0]), at<float>(ws, pl.u[1])};
+    float *Pp[2] = {at<float>(ws, pl.p[0]), at<float>(ws, pl.p[1])};
+    CUtensorMap uh[2], up[2], ph[2], pp[2];
+    for (int b = 0; b < 2; ++b)
+        if ((s = maps3(pl, U[b], g, &uh[b], &up[b])) != FWI_OK || (s = maps3(pl, Pp[b], g, &ph[b], &pp[b])) != FWI_OK)
+            return s;
+    Bwd3Args a{};
+    a.c = make_common3(pl, ge, 0, g, ws, pl.tb);
+    a.rt = rec_table3(pl, ws);
+    a.adj = pl.nrec > 0 ? at<float>(ws, pl.syn) : nullptr;
+    a.acc_grad = at<float>(ws, pl.acc_g);
+    a.adj_scale = pl.L.dx * pl.L.dx;
+    if ((s = maps3(pl, at<float>(ws, pl.c2), 1, nullptr, &a.tm_c2)) != FWI_OK) return s;
+    if ((s = maps3(pl, at<float>(ws, pl.damp), 1, nullptr, &a.tm_damp)) != FWI_OK) return s;
+    if ((e = cudaMemsetAsync(at<char>(ws, pl.sched), 0, pl.sched.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    if ((e = cudaEventRecord(ea, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (int m = pl.nt - 1; m >= 1 && m > pl.nt - 1 - nlev; --m) {
+        a.m = m;
+        a.tm_u = uh[(m - 1) & 1];
+        a.tm_upt = up[(m - 1) & 1];
+        a.tm_p = ph[(m + 1) & 1];
+        a.tm_ppt = pp[(m + 1) & 1];
+        a.tm_pb = pp[m & 1];
+        a.pb = Pp[m & 1];
+        a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
+        if ((e = launch_bwd3d(a, pl.tb, pl.vb, st)) != cudaSuccess) return cuda_fail(e, "3-D backward step");
+    }
+    if ((e = cudaEventRecord(eb, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     return FWI_OK;
 }
 
@@ -2033,7 +2083,6 @@ fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_op
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     begin_call(st);
     if ((s = setup(pl, geom, v, ws, st)) != FWI_OK) return s;
-    cudaError_t e;
     if ((s = prep_dc2(pl, v, dv, ws, st)) != FWI_OK) return s;
     if ((s = run_born(pl, geom, ws, dseis, false, st)) != FWI_OK) return s;
     prof_record(1, st);
@@ -2075,9 +2124,78 @@ fwi_status fwi_gauss_newton_hvp(const fwi_grid *grid, const fwi_geometry *geom, 
     return finish(pl, ws, st);
 }
 
+// fwi_autotune of a 3-D gradient: every compiled variant of the forward and
+// backward steps timed on a few levels of the first shot group (the second
+// of two passes), the fastest kept for the shape
+fwi_status autotune3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
+                     void *ws, size_t ws_bytes, cudaStream_t st, int *choice)
+{
+    Plan3 pl;
+    fwi_status s = make_plan3(grid, geom, opts, FWI_OP_GRADIENT, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v) return fail(FWI_ERR_INVALID_ARG, "v is NULL");
+    if ((s = check_ws3(pl, ws, ws_bytes)) != FWI_OK) return s;
+    const bool prof = t_prof;
+    t_prof = false;
+    struct Ev {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Ev()
+        {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&ev.a)) != cudaSuccess || (e = cudaEventCreate(&ev.b)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    if ((s = setup3(pl, v, ws, st)) != FWI_OK) return s;
+    if ((s = upload_tables3(pl, geom, 0, pl.G, ws, st)) != FWI_OK) return s;
+    const int nlev = std::min(6, pl.nt - 1);
+    int best[2] = {0, 0};
+    for (int b = 0; b < 2 && s == FWI_OK; ++b) {
+        float best_ms = 1e30f;
+        for (int vi = 0; vi < step3_variants(b != 0) && s == FWI_OK; ++vi) {
+            Plan3 p = pl;
+            if (b == 0) {
+                p.vf = vi;
+                p.tf = make_tiling3(p.L, p.G, false, vi);
+            } else {
+                p.vb = vi;
+                p.tb = make_tiling3(p.L, p.G, true, vi);
+            }
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && s == FWI_OK; ++rep) { // first pass warms up
+                s = b == 0 ? run_forward3(p, geom, 0, p.G, ws, nullptr, nullptr, 0, false, st, 1, 1 + nlev, ev.a,
+                                          ev.b)
+                           : time_backward3(p, geom, ws, nlev, st, ev.a, ev.b);
+                if (s == FWI_OK && (e = cudaEventSynchronize(ev.b)) != cudaSuccess) s = cuda_fail(e, "sync");
+                if (s == FWI_OK) cudaEventElapsedTime(&ms, ev.a, ev.b);
+            }
+            if (s == FWI_OK && ms < best_ms) {
+                best_ms = ms;
+                best[b] = vi;
+            }
+        }
+        if (s == FWI_OK) step3_tuned_store(pl.L, pl.G, b != 0, best[b]);
+    }
+    t_prof = prof;
+    if (s != FWI_OK) return s;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronize");
+    if (choice) {
+        choice[0] = best[0];
+        choice[1] = 1;
+        choice[2] = best[1];
+        choice[3] = 1;
+    }
+    t_err.clear();
+    return FWI_OK;
+}
+
 fwi_status fwi_autotune(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                         void *ws, size_t ws_bytes, void *stream, int *choice)
 {
+    if (grid && grid->ndim == 3)
+        return autotune3(grid, geom, opts, v, ws, ws_bytes, static_cast<cudaStream_t>(stream), choice);
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_GRADIENT, true, pl);
     if (s != FWI_OK) return s;
@@ -2169,6 +2287,19 @@ fwi_status fwi_autotune_set(const fwi_grid *grid, const fwi_geometry *geom, cons
                             const int *choice)
 {
     if (!choice) return fail(FWI_ERR_INVALID_ARG, "choice is NULL");
+    if (grid && grid->ndim == 3) {
+        Plan3 p3;
+        fwi_status s3 = make_plan3(grid, geom, opts, FWI_OP_GRADIENT, false, p3);
+        if (s3 != FWI_OK) return s3;
+        if (choice[0] < 0 || choice[0] >= step3_variants(false) || choice[2] < 0 || choice[2] >= step3_variants(true))
+            return fail(FWI_ERR_INVALID_ARG, "variant outside the compiled ones (%d forward, %d backward)",
+                        step3_variants(false), step3_variants(true));
+        if (choice[1] < 1 || choice[3] < 1) return fail(FWI_ERR_INVALID_ARG, "chunk must be >= 1");
+        step3_tuned_store(p3.L, p3.G, false, choice[0]);
+        step3_tuned_store(p3.L, p3.G, true, choice[2]);
+        t_err.clear();
+        return FWI_OK;
+    }
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_GRADIENT, false, pl);
     if (s != FWI_OK) return s;
@@ -2186,6 +2317,7 @@ fwi_status fwi_autotune_set(const fwi_grid *grid, const fwi_geometry *geom, cons
 fwi_status fwi_autotune_reset(void)
 {
     step_tuned_clear();
+    step3_tuned_clear();
     return FWI_OK;
 }
 

@@ -6,11 +6,18 @@
 #include "fwi_args.h"
 
 namespace fwi {
-Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward);
+// 3-D steps: compiled variants of the forward (backward = false) or backward
+// step, the autotuned one of a problem shape (0 if none is kept), the
+// tiling of a variant (an out-of-range one is taken as 0), launches
+int step3_variants(bool backward);
+int step3_variant_for(const Lay3D &L, int ns, bool backward);
+void step3_tuned_store(const Lay3D &L, int ns, bool backward, int variant);
+void step3_tuned_clear();
+Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward, int variant);
 // tensor map over nfields 3-D fields with a box of bx x by cells of one plane
 bool encode_field_map3(CUtensorMap *map, const float *base, const Lay3D &L, int nfields, int bx, int by);
-cudaError_t launch_fwd3d(const Fwd3Args &a, const Tiling3 &t, cudaStream_t st);
-cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, cudaStream_t st);
+cudaError_t launch_fwd3d(const Fwd3Args &a, const Tiling3 &t, int variant, cudaStream_t st);
+cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, int variant, cudaStream_t st);
 cudaError_t launch_prep3d(const Lay3D &L, const float *v, float *c2, float *damp, float cfl_limit, int *status,
                           cudaStream_t st);
 cudaError_t launch_fold_grad3d(const Lay3D &L, const float *acc, const float *v, float *grad, cudaStream_t st);

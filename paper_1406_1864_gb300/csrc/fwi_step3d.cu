@@ -23,7 +23,9 @@
 // point and plane: a column's planes do not fit in registers.
 #include "fwi_device.cuh"
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 namespace fwi {
 namespace {
@@ -444,32 +446,58 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
     }
 }
 
-constexpr int F3_ST = 3, F3_MINB = 4, B3_ST = 3, B3_MINB = 3;
-#define K_FWD3 k_fwd3d<F3_ST, F3_MINB>
-#define K_BWD3 k_bwd3d<B3_ST, B3_MINB>
-constexpr int SMEM_FWD3 = 128 + 128 + F3_ST * FWD3_STAGE_F * 4;
-constexpr int SMEM_BWD3 = 128 + 128 + B3_ST * BWD3_STAGE_F * 4;
+// Compiled variants of each step (index 0 is the default; fwi_autotune may
+// pick another per problem shape): ring stages and minimum resident CTAs per
+// SM (the register cap). Forward: 3 stages at 4 CTAs per SM, 3 or 2 stages
+// at 5 (96 registers); backward: 3 stages at 3 CTAs per SM (shared memory
+// allows no more), 2 stages at 4 (128 registers).
+struct Variant3 {
+    int smem;
+    const void *fn;
+    int occ; // resident CTAs per SM (occupancy calculator)
+};
+#define V3F(ST, MINB) {256 + (ST) * FWD3_STAGE_F * 4, (const void *)k_fwd3d<ST, MINB>, 0}
+#define V3B(ST, MINB) {256 + (ST) * BWD3_STAGE_F * 4, (const void *)k_bwd3d<ST, MINB>, 0}
+Variant3 g_var3f[] = {V3F(3, 4), V3F(3, 5), V3F(2, 5)};
+Variant3 g_var3b[] = {V3B(3, 3), V3B(2, 4)};
+constexpr int NV3F = (int)(sizeof g_var3f / sizeof g_var3f[0]);
+constexpr int NV3B = (int)(sizeof g_var3b / sizeof g_var3b[0]);
 
-int g_occ3[2] = {0, 0};
+Variant3 &variant3(bool backward, int v) { return backward ? g_var3b[v] : g_var3f[v]; }
+
 std::once_flag g_prep3_once;
 
 void prepare_kernels3()
 {
     std::call_once(g_prep3_once, [] {
         int dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess) {
-            cudaFuncSetAttribute(K_FWD3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FWD3);
-            cudaFuncSetAttribute(K_BWD3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BWD3);
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ3[0], K_FWD3, TPB, SMEM_FWD3) != cudaSuccess)
-                g_occ3[0] = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ3[1], K_BWD3, TPB, SMEM_BWD3) != cudaSuccess)
-                g_occ3[1] = 0;
-        }
+        const bool have_dev = cudaGetDevice(&dev) == cudaSuccess;
+        for (int b = 0; b < 2; ++b)
+            for (int i = 0; i < (b ? NV3B : NV3F); ++i) {
+                Variant3 &v = variant3(b != 0, i);
+                int occ = 0;
+                if (have_dev) {
+                    cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem);
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, TPB, v.smem) != cudaSuccess)
+                        occ = 0;
+                }
+                v.occ = occ > 0 ? occ : 2;
+            }
         cudaGetLastError();
-        for (int k = 0; k < 2; ++k)
-            if (g_occ3[k] < 1) g_occ3[k] = 2;
     });
 }
+
+// variants kept by the autotuner per (step, padded shape, shots of a group)
+struct TuneKey3 {
+    bool backward;
+    int nzp, nyp, nxp, ns;
+    bool operator<(const TuneKey3 &o) const
+    {
+        return std::tie(backward, nzp, nyp, nxp, ns) < std::tie(o.backward, o.nzp, o.nyp, o.nxp, o.ns);
+    }
+};
+std::mutex g_tune3_mu;
+std::map<TuneKey3, int> g_tuned3;
 
 int sm_count3()
 {
@@ -482,34 +510,61 @@ int sm_count3()
 }
 } // namespace
 
-Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward)
+int step3_variants(bool backward) { return backward ? NV3B : NV3F; }
+
+int step3_variant_for(const Lay3D &L, int ns, bool backward)
+{
+    std::lock_guard<std::mutex> lock(g_tune3_mu);
+    auto it = g_tuned3.find(TuneKey3{backward, L.nzp, L.nyp, L.nxp, ns});
+    return it == g_tuned3.end() ? 0 : it->second;
+}
+
+void step3_tuned_store(const Lay3D &L, int ns, bool backward, int variant)
+{
+    std::lock_guard<std::mutex> lock(g_tune3_mu);
+    g_tuned3[TuneKey3{backward, L.nzp, L.nyp, L.nxp, ns}] = variant;
+}
+
+void step3_tuned_clear()
+{
+    std::lock_guard<std::mutex> lock(g_tune3_mu);
+    g_tuned3.clear();
+}
+
+Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward, int variant)
 {
     prepare_kernels3();
+    if (variant < 0 || variant >= step3_variants(backward)) variant = 0;
     Tiling3 t;
     t.nty = (L.nyp + TY3 - 1) / TY3;
     t.ntx = (L.nxp + TX - 1) / TX;
     const long long items = (long long)t.nty * t.ntx * ns;
-    const long long slots = (long long)sm_count3() * g_occ3[backward ? 1 : 0];
+    const long long slots = (long long)sm_count3() * variant3(backward, variant).occ;
     t.ctas = (int)(items < slots ? items : slots);
     return t;
 }
 
-cudaError_t launch_fwd3d(const Fwd3Args &a, const Tiling3 &t, cudaStream_t st)
+namespace {
+template <class A> cudaError_t launch3(const Variant3 &v, const A &a, const Tiling3 &t, cudaStream_t st)
 {
     if (t.ctas <= 0) return cudaSuccess;
-    K_FWD3<<<t.ctas, TPB, SMEM_FWD3, st>>>(a);
-    return cudaGetLastError();
+    void *args[] = {const_cast<A *>(&a)};
+    return cudaLaunchKernel(v.fn, dim3(t.ctas), dim3(TPB), args, v.smem, st);
 }
+} // namespace
 
-cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, cudaStream_t st)
+cudaError_t launch_fwd3d(const Fwd3Args &a, const Tiling3 &t, int variant, cudaStream_t st)
 {
-    if (t.ctas <= 0) return cudaSuccess;
-    K_BWD3<<<t.ctas, TPB, SMEM_BWD3, st>>>(a);
-    return cudaGetLastError();
+    if (variant < 0 || variant >= NV3F) return cudaErrorInvalidValue;
+    return launch3(g_var3f[variant], a, t, st);
 }
 
-// Tensor map over `nfields` stored 3-D fields [nfields][planes][rows][pitch]
-// with a box of bx x by cells of one plane; out-of-range cells read as zero.
+cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, int variant, cudaStream_t st)
+{
+    if (variant < 0 || variant >= NV3B) return cudaErrorInvalidValue;
+    return launch3(g_var3b[variant], a, t, st);
+}
+
 bool encode_field_map3(CUtensorMap *map, const float *base, const Lay3D &L, int nfields, int bx, int by)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;

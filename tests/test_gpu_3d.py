@@ -113,3 +113,34 @@ def test_3d_errors(torch_cuda, case):
     assert e.value.status == _lib.FWI_ERR_CFL
     again = fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot"))
     assert np.isfinite(again["grad"].cpu().numpy()).all()
+
+
+N3_FWD, N3_BWD = 3, 2  # compiled 3-D step variants
+
+
+def test_3d_every_variant_matches_the_oracle(torch_cuda, case):
+    """Each 3-D step variant (ring depth, CTAs per SM), pinned with
+    fwi_autotune_set, gives the oracle's gradient (1e-4) and the default
+    variant's (the same arithmetic: 1e-6); fwi_autotune's choice is in range
+    and used by the next call."""
+    import itertools
+    from paper_1406_1864_gb300 import fwi
+    p, g, grid, geom, v, d, d_true, ref = case
+    opts = fwi.Options(ckpt="snapshot", snap="f32", shot_group=2)
+    fwi.autotune_reset()
+    default = fwi.adjoint_gradient(grid, geom, v, d, opts)
+    try:
+        for fv, bv in itertools.product(range(N3_FWD), range(N3_BWD)):
+            fwi.autotune_set(grid, geom, opts, {"forward_variant": fv, "forward_chunk": 1,
+                                                 "backward_variant": bv, "backward_chunk": 1})
+            r = fwi.adjoint_gradient(grid, geom, v, d, opts)
+            assert rel(r["grad"].cpu(), ref["grad"]) <= 1e-4, (fv, bv)
+            assert rel(r["grad"].cpu(), default["grad"].cpu()) <= 1e-6, (fv, bv)
+            assert rel(r["illum"].cpu(), ref["illum"]) <= 1e-4, (fv, bv)
+            assert abs(float(r["misfit"]) - float(default["misfit"])) <= 1e-12 * float(default["misfit"])
+        choice = fwi.autotune(grid, geom, v, opts)
+        assert 0 <= choice["forward_variant"] < N3_FWD and 0 <= choice["backward_variant"] < N3_BWD
+        r = fwi.adjoint_gradient(grid, geom, v, d, opts)
+        assert rel(r["grad"].cpu(), ref["grad"]) <= 1e-4
+    finally:
+        fwi.autotune_reset()
