@@ -26,7 +26,8 @@
  * Conventions for every entry point:
  *   - Arrays are caller-owned, contiguous, C order. "DEVICE" arrays live in
  *     CUDA device memory of the current device; "HOST" arrays in host memory.
- *   - Physical-grid shapes only: [nz][nx] in 2-D. Padding is internal.
+ *   - Physical-grid shapes only: [nz][nx] in 2-D, [nz][ny][nx] in 3-D.
+ *     Padding is internal.
  *   - float is IEEE binary32 (the stencil arithmetic), double is binary64
  *     (misfit reductions only).
  *   - `ws` is a DEVICE workspace of at least the size reported by
@@ -41,8 +42,13 @@
  *     the call, which synchronises `stream` once.
  *   - Return value: FWI_OK or an error code; fwi_last_error() then gives a
  *     message (per host thread). On error the outputs are unspecified.
- *   - Only ndim = 2 is supported by this version; ndim = 3 returns
- *     FWI_ERR_INVALID_ARG.
+ *   - Dimensions: every entry point takes 2-D grids (ndim = 2). 3-D grids
+ *     (ndim = 3; 25-point Laplacian, source f / dx^3) are taken by
+ *     fwi_workspace_bytes, fwi_forward (save = 1 with ckpt =
+ *     FWI_CKPT_SNAPSHOT and all shots in one group), fwi_adjoint_apply,
+ *     fwi_adjoint_gradient (ckpt = FWI_CKPT_SNAPSHOT, hmax = -1),
+ *     fwi_illumination and fwi_autotune*; the other entry points return
+ *     FWI_ERR_INVALID_ARG for them.
  */
 #ifndef FWI_H
 #define FWI_H

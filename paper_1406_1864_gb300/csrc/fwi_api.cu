@@ -1013,12 +1013,17 @@ fwi_status make_plan3(const fwi_grid *g, const fwi_geometry *ge, const fwi_optio
     if ((st = check_grid3(g)) != FWI_OK) return st;
     if ((st = check_geom3(g, ge, coords)) != FWI_OK) return st;
     if ((st = check_opts(o, op)) != FWI_OK) return st;
-    if (op != FWI_OP_FORWARD && op != FWI_OP_GRADIENT && op != FWI_OP_ILLUMINATION)
-        return fail(FWI_ERR_INVALID_ARG, "3-D grids support forward modelling, gradients and illumination");
+    if (op != FWI_OP_FORWARD && op != FWI_OP_FORWARD_SAVE && op != FWI_OP_GRADIENT && op != FWI_OP_ILLUMINATION)
+        return fail(FWI_ERR_INVALID_ARG, "3-D grids support forward modelling (with or without checkpoints for "
+                                         "fwi_adjoint_apply), gradients and illumination");
     if (o && o->hmax >= 0) return fail(FWI_ERR_INVALID_ARG, "the offset Hessian is 2-D only (hmax must be -1)");
-    if (op == FWI_OP_GRADIENT && o->ckpt != FWI_CKPT_SNAPSHOT)
-        return fail(FWI_ERR_INVALID_ARG, "3-D gradients need ckpt = FWI_CKPT_SNAPSHOT (a per-level sponge band "
-                                         "of a 3-D grid does not fit)");
+    const bool ckpts = op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE;
+    if (ckpts && (!o || o->ckpt != FWI_CKPT_SNAPSHOT))
+        return fail(FWI_ERR_INVALID_ARG, "3-D gradients and fwi_forward(save = 1) need ckpt = FWI_CKPT_SNAPSHOT "
+                                         "(a per-level sponge band of a 3-D grid does not fit)");
+    if (op == FWI_OP_FORWARD_SAVE && o->shot_group > 0 && o->shot_group < ge->nshots)
+        return fail(FWI_ERR_INVALID_ARG, "3-D fwi_forward(save = 1) keeps the snapshots of every shot for "
+                                         "fwi_adjoint_apply: shot_group must be 0 or >= nshots");
     if (op == FWI_OP_GRADIENT && o->precond == FWI_PRECOND_OFFSET)
         return fail(FWI_ERR_INVALID_ARG, "precond=OFFSET needs the offset Hessian (2-D only)");
     pl.L = make_layout3(g);
@@ -1027,7 +1032,7 @@ fwi_status make_plan3(const fwi_grid *g, const fwi_geometry *ge, const fwi_optio
     pl.ns_all = ge->nshots;
     pl.nrec = ge->nrec;
     pl.G = (o && o->shot_group > 0 && o->shot_group < ge->nshots) ? o->shot_group : ge->nshots;
-    pl.need_bwd = op == FWI_OP_GRADIENT;
+    pl.need_bwd = ckpts; // forward-with-checkpoints has the gradient's layout
     const Lay3D &L = pl.L;
     pl.vf = step3_variant_for(L, pl.G, false);
     pl.vb = step3_variant_for(L, pl.G, true);
@@ -1427,7 +1432,8 @@ fwi_status forward3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_op
         const int g = std::min(pl.G, pl.ns_all - s0);
         if ((s = upload_tables3(pl, geom, s0, g, ws, st)) != FWI_OK) return s;
         float *sg = seis ? seis + (size_t)s0 * pl.nt * pl.nrec : nullptr;
-        if ((s = run_forward3(pl, geom, s0, g, ws, sg, acc_i, utt, false, st)) != FWI_OK) return s;
+        if ((s = run_forward3(pl, geom, s0, g, ws, sg, acc_i, utt, op == FWI_OP_FORWARD_SAVE, st)) != FWI_OK)
+            return s;
     }
     prof_record(1, st);
     prof_record(2, st);
@@ -1501,6 +1507,32 @@ fwi_status gradient3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_o
     }
     if (misfit && (e = cudaMemcpyAsync(misfit, J, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "copy");
+    prof_record(3, st);
+    return finish3(pl, ws, st);
+}
+
+// fwi_adjoint_apply on a 3-D grid: J^T of adj_src after fwi_forward(save = 1)
+// on the same workspace, from its snapshots (one group: all shots)
+fwi_status adjoint_apply3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
+                          const float *adj_src, float *grad, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    Plan3 pl;
+    fwi_status s = make_plan3(grid, geom, opts, FWI_OP_FORWARD_SAVE, true, pl);
+    if (s != FWI_OK) return s;
+    if (!v || !grad || (!adj_src && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v, adj_src or grad is NULL");
+    if ((s = check_ws3(pl, ws, ws_bytes)) != FWI_OK) return s;
+    begin_call(st);
+    prof_record(1, st);
+    // c2 and the sponge factor again from v, the imaging sum cleared; the
+    // snapshots stay
+    if ((s = setup3(pl, v, ws, st)) != FWI_OK) return s;
+    if ((s = upload_tables3(pl, geom, 0, pl.G, ws, st)) != FWI_OK) return s;
+    if ((s = run_backward3(pl, geom, 0, pl.G, ws, adj_src, st)) != FWI_OK) return s;
+    prof_record(2, st);
+    cudaError_t e;
+    if ((e = launch_fold_grad3d(pl.L, at<float>(ws, pl.acc_g), v, grad, st)) != cudaSuccess)
+        return cuda_fail(e, "fold kernel");
+    t_launch[2]++;
     prof_record(3, st);
     return finish3(pl, ws, st);
 }
@@ -1663,10 +1695,9 @@ fwi_status fwi_forward(const fwi_grid *grid, const fwi_geometry *geom, const fwi
                        const float *v, float *seis, int save, void *ws, size_t ws_bytes, void *stream)
 {
     if (grid && grid->ndim == 3) {
-        if (save) return fail(FWI_ERR_INVALID_ARG, "3-D grids: fwi_forward(save = 1) is not available");
         if (!v || (!seis && geom && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v or seis is NULL");
-        return forward3(grid, geom, opts, FWI_OP_FORWARD, v, seis, nullptr, ws, ws_bytes,
-                        static_cast<cudaStream_t>(stream));
+        return forward3(grid, geom, opts, save ? FWI_OP_FORWARD_SAVE : FWI_OP_FORWARD, v, seis, nullptr, ws,
+                        ws_bytes, static_cast<cudaStream_t>(stream));
     }
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, save ? FWI_OP_FORWARD_SAVE : FWI_OP_FORWARD, true, pl);
@@ -1687,6 +1718,8 @@ fwi_status fwi_adjoint_apply(const fwi_grid *grid, const fwi_geometry *geom, con
                              const float *v, const float *adj_src, float *grad, void *ws, size_t ws_bytes,
                              void *stream)
 {
+    if (grid && grid->ndim == 3)
+        return adjoint_apply3(grid, geom, opts, v, adj_src, grad, ws, ws_bytes, static_cast<cudaStream_t>(stream));
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_FORWARD_SAVE, true, pl);
     if (s != FWI_OK) return s;

@@ -338,7 +338,8 @@ def test_batch_workspace_and_errors(lib):
 
 
 def test_3d_workspace_and_options(lib):
-    """3-D plans: snapshot checkpoints required for gradients, no offset
+    """3-D plans: snapshot checkpoints required for gradients and for forward
+    modelling that keeps checkpoints (all shots in one group), no offset
     Hessian; shot groups bound the workspace (one group's fields and
     snapshots); forward modelling needs no checkpoints."""
     from paper_1406_1864_gb300 import _lib as L
@@ -369,8 +370,15 @@ def test_3d_workspace_and_options(lib):
     o.hmax, o.precond = -1, L.FWI_PRECOND_OFFSET
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[0] == L.FWI_ERR_INVALID_ARG
     o.precond = L.FWI_PRECOND_ILLUM
-    for op in (L.FWI_OP_FORWARD_SAVE, L.FWI_OP_OFFSET_HESSIAN):
-        assert ws_bytes(lib, g, ge, o, op)[0] == L.FWI_ERR_INVALID_ARG
+    # forward with checkpoints keeps every shot's snapshots: one group only
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_FORWARD_SAVE)[0] == L.FWI_ERR_INVALID_ARG
+    o.shot_group = 0
+    st, fs = ws_bytes(lib, g, ge, o, L.FWI_OP_FORWARD_SAVE)
+    assert st == L.FWI_OK and fs > one
+    o.ckpt = L.FWI_CKPT_SPONGE
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_FORWARD_SAVE)[0] == L.FWI_ERR_INVALID_ARG
+    o.ckpt = L.FWI_CKPT_SNAPSHOT
+    assert ws_bytes(lib, g, ge, o, L.FWI_OP_OFFSET_HESSIAN)[0] == L.FWI_ERR_INVALID_ARG
     o.shot_group = -1
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[0] == L.FWI_ERR_INVALID_ARG
 

@@ -144,3 +144,23 @@ def test_3d_every_variant_matches_the_oracle(torch_cuda, case):
         assert rel(r["grad"].cpu(), ref["grad"]) <= 1e-4
     finally:
         fwi.autotune_reset()
+
+
+def test_3d_autograd_with_snapshots(torch_cuda, case):
+    """autograd.traces on a 3-D grid: fwi_forward(save = 1) keeps F32 (or
+    bfloat16) snapshots, fwi_adjoint_apply is the backward. The OLS loss
+    gives the oracle's gradient (1e-4; 1e-2 with bfloat16 snapshots) and its
+    traces are the oracle's (1e-5); a shot group smaller than the shots is
+    refused for the forward that keeps checkpoints."""
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import autograd, fwi, _lib
+    p, g, grid, geom, v, d, d_true, ref = case
+    for snap, tol in (("f32", 1e-4), ("bf16", 1e-2)):
+        vv = v.clone().requires_grad_(True)
+        seis = autograd.traces(vv, grid, geom, fwi.Options(ckpt="snapshot", snap=snap))
+        assert rel(seis.detach().cpu(), ref["seis"]) <= 1e-5
+        (0.5 * ((seis.double() - d.double()) ** 2).sum()).backward()
+        assert rel(vv.grad.cpu(), ref["grad"]) <= tol, snap
+    with pytest.raises(_lib.FwiError):
+        autograd.traces(v.clone().requires_grad_(True), grid, geom,
+                        fwi.Options(ckpt="snapshot", shot_group=1))
