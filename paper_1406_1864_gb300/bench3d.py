@@ -29,6 +29,8 @@ def main():
     ap.add_argument("--shot-group", type=int, default=4)
     ap.add_argument("--snap", default="f32,bf16")
     ap.add_argument("--no-autotune", action="store_true", help="default step variants (no fwi_autotune)")
+    ap.add_argument("--variants", default="", help="F,B: pin the forward and backward step variants "
+                    "(fwi_autotune_set) instead of autotuning")
     args = ap.parse_args()
     p = W.dipping3d(nz=args.nz, ny=args.ny, nx=args.nx, nt=args.nt, ns=args.shots)
     grid, geom = fwi.from_problem(p)
@@ -37,7 +39,11 @@ def main():
     npad = (p.nz + 2 * p.sponge) * (p.ny + 2 * p.sponge) * (p.nx + 2 * p.sponge)
     g = min(p.nshots, args.shot_group or p.nshots)
     tiles = "default"
-    if not args.no_autotune:  # step variants timed on this problem (not timed)
+    if args.variants:
+        fv, bv = (int(x) for x in args.variants.split(","))
+        tiles = {"forward_variant": fv, "forward_chunk": 1, "backward_variant": bv, "backward_chunk": 1}
+        fwi.autotune_set(grid, geom, fwi.Options(ckpt="snapshot", shot_group=args.shot_group), tiles)
+    elif not args.no_autotune:  # step variants timed on this problem (not timed)
         tiles = fwi.autotune(grid, geom, torch.as_tensor(p.v_init, device="cuda"),
                              fwi.Options(ckpt="snapshot", shot_group=args.shot_group), ws=ws)
     fwi.profile(True)
