@@ -39,3 +39,51 @@ def test_reference_arm_prints_one_contract_line():
 def test_reference_arm_other_ranks_do_no_work():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_clock_summary_parses_reasons():
+    """nvidia-smi samples (sm, max, power, active mask, hw_slowdown,
+    hw_thermal, sw_thermal, sw_power_cap): median SM clock, the maximum, and
+    every throttle reason seen Active."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.out = "\n".join([
+        "2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "2055, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ])
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.out = "1500, 2070, 800, 0x8, Active, Not Active, Active, Not Active"
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.out = ""
+    assert c.summary()["reasons"] == ["unavailable"]
+
+
+def test_traffic_record_needs_the_captured_source(tmp_path, monkeypatch):
+    """The ncu traffic of a kernel is reported only for the workload it was
+    captured on and while the step-kernel sources hash as at the capture."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = {"k_bwd_step": {"workload": "w", "source_hash": bench.kernel_source_hash(), "bytes_per_launch": 5.0}}
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.read_traffic("k_bwd_step", "w") == 5.0
+    assert bench.read_traffic("k_bwd_step", "other") is None
+    assert bench.read_traffic("k_fwd_step", "w") is None
+    rec["k_bwd_step"]["source_hash"] = "0" * 16
+    f.write_text(json.dumps(rec))
+    assert bench.read_traffic("k_bwd_step", "w") is None
+
+
+def test_committed_traffic_matches_the_current_kernels():
+    """profiles/traffic.json was captured on the step-kernel sources in the
+    tree (a kernel change without a new capture reports traffic null)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    assert t and all(e["source_hash"] == bench.kernel_source_hash() for e in t.values())
+    assert bench.read_traffic("k_bwd_step", "dipping_300x1000_96shots") > 0
