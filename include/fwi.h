@@ -73,7 +73,7 @@ typedef enum {
    v dt / dx <= FWI_CFL_LIMIT_2D (2-D, 17-point Laplacian) or
    FWI_CFL_LIMIT_3D (3-D, 25-point); calls over it return FWI_ERR_CFL. */
 #define FWI_CFL_LIMIT_2D 0.5546f
-#define FWI_CFL_LIMIT_3D 0.4529f
+#define FWI_CFL_LIMIT_3D 0.4528f
 
 enum { FWI_MISFIT_OLS = 0, FWI_MISFIT_TIME_INTEGRAL = 1 };
 enum { FWI_ILLUM_U2 = 0, FWI_ILLUM_UTT2 = 1 };

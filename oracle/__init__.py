@@ -125,6 +125,25 @@ def _check(rc, name):
         raise ValueError(f"{name}: invalid arguments (code {rc})")
 
 
+# weights of the 8th-order second difference (the C oracle's W8)
+_W8 = (-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0)
+
+
+def stability_limit(ndim: int) -> float:
+    """Largest v dt / dx for which leapfrog with the 8th-order Laplacian is
+    stable: (v dt / dx)^2 ndim |s(pi)| <= 4, s the symbol of the 1-D second
+    difference, s(pi) = w0 + 2 sum_k (-1)^k w_k."""
+    s_pi = _W8[0] + 2.0 * sum((-1) ** k * w for k, w in enumerate(_W8) if k > 0)
+    return 2.0 / np.sqrt(ndim * abs(s_pi))
+
+
+def _check_stable(grid: Grid, v):
+    c = float(np.max(v)) * grid.dt / grid.dx
+    if not c <= stability_limit(grid.ndim):
+        raise ValueError(f"v dt / dx = {c:.4f} above the {grid.ndim}-D stability limit "
+                         f"{stability_limit(grid.ndim):.4f}: the oracle would model noise")
+
+
 def forward(grid: Grid, v, src, rec, wav, *, illum=False, illum_utt=False, hmax=None,
             dump_shot=None, nthreads=0):
     """Forward modelling of every shot.
@@ -137,6 +156,7 @@ def forward(grid: Grid, v, src, rec, wav, *, illum=False, illum_utt=False, hmax=
     lib = _load()
     src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    _check_stable(grid, v)
     seis = np.zeros((ns, grid.nt, nrec))
     out = {"seis": seis}
     il = np.zeros((grid.nz, grid.ny, grid.nx)) if illum else None
@@ -165,6 +185,7 @@ def gradient_for_adjoint_source(grid: Grid, v, src, rec, wav, adj, *, want_pad=F
     lib = _load()
     src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    _check_stable(grid, v)
     adj = np.ascontiguousarray(adj, dtype=np.float64).reshape(ns, grid.nt, nrec)
     grad = np.zeros((grid.nz, grid.ny, grid.nx))
     gpad = np.zeros(grid.padded_shape) if want_pad else None
@@ -185,6 +206,7 @@ def born(grid: Grid, v, dv, src, rec, wav, nthreads=0):
     lib = _load()
     src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    _check_stable(grid, v)
     dv = np.ascontiguousarray(dv, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
     dseis = np.zeros((ns, grid.nt, nrec))
     rc = lib.oracle_born(*grid.args(), _ptr(v), _ptr(dv), ns, _ptr(src), _ptr(wav), nrec,
@@ -200,6 +222,7 @@ def extended_born(grid: Grid, v, dv_ext, src, rec, wav, he, nthreads=0):
     lib = _load()
     src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    _check_stable(grid, v)
     dv_ext = np.ascontiguousarray(dv_ext, dtype=np.float64).reshape(2 * he + 1, grid.nz, grid.ny, grid.nx)
     dseis = np.zeros((ns, grid.nt, nrec))
     rc = lib.oracle_ext_born(*grid.args(), _ptr(v), _ptr(dv_ext), int(he), ns, _ptr(src), _ptr(wav), nrec,
@@ -214,6 +237,7 @@ def extended_migration(grid: Grid, v, src, rec, wav, adj, he, nthreads=0):
     lib = _load()
     src, rec, wav, ns, nrec = _geom(src, rec, wav, grid.nt)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(grid.nz, grid.ny, grid.nx)
+    _check_stable(grid, v)
     adj = np.ascontiguousarray(adj, dtype=np.float64).reshape(ns, grid.nt, nrec)
     image = np.zeros((2 * he + 1, grid.nz, grid.ny, grid.nx))
     rc = lib.oracle_ext_migration(*grid.args(), _ptr(v), ns, _ptr(src), _ptr(wav), nrec, _ptr(rec), _ptr(adj),

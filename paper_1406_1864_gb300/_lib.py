@@ -29,7 +29,7 @@ FWI_SNAP_F32, FWI_SNAP_BF16, FWI_SNAP_F16S = 0, 1, 2
  FWI_OP_PM_HESSIAN) = range(14)
 FWI_HEXT_LIMIT = 6
 FWI_RECV_PLESSIX_MULDER, FWI_RECV_GREEN = 0, 1
-FWI_CFL_LIMIT_2D, FWI_CFL_LIMIT_3D = 0.5546, 0.4529  # v dt / dx limits (include/fwi.h)
+FWI_CFL_LIMIT_2D, FWI_CFL_LIMIT_3D = 0.5546, 0.4528  # v dt / dx limits (include/fwi.h)
 FWI_HMAX_LIMIT = 12
 FWI_BATCH_MAX = 4
 

@@ -225,3 +225,27 @@ def test_planted_adjoint_integral_fails(oracle_mod, monkeypatch):
     monkeypatch.setattr(oracle_mod, "time_integral_adjoint", oracle_mod.time_integral)
     gi = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w, d, misfit="integral")
     assert np.linalg.norm(gi["grad"] - go["grad"]) > 0.1 * np.linalg.norm(go["grad"])
+
+
+def test_stability_limits_of_the_scheme(oracle_mod):
+    """The leapfrog limit from the symbol of the 8th-order second difference,
+    v dt / dx <= 2 / sqrt(ndim |s(pi)|), is the bound the library enforces
+    (its header constants, rounded down to 4 decimals), and the oracle
+    refuses models above it."""
+    from paper_1406_1864_gb300 import _lib as L
+    for ndim, lim in ((2, L.FWI_CFL_LIMIT_2D), (3, L.FWI_CFL_LIMIT_3D)):
+        exact = oracle_mod.stability_limit(ndim)
+        assert lim <= exact < lim + 1e-4, (ndim, exact, lim)
+    # 1-D check of the symbol: the Nyquist mode's growth factor of the
+    # second difference, computed from an explicit stencil application
+    n = 64
+    u = (-1.0) ** np.arange(n)
+    w = oracle_mod._W8
+    lap = w[0] * u + sum(w[k] * (np.roll(u, k) + np.roll(u, -k)) for k in range(1, 5))
+    s_pi = lap[10] / u[10]
+    assert abs(2.0 / np.sqrt(2 * abs(s_pi)) - oracle_mod.stability_limit(2)) <= 1e-15
+    p = W.homogeneous(10, 10, v=2000.0, dx=10.0, dt=0.003, nt=5, src=[[5, 0, 5]], rec=[[0, 0, 0]], sponge=4)
+    g = oracle_mod.Grid.of(p)  # v dt / dx = 0.6 > 0.5546
+    import pytest
+    with pytest.raises(ValueError):
+        oracle_mod.forward(g, p.v_true, p.src, p.rec, p.wavelet)
