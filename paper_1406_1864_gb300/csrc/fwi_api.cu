@@ -13,6 +13,8 @@
 #include "fwi.h"
 #include "fwi_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -26,6 +28,15 @@
 using namespace fwi;
 
 namespace {
+
+// NVTX range over one library call on the host timeline of a tracing tool
+// (nsys and the like); without a tool attached the calls return at once.
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace &) = delete;
+    Trace &operator=(const Trace &) = delete;
+};
 
 thread_local std::string t_err;
 thread_local bool t_prof = false;
@@ -1694,6 +1705,7 @@ fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, c
 fwi_status fwi_forward(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
                        const float *v, float *seis, int save, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_forward");
     if (grid && grid->ndim == 3) {
         if (!v || (!seis && geom && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v or seis is NULL");
         return forward3(grid, geom, opts, save ? FWI_OP_FORWARD_SAVE : FWI_OP_FORWARD, v, seis, nullptr, ws,
@@ -1718,6 +1730,7 @@ fwi_status fwi_adjoint_apply(const fwi_grid *grid, const fwi_geometry *geom, con
                              const float *v, const float *adj_src, float *grad, void *ws, size_t ws_bytes,
                              void *stream)
 {
+    Trace trace_("fwi_adjoint_apply");
     if (grid && grid->ndim == 3)
         return adjoint_apply3(grid, geom, opts, v, adj_src, grad, ws, ws_bytes, static_cast<cudaStream_t>(stream));
     Plan pl;
@@ -1745,6 +1758,7 @@ fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom, 
                                 const float *v, const float *d_obs, float *grad, float *grad_pre, double *misfit,
                                 float *illum, float *offh, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_adjoint_gradient");
     if (grid && grid->ndim == 3) {
         if (offh) return fail(FWI_ERR_INVALID_ARG, "the offset Hessian is 2-D only");
         return gradient3(grid, geom, opts, v, d_obs, grad, grad_pre, misfit, illum, ws, ws_bytes,
@@ -1765,6 +1779,7 @@ fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom, 
 fwi_status fwi_illumination(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
                             const float *v, float *illum, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_illumination");
     if (grid && grid->ndim == 3) {
         if (!v || !illum) return fail(FWI_ERR_INVALID_ARG, "v or illum is NULL");
         return forward3(grid, geom, opts, FWI_OP_ILLUMINATION, v, nullptr, illum, ws, ws_bytes,
@@ -1794,6 +1809,7 @@ fwi_status fwi_illumination(const fwi_grid *grid, const fwi_geometry *geom, cons
 fwi_status fwi_offset_hessian_diag(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
                                    const float *v, float *offh, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_offset_hessian_diag");
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_OFFSET_HESSIAN, true, pl);
     if (s != FWI_OK) return s;
@@ -1818,6 +1834,7 @@ fwi_status fwi_offset_hessian_diag(const fwi_grid *grid, const fwi_geometry *geo
 fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float *scale, int kind, int hmax,
                             float eps, float *out, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_precondition");
     Plan pl;
     fwi_status s = make_plan(grid, nullptr, nullptr, FWI_OP_PRECONDITION, false, pl);
     if (s != FWI_OK) return s;
@@ -1843,6 +1860,7 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
 fwi_status fwi_misfit(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                       const float *d_obs, double *misfit, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_misfit");
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_MISFIT, true, pl);
     if (s != FWI_OK) return s;
@@ -1878,6 +1896,7 @@ fwi_status fwi_misfit(const fwi_grid *grid, const fwi_geometry *geom, const fwi_
 fwi_status fwi_receiver_factor(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int kind,
                                const float *v, float *out, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_receiver_factor");
     fwi_status s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (kind == FWI_RECV_PLESSIX_MULDER) {
@@ -1922,6 +1941,7 @@ fwi_status fwi_receiver_factor(const fwi_grid *grid, const fwi_geometry *geom, c
 fwi_status fwi_plessix_mulder_hessian(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
                                       const float *v, float *out, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_plessix_mulder_hessian");
     // the plan of all shots bounds every run's plan; the run's illumination
     // goes to a buffer after it
     fwi_options dflt;
@@ -1990,6 +2010,7 @@ fwi_status fwi_precondition_receiver(const fwi_grid *grid, const float *grad, co
                                      int hmax, const float *recv, int recv_planes, float eps, float *out, void *ws,
                                      size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_precondition_receiver");
     Plan pl;
     fwi_status s = make_plan(grid, nullptr, nullptr, FWI_OP_PRECONDITION_RECEIVER, false, pl);
     if (s != FWI_OK) return s;
@@ -2022,6 +2043,7 @@ fwi_status fwi_precondition_receiver(const fwi_grid *grid, const float *grad, co
 fwi_status fwi_extended_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int hext,
                              const float *v, const float *dv_ext, float *dseis, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_extended_born");
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_EXT_BORN, true, pl);
     if (s != FWI_OK) return s;
@@ -2049,6 +2071,7 @@ fwi_status fwi_extended_migration(const fwi_grid *grid, const fwi_geometry *geom
                                   const float *v, const float *adj_src, float *image, void *ws, size_t ws_bytes,
                                   void *stream)
 {
+    Trace trace_("fwi_extended_migration");
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_EXT_MIGRATION, true, pl);
     if (s != FWI_OK) return s;
@@ -2108,6 +2131,7 @@ fwi_status prep_dc2(const Plan &pl, const float *v, const float *dv, void *ws, c
 fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                     const float *dv, float *dseis, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_born");
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_BORN, true, pl);
     if (s != FWI_OK) return s;
@@ -2127,6 +2151,7 @@ fwi_status fwi_born(const fwi_grid *grid, const fwi_geometry *geom, const fwi_op
 fwi_status fwi_gauss_newton_hvp(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts,
                                 const float *v, const float *dv, float *hv, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_gauss_newton_hvp");
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_GN_HVP, true, pl);
     if (s != FWI_OK) return s;
@@ -2227,6 +2252,7 @@ fwi_status autotune3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_o
 fwi_status fwi_autotune(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                         void *ws, size_t ws_bytes, void *stream, int *choice)
 {
+    Trace trace_("fwi_autotune");
     if (grid && grid->ndim == 3)
         return autotune3(grid, geom, opts, v, ws, ws_bytes, static_cast<cudaStream_t>(stream), choice);
     Plan pl;
@@ -2427,6 +2453,7 @@ fwi_status fwi_batch_gradient(int nmodels, const fwi_grid *grids, const fwi_geom
                               float *const *grad, float *const *grad_pre, double *misfit, float *const *illum,
                               float *const *offh, void *ws, size_t ws_bytes, void *stream)
 {
+    Trace trace_("fwi_batch_gradient");
     BatchCall bc;
     fwi_status s = batch_prepare(nmodels, grids, geoms, opts, v, d_obs, grad, grad_pre, misfit, illum, offh, ws,
                                  ws_bytes, bc);
@@ -2443,6 +2470,7 @@ fwi_status fwi_exec_gradient_create(int nmodels, const fwi_grid *grids, const fw
                                     float *const *illum, float *const *offh, void *ws, size_t ws_bytes,
                                     void *stream, fwi_exec **out)
 {
+    Trace trace_("fwi_exec_gradient_create");
     if (!out) return fail(FWI_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!stream) return fail(FWI_ERR_INVALID_ARG, "recording a graph needs a stream other than the default stream");
@@ -2500,6 +2528,7 @@ fwi_status fwi_exec_input_ready(fwi_exec *ex, void *stream)
 
 fwi_status fwi_exec_run(fwi_exec *ex, void *stream)
 {
+    Trace trace_("fwi_exec_run");
     if (!ex || !ex->exec) return fail(FWI_ERR_INVALID_ARG, "exec is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     t_ev_recorded = ex->prof && t_prof && t_ev[0];
@@ -2565,6 +2594,7 @@ fwi_status noalloc_scratch(void **ptr)
 extern "C" fwi_status fwi_forward_noalloc(const fwi_grid *grid, const fwi_geometry *geom, const float *v,
                                           float *seis, void *stream)
 {
+    Trace trace_("fwi_forward_noalloc");
     Plan pl;
     fwi_status s = make_plan(grid, geom, nullptr, FWI_OP_FORWARD, true, pl);
     if (s != FWI_OK) return s;
