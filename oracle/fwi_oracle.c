@@ -10,10 +10,11 @@
  *
  * What it computes (paper sections / equations in brackets):
  *   - the constant-density acoustic wave equation 1/v^2 u_tt - lap u = delta f
- *     [Sec. 2, below the OLS misfit], discretised by the readings listed in the
- *     repository design notes: 8th-order centred Laplacian, second-order
- *     leapfrog in time, and an absorbing sponge u_tt + 2 eta u_t outside the
- *     physical model, the model padded by edge replication;
+ *     [Sec. 2, below the OLS misfit]; the paper names only a time-domain
+ *     finite-difference scheme, so this one is a reading: 8th-order centred
+ *     Laplacian, second-order leapfrog in time, and an absorbing sponge
+ *     u_tt + 2 eta u_t outside the physical model, the model padded by edge
+ *     replication;
  *   - synthetic traces d = R u at the receivers [Sec. 2, OLS misfit];
  *   - the adjoint (back-propagated residual) wavefield and the zero-lag
  *     cross-correlation gradient g = 2/v^3 sum_s int u_tt v_s dt [Sec. 2],
