@@ -30,8 +30,8 @@ central finite differences, the cumulative-source identity of Sec. 2 and brute
 force sums over dumped wavefields. The integral-misfit gradient is pinned
 exactly against the OLS gradient of the integrated wavefield (Sec. 2), and
 Eq. 3's form of it, -sum int u v dt with v = (2/v^3) dLambda/dt (Lambda the
-back-propagated integrated residual), is a continuum identity that the
-discrete gradient meets to a few per cent, converging under refinement.
+back-propagated integrated residual), holds exactly in the discrete scheme's
+undamped interior with a forward time difference.
 """
 from __future__ import annotations
 
