@@ -11,8 +11,9 @@ loss.backward(), with every wave-equation step in the library's kernels.
 
 Each call owns its workspace (the forward checkpoints live there until the
 backward pass has run), so several calls may be in flight in one graph.
-opts.ckpt / opts.snap choose the checkpoints: the exact sponge-band mode, or
-about sqrt(nt) whole-field snapshots in F32, bfloat16 or scaled float16.
+opts.ckpt / opts.snap choose the checkpoints: the exact sponge-band mode (2-D),
+or about sqrt(nt) whole-field snapshots in F32, bfloat16 or scaled float16
+(2-D and 3-D).
 """
 from __future__ import annotations
 
@@ -43,7 +44,9 @@ class _Traces(torch.autograd.Function):
 
 def traces(v: torch.Tensor, grid: fwi.Grid, geom: fwi.Geometry,
            opts: fwi.Options | None = None) -> torch.Tensor:
-    """Traces [nshots, nt, nrec] of velocity v [nz, nx]; differentiable in v."""
+    """Traces [nshots, nt, nrec] of velocity v (grid.shape: [nz, nx], or
+    [nz, ny, nx] on a 3-D grid, where opts needs ckpt="snapshot" and all shots
+    in one group); differentiable in v."""
     return _Traces.apply(v, grid, geom, opts)
 
 
