@@ -399,3 +399,35 @@ def test_3d_autotune_set_checks_the_variants(lib):
         st = lib.fwi_autotune_set(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o), ch)
         assert (st == L.FWI_OK) == ok, (fv, bv, st)
     assert lib.fwi_autotune_reset() == L.FWI_OK
+
+
+def test_3d_forward_save_and_adjoint_apply_errors(lib):
+    """3-D fwi_forward(save = 1) and fwi_adjoint_apply reject, before any
+    device work: sponge checkpoints, shot groups smaller than the shots,
+    NULL outputs and small workspaces."""
+    from paper_1406_1864_gb300 import _lib as L
+    g = L.FwiGrid(3, 20, 24, 28, 10.0, 1e-3, 100, 8, 3000.0, 0.05)
+    src = np.array([[0, 12, 3], [0, 12, 20]], np.int32)
+    rec = np.array([[[0, 12, 8], [0, 12, 16]]] * 2, np.int32)
+    ge = L.FwiGeometry(2, 2, src.ctypes.data, rec.ctypes.data, 1)
+    o = L.FwiOptions(0, 0, -1, 1, 1e-3)
+    p1, big = ctypes.c_void_p(256), 1 << 40
+
+    def fwd(opts, seis=ctypes.c_void_p(256), nbytes=big):
+        return lib.fwi_forward(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(opts) if opts else None,
+                               ctypes.c_void_p(256), seis, 1, p1, nbytes, None)
+
+    assert fwd(None) == L.FWI_ERR_INVALID_ARG and b"SNAPSHOT" in lib.fwi_last_error()
+    assert fwd(o) == L.FWI_ERR_INVALID_ARG                      # sponge checkpoints
+    o.ckpt = L.FWI_CKPT_SNAPSHOT
+    o.shot_group = 1
+    assert fwd(o) == L.FWI_ERR_INVALID_ARG and b"shot_group" in lib.fwi_last_error()
+    o.shot_group = 0
+    assert fwd(o, seis=None) == L.FWI_ERR_INVALID_ARG
+    assert fwd(o, nbytes=16) == L.FWI_ERR_NOMEM
+    st = lib.fwi_adjoint_apply(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o), ctypes.c_void_p(256),
+                               ctypes.c_void_p(256), None, p1, big, None)
+    assert st == L.FWI_ERR_INVALID_ARG                          # grad is NULL
+    st = lib.fwi_adjoint_apply(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o), ctypes.c_void_p(256),
+                               ctypes.c_void_p(256), ctypes.c_void_p(256), p1, 16, None)
+    assert st == L.FWI_ERR_NOMEM
