@@ -39,3 +39,23 @@ def test_bounded_wait_runs_out_and_the_context_survives(torch_cuda, oracle_mod, 
     seis = fwi.forward(grid, geom, torch.as_tensor(np.ascontiguousarray(p.v_true), device="cuda")).cpu().numpy()
     ref = oracle_mod.forward(oracle_mod.Grid.of(p), p.v_true, p.src, p.rec, p.wavelet.astype(np.float64))["seis"]
     assert np.linalg.norm(seis - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_non_finite_wavefield_is_reported(torch_cuda, oracle_mod):
+    """A non-finite source sample (a blow-up injected on the host, no GPU
+    fault) makes the wavefield non-finite; the finite check at the end of the
+    time loop turns it into FWI_ERR_UNSTABLE, and the next call with a finite
+    wavelet models normally."""
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import fwi, _lib as L
+    p = W.dipping(nz=20, nx=40, dx=10.0, dt=1e-3, nt=60, ns=2, nrec=10, rec_step=4, f0=15.0, sponge=5)
+    grid, geom = fwi.from_problem(p)
+    v = torch.as_tensor(np.ascontiguousarray(p.v_true), device="cuda")
+    bad_w = geom.wavelet.clone()
+    bad_w[1, 5] = float("nan")
+    with pytest.raises(L.FwiError) as e:
+        fwi.forward(grid, fwi.Geometry(p.src, p.rec, bad_w), v)
+    assert e.value.status == L.FWI_ERR_UNSTABLE
+    seis = fwi.forward(grid, geom, v).cpu().numpy()
+    ref = oracle_mod.forward(oracle_mod.Grid.of(p), p.v_true, p.src, p.rec, p.wavelet.astype(np.float64))["seis"]
+    assert np.linalg.norm(seis - ref) <= 1e-5 * np.linalg.norm(ref)
