@@ -27,7 +27,10 @@ parts that are clearest in numpy, each following the paper:
 Parity pins: none of these functions is trusted on its own; tests/test_oracle_*
 check them against closed forms (2-D Green's function), adjoint dot products,
 central finite differences, the cumulative-source identity of Sec. 2 and brute
-force sums over dumped wavefields. The integral-misfit gradient is pinned
+force sums over dumped wavefields. The offset-preconditioner scale is pinned
+against explicit sums over every negative and positive offset, and the
+water-level division against hand cases with exact quotients. The
+integral-misfit gradient is pinned
 exactly against the OLS gradient of the integrated wavefield (Sec. 2), and
 Eq. 3's form of it, -sum int u v dt with v = (2/v^3) dLambda/dt (Lambda the
 back-propagated integrated residual), holds exactly in the discrete scheme's
