@@ -414,12 +414,17 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
    scratch array the library holds itself: FWI_NOALLOC_SCRATCH_BYTES of device
    memory, reserved on every GPU that loads this part of the library and kept
    until the process exits. It allocates no device memory.
+   Only 2-D grids (ndim = 2).
    v     DEVICE [nz][nx] velocity; seis DEVICE [nshots][nt][nrec] output traces.
-   Errors: FWI_ERR_NOMEM (with a message giving both sizes) when the problem's
-   forward workspace, fwi_workspace_bytes(..., FWI_OP_FORWARD, ...), exceeds
-   FWI_NOALLOC_SCRATCH_BYTES; otherwise as fwi_forward.
-   The first call on a device looks up the scratch array's device address
-   (cudaGetSymbolAddress), so make that first call before any stream capture.
+   Errors, all returned before any device work: FWI_ERR_INVALID_ARG for a NULL
+   or 3-D grid, a NULL geometry, bad coordinates, a NULL v or (nrec > 0) a NULL
+   seis, as fwi_forward; FWI_ERR_NOMEM (with a message giving both sizes) when
+   the problem's forward workspace, fwi_workspace_bytes(..., FWI_OP_FORWARD,
+   ...), exceeds FWI_NOALLOC_SCRATCH_BYTES. Like fwi_forward, the call waits
+   for its stream at the end to read the kernels' status word.
+   The first call on a device (and the first after a device reset) looks up
+   the scratch array's device address (cudaGetSymbolAddress), so make that
+   first call before any stream capture.
    All calls share the one array, which keeps the previous call's contents
    (every call clears what must start at zero): calls that may overlap on the
    GPU -- on different streams, or from different host threads -- race and

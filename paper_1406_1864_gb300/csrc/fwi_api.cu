@@ -13,6 +13,8 @@
 #include "fwi.h"
 #include "fwi_internal.h"
 
+#include <cudaTypedefs.h>
+
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
@@ -2568,24 +2570,59 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[FWI_NOALLOC_SCR
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+struct NoallocSlot {
+    void *ptr;               // device address of the scratch array
+    unsigned long long ctx;  // context it was looked up in
+};
+NoallocSlot g_noalloc[NOALLOC_MAX_DEVICES] = {};
+
+// Unique id of the calling thread's current context; false when no context
+// is current yet (or the driver entry points are unavailable).
+bool current_context_id(unsigned long long &id)
+{
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+        fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, &id) == CUDA_SUCCESS;
+}
 
 // Device address of the scratch array on the current device (host code sees
-// only a host-side stand-in under its name). Set up once per device.
+// only a host-side stand-in under its name). Looked up once per device and
+// context: after a device reset the new context may place the array
+// elsewhere, so a changed context id triggers a new lookup.
 fwi_status noalloc_scratch(void **ptr)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(FWI_ERR_INVALID_ARG, "device %d out of range", dev);
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(id);
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoallocSlot &sl = g_noalloc[dev];
+    if (!sl.ptr || !have_id || sl.ctx != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress of the library scratch");
-        g_noalloc_ptr[dev] = p;
+        if (!have_id && !current_context_id(id)) id = 0; // the lookup made the context current
+        sl.ptr = p;
+        sl.ctx = id;
     }
-    *ptr = g_noalloc_ptr[dev];
+    *ptr = sl.ptr;
     return FWI_OK;
 }
 

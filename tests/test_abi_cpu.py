@@ -431,3 +431,28 @@ def test_3d_forward_save_and_adjoint_apply_errors(lib):
     st = lib.fwi_adjoint_apply(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o), ctypes.c_void_p(256),
                                ctypes.c_void_p(256), ctypes.c_void_p(256), p1, 16, None)
     assert st == L.FWI_ERR_NOMEM
+
+
+def test_forward_noalloc_argument_errors(lib):
+    """fwi_forward_noalloc rejects bad arguments before any device work and
+    before it looks up its scratch array's address: on this GPU-less host a
+    call that got that far would fail with a CUDA error instead."""
+    from paper_1406_1864_gb300 import _lib as L
+    g, ge, o, (src, rec) = _structs()
+    p1 = ctypes.c_void_p(256)
+
+    def call(grid=g, geom=ge, v=p1, seis=p1):
+        return lib.fwi_forward_noalloc(ctypes.byref(grid) if grid is not None else None,
+                                       ctypes.byref(geom) if geom is not None else None, v, seis, None)
+
+    assert call(grid=None) == L.FWI_ERR_INVALID_ARG and b"grid is NULL" in lib.fwi_last_error()
+    g3 = L.FwiGrid(3, 20, 24, 28, 10.0, 1e-3, 100, 8, 3000.0, 0.05)
+    assert call(grid=g3) == L.FWI_ERR_INVALID_ARG and b"2-D" in lib.fwi_last_error()
+    assert call(geom=None) == L.FWI_ERR_INVALID_ARG and b"geometry is NULL" in lib.fwi_last_error()
+    assert call(v=None) == L.FWI_ERR_INVALID_ARG and b"NULL" in lib.fwi_last_error()
+    assert call(seis=None) == L.FWI_ERR_INVALID_ARG and b"NULL" in lib.fwi_last_error()
+    src[0, 0] = 30  # row out of range
+    assert call() == L.FWI_ERR_INVALID_ARG and b"outside" in lib.fwi_last_error()
+    src[0, 0] = 0
+    big = L.FwiGrid(2, 1500, 1, 1500, 10.0, 1e-3, 10, 20, 3000.0, 0.05)
+    assert call(grid=big) == L.FWI_ERR_NOMEM and b"scratch" in lib.fwi_last_error()
