@@ -354,6 +354,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
             if (s_desc[k].tile >= 0) issue(s_desc[k], k);
 
     float2 acc_i[RZ][2];
+    // offset Hessian of the thread's points 0..3: even h: [0] = (0, 1), [1] = (2, 3);
+    // odd h: [0] = (1, 2), [1] = (0, 3)
     float2 acc_h[NH][2];
     int cur_tile = -1, cur_model = 0, bi = 0, bj = 0, i0 = 0, j0 = 0;
     bool tile_sponge = false, colok = false;
@@ -379,20 +381,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
 #pragma unroll
                     for (int h = 0; h < NH; ++h)
                         if (h <= a0.hmax)
-                            atomicAdd(a.acc_offh + h * nphys + o, (p & 1) ? acc_h[h][p >> 1].y : acc_h[h][p >> 1].x);
+                            atomicAdd(a.acc_offh + h * nphys + o,
+                                      (h & 1) ? (p == 0 ? acc_h[h][1].x : p == 1 ? acc_h[h][0].x
+                                                 : p == 2 ? acc_h[h][0].y : acc_h[h][1].y)
+                                              : ((p & 1) ? acc_h[h][p >> 1].y : acc_h[h][p >> 1].x));
                 }
             }
         }
     };
-
-    // receiver entry of this thread for an item (local index, receiver)
-    auto fetch_rec = [&](const ItemDesc &v, int2 &en) {
-        en = make_int2(-1, 0);
-        const int e = v.rb + (int)threadIdx.x;
-        if (v.tile >= 0 && e < v.re) en = B.m[NM == 1 ? 0 : v.model].rt.ent[e];
-    };
-    int2 rec_en;
-    fetch_rec(s_desc[0], rec_en);
 
     int k = 0;
     for (;; ++k) {
@@ -407,14 +403,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
             if (threadIdx.x == 32) cp_async_wait_all(); // (none in flight once the cursor is done)
             break;
         }
-        const ItemDesc nx = s_desc[(k + 1) % DESC_RING];
         const int s = now.s;
         const int mi = NM == 1 ? 0 : now.model;
         const FwdArgs &a = B.m[mi];
         const StepCommon &c = a.c;
         const Lay2D &L = c.L;
-        const int2 now_en = rec_en;
-        fetch_rec(nx, rec_en);
         if (now.tile != cur_tile || mi != cur_model) {
             if (cur_tile >= 0) flush();
             cur_tile = now.tile;
@@ -439,6 +432,20 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
         }
         const int st = k % STAGES;
         const bool ready = stage_ready<STAGES>(bars, k, &s_abort);
+        // receiver extraction d^n = R u^n of the item's shots: the entries of
+        // (tile, s) and (tile, s + 1) are consecutive in the receiver table.
+        // One warp-uniform test skips the (common) tiles without receivers.
+        const int rend = (SPI > 1 && now.nsh > 1) ? now.re1 : now.re;
+        if (ready && rend > now.rb) {
+#pragma unroll 1
+            for (int e = now.rb + (int)threadIdx.x; e < rend; e += TPB) {
+                const int2 en = a.rt.ent[e];
+                const int sh = (SPI > 1 && e >= now.re) ? 1 : 0;
+                const int zl = en.x / TX, xl = en.x - zl * TX;
+                a.seis[((long long)(s + sh) * c.nt + a.n) * c.nrec + en.y] =
+                    R::halo(smem, st, sh)[(zl + RADIUS) * TXS + HX + xl];
+            }
+        }
         // the item's shots, one after the other (accumulators are shared)
 #pragma unroll 1
         for (int sh = 0; sh < SPI && ready; ++sh) {
@@ -448,20 +455,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
             const float *pm = R::point(smem, st, sh);
             float *up = a.uout + (long long)ss * L.fstride;
 
-            // receiver extraction d^n = R u^n
-            float *seis_s = a.seis + ((long long)ss * c.nt + a.n) * c.nrec;
-            if (sh == 0 && now_en.x >= 0) {
-                const int zl = now_en.x / TX, xl = now_en.x - zl * TX;
-                seis_s[now_en.y] = sm[(zl + RADIUS) * TXS + HX + xl];
-            }
-            const int rb = sh == 0 ? now.rb + TPB : now.rb1, re = sh == 0 ? now.re : now.re1;
-            for (int e = rb + (int)threadIdx.x; e < re; e += TPB) {
-                const int2 en = a.rt.ent[e];
-                const int zl = en.x / TX, xl = en.x - zl * TX;
-                seis_s[en.y] = sm[(zl + RADIUS) * TXS + HX + xl];
-            }
-            const int sslot = sh == 0 ? source_slot<RZ>(now.si, now.sj, i0, j0)
-                                      : source_slot<RZ>(now.si1, now.sj1, i0, j0);
+            // the shot's source cell, if it lies in this tile (warp-uniform)
+            const int si = sh == 0 ? now.si : now.si1, sj = sh == 0 ? now.sj : now.sj1;
+            const bool src_tile = (unsigned)(si - bi) < (unsigned)TZ && (unsigned)(sj - bj) < (unsigned)TX;
+            const int sslot = src_tile ? source_slot<RZ>(si, sj, i0, j0) : -1;
 
             float4 zc[RZ + 2 * RADIUS];
 #pragma unroll
@@ -480,11 +477,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                 if (!a.last) {
                     float2 q[2];
                     lap4<WL>(q, w, zc, r);
-                    const float amp = (sh == 0 ? now.amp : now.amp1) * c.src_scale;
-                    if (sslot == r * 4 + 0) q[0].x += amp;
-                    if (sslot == r * 4 + 1) q[0].y += amp;
-                    if (sslot == r * 4 + 2) q[1].x += amp;
-                    if (sslot == r * 4 + 3) q[1].y += amp;
+                    if (src_tile) {
+                        const float amp = (sh == 0 ? now.amp : now.amp1) * c.src_scale;
+                        if (sslot == r * 4 + 0) q[0].x += amp;
+                        if (sslot == r * 4 + 1) q[0].y += amp;
+                        if (sslot == r * 4 + 2) q[1].x += amp;
+                        if (sslot == r * 4 + 3) q[1].y += amp;
+                    }
                     const float4 um4 = lds4(&pm[(ty * RZ + r) * TX + 4 * tx]);
                     const float4 c24 = lds4(&c2s[(ty * RZ + r) * TX + 4 * tx]);
                     float2 out[2];
@@ -531,7 +530,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                     acc_i[r][1] = fma2(u0[1], u0[1], acc_i[r][1]);
                 }
                 if (WITH_H) {
-                    // u(x+h) u(x-h); even h on aligned lane pairs
+                    // u(x+h) u(x-h); even h: points (0, 1) and (2, 3) on
+                    // aligned lane pairs; odd h: (1, 2) paired, 0 and 3 scalar
 #pragma unroll
                     for (int h = 0; h < NH; ++h) {
                         if ((h & 1) == 0) {
@@ -540,11 +540,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                                 acc_h[h][q] = fma2(f2(w[WL + 2 * q + h], w[WL + 2 * q + 1 + h]),
                                                    f2(w[WL + 2 * q - h], w[WL + 2 * q + 1 - h]), acc_h[h][q]);
                         } else {
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                acc_h[h][q].x = fmaf(w[WL + 2 * q + h], w[WL + 2 * q - h], acc_h[h][q].x);
-                                acc_h[h][q].y = fmaf(w[WL + 2 * q + 1 + h], w[WL + 2 * q + 1 - h], acc_h[h][q].y);
-                            }
+                            // odd h: points 1 and 2 on an aligned lane pair, 0 and 3 scalar
+                            acc_h[h][0] = fma2(f2(w[WL + 1 + h], w[WL + 2 + h]), f2(w[WL + 1 - h], w[WL + 2 - h]),
+                                               acc_h[h][0]);
+                            acc_h[h][1].x = fmaf(w[WL + h], w[WL - h], acc_h[h][1].x);
+                            acc_h[h][1].y = fmaf(w[WL + 3 + h], w[WL + 3 - h], acc_h[h][1].y);
                         }
                     }
                 }
