@@ -1632,13 +1632,21 @@ fwi_status make_batch(int nm, const fwi_grid *grids, const fwi_geometry *geoms, 
         if (grids[k].nt != grids[0].nt)
             return fail(FWI_ERR_INVALID_ARG, "model %d has nt=%d, model 0 nt=%d: a batch shares nt", k, grids[k].nt,
                         grids[0].nt);
-        if (k > 0) { // a launch runs one kernel: model 0's tile variants for all
-            const StepKind fk = pl[k].with_offh ? STEP_FWD_OFFH : STEP_FWD;
-            pl[k].tf = make_tiling(pl[k].L, pl[k].ns, fk, pl[0].tf.variant, pl[0].tf.chunk, pl[k].hmax);
-            pl[k].tb = make_tiling(pl[k].L, pl[k].ns, STEP_BWD, pl[0].tb.variant, pl[0].tb.chunk);
-        }
         base[k] = total;
         total = align_up(total + pl[k].total);
+    }
+    // a launch runs one kernel for all models: the tile variants and chunks
+    // of the model with the most work (padded points x shots); the workspace
+    // does not depend on the tiling
+    int kmax = 0;
+    for (int k = 1; k < nm; ++k)
+        if ((long long)pl[k].L.nzp * pl[k].L.nxp * pl[k].ns > (long long)pl[kmax].L.nzp * pl[kmax].L.nxp * pl[kmax].ns)
+            kmax = k;
+    for (int k = 0; k < nm; ++k) {
+        if (k == kmax) continue;
+        const StepKind fk = pl[k].with_offh ? STEP_FWD_OFFH : STEP_FWD;
+        pl[k].tf = make_tiling(pl[k].L, pl[k].ns, fk, pl[kmax].tf.variant, pl[kmax].tf.chunk, pl[k].hmax);
+        pl[k].tb = make_tiling(pl[k].L, pl[k].ns, STEP_BWD, pl[kmax].tb.variant, pl[kmax].tb.chunk);
     }
     return FWI_OK;
 }

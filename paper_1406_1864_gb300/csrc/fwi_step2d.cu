@@ -865,7 +865,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         }
         // prefetch for the next item: adjoint entry, and its checkpoint values
         // when it is on the same tile
-        fetch_adj(nx, adj_loc, adj_val);
+        if (nx.re > nx.rb) {
+            fetch_adj(nx, adj_loc, adj_val);
+        } else { // (warp-uniform) no receivers in the next item's tile
+            adj_loc = -1;
+            adj_val = 0.f;
+        }
         bval_ok = tile_sponge && nx.tile == cur_tile && (NM == 1 || nx.model == cur_model);
         if (bval_ok) fetch_band(nx.s, bval);
         if (has_rec) __syncthreads();
@@ -889,7 +894,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             const float *pua = R::point(smem, st, 0);
             const float *ppb = R::point(smem, st, 1);
             const long long so = (long long)s * L.fstride;
-            const int sslot = source_slot<RZ>(now, i0, j0);
+            // the shot's source cell, if it lies in this tile (warp-uniform)
+            const bool src_tile = (unsigned)(now.si - bi) < (unsigned)TZ && (unsigned)(now.sj - bj) < (unsigned)TX;
+            const int sslot = src_tile ? source_slot<RZ>(now, i0, j0) : -1;
 
             // q^{m-1} = Lhat u^{m-1} + f(t_{m-1}) delta_s (as in the forward
             // step m-1; done above with the extended image), then Lhat psi^{m+1};
@@ -915,7 +922,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 #pragma unroll
             for (int r = 0; r < RZ; ++r) {
                 const float amp = now.amp * c.src_scale;
-                if constexpr (HE == 0) {
+                if (HE == 0 && src_tile) {
                     if (sslot == r * 4 + 0) qu[r][0].x += amp;
                     if (sslot == r * 4 + 1) qu[r][0].y += amp;
                     if (sslot == r * 4 + 2) qu[r][1].x += amp;

@@ -87,3 +87,24 @@ def test_committed_traffic_matches_the_current_kernels():
     t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     assert t and all(e["source_hash"] == bench.kernel_source_hash() for e in t.values())
     assert bench.read_traffic("k_bwd_step", "dipping_300x1000_96shots") > 0
+
+
+def test_traffic_tool_reads_ncu_csv(tmp_path):
+    """The traffic tool keys launches by step kind and averages DRAM bytes
+    (read + write) over each kind's captured launches."""
+    from paper_1406_1864_gb300 import traffic
+    assert traffic.key_of("void k_fwd_step<1, 12, 1, 3, 4, 1, 2, 11>(Batch<FwdArgs, T6>)") == \
+        "k_fwd_step<offset Hessian>"
+    assert traffic.key_of("void k_fwd_step<2, 4, 0, 2, 4, 1, 2, 13>(Batch<FwdArgs, T6>)") == "k_fwd_step"
+    assert traffic.key_of("void k_bwd_step<2, 2, 4, 1, 0>(Batch<BwdArgs, T4>)") == "k_bwd_step"
+    assert traffic.key_of("k_prep_c2(...)") is None
+    hdr = '"ID","Kernel Name","Metric Name","Metric Value"\n'
+    rows = []
+    for i, (rd, wr) in enumerate([(100.0, 20.0), (140.0, 40.0)]):
+        name = "void k_bwd_step<2, 2, 4, 1, 0>(Batch<BwdArgs, T4>)"
+        rows.append(f'"{i}","{name}","dram__bytes_read.sum","{rd:,.0f}"\n')
+        rows.append(f'"{i}","{name}","dram__bytes_write.sum","{wr:,.0f}"\n')
+    f = tmp_path / "t.csv"
+    f.write_text("==PROF== noise\n" + hdr + "".join(rows))
+    per = traffic.read_csv(str(f))
+    assert list(per) == ["k_bwd_step"] and sorted(per["k_bwd_step"][1]) == [120.0, 180.0]
