@@ -14,13 +14,15 @@ python -m paper_1406_1864_gb300.convergence [options].
 
 Defaults: 150 x 460 cells of 20 m (3 km x 9.2 km), 80 shots at 20 m depth,
 receivers at 20 m depth on every cell (full aperture), 1.2 s recording
-(nt 800 at dt 1.5 ms), Ricker f0 6 Hz. Reports per iteration the misfit
-(relative to the first), the relative model error ||v - v_true|| / ||v_0 -
-v_true|| over the whole model and over the depth band from a quarter to half
-of the model depth (0.75 - 1.5 km: the deepest part a 1.2 s recording
-constrains; below about v T / 2 the forward and back-propagated fields do
-not meet and the gradient is zero), and gradient and misfit-evaluation
-counts, as one JSON line (and into --out).
+(nt 800 at dt 1.5 ms; --record sets it: reflections from the bottom of the
+model arrive after about 2.5 s), Ricker f0 6 Hz. Reports per iteration the
+misfit (relative to the first), the relative model error ||v - v_true|| /
+||v_0 - v_true|| over the whole model, over its upper and lower halves, and
+over the depth band from a quarter to half of the model depth (0.75 - 1.5
+km: the deepest part a 1.2 s recording constrains; below about v T / 2 the
+forward and back-propagated fields do not meet and the gradient is zero),
+and gradient and misfit-evaluation counts, as one JSON line (and into
+--out).
 """
 from __future__ import annotations
 
@@ -53,14 +55,16 @@ def run(p, configs, iters, max_update):
     d_obs = fwi.forward(grid, geom, v_true)
     v0 = torch.as_tensor(p.v_init, device="cuda")
     z0, z1 = p.nz // 4, p.nz // 2
-    e0_deep = float(torch.linalg.vector_norm((v0[z0:z1] - v_true[z0:z1]).double()))
+    bands = {"deep_band": (z0, z1), "upper_half": (0, p.nz // 2), "lower_half": (p.nz // 2, p.nz)}
+    e0b = {k: float(torch.linalg.vector_norm((v0[a:b] - v_true[a:b]).double())) for k, (a, b) in bands.items()}
     ws = fwi.Workspace()
     out = {}
     for name, method, opts, recv in configs:
-        deep = [1.0]
+        err_b = {k: [1.0] for k in bands}
 
         def cb(k, x, ev, h):
-            deep.append(float(torch.linalg.vector_norm((x[z0:z1] - v_true[z0:z1]).double())) / e0_deep)
+            for kb, (a, b) in bands.items():
+                err_b[kb].append(float(torch.linalg.vector_norm((x[a:b] - v_true[a:b]).double())) / e0b[kb])
         obj = I.FwiObjective(grid, geom, d_obs, opts, ws=ws, mute_top=I.default_mute(geom), receiver=recv,
                              receiver_every=10)
         lo, hi = I.velocity_bounds(grid, v0)
@@ -79,8 +83,9 @@ def run(p, configs, iters, max_update):
         torch.cuda.synchronize()
         m = np.asarray(hist.misfit)
         out[name] = {"method": method, "misfit": (m / m[0]).tolist(), "model_error": hist.model_error,
-                     "model_error_deep_band": deep, "gradients": obj.n_gradients, "misfits": obj.n_misfits,
-                     "seconds": time.perf_counter() - t0}
+                     "model_error_deep_band": err_b["deep_band"], "model_error_upper_half": err_b["upper_half"],
+                     "model_error_lower_half": err_b["lower_half"], "gradients": obj.n_gradients,
+                     "misfits": obj.n_misfits, "seconds": time.perf_counter() - t0}
     return out
 
 
@@ -91,10 +96,12 @@ def main():
     ap.add_argument("--iters", type=int, default=0, help="0: the paper's count (200 / 270)")
     ap.add_argument("--shots", type=int, default=80)
     ap.add_argument("--max-update", type=float, default=50.0)
+    ap.add_argument("--record", type=float, default=1.2, help="recording length in s (dt 1.5 ms)")
+    ap.add_argument("--f0", type=float, default=6.0, help="Ricker peak frequency in Hz")
     ap.add_argument("--out", default="")
     ap.add_argument("--only", default="", help="comma-separated configuration names")
     args = ap.parse_args()
-    p = problem(ns=args.shots, example=args.example)
+    p = problem(ns=args.shots, example=args.example, nt=int(round(args.record / 1.5e-3)), f0=args.f0)
     if args.example == 1:
         iters = args.iters or 200
         configs = [("ols", "lbfgs", fwi.Options(misfit="ols", precond="illum"), None),
@@ -111,12 +118,15 @@ def main():
         configs = [c for c in configs if c[0] in keep]
     res = run(p, configs, iters, args.max_update)
     line = {"example": args.example, "workload": f"dipping {p.nz}x{p.nx}, dx {p.dx} m, {p.nshots} shots, "
-            f"nt {p.nt}, dt {p.dt}", "iterations": iters, "results": res}
+            f"nt {p.nt}, dt {p.dt}, f0 {args.f0} Hz, max update {args.max_update} m/s", "iterations": iters,
+            "results": res}
     if args.out:
         with open(args.out, "w") as f:
             json.dump(line, f)
     summary = {k: {"misfit": round(v["misfit"][-1], 4), "model_error": round(v["model_error"][-1], 4),
-                   "deep_band": round(v["model_error_deep_band"][-1], 4), "gradients": v["gradients"],
+                   "deep_band": round(v["model_error_deep_band"][-1], 4),
+                   "upper_half": round(v["model_error_upper_half"][-1], 4),
+                   "lower_half": round(v["model_error_lower_half"][-1], 4), "gradients": v["gradients"],
                    "misfits": v["misfits"], "seconds": round(v["seconds"], 1)} for k, v in res.items()}
     print(json.dumps({"example": args.example, "iterations": iters, "final": summary}), flush=True)
 
