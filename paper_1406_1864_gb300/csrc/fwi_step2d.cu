@@ -884,7 +884,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             // the padded grid), for the extended image
             if (ready) {
                 tile_lap<RZ, TXS, HX>(qu, su, tx, ty);
-                add_source<RZ>(qu, source_slot<RZ>(now, i0, j0), now.amp * c.src_scale);
+                if ((unsigned)(now.si - bi) < (unsigned)TZ && (unsigned)(now.sj - bj) < (unsigned)TX)
+                    add_source<RZ>(qu, source_slot<RZ>(now, i0, j0), now.amp * c.src_scale);
                 q_own_to_smem<RZ, HE>(qs, qu, i0, j0, L, tx, ty);
                 q_edges_to_smem<RZ, HE, TXS, HX>(qs, su, now, bi, bj, L, c.src_scale);
             }
@@ -1125,7 +1126,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
             if (ready && !a.last) {
                 const float *su = R::halo(smem, st, 0);
                 tile_lap<RZ, TXS, HX>(qu, su, tx, ty);
-                add_source<RZ>(qu, source_slot<RZ>(now, i0, j0), now.amp * c.src_scale);
+                if ((unsigned)(now.si - bi) < (unsigned)TZ && (unsigned)(now.sj - bj) < (unsigned)TX)
+                    add_source<RZ>(qu, source_slot<RZ>(now, i0, j0), now.amp * c.src_scale);
                 q_own_to_smem<RZ, HE>(qs, qu, i0, j0, L, tx, ty);
                 q_edges_to_smem<RZ, HE, TXS, HX>(qs, su, now, bi, bj, L, c.src_scale);
             }
@@ -1134,9 +1136,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
         if (ready) {
             const float *su = R::halo(smem, st, 0);
             const float *sd = R::halo(smem, st, 1);
-            // Born traces du^n = R du^n
-            if (a.dseis != nullptr) {
+            // Born traces du^n = R du^n (one warp-uniform test skips the
+            // tiles without receivers)
+            if (now.re > now.rb) {
                 float *ds = a.dseis + ((long long)s * c.nt + a.n) * c.nrec;
+#pragma unroll 1
                 for (int e = now.rb + (int)threadIdx.x; e < now.re; e += TPB) {
                     const int2 en = a.rt.ent[e];
                     const int zl = en.x / TX, xl = en.x - zl * TX;
@@ -1147,7 +1151,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
                 const float *pu = R::point(smem, st, 0);
                 const float *pd = R::point(smem, st, 1);
                 const long long so = (long long)s * L.fstride;
-                const int sslot = source_slot<RZ>(now, i0, j0);
+                // the shot's source cell, if it lies in this tile (warp-uniform)
+                const bool src_tile = (unsigned)(now.si - bi) < (unsigned)TZ && (unsigned)(now.sj - bj) < (unsigned)TX;
+                const int sslot = src_tile ? source_slot<RZ>(now, i0, j0) : -1;
                 // dc2 of the thread's points, one float4 per row from L2
                 // (the tile stays out of shared memory: four CTAs per SM)
                 float4 dcg[RZ];
@@ -1178,7 +1184,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
                 const float amp = now.amp * c.src_scale;
 #pragma unroll
                 for (int r = 0; r < RZ; ++r) {
-                    if constexpr (HE == 0) {
+                    if (HE == 0 && src_tile) {
                         if (sslot == r * 4 + 0) qu[r][0].x += amp;
                         if (sslot == r * 4 + 1) qu[r][0].y += amp;
                         if (sslot == r * 4 + 2) qu[r][1].x += amp;
