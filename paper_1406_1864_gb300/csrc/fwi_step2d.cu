@@ -368,7 +368,27 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
         const long long nphys = (long long)L.nz * L.nx;
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
-            const int iz = i0 + r - L.P;
+            const int iz = i0 + r - L.P, ix0 = j0 - L.P;
+            if (((L.P | L.nx) & 3) == 0 && iz >= 0 && iz < L.nz && ix0 >= 0 && ix0 + 3 < L.nx) {
+                // the thread's 4 points inside the model, 16-byte aligned: one
+                // vector reduction per sum
+                const long long o = (long long)iz * L.nx + ix0;
+                if (a.acc_illum != nullptr)
+                    red_add4(a.acc_illum + o, acc_i[r][0].x, acc_i[r][0].y, acc_i[r][1].x, acc_i[r][1].y);
+                if (WITH_H) {
+#pragma unroll
+                    for (int h = 0; h < NH; ++h)
+                        if (h <= a0.hmax) {
+                            if (h & 1)
+                                red_add4(a.acc_offh + h * nphys + o, acc_h[h][1].x, acc_h[h][0].x, acc_h[h][0].y,
+                                         acc_h[h][1].y);
+                            else
+                                red_add4(a.acc_offh + h * nphys + o, acc_h[h][0].x, acc_h[h][0].y, acc_h[h][1].x,
+                                         acc_h[h][1].y);
+                        }
+                }
+                continue;
+            }
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const int ix = j0 + p - L.P;
@@ -747,6 +767,18 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
             const int i = i0 + r;
+            if ((L.nxp & 3) == 0 && i < L.nzp && j0 + 3 < L.nxp) {
+                // the thread's 4 columns: one vector reduction per sum
+                red_add4(a.acc_grad + (long long)i * L.nxp + j0, acc_g[r][0].x, acc_g[r][0].y, acc_g[r][1].x,
+                         acc_g[r][1].y);
+                if constexpr (HE > 0) {
+#pragma unroll
+                    for (int e = 0; e < NE; ++e)
+                        red_add4(a.acc_ext + ((long long)e * L.nzp + i) * L.nxp + j0, acc_e[r][0][e], acc_e[r][1][e],
+                                 acc_e[r][2][e], acc_e[r][3][e]);
+                }
+                continue;
+            }
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const int j = j0 + p;

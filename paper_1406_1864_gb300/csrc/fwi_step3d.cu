@@ -244,10 +244,15 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
                     const float2 e0 = utt ? out[0] : u0[0], e1 = utt ? out[1] : u0[1];
                     const float ev[4] = {e0.x, e0.y, e1.x, e1.y};
                     const long long rowb = ((long long)(i - L.P) * L.ny + (k0 - L.P)) * L.nx;
+                    const int ix0 = j0 - L.P;
+                    if (((L.P | L.nx) & 3) == 0 && ix0 >= 0 && ix0 + 3 < L.nx) {
+                        red_add4(a.acc_illum + rowb + ix0, ev[0] * ev[0], ev[1] * ev[1], ev[2] * ev[2], ev[3] * ev[3]);
+                    } else {
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const int ix = j0 + p - L.P;
-                        if (ix >= 0 && ix < L.nx) atomicAdd(a.acc_illum + rowb + ix, ev[p] * ev[p]);
+                        for (int p = 0; p < 4; ++p) {
+                            const int ix = ix0 + p;
+                            if (ix >= 0 && ix < L.nx) atomicAdd(a.acc_illum + rowb + ix, ev[p] * ev[p]);
+                        }
                     }
                 }
             }
@@ -420,9 +425,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
                     // imaging: G += psi^m (Lhat u^{m-1} + f delta_s / dx), padded grid
                     const float g[4] = {pn[0].x * qu[0].x, pn[0].y * qu[0].y, pn[1].x * qu[1].x, pn[1].y * qu[1].y};
                     const long long rowb = ((long long)i * L.nyp + k0) * L.nxp;
+                    if ((L.nxp & 3) == 0 && j0 + 3 < L.nxp) {
+                        red_add4(a.acc_grad + rowb + j0, g[0], g[1], g[2], g[3]);
+                    } else {
 #pragma unroll
-                    for (int p = 0; p < 4; ++p)
-                        if (j0 + p < L.nxp) atomicAdd(a.acc_grad + rowb + j0 + p, g[p]);
+                        for (int p = 0; p < 4; ++p)
+                            if (j0 + p < L.nxp) atomicAdd(a.acc_grad + rowb + j0 + p, g[p]);
+                    }
                 }
             }
         }
