@@ -96,8 +96,18 @@ __device__ __forceinline__ void cursor_set(Cursor &cu, int q, const BT &B)
     const int blk = local / ntiles;
     cu.model = m;
     cu.tile = local - blk * ntiles;
-    cu.s = blk * B.chunk;
-    cu.s_end = min(c.ns, cu.s + B.chunk);
+    // shot blocks of `chunk` shots; of two or more, the last block of the
+    // model is cut in two (the level's last chunks are shorter, so the CTAs
+    // run out of work closer together)
+    const int nb = (c.ns + B.chunk - 1) / B.chunk;
+    if (blk < nb - 1 || nb == 1) {
+        cu.s = blk * B.chunk;
+        cu.s_end = min(c.ns, cu.s + B.chunk);
+    } else {
+        const int s0 = (nb - 1) * B.chunk, h = (c.ns - s0 + 1) / 2;
+        cu.s = blk == nb - 1 ? s0 : s0 + h;
+        cu.s_end = blk == nb - 1 ? s0 + h : c.ns;
+    }
 }
 
 template <class BT>
@@ -1394,6 +1404,14 @@ int sm_count_dev()
     return n;
 }
 
+// shot blocks of a model's level: blocks of `chunk` shots, the last one cut in
+// two when there are two or more (cursor_set)
+int chunk_blocks(int ns, int chunk)
+{
+    const int nb = (ns + chunk - 1) / chunk;
+    return nb == 1 ? 1 : nb - 1 + (ns - (nb - 1) * chunk >= 2 ? 2 : 1);
+}
+
 // autotuned (variant, chunk) per problem shape
 struct TuneKey {
     int kind, nzp, nxp, ns;
@@ -1412,7 +1430,7 @@ int batch_fill(Batch<A, N> &b, const A *a, const Tiling *t, int nm, int occ)
     long long total = 0;
     for (int k = 0; k < nm; ++k) {
         b.m[k] = a[k];
-        total += (long long)t[k].ntx * t[k].ntz * ((a[k].c.ns + t[0].chunk - 1) / t[0].chunk);
+        total += (long long)t[k].ntx * t[k].ntz * chunk_blocks(a[k].c.ns, t[0].chunk);
         b.chunk_end[k] = (int)total;
     }
     for (int k = nm; k < N; ++k) b.chunk_end[k] = (int)total;
@@ -1516,7 +1534,7 @@ Tiling make_tiling(const Lay2D &L, int ns, StepKind kind, int variant, int chunk
     t.ntz = (L.nzp + t.tz - 1) / t.tz;
     const int tiles = t.ntx * t.ntz;
     t.chunk = chunk > ns ? ns : chunk;
-    const long long chunks = (long long)tiles * ((ns + t.chunk - 1) / t.chunk);
+    const long long chunks = (long long)tiles * chunk_blocks(ns, t.chunk);
     const long long slots = (long long)sm_count_dev() * vs[variant].occ[0];
     t.ctas = (int)(chunks < slots ? chunks : slots);
     return t;
