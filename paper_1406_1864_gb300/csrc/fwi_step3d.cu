@@ -129,17 +129,29 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
     }
     __syncthreads();
 
-    // thread 0: copies of global step t (item t / NS, plane t % NS - 4)
+    // thread 0: copies of global step t (item t / NS, plane t % NS - 4), for
+    // t = 0, 1, 2, ...: the item and plane are counted, the tile origin taken
+    // once per item (no division per plane on the issuing warp)
     Item3 iss{-1, 0};
+    int i_slot = 0, i_ls = 0, ibk = 0, ibj = 0;
     auto issue = [&](int t) {
-        const int slot = t / NS, ls = t - slot * NS;
+        const int slot = i_slot, ls = i_ls;
+        if (++i_ls == NS) {
+            i_ls = 0;
+            ++i_slot;
+        }
         if (ls == 0) {
             iss = grab_item(c.sched, ntiles, nitems);
             s_item[slot & 3] = iss;
+            if (iss.tile >= 0) {
+                const int tz = iss.tile / c.ntx;
+                ibk = tz * TY3;
+                ibj = (iss.tile - tz * c.ntx) * TX;
+            }
         }
         if (iss.tile < 0) return;
         const int i = ls - RADIUS;
-        const int bk = (iss.tile / c.ntx) * TY3, bj = (iss.tile % c.ntx) * TX;
+        const int bk = ibk, bj = ibj;
         const int st = t % STAGES;
         float *sg = ring + st * FWD3_STAGE_F;
         const uint32_t bar = smem_u32(&bars[st]);
@@ -306,16 +318,27 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
     for (int e = threadIdx.x; e < PT3; e += TPB) sinj[e] = 0.f;
     __syncthreads();
 
+    // (issue: as in the forward step, steps t = 0, 1, 2, ... counted)
     Item3 iss{-1, 0};
+    int i_slot = 0, i_ls = 0, ibk = 0, ibj = 0;
     auto issue = [&](int t) {
-        const int slot = t / NS, ls = t - slot * NS;
+        const int slot = i_slot, ls = i_ls;
+        if (++i_ls == NS) {
+            i_ls = 0;
+            ++i_slot;
+        }
         if (ls == 0) {
             iss = grab_item(c.sched, ntiles, nitems);
             s_item[slot & 3] = iss;
+            if (iss.tile >= 0) {
+                const int tz = iss.tile / c.ntx;
+                ibk = tz * TY3;
+                ibj = (iss.tile - tz * c.ntx) * TX;
+            }
         }
         if (iss.tile < 0) return;
         const int i = ls - RADIUS;
-        const int bk = (iss.tile / c.ntx) * TY3, bj = (iss.tile % c.ntx) * TX;
+        const int bk = ibk, bj = ibj;
         const int st = t % STAGES;
         float *sg = ring + st * BWD3_STAGE_F;
         const uint32_t bar = smem_u32(&bars[st]);
