@@ -598,34 +598,40 @@ using BwdRing = Ring<8 * RZ, RADIUS, 2, 2, STAGES, 3 * 8 * RZ * TX * 4>; // + c2
 // tile on the TZ x (TX + 4 HE) columns bj - 2 HE .. bj + TX + 2 HE - 1 (the
 // x-extension of the offsets 2h, |h| <= HE), zero where a column leaves the
 // padded grid or a row its padded rows. The thread's own columns come from
-// its registers (q_own_to_smem); the 2 HE columns on each side are scalar
-// points here, with lap4's second-difference arithmetic (lap8x2 on a
-// duplicated lane).
+// its registers (q_own_to_smem); the 2 HE columns on each side (q_edges_to_smem)
+// as rows of 4 points (2 HE / 4 groups per side, TZ rows), which one warp
+// computes with the paired Laplacian of the tile's own points (lap4: bitwise
+// the same q).
 template <int RZ, int HE, int TXS, int HX>
 __device__ __forceinline__ void q_edges_to_smem(float *qs, const float *su, const ItemDesc &d, int bi, int bj,
-                                                const Lay2D &L, float src_scale)
+                                                  const Lay2D &L, float src_scale)
 {
-    constexpr int TZ = 8 * RZ, QW = TX + 4 * HE, EW = 4 * HE;
-    for (int e = threadIdx.x; e < TZ * EW; e += TPB) {
-        const int r = e / EW, cc = e - r * EW;
-        const int col = cc < 2 * HE ? cc - 2 * HE : TX + cc - 2 * HE; // column in the tile
-        const int gi = bi + r, gj = bj + col;
-        float q = 0.f;
-        if (gi < L.nzp && gj >= 0 && gj < L.nxp) {
-            const float *ctr = su + (r + RADIUS) * TXS + HX + col;
-            const float cv = ctr[0];
-            float2 xs[4], zs[4];
+    constexpr int TZ = 8 * RZ, QW = TX + 4 * HE, G = HE; // groups of 4 columns on each side: 2 HE / 4 * 2 = HE
+    static_assert(HE % 2 == 0, "edge groups of 4 columns");
+    constexpr int NU = TZ * G;                             // units of (row, group)
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wid != 3) return;
+    for (int u = lane; u < NU; u += 32) {
+        const int r = u / G, g = u - r * G;
+        const int c0 = g < G / 2 ? -2 * HE + 4 * g : TX + 4 * (g - G / 2); // first column of the group
+        const float *ctr = su + (r + RADIUS) * TXS + HX + c0;
+        float4 zc[1 + 2 * RADIUS];
 #pragma unroll
-            for (int k = 1; k <= 4; ++k) {
-                const float xsum = ctr[-k] + ctr[k];
-                const float zsum = ctr[-k * TXS] + ctr[k * TXS];
-                xs[k - 1] = make_float2(xsum, xsum);
-                zs[k - 1] = make_float2(zsum, zsum);
-            }
-            q = lap8x2(make_float2(cv, cv), xs, zs).x;
-            if (gi == d.si && gj == d.sj) q += d.amp * src_scale;
+        for (int kk = 0; kk < 1 + 2 * RADIUS; ++kk) zc[kk] = lds4(ctr + (kk - RADIUS) * TXS);
+        const float4 a0 = lds4(ctr - 4), a2 = lds4(ctr + 4);
+        const float4 a1 = zc[RADIUS];
+        const float w[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+        float2 q[2];
+        lap4<4, 1 + 2 * RADIUS, false>(q, w, zc, 0);
+        const float v[4] = {q[0].x, q[0].y, q[1].x, q[1].y};
+        const int gi = bi + r;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int gj = bj + c0 + p;
+            float qq = (gi < L.nzp && gj >= 0 && gj < L.nxp) ? v[p] : 0.f;
+            if (gi == d.si && gj == d.sj) qq += d.amp * src_scale;
+            qs[r * QW + c0 + p + 2 * HE] = qq;
         }
-        qs[r * QW + col + 2 * HE] = q;
     }
 }
 
