@@ -423,8 +423,7 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
    ...), exceeds FWI_NOALLOC_SCRATCH_BYTES. Like fwi_forward, the call waits
    for its stream at the end to read the kernels' status word.
    The first call on a device (and the first after a device reset) looks up
-   the scratch array's device address (cudaGetSymbolAddress), so make that
-   first call before any stream capture.
+   the scratch array's device address (cudaGetSymbolAddress).
    All calls share the one array, which keeps the previous call's contents
    (every call clears what must start at zero): calls that may overlap on the
    GPU -- on different streams, or from different host threads -- race and

@@ -276,18 +276,42 @@ __device__ __forceinline__ int source_slot(const ItemDesc &v, int i0, int j0)
     return source_slot<RZ>(v.si, v.sj, i0, j0);
 }
 
-// load a TZ x TX tile of a field-layout coefficient array (c2, damping) into
-// shared memory (0 below the padded grid)
-template <int TZ>
-__device__ __forceinline__ void load_c2_tile(float *dst, const float *c2, const Lay2D &L, int bi, int bj)
+// N TZ x TX tiles of field-layout coefficient arrays (c2, damping, the planes
+// of D~) into shared memory (0 below the padded grid; a null source is
+// skipped). Every load is issued before the first store, so that a tile
+// change waits for one memory latency rather than one per tile.
+template <int TZ, int N>
+__device__ __forceinline__ void load_tiles(float *(&dst)[N], const float *(&src)[N], const Lay2D &L, int bi, int bj)
 {
-    for (int e = threadIdx.x; e < TZ * (TX / 4); e += TPB) {
-        const int r = e / (TX / 4), v = e - r * (TX / 4);
-        const int i = bi + r;
-        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < L.nzp) val = __ldg(reinterpret_cast<const float4 *>(c2 + fidx(L, i, bj + 4 * v)));
-        *reinterpret_cast<float4 *>(&dst[r * TX + 4 * v]) = val;
-    }
+    constexpr int PER = TZ * (TX / 4), NV = (PER + TPB - 1) / TPB; // float4s of one tile, per thread
+    float4 v[N][NV];
+#pragma unroll
+    for (int e = 0; e < N; ++e)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const int idx = threadIdx.x + q * TPB, r = idx / (TX / 4), c4 = idx - r * (TX / 4);
+            v[e][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (src[e] != nullptr && (PER % TPB == 0 || idx < PER) && bi + r < L.nzp)
+                v[e][q] = __ldg(reinterpret_cast<const float4 *>(src[e] + fidx(L, bi + r, bj + 4 * c4)));
+        }
+#pragma unroll
+    for (int e = 0; e < N; ++e)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const int idx = threadIdx.x + q * TPB, r = idx / (TX / 4), c4 = idx - r * (TX / 4);
+            if (src[e] != nullptr && (PER % TPB == 0 || idx < PER))
+                *reinterpret_cast<float4 *>(&dst[e][r * TX + 4 * c4]) = v[e][q];
+        }
+}
+
+// c2 and (in sponge tiles) the damping factor of one tile
+template <int TZ>
+__device__ __forceinline__ void load_coef_tiles(float *c2s, float *dms, const StepCommon &c, bool sponge, int bi,
+                                                int bj)
+{
+    float *dst[2] = {c2s, dms};
+    const float *src[2] = {c.c2, sponge ? c.damp : nullptr};
+    load_tiles<TZ, 2>(dst, src, c.L, bi, bj);
 }
 
 // ------------------------------------------------------------ forward step
@@ -456,8 +480,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
             for (int r = 0; r < RZ; ++r) acc_i[r][0] = acc_i[r][1] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int h = 0; h < NH; ++h) acc_h[h][0] = acc_h[h][1] = make_float2(0.f, 0.f);
-            load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
-            if (tile_sponge) load_c2_tile<TZ>(dms, c.damp, L, bi, bj);
+            load_coef_tiles<TZ>(c2s, dms, c, tile_sponge, bi, bj);
             __syncthreads();
         }
         const int st = k % STAGES;
@@ -682,15 +705,13 @@ __device__ __forceinline__ void add_source(float2 (&q)[RZ][2], int sslot, float 
 // acc[p][h + HE] += psi(y_p) q(y_p + 2h) for the two lanes (points 2 lane,
 // 2 lane + 1 of the thread's four) of one row; qrow is the q tile's row
 template <int HE, int QW>
-__device__ __forceinline__ void ext_accumulate(float (&acc)[4][2 * HE + 1], float2 psi, int lane, const float *qrow,
+__device__ __forceinline__ void ext_accumulate(float2 (&acc)[2][2 * HE + 1], float2 psi, int lane, const float *qrow,
                                                int tx)
 {
 #pragma unroll
     for (int hh = 0; hh < 2 * HE + 1; ++hh) {
         const int c0 = 4 * tx + 2 * lane + 2 * hh;   // column of y + 2h in the q tile (even: 8-byte aligned)
-        const float2 q2 = *reinterpret_cast<const float2 *>(qrow + c0);
-        acc[2 * lane][hh] = fmaf(psi.x, q2.x, acc[2 * lane][hh]);
-        acc[2 * lane + 1][hh] = fmaf(psi.y, q2.y, acc[2 * lane + 1][hh]);
+        acc[lane][hh] = fma2(psi, *reinterpret_cast<const float2 *>(qrow + c0), acc[lane][hh]);
     }
 }
 
@@ -771,7 +792,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             if (s_desc[k].tile >= 0) issue(s_desc[k], k);
 
     float2 acc_g[RZ][2];
-    float acc_e[RZ][4][NE]; // extended image at (own point y, h): sum psi^m(y) q^{m-1}(y + 2h)
+    float2 acc_e[RZ][2][NE]; // extended image at (own point y, h): sum psi^m(y) q^{m-1}(y + 2h)
     int cur_tile = -1, cur_model = 0, bi = 0, bj = 0, i0 = 0, j0 = 0;
     bool tile_sponge = false, colok = false;
     SpongeInfo<RZ> sg;
@@ -790,8 +811,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                 if constexpr (HE > 0) {
 #pragma unroll
                     for (int e = 0; e < NE; ++e)
-                        red_add4(a.acc_ext + ((long long)e * L.nzp + i) * L.nxp + j0, acc_e[r][0][e], acc_e[r][1][e],
-                                 acc_e[r][2][e], acc_e[r][3][e]);
+                        red_add4(a.acc_ext + ((long long)e * L.nzp + i) * L.nxp + j0, acc_e[r][0][e].x, acc_e[r][0][e].y,
+                                 acc_e[r][1][e].x, acc_e[r][1][e].y);
                 }
                 continue;
             }
@@ -804,7 +825,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                     if (i < L.nzp && j < L.nxp)
 #pragma unroll
                         for (int e = 0; e < NE; ++e)
-                            atomicAdd(a.acc_ext + ((long long)e * L.nzp + i) * L.nxp + j, acc_e[r][p][e]);
+                            atomicAdd(a.acc_ext + ((long long)e * L.nzp + i) * L.nxp + j, (p & 1) ? acc_e[r][p >> 1][e].y : acc_e[r][p >> 1][e].x);
                 }
             }
         }
@@ -889,12 +910,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 #pragma unroll
                 for (int r = 0; r < RZ; ++r)
 #pragma unroll
-                    for (int p = 0; p < 4; ++p)
+                    for (int p = 0; p < 2; ++p)
 #pragma unroll
-                        for (int e = 0; e < NE; ++e) acc_e[r][p][e] = 0.f;
+                        for (int e = 0; e < NE; ++e) acc_e[r][p][e] = make_float2(0.f, 0.f);
             }
-            load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
-            if (tile_sponge) load_c2_tile<TZ>(dms, c.damp, L, bi, bj);
+            load_coef_tiles<TZ>(c2s, dms, c, tile_sponge, bi, bj);
             bval_ok = false;
             __syncthreads();
         }
@@ -1158,11 +1178,23 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
             tile_sponge = bi < L.P || bi + TZ > L.P + L.nz || bj < L.P || bj + TX > L.P + L.nx;
             colok = j0 < L.nxp;
             if (tile_sponge) sg.init(L, i0, j0);
-            load_c2_tile<TZ>(c2s, c.c2, L, bi, bj);
             if constexpr (HE > 0) {
-                for (int e = 0; e < NE; ++e) load_c2_tile<TZ>(des + e * TZ * TX, a.dext + e * L.fstride, L, bi, bj);
+                // c2, damping and the 2 HE + 1 planes of D~
+                float *dst[NE + 2];
+                const float *src[NE + 2];
+                dst[0] = c2s;
+                src[0] = c.c2;
+                dst[1] = dms;
+                src[1] = tile_sponge ? c.damp : nullptr;
+#pragma unroll
+                for (int e = 0; e < NE; ++e) {
+                    dst[2 + e] = des + e * TZ * TX;
+                    src[2 + e] = a.dext + e * L.fstride;
+                }
+                load_tiles<TZ, NE + 2>(dst, src, L, bi, bj);
+            } else {
+                load_coef_tiles<TZ>(c2s, dms, c, tile_sponge, bi, bj);
             }
-            if (tile_sponge) load_c2_tile<TZ>(dms, c.damp, L, bi, bj);
             __syncthreads();
         }
         const int st = k % STAGES;
