@@ -648,13 +648,14 @@ __device__ __forceinline__ void q_edges_to_smem(float *qs, const float *su, cons
         lap4<4, 1 + 2 * RADIUS, false>(q, w, zc, 0);
         const float v[4] = {q[0].x, q[0].y, q[1].x, q[1].y};
         const int gi = bi + r;
+        float qq[4];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const int gj = bj + c0 + p;
-            float qq = (gi < L.nzp && gj >= 0 && gj < L.nxp) ? v[p] : 0.f;
-            if (gi == d.si && gj == d.sj) qq += d.amp * src_scale;
-            qs[r * QW + c0 + p + 2 * HE] = qq;
+            qq[p] = (gi < L.nzp && gj >= 0 && gj < L.nxp) ? v[p] : 0.f;
+            if (gi == d.si && gj == d.sj) qq[p] += d.amp * src_scale;
         }
+        *reinterpret_cast<float4 *>(qs + r * QW + c0 + 2 * HE) = make_float4(qq[0], qq[1], qq[2], qq[3]);
     }
 }
 
@@ -666,10 +667,10 @@ __device__ __forceinline__ void q_own_to_smem(float *qs, const float2 (&q)[RZ][2
 #pragma unroll
     for (int r = 0; r < RZ; ++r) {
         const bool rowok = i0 + r < L.nzp;
-        const float v[4] = {q[r][0].x, q[r][0].y, q[r][1].x, q[r][1].y};
-        float *dst = qs + (ty * RZ + r) * QW + 2 * HE + 4 * tx;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) dst[p] = (rowok && j0 + p < L.nxp) ? v[p] : 0.f;
+        // one 16-byte store per row (QW and 2 HE are multiples of 4)
+        *reinterpret_cast<float4 *>(qs + (ty * RZ + r) * QW + 2 * HE + 4 * tx) =
+            make_float4(rowok && j0 < L.nxp ? q[r][0].x : 0.f, rowok && j0 + 1 < L.nxp ? q[r][0].y : 0.f,
+                        rowok && j0 + 2 < L.nxp ? q[r][1].x : 0.f, rowok && j0 + 3 < L.nxp ? q[r][1].y : 0.f);
     }
 }
 
@@ -702,16 +703,27 @@ __device__ __forceinline__ void add_source(float2 (&q)[RZ][2], int sslot, float 
     }
 }
 
-// acc[p][h + HE] += psi(y_p) q(y_p + 2h) for the two lanes (points 2 lane,
-// 2 lane + 1 of the thread's four) of one row; qrow is the q tile's row
-template <int HE, int QW>
-__device__ __forceinline__ void ext_accumulate(float2 (&acc)[2][2 * HE + 1], float2 psi, int lane, const float *qrow,
-                                               int tx)
+// The q values a thread's row needs, columns 4 tx .. 4 tx + 4 HE + 3 of the
+// q tile (x = y - 2 HE .. y + 2 HE + 1 for its 4 points y), as HE + 1
+// 16-byte loads: lane pair j of them (columns 4 tx + 2j, 4 tx + 2j + 1) is
+// half j & 1 of qv[j >> 1]
+template <int HE>
+__device__ __forceinline__ void q_row(float4 (&qv)[HE + 1], const float *qrow, int tx)
+{
+#pragma unroll
+    for (int m = 0; m <= HE; ++m) qv[m] = lds4(qrow + 4 * tx + 4 * m);
+}
+
+// acc[lane][h + HE] += psi(y) q(y + 2h) for the two points of lane pair
+// `lane` (points 2 lane, 2 lane + 1 of the thread's four) of one row
+template <int HE>
+__device__ __forceinline__ void ext_accumulate(float2 (&acc)[2][2 * HE + 1], float2 psi, int lane,
+                                               const float4 (&qv)[HE + 1])
 {
 #pragma unroll
     for (int hh = 0; hh < 2 * HE + 1; ++hh) {
-        const int c0 = 4 * tx + 2 * lane + 2 * hh;   // column of y + 2h in the q tile (even: 8-byte aligned)
-        acc[lane][hh] = fma2(psi, *reinterpret_cast<const float2 *>(qrow + c0), acc[lane][hh]);
+        const int j = lane + hh; // lane pair of columns y + 2h
+        acc[lane][hh] = fma2(psi, half2of(qv[j >> 1], j & 1), acc[lane][hh]);
     }
 }
 
@@ -1010,6 +1022,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                 const float4 ua4 = lds4(&pua[(ty * RZ + r) * TX + 4 * tx]);
                 const float4 pb4 = lds4(&ppb[(ty * RZ + r) * TX + 4 * tx]);
                 const float4 c24 = lds4(&c2s[(ty * RZ + r) * TX + 4 * tx]);
+                float4 qv[HE + 1]; // HE > 0: the row's q values for the extended image
+                if constexpr (HE > 0) q_row<HE>(qv, qs + (ty * RZ + r) * QW, tx);
                 if (!tile_sponge) {
                     float2 pn[2], un[2];
 #pragma unroll
@@ -1017,7 +1031,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                         const float2 c2v = half2of(c24, h);
                         pn[h] = add2(p1[h], fma2(c2v, qp[r][h], sub2(p1[h], half2of(pb4, h))));
                         acc_g[r][h] = fma2(pn[h], qu[r][h], acc_g[r][h]);
-                        if constexpr (HE > 0) ext_accumulate<HE, QW>(acc_e[r], pn[h], h, qs + (ty * RZ + r) * QW, tx);
+                        if constexpr (HE > 0) ext_accumulate<HE>(acc_e[r], pn[h], h, qv);
                         // leap_back on two lanes: u1 - (-(c2 q) + (u^m - u1))
                         un[h] = sub2(u1[h], fma2(make_float2(-c2v.x, -c2v.y), qu[r][h], sub2(half2of(ua4, h), u1[h])));
                     }
@@ -1039,7 +1053,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                         const float2 kb = fma2(ia2, make_float2(2.f, 2.f), make_float2(-1.f, -1.f));
                         pn[h] = add2(p1[h], fma2(mul2(c2v, ia2), qp[r][h], mul2(kb, sub2(p1[h], half2of(pb4, h)))));
                         acc_g[r][h] = fma2(pn[h], qu[r][h], acc_g[r][h]);
-                        if constexpr (HE > 0) ext_accumulate<HE, QW>(acc_e[r], pn[h], h, qs + (ty * RZ + r) * QW, tx);
+                        if constexpr (HE > 0) ext_accumulate<HE>(acc_e[r], pn[h], h, qv);
                         un[h] = sub2(u1[h], fma2(make_float2(-c2v.x, -c2v.y), qu[r][h], sub2(half2of(ua4, h), u1[h])));
                     }
                     float pnew[4] = {pn[0].x, pn[0].y, pn[1].x, pn[1].y};
@@ -1280,13 +1294,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
                     // extended scattering source S(y) = sum_h D~(y, h) q(y + 2h)
                     float2 sx[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
                     if constexpr (HE > 0) {
-                        const float *qrow = qs + (ty * RZ + r) * QW;
+                        float4 qv[HE + 1];
+                        q_row<HE>(qv, qs + (ty * RZ + r) * QW, tx);
 #pragma unroll
                         for (int hh = 0; hh < NE; ++hh) {
                             const float4 d4 = lds4(&des[(hh * TZ + ty * RZ + r) * TX + 4 * tx]);
-                            const int c0 = 4 * tx + 2 * hh;   // column of y + 2h for the first point (even)
-                            sx[0] = fma2(lo2(d4), *reinterpret_cast<const float2 *>(qrow + c0), sx[0]);
-                            sx[1] = fma2(hi2(d4), *reinterpret_cast<const float2 *>(qrow + c0 + 2), sx[1]);
+                            // lane pairs hh and hh + 1: columns y + 2h of points (0, 1) and (2, 3)
+                            sx[0] = fma2(lo2(d4), half2of(qv[hh >> 1], hh & 1), sx[0]);
+                            sx[1] = fma2(hi2(d4), half2of(qv[(hh + 1) >> 1], (hh + 1) & 1), sx[1]);
                         }
                     }
                     float2 un[2], dn[2];
