@@ -347,7 +347,10 @@ fwi_status fwi_gauss_newton_hvp(const fwi_grid *grid, const fwi_geometry *geom, 
    3-D grids (opts as for a 3-D gradient: ckpt = FWI_CKPT_SNAPSHOT): the
    compiled ring-depth / CTAs-per-SM variants of the 3-D forward and backward
    steps are timed on the first shot group, keyed by padded shape and group
-   size; the chunks are 1 (a 3-D item is one column of one shot). */
+   size. A 3-D item is one z-segment of one column (64 x 8 cells) of one
+   shot; the chunks are the z-segments per column, which fwi_autotune
+   chooses from the item count and the resident CTAs of the chosen variant
+   (and reports), and fwi_autotune_set takes as given (0: that choice). */
 fwi_status fwi_autotune(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
                         void *ws, size_t ws_bytes, void *stream, int *choice);
 /* Keep a given choice (int[4] as above) for this problem's shape, as if

@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default step variants (no fwi_autotune)")
     ap.add_argument("--variants", default="", help="F,B: pin the forward and backward step variants "
                     "(fwi_autotune_set) instead of autotuning")
+    ap.add_argument("--segments", default="0,0", help="F,B: z-segments per column with --variants "
+                    "(0: chosen from the items and resident CTAs)")
     args = ap.parse_args()
     p = W.dipping3d(nz=args.nz, ny=args.ny, nx=args.nx, nt=args.nt, ns=args.shots)
     grid, geom = fwi.from_problem(p)
@@ -41,7 +43,8 @@ def main():
     tiles = "default"
     if args.variants:
         fv, bv = (int(x) for x in args.variants.split(","))
-        tiles = {"forward_variant": fv, "forward_chunk": 1, "backward_variant": bv, "backward_chunk": 1}
+        fs, bs = (int(x) for x in args.segments.split(","))
+        tiles = {"forward_variant": fv, "forward_chunk": fs, "backward_variant": bv, "backward_chunk": bs}
         fwi.autotune_set(grid, geom, fwi.Options(ckpt="snapshot", shot_group=args.shot_group), tiles)
     elif not args.no_autotune:  # step variants timed on this problem (not timed)
         tiles = fwi.autotune(grid, geom, torch.as_tensor(p.v_init, device="cuda"),

@@ -1049,8 +1049,8 @@ fwi_status make_plan3(const fwi_grid *g, const fwi_geometry *ge, const fwi_optio
     const Lay3D &L = pl.L;
     pl.vf = step3_variant_for(L, pl.G, false);
     pl.vb = step3_variant_for(L, pl.G, true);
-    pl.tf = make_tiling3(L, pl.G, false, pl.vf);
-    pl.tb = make_tiling3(L, pl.G, true, pl.vb);
+    pl.tf = make_tiling3(L, pl.G, false, pl.vf, step3_segments_for(L, pl.G, false));
+    pl.tb = make_tiling3(L, pl.G, true, pl.vb, step3_segments_for(L, pl.G, true));
     size_t off = 0;
     auto take = [&](Part &p, size_t bytes) {
         p.off = off;
@@ -1157,6 +1157,8 @@ Step3Common make_common3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g,
     c.nrec = pl.nrec;
     c.nty = t.nty;
     c.ntx = t.ntx;
+    c.nseg = t.nseg;
+    c.segl = t.segl;
     c.status = at<int>(ws, pl.scal, 8);
     c.sched = at<int>(ws, pl.sched);
     return c;
@@ -1253,6 +1255,7 @@ fwi_status run_forward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, 
         a.tm_u = mh[n & 1];
         a.tm_upt = mp[n & 1];
         a.tm_prev = mp[(n + 1) & 1];
+        a.uin = U[n & 1];
         a.uout = U[(n + 1) & 1];
         a.c.sched = at<int>(ws, pl.sched) + n;
         if ((e = launch_fwd3d(a, pl.tf, pl.vf, st)) != cudaSuccess) return cuda_fail(e, "3-D forward step");
@@ -1318,6 +1321,7 @@ fwi_status run_backward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g,
             f.tm_u = sh[i];
             f.tm_upt = sp[i];
             f.tm_prev = sp[i == 0 ? K : i - 1];
+            f.uin = S[i];
             f.uout = S[i + 1];
             f.c.sched = at<int>(ws, pl.sched) + 2 * pl.nt + n;
             if ((e = launch_fwd3d(f, pl.tf, pl.vf, st)) != cudaSuccess) return cuda_fail(e, "3-D segment step");
@@ -1330,6 +1334,8 @@ fwi_status run_backward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g,
             a.tm_p = ph[(m + 1) & 1];
             a.tm_ppt = pp[(m + 1) & 1];
             a.tm_pb = pp[m & 1];
+            a.uin = S[m - 1 - n0];
+            a.pin = Pp[(m + 1) & 1];
             a.pb = Pp[m & 1];
             a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
             if ((e = launch_bwd3d(a, pl.tb, pl.vb, st)) != cudaSuccess) return cuda_fail(e, "3-D backward step");
@@ -1375,6 +1381,8 @@ fwi_status time_backward3(const Plan3 &pl, const fwi_geometry *ge, void *ws, int
         a.tm_p = ph[(m + 1) & 1];
         a.tm_ppt = pp[(m + 1) & 1];
         a.tm_pb = pp[m & 1];
+        a.uin = U[(m - 1) & 1];
+        a.pin = Pp[(m + 1) & 1];
         a.pb = Pp[m & 1];
         a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
         if ((e = launch_bwd3d(a, pl.tb, pl.vb, st)) != cudaSuccess) return cuda_fail(e, "3-D backward step");
@@ -2244,16 +2252,16 @@ fwi_status autotune3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_o
                 best[b] = vi;
             }
         }
-        if (s == FWI_OK) step3_tuned_store(pl.L, pl.G, b != 0, best[b]);
+        if (s == FWI_OK) step3_tuned_store(pl.L, pl.G, b != 0, best[b], 0);
     }
     t_prof = prof;
     if (s != FWI_OK) return s;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronize");
     if (choice) {
         choice[0] = best[0];
-        choice[1] = 1;
+        choice[1] = make_tiling3(pl.L, pl.G, false, best[0]).nseg;
         choice[2] = best[1];
-        choice[3] = 1;
+        choice[3] = make_tiling3(pl.L, pl.G, true, best[1]).nseg;
     }
     t_err.clear();
     return FWI_OK;
@@ -2363,9 +2371,10 @@ fwi_status fwi_autotune_set(const fwi_grid *grid, const fwi_geometry *geom, cons
         if (choice[0] < 0 || choice[0] >= step3_variants(false) || choice[2] < 0 || choice[2] >= step3_variants(true))
             return fail(FWI_ERR_INVALID_ARG, "variant outside the compiled ones (%d forward, %d backward)",
                         step3_variants(false), step3_variants(true));
-        if (choice[1] < 1 || choice[3] < 1) return fail(FWI_ERR_INVALID_ARG, "chunk must be >= 1");
-        step3_tuned_store(p3.L, p3.G, false, choice[0]);
-        step3_tuned_store(p3.L, p3.G, true, choice[2]);
+        if (choice[1] < 0 || choice[3] < 0)
+            return fail(FWI_ERR_INVALID_ARG, "3-D z-segments must be >= 0 (0: chosen per launch shape)");
+        step3_tuned_store(p3.L, p3.G, false, choice[0], choice[1]);
+        step3_tuned_store(p3.L, p3.G, true, choice[2], choice[3]);
         t_err.clear();
         return FWI_OK;
     }

@@ -180,6 +180,7 @@ struct Step3Common {
     float src_scale;    // dx^(2 - ndim) = 1/dx
     int ns, nt, nrec;
     int nty, ntx;       // tiles along y and x
+    int nseg, segl;     // z-segments of a column and their length in planes
     int *status;        // device status flags
     int *sched;         // this launch's item counter (zero at launch)
 };
@@ -200,6 +201,7 @@ struct Fwd3Args {
     CUtensorMap tm_c2;   // c2, point box (one field)
     CUtensorMap tm_damp; // damping factor, point box (one field)
     Step3Common c;
+    const float *uin;    // u^n (the buffer of tm_u / tm_upt): a segment's first planes
     float *uout;         // u^{n+1} written here
     float *seis;         // [ns][nt][nrec] or null
     float *acc_illum;    // [nz][ny][nx] or null (red.add)
@@ -213,6 +215,7 @@ struct Bwd3Args {
     CUtensorMap tm_pb;        // psi^{m+2}: point box
     CUtensorMap tm_c2, tm_damp;
     Step3Common c;
+    const float *uin, *pin;   // u^{m-1}, psi^{m+1} (the buffers of tm_u, tm_p): a segment's first planes
     float *pb;                // psi^m written here (the psi^{m+2} buffer)
     const float *adj;         // [ns][nt][nrec] adjoint source or null
     float *acc_grad;          // [nzp][nyp][nxp] (red.add)
@@ -223,6 +226,7 @@ struct Bwd3Args {
 
 struct Tiling3 {
     int nty, ntx, ctas;
+    int nseg, segl; // z-segments per column (items: segment x tile x shot), planes per segment
 };
 // Born (tangent-linear) step: u and du = J dv advanced together
 struct BornArgs {

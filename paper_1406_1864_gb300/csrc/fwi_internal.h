@@ -11,9 +11,11 @@ namespace fwi {
 // tiling of a variant (an out-of-range one is taken as 0), launches
 int step3_variants(bool backward);
 int step3_variant_for(const Lay3D &L, int ns, bool backward);
-void step3_tuned_store(const Lay3D &L, int ns, bool backward, int variant);
+int step3_segments_for(const Lay3D &L, int ns, bool backward); // 0: chosen per launch shape
+void step3_tuned_store(const Lay3D &L, int ns, bool backward, int variant, int nseg);
 void step3_tuned_clear();
-Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward, int variant);
+// nseg: z-segments per column, 0 to choose them from the items and resident CTAs
+Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward, int variant, int nseg = 0);
 // tensor map over nfields 3-D fields with a box of bx x by cells of one plane
 bool encode_field_map3(CUtensorMap *map, const float *base, const Lay3D &L, int nfields, int bx, int by);
 cudaError_t launch_fwd3d(const Fwd3Args &a, const Tiling3 &t, int variant, cudaStream_t st);

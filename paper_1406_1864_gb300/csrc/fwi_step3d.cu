@@ -17,12 +17,17 @@
 // the point tile of plane i+4 that enters the register window and the point
 // tiles of u^{n-1}, c2 and the damping factor of plane i: one ring stage per
 // plane, STAGES-1 planes ahead of the compute, on mbarriers with bounded
-// waits. Items (column, shot) are handed out by an atomic counter, shot-major,
-// so neighbouring columns of one shot are in flight together and their halo
-// re-reads hit L2. Accumulations (illumination, gradient) are red.add per
-// point and plane: a column's planes do not fit in registers.
+// waits. A column may be cut into z-segments, so that the items (segment,
+// column, shot) come in units fine enough for the last round of a launch to
+// keep the SMs busy; a segment's march starts with its window planes loaded
+// straight from global memory. Items are handed out by an atomic counter,
+// segment-major, the shots of one column consecutively, so neighbouring
+// columns are in flight together and their halo re-reads hit L2.
+// Accumulations (illumination, gradient) are red.add per point and plane: a
+// column's planes do not fit in registers.
 #include "fwi_device.cuh"
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -36,6 +41,7 @@ constexpr int PT3 = TY3 * TX;                     // floats of one point tile
 
 struct Item3 {
     int tile, s; // tile < 0: no more work
+    int z0, z1;  // planes z0 .. z1 - 1 of the column
 };
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, int w,
@@ -88,16 +94,33 @@ __device__ __forceinline__ void lap3_4(float2 (&q)[2], const float *sh, const fl
     }
 }
 
-// next item of this CTA (thread 0): the shots of one column consecutively
-// (CTAs running at the same time add into the same column of the imaging and
-// illumination sums, which then stay in L2), columns in order
-__device__ __forceinline__ Item3 grab_item(int *counter, int ntiles, int nitems)
+// next item of this CTA (thread 0): segment-major, then columns in order,
+// the shots of one column consecutively (CTAs running at the same time add
+// into the same column of the imaging and illumination sums, which then stay
+// in L2)
+__device__ __forceinline__ Item3 grab_item(const Step3Common &c, int ntiles)
 {
-    const int q = atomicAdd(counter, 1);
-    if (q >= nitems) return Item3{-1, 0};
-    const int ns = nitems / ntiles;
-    const int tile = q / ns;
-    return Item3{tile, q - tile * ns};
+    const int q = atomicAdd(c.sched, 1);
+    const int per = ntiles * c.ns; // items of one segment
+    if (q >= per * c.nseg) return Item3{-1, 0, 0, 0};
+    const int g = q / per, r = q - g * per;
+    const int tile = r / c.ns;
+    const int z0 = g * c.segl;
+    return Item3{tile, r - tile * c.ns, z0, min(c.L.nzp, z0 + c.segl)};
+}
+
+// the thread's 4 points of planes z0 - 4 .. z0 + 3 of field f (rows k0 >= nyp
+// or columns j0 >= nxp: zeros), the z window at the start of a segment;
+// planes above the grid are the zero ghost planes
+__device__ __forceinline__ void load_window(float4 (&zw)[9], const float *f, const Lay3D &L, int z0, int k0, int j0)
+{
+    const bool ok = k0 < L.nyp && j0 < L.nxp; // j0 + 3 stays inside the row's ghost columns
+    const float *b = f + fidx3(L, z0 - 4, k0, j0);
+#pragma unroll
+    for (int z = 0; z < 8; ++z)
+        zw[z] = (ok && z0 - 4 + z >= 0) ? __ldg(reinterpret_cast<const float4 *>(b + z * L.plane))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    zw[8] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // ------------------------------------------------------------ forward step
@@ -119,8 +142,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
     const Step3Common &c = a.c;
     const Lay3D &L = c.L;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int NS = L.nzp + RADIUS; // steps per item: planes -4 .. nzp-1
-    const int ntiles = c.nty * c.ntx, nitems = ntiles * c.ns;
+    const int ntiles = c.nty * c.ntx;
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < STAGES; ++k) mbar_init(smem_u32(&bars[k]), 1);
@@ -129,41 +151,39 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
     }
     __syncthreads();
 
-    // thread 0: copies of global step t (item t / NS, plane t % NS - 4), for
-    // t = 0, 1, 2, ...: the item and plane are counted, the tile origin taken
-    // once per item (no division per plane on the issuing warp)
-    Item3 iss{-1, 0};
-    int i_slot = 0, i_ls = 0, ibk = 0, ibj = 0;
+    // thread 0: copies of global step t = 0, 1, 2, ..., one plane of an item
+    // per step: the item and plane are counted, the tile origin taken once per
+    // item (no division per plane on the issuing warp)
+    Item3 iss{-1, 0, 0, 0};
+    int i_slot = 0, i_ls = 0, i_n = 1, ibk = 0, ibj = 0;
     auto issue = [&](int t) {
-        const int slot = i_slot, ls = i_ls;
-        if (++i_ls == NS) {
-            i_ls = 0;
-            ++i_slot;
-        }
-        if (ls == 0) {
-            iss = grab_item(c.sched, ntiles, nitems);
-            s_item[slot & 3] = iss;
+        if (i_ls == 0) {
+            iss = grab_item(c, ntiles);
+            s_item[i_slot & 3] = iss;
             if (iss.tile >= 0) {
                 const int tz = iss.tile / c.ntx;
                 ibk = tz * TY3;
                 ibj = (iss.tile - tz * c.ntx) * TX;
+                i_n = iss.z1 - iss.z0;
             }
         }
-        if (iss.tile < 0) return;
-        const int i = ls - RADIUS;
+        if (iss.tile < 0) return; // no more items
+        const int i = iss.z0 + i_ls;
+        if (++i_ls == i_n) {
+            i_ls = 0;
+            ++i_slot;
+        }
         const int bk = ibk, bj = ibj;
         const int st = t % STAGES;
         float *sg = ring + st * FWD3_STAGE_F;
         const uint32_t bar = smem_u32(&bars[st]);
         fence_proxy_async_smem();
-        mbar_expect_tx(bar, (i >= 0 ? HALO3 + 4 * PT3 : PT3) * 4);
+        mbar_expect_tx(bar, (HALO3 + 4 * PT3) * 4);
         tma_load_4d(smem_u32(sg + HALO3), &a.tm_upt, GXL + bj, bk + GY, i + RADIUS + GZ, iss.s, bar);
-        if (i >= 0) {
-            tma_load_4d(smem_u32(sg), &a.tm_u, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
-            tma_load_4d(smem_u32(sg + HALO3 + PT3), &a.tm_prev, GXL + bj, bk + GY, i + GZ, iss.s, bar);
-            tma_load_4d(smem_u32(sg + HALO3 + 2 * PT3), &a.tm_c2, GXL + bj, bk + GY, i + GZ, 0, bar);
-            tma_load_4d(smem_u32(sg + HALO3 + 3 * PT3), &a.tm_damp, GXL + bj, bk + GY, i + GZ, 0, bar);
-        }
+        tma_load_4d(smem_u32(sg), &a.tm_u, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
+        tma_load_4d(smem_u32(sg + HALO3 + PT3), &a.tm_prev, GXL + bj, bk + GY, i + GZ, iss.s, bar);
+        tma_load_4d(smem_u32(sg + HALO3 + 2 * PT3), &a.tm_c2, GXL + bj, bk + GY, i + GZ, 0, bar);
+        tma_load_4d(smem_u32(sg + HALO3 + 3 * PT3), &a.tm_damp, GXL + bj, bk + GY, i + GZ, 0, bar);
     };
     if (threadIdx.x == 0)
         for (int t = 0; t < D; ++t) issue(t);
@@ -171,7 +191,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
 
     float4 zw[9];
     int slot = 0, ls = 0;
-    Item3 it{-1, 0};
+    Item3 it{-1, 0, 0, 0};
     int k0 = 0, j0 = 0, my_e = 0, re = 0, my_plane = 0x7fffffff;
     int4 src = make_int4(-1, -1, -1, 0);
     float amp = 0.f;
@@ -185,8 +205,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
             k0 = bk + ty;
             j0 = bj + 4 * tx;
             rowok = k0 < L.nyp;
-#pragma unroll
-            for (int z = 0; z < 9; ++z) zw[z] = make_float4(0.f, 0.f, 0.f, 0.f);
+            load_window(zw, a.uin + (long long)it.s * L.fstride, L, it.z0, k0, j0);
             src = c.src[it.s];
             amp = a.last ? 0.f : c.wav[(long long)it.s * c.nt + a.n] * c.src_scale;
             re = 0;
@@ -196,6 +215,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
                 re = a.rt.ptr[it.tile * c.ns + it.s + 1];
                 my_e = e0 + (int)threadIdx.x;
                 if (my_e < re) my_plane = a.rt.ent[my_e].x;
+                while (my_plane < it.z0) { // entries of the segments above
+                    my_e += TPB;
+                    my_plane = my_e < re ? a.rt.ent[my_e].x : 0x7fffffff;
+                }
             }
         }
         const int st = t % STAGES;
@@ -203,8 +226,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
         if (ok) {
             const float *sg = ring + st * FWD3_STAGE_F;
             zw[8] = lds4(&sg[HALO3 + ty * TX + 4 * tx]);
-            const int i = ls - RADIUS;
-            if (i >= 0) {
+            const int i = it.z0 + ls;
+            {
                 const float4 cu = zw[4];
                 const float2 u0[2] = {lo2(cu), hi2(cu)};
                 float2 out[2] = {u0[0], u0[1]};
@@ -279,7 +302,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
             }
             return;
         }
-        if (++ls == NS) {
+        if (++ls == it.z1 - it.z0) {
             ls = 0;
             ++slot;
         }
@@ -306,8 +329,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
     const Step3Common &c = a.c;
     const Lay3D &L = c.L;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int NS = L.nzp + RADIUS;
-    const int ntiles = c.nty * c.ntx, nitems = ntiles * c.ns;
+    const int ntiles = c.nty * c.ntx;
     const int m = a.m;
 
     if (threadIdx.x == 0) {
@@ -319,40 +341,38 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
     __syncthreads();
 
     // (issue: as in the forward step, steps t = 0, 1, 2, ... counted)
-    Item3 iss{-1, 0};
-    int i_slot = 0, i_ls = 0, ibk = 0, ibj = 0;
+    Item3 iss{-1, 0, 0, 0};
+    int i_slot = 0, i_ls = 0, i_n = 1, ibk = 0, ibj = 0;
     auto issue = [&](int t) {
-        const int slot = i_slot, ls = i_ls;
-        if (++i_ls == NS) {
-            i_ls = 0;
-            ++i_slot;
-        }
-        if (ls == 0) {
-            iss = grab_item(c.sched, ntiles, nitems);
-            s_item[slot & 3] = iss;
+        if (i_ls == 0) {
+            iss = grab_item(c, ntiles);
+            s_item[i_slot & 3] = iss;
             if (iss.tile >= 0) {
                 const int tz = iss.tile / c.ntx;
                 ibk = tz * TY3;
                 ibj = (iss.tile - tz * c.ntx) * TX;
+                i_n = iss.z1 - iss.z0;
             }
         }
-        if (iss.tile < 0) return;
-        const int i = ls - RADIUS;
+        if (iss.tile < 0) return; // no more items
+        const int i = iss.z0 + i_ls;
+        if (++i_ls == i_n) {
+            i_ls = 0;
+            ++i_slot;
+        }
         const int bk = ibk, bj = ibj;
         const int st = t % STAGES;
         float *sg = ring + st * BWD3_STAGE_F;
         const uint32_t bar = smem_u32(&bars[st]);
         fence_proxy_async_smem();
-        mbar_expect_tx(bar, (i >= 0 ? 2 * HALO3 + 5 * PT3 : 2 * PT3) * 4);
+        mbar_expect_tx(bar, (2 * HALO3 + 5 * PT3) * 4);
         tma_load_4d(smem_u32(sg + 2 * HALO3), &a.tm_upt, GXL + bj, bk + GY, i + RADIUS + GZ, iss.s, bar);
         tma_load_4d(smem_u32(sg + 2 * HALO3 + PT3), &a.tm_ppt, GXL + bj, bk + GY, i + RADIUS + GZ, iss.s, bar);
-        if (i >= 0) {
-            tma_load_4d(smem_u32(sg), &a.tm_u, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
-            tma_load_4d(smem_u32(sg + HALO3), &a.tm_p, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
-            tma_load_4d(smem_u32(sg + 2 * HALO3 + 2 * PT3), &a.tm_pb, GXL + bj, bk + GY, i + GZ, iss.s, bar);
-            tma_load_4d(smem_u32(sg + 2 * HALO3 + 3 * PT3), &a.tm_c2, GXL + bj, bk + GY, i + GZ, 0, bar);
-            tma_load_4d(smem_u32(sg + 2 * HALO3 + 4 * PT3), &a.tm_damp, GXL + bj, bk + GY, i + GZ, 0, bar);
-        }
+        tma_load_4d(smem_u32(sg), &a.tm_u, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
+        tma_load_4d(smem_u32(sg + HALO3), &a.tm_p, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
+        tma_load_4d(smem_u32(sg + 2 * HALO3 + 2 * PT3), &a.tm_pb, GXL + bj, bk + GY, i + GZ, iss.s, bar);
+        tma_load_4d(smem_u32(sg + 2 * HALO3 + 3 * PT3), &a.tm_c2, GXL + bj, bk + GY, i + GZ, 0, bar);
+        tma_load_4d(smem_u32(sg + 2 * HALO3 + 4 * PT3), &a.tm_damp, GXL + bj, bk + GY, i + GZ, 0, bar);
     };
     if (threadIdx.x == 0)
         for (int t = 0; t < D; ++t) issue(t);
@@ -360,7 +380,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
 
     float4 zu[9], zp[9];
     int slot = 0, ls = 0;
-    Item3 it{-1, 0};
+    Item3 it{-1, 0, 0, 0};
     int k0 = 0, j0 = 0, my_e = 0, re = 0, my_plane = 0x7fffffff;
     int2 zr = make_int2(1, 0);
     int4 src = make_int4(-1, -1, -1, 0);
@@ -375,8 +395,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
             k0 = bk + ty;
             j0 = bj + 4 * tx;
             rowok = k0 < L.nyp;
-#pragma unroll
-            for (int z = 0; z < 9; ++z) zu[z] = zp[z] = make_float4(0.f, 0.f, 0.f, 0.f);
+            load_window(zu, a.uin + (long long)it.s * L.fstride, L, it.z0, k0, j0);
+            load_window(zp, a.pin + (long long)it.s * L.fstride, L, it.z0, k0, j0);
             src = c.src[it.s];
             amp = c.wav[(long long)it.s * c.nt + (m - 1)] * c.src_scale;
             re = 0;
@@ -388,10 +408,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
                 zr = a.rt.zr[it.tile * c.ns + it.s];
                 my_e = e0 + (int)threadIdx.x;
                 if (my_e < re) my_plane = a.rt.ent[my_e].x;
+                while (my_plane < it.z0) { // entries of the segments above
+                    my_e += TPB;
+                    my_plane = my_e < re ? a.rt.ent[my_e].x : 0x7fffffff;
+                }
             }
         }
         const int st = t % STAGES;
-        const int i = ls - RADIUS;
+        const int i = it.z0 + ls;
         // adjoint source of this plane into shared memory (uniform test)
         const bool inj = i >= zr.x && i <= zr.y;
         if (inj) {
@@ -408,7 +432,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
             const float *sg = ring + st * BWD3_STAGE_F;
             zu[8] = lds4(&sg[2 * HALO3 + ty * TX + 4 * tx]);
             zp[8] = lds4(&sg[2 * HALO3 + PT3 + ty * TX + 4 * tx]);
-            if (i >= 0) {
+            {
                 float2 qu[2], qp[2];
                 lap3_4(qu, sg, zu, tx, ty);
                 lap3_4(qp, sg + HALO3, zp, tx, ty);
@@ -471,7 +495,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
             }
             return;
         }
-        if (++ls == NS) {
+        if (++ls == it.z1 - it.z0) {
             ls = 0;
             ++slot;
         }
@@ -529,7 +553,7 @@ struct TuneKey3 {
     }
 };
 std::mutex g_tune3_mu;
-std::map<TuneKey3, int> g_tuned3;
+std::map<TuneKey3, std::pair<int, int>> g_tuned3; // (variant, z-segments; 0: chosen per launch shape)
 
 int sm_count3()
 {
@@ -548,13 +572,20 @@ int step3_variant_for(const Lay3D &L, int ns, bool backward)
 {
     std::lock_guard<std::mutex> lock(g_tune3_mu);
     auto it = g_tuned3.find(TuneKey3{backward, L.nzp, L.nyp, L.nxp, ns});
-    return it == g_tuned3.end() ? 0 : it->second;
+    return it == g_tuned3.end() ? 0 : it->second.first;
 }
 
-void step3_tuned_store(const Lay3D &L, int ns, bool backward, int variant)
+int step3_segments_for(const Lay3D &L, int ns, bool backward)
 {
     std::lock_guard<std::mutex> lock(g_tune3_mu);
-    g_tuned3[TuneKey3{backward, L.nzp, L.nyp, L.nxp, ns}] = variant;
+    auto it = g_tuned3.find(TuneKey3{backward, L.nzp, L.nyp, L.nxp, ns});
+    return it == g_tuned3.end() ? 0 : it->second.second;
+}
+
+void step3_tuned_store(const Lay3D &L, int ns, bool backward, int variant, int nseg)
+{
+    std::lock_guard<std::mutex> lock(g_tune3_mu);
+    g_tuned3[TuneKey3{backward, L.nzp, L.nyp, L.nxp, ns}] = {variant, nseg};
 }
 
 void step3_tuned_clear()
@@ -563,15 +594,47 @@ void step3_tuned_clear()
     g_tuned3.clear();
 }
 
-Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward, int variant)
+// z-segments per column for `per` items (columns x shots) of a launch with
+// `slots` resident CTAs: the count whose rounds of items, times the planes
+// of one item (+2 for the window loads that start a segment), are fewest;
+// segments of at least 16 planes, and a smaller count unless 2% shorter.
+// A column's items are long (every plane of it), so with few items per slot
+// the last round leaves many SMs idle: 200 x 400 x 400 padded to
+// 240 x 440 x 440 in groups of 4 shots has 1540 columns x shots for 608
+// slots (2.53 rounds: 3 x 242 planes), cut in 3 segments 7.6 rounds (8 x
+// 82 planes).
+int pick_segments(int nzp, long long per, long long slots)
+{
+    int best = 1;
+    double best_cost = 1e300;
+    for (int k = 1; k <= 8; ++k) {
+        const int segl = (nzp + k - 1) / k;
+        if (k > 1 && segl < 16) break;
+        if ((nzp + segl - 1) / segl != k) continue; // the same cut as a smaller count
+        const long long rounds = (per * k + slots - 1) / slots;
+        const double cost = (double)rounds * (segl + 2);
+        if (cost < 0.98 * best_cost) {
+            best_cost = cost;
+            best = k;
+        }
+    }
+    return best;
+}
+
+Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward, int variant, int nseg)
 {
     prepare_kernels3();
     if (variant < 0 || variant >= step3_variants(backward)) variant = 0;
     Tiling3 t;
     t.nty = (L.nyp + TY3 - 1) / TY3;
     t.ntx = (L.nxp + TX - 1) / TX;
-    const long long items = (long long)t.nty * t.ntx * ns;
+    const long long per = (long long)t.nty * t.ntx * ns;
     const long long slots = (long long)sm_count3() * variant3(backward, variant).occ;
+    if (nseg <= 0) nseg = pick_segments(L.nzp, per, slots);
+    nseg = std::min(nseg, L.nzp);
+    t.segl = (L.nzp + nseg - 1) / nseg;
+    t.nseg = (L.nzp + t.segl - 1) / t.segl;
+    const long long items = per * t.nseg;
     t.ctas = (int)(items < slots ? items : slots);
     return t;
 }

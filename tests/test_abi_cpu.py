@@ -385,8 +385,8 @@ def test_3d_workspace_and_options(lib):
 
 def test_3d_autotune_set_checks_the_variants(lib):
     """fwi_autotune_set on a 3-D problem accepts the compiled variants (3
-    forward, 2 backward) and refuses others, before any device work;
-    fwi_autotune_reset forgets the choice."""
+    forward, 2 backward) and z-segment counts >= 0 and refuses others, before
+    any device work; fwi_autotune_reset forgets the choice."""
     from paper_1406_1864_gb300 import _lib as L
     g = L.FwiGrid(3, 20, 24, 28, 10.0, 1e-3, 100, 8, 3000.0, 0.05)
     src = np.array([[0, 12, 3]], np.int32)
@@ -398,6 +398,11 @@ def test_3d_autotune_set_checks_the_variants(lib):
         ch = (ctypes.c_int * 4)(fv, 1, bv, 1)
         st = lib.fwi_autotune_set(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o), ch)
         assert (st == L.FWI_OK) == ok, (fv, bv, st)
+    # the 3-D chunks are z-segments per column: 0 (chosen per launch shape) or more
+    for fs, bs, ok in ((0, 0, True), (3, 40, True), (-1, 0, False), (0, -2, False)):
+        ch = (ctypes.c_int * 4)(0, fs, 0, bs)
+        st = lib.fwi_autotune_set(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o), ch)
+        assert (st == L.FWI_OK) == ok, (fs, bs, st)
     assert lib.fwi_autotune_reset() == L.FWI_OK
 
 

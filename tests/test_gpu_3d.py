@@ -146,6 +146,38 @@ def test_3d_every_variant_matches_the_oracle(torch_cuda, case):
         fwi.autotune_reset()
 
 
+def test_3d_z_segments_match_the_oracle(torch_cuda, case):
+    """Columns cut into z-segments (items of segment x column x shot; a
+    segment's first window planes loaded straight from global memory),
+    pinned with the 3-D chunks of fwi_autotune_set: 2 to 30 segments of the
+    30 padded planes (down to one plane per item), so that the receivers at
+    depth and the source in the bottom corner fall in later segments. Traces
+    are the oracle's (1e-5), gradient and illumination too (1e-4), and the
+    gradient is the one-segment gradient up to summation order (1e-6)."""
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import fwi
+    p, g, grid, geom, v, d, d_true, ref = case
+    opts = fwi.Options(ckpt="snapshot", snap="f32")
+    vt = torch.as_tensor(np.ascontiguousarray(p.v_true), device="cuda")
+    try:
+        fwi.autotune_set(grid, geom, opts, {"forward_variant": 0, "forward_chunk": 1,
+                                             "backward_variant": 0, "backward_chunk": 1})
+        one = fwi.adjoint_gradient(grid, geom, v, d, opts)
+        for fs, bs in ((2, 2), (3, 7), (7, 3), (30, 5)):
+            fwi.autotune_set(grid, geom, opts, {"forward_variant": 0, "forward_chunk": fs,
+                                                 "backward_variant": 1, "backward_chunk": bs})
+            seis = fwi.forward(grid, geom, vt, opts=opts).cpu().numpy()
+            for s in range(p.nshots):
+                assert rel(seis[s], d_true[s]) <= 1e-5, (fs, s)
+            r = fwi.adjoint_gradient(grid, geom, v, d, opts)
+            assert rel(r["grad"].cpu(), ref["grad"]) <= 1e-4, (fs, bs)
+            assert rel(r["illum"].cpu(), ref["illum"]) <= 1e-4, (fs, bs)
+            assert rel(r["grad"].cpu(), one["grad"].cpu()) <= 1e-6, (fs, bs)
+            assert abs(float(r["misfit"]) - float(one["misfit"])) <= 1e-12 * float(one["misfit"])
+    finally:
+        fwi.autotune_reset()
+
+
 def test_3d_autograd_with_snapshots(torch_cuda, case):
     """autograd.traces on a 3-D grid: fwi_forward(save = 1) keeps F32 (or
     bfloat16) snapshots, fwi_adjoint_apply is the backward. The OLS loss
