@@ -5,8 +5,10 @@ receivers every cell, shots on a grid at depth 2), times forward modelling
 (per-level step time and algorithmic bandwidth at 16 B per padded
 point-step per shot) and one snapshot-checkpointed gradient per snapshot
 precision, with CUDA events on the library's stream, after fwi_autotune has
-picked the step variants (``--no-autotune``: the defaults). Prints one JSON
-line.
+picked the step variants (``--no-autotune``: the defaults), and from the
+gradient's phase times an upper bound of the backward step per level (20 B
+of fields per padded point-step per shot: psi^{m+1}, psi^{m+2}, psi^m,
+u^{m-1}, c2). Prints one JSON line.
 Defaults: the 200 x 400 x 400, 8-shot, nt 3000 workload in shot groups of 4.
 """
 from __future__ import annotations
@@ -67,6 +69,20 @@ def main():
         dt = time.perf_counter() - t0
         out["gradients"][snap] = {"seconds": dt, "Gpts_per_s": p.phys_points * p.nt * p.nshots / dt / 1e9,
                                   "workspace_GB": fwi.workspace_bytes(grid, geom, o, "gradient") / 1e9}
+        # backward step per level: the 3-D gradient's first phase spans the
+        # time loops of all shot groups (forward passes, the segments'
+        # re-propagation, the backward steps, residuals and snapshot copies);
+        # the forward and re-propagation steps are counted at the forward
+        # pass's step time, the rest is put on the nt - 1 backward steps per
+        # group (an upper bound of the backward step time)
+        ph = fwi.last_phase_times()
+        groups = -(-p.nshots // g)
+        n_bwd = (p.nt - 1) * groups
+        n_rep = ph["adjoint_launches"] - n_bwd
+        if n_bwd > 0 and n_rep >= 0:
+            bus = (1e3 * ph["forward_ms"] - (ph["forward_launches"] + n_rep) * us) / n_bwd
+            out["gradients"][snap]["backward_us_per_level_est"] = bus
+            out["gradients"][snap]["backward_alg_GBps_est"] = 20 * npad * g / (bus * 1e-6) / 1e9
     fwi.profile(False)
     print(json.dumps(out), flush=True)
 

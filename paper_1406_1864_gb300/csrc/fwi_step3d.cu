@@ -342,24 +342,24 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
 
     // (issue: as in the forward step, steps t = 0, 1, 2, ... counted)
     Item3 iss{-1, 0, 0, 0};
-    int i_slot = 0, i_ls = 0, i_n = 1, ibk = 0, ibj = 0;
+    // (plane i_z of the item of slot i_slot; the plane as the counter keeps
+    // the step state to two registers)
+    int i_slot = 0, i_z = 0, i_zend = 0, ibk = 0, ibj = 0;
     auto issue = [&](int t) {
-        if (i_ls == 0) {
+        if (i_z == i_zend) {
             iss = grab_item(c, ntiles);
             s_item[i_slot & 3] = iss;
             if (iss.tile >= 0) {
                 const int tz = iss.tile / c.ntx;
                 ibk = tz * TY3;
                 ibj = (iss.tile - tz * c.ntx) * TX;
-                i_n = iss.z1 - iss.z0;
+                i_z = iss.z0;
+                i_zend = iss.z1;
             }
         }
         if (iss.tile < 0) return; // no more items
-        const int i = iss.z0 + i_ls;
-        if (++i_ls == i_n) {
-            i_ls = 0;
-            ++i_slot;
-        }
+        const int i = i_z;
+        if (++i_z == i_zend) ++i_slot;
         const int bk = ibk, bj = ibj;
         const int st = t % STAGES;
         float *sg = ring + st * BWD3_STAGE_F;
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
     __syncthreads();
 
     float4 zu[9], zp[9];
-    int slot = 0, ls = 0;
+    int slot = 0, zi = 0, zend = 0; // plane zi of the item of slot `slot`
     Item3 it{-1, 0, 0, 0};
     int k0 = 0, j0 = 0, my_e = 0, re = 0, my_plane = 0x7fffffff;
     int2 zr = make_int2(1, 0);
@@ -388,9 +388,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
     bool rowok = false;
     for (int t = 0;; ++t) {
         if (threadIdx.x == 0) issue(t + D);
-        if (ls == 0) {
+        if (zi == zend) {
             it = s_item[slot & 3];
             if (it.tile < 0) break;
+            zi = it.z0;
+            zend = it.z1;
             const int bk = (it.tile / c.ntx) * TY3, bj = (it.tile % c.ntx) * TX;
             k0 = bk + ty;
             j0 = bj + 4 * tx;
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
             }
         }
         const int st = t % STAGES;
-        const int i = it.z0 + ls;
+        const int i = zi;
         // adjoint source of this plane into shared memory (uniform test)
         const bool inj = i >= zr.x && i <= zr.y;
         if (inj) {
@@ -495,10 +497,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
             }
             return;
         }
-        if (++ls == it.z1 - it.z0) {
-            ls = 0;
-            ++slot;
-        }
+        if (++zi == zend) ++slot;
     }
 }
 
