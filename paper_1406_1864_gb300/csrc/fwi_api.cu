@@ -1311,30 +1311,35 @@ fwi_status run_backward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g,
     a.tm_damp = dm;
     if ((e = cudaMemsetAsync(at<char>(ws, pl.sched), 0, pl.sched.bytes, st)) != cudaSuccess)
         return cuda_fail(e, "memset");
+    // Segment j: S[0] = u^{n0}, S[K] = u^{n0-1} from the snapshots; the
+    // re-propagation's step n (levels n0 .. n1) reads u^n (S[n - n0]) and
+    // u^{n-1}, writes u^{n+1} (S[n - n0 + 1]; not at n1) and, in place of
+    // u^{n-1}, which nothing reads after it, the imaging factor
+    // q^n = Lhat u^n + f delta_s / dx of the backward step n + 1.
+    auto qbuf = [&](int i) { return i == 0 ? K : i - 1; }; // buffer of q^{n0 + i}
     for (int j = pl.nck - 1; j >= 0; --j) {
         const int n0 = j * K, n1 = std::min(n0 + K - 1, pl.nt - 2);
         if ((s = snap3_restore(pl, ws, g, j, S[0], S[K], st)) != FWI_OK) return s;
-        for (int n = n0; n < n1; ++n) {
+        for (int n = n0; n <= n1; ++n) {
             const int i = n - n0;
             f.n = n;
             f.last = 0;
             f.tm_u = sh[i];
             f.tm_upt = sp[i];
-            f.tm_prev = sp[i == 0 ? K : i - 1];
+            f.tm_prev = sp[qbuf(i)];
             f.uin = S[i];
-            f.uout = S[i + 1];
+            f.uout = n < n1 ? S[i + 1] : nullptr;
+            f.qout = S[qbuf(i)];
             f.c.sched = at<int>(ws, pl.sched) + 2 * pl.nt + n;
             if ((e = launch_fwd3d(f, pl.tf, pl.vf, st)) != cudaSuccess) return cuda_fail(e, "3-D segment step");
             t_launch[1]++;
         }
         for (int m = n1 + 1; m >= n0 + 1; --m) {
             a.m = m;
-            a.tm_u = sh[m - 1 - n0];
-            a.tm_upt = sp[m - 1 - n0];
+            a.tm_q = sp[qbuf(m - 1 - n0)];
             a.tm_p = ph[(m + 1) & 1];
             a.tm_ppt = pp[(m + 1) & 1];
             a.tm_pb = pp[m & 1];
-            a.uin = S[m - 1 - n0];
             a.pin = Pp[(m + 1) & 1];
             a.pb = Pp[m & 1];
             a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
@@ -1376,12 +1381,10 @@ fwi_status time_backward3(const Plan3 &pl, const fwi_geometry *ge, void *ws, int
     if ((e = cudaEventRecord(ea, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     for (int m = pl.nt - 1; m >= 1 && m > pl.nt - 1 - nlev; --m) {
         a.m = m;
-        a.tm_u = uh[(m - 1) & 1];
-        a.tm_upt = up[(m - 1) & 1];
+        a.tm_q = up[(m - 1) & 1]; // (timing only: any field as the imaging factor)
         a.tm_p = ph[(m + 1) & 1];
         a.tm_ppt = pp[(m + 1) & 1];
         a.tm_pb = pp[m & 1];
-        a.uin = U[(m - 1) & 1];
         a.pin = Pp[(m + 1) & 1];
         a.pb = Pp[m & 1];
         a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;

@@ -202,7 +202,9 @@ struct Fwd3Args {
     CUtensorMap tm_damp; // damping factor, point box (one field)
     Step3Common c;
     const float *uin;    // u^n (the buffer of tm_u / tm_upt): a segment's first planes
-    float *uout;         // u^{n+1} written here
+    float *uout;         // u^{n+1} written here (null: not written)
+    float *qout;         // null, or q^n = Lhat u^n + f delta_s / dx written here; may be the
+                         // u^{n-1} buffer (each point's u^{n-1} is read before its q^n is written)
     float *seis;         // [ns][nt][nrec] or null
     float *acc_illum;    // [nz][ny][nx] or null (red.add)
     Rec3Table rt;
@@ -210,12 +212,12 @@ struct Fwd3Args {
 };
 
 struct Bwd3Args {
-    CUtensorMap tm_u, tm_upt; // u^{m-1}: halo, point boxes
+    CUtensorMap tm_q;         // q^{m-1} = Lhat u^{m-1} + f delta_s / dx (kept by the re-propagation): point box
     CUtensorMap tm_p, tm_ppt; // psi^{m+1}: halo, point boxes
     CUtensorMap tm_pb;        // psi^{m+2}: point box
     CUtensorMap tm_c2, tm_damp;
     Step3Common c;
-    const float *uin, *pin;   // u^{m-1}, psi^{m+1} (the buffers of tm_u, tm_p): a segment's first planes
+    const float *pin;         // psi^{m+1} (the buffer of tm_p): a segment's first planes
     float *pb;                // psi^m written here (the psi^{m+2} buffer)
     const float *adj;         // [ns][nt][nrec] adjoint source or null
     float *acc_grad;          // [nzp][nyp][nxp] (red.add)

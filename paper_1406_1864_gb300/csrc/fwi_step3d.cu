@@ -253,8 +253,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
                                                   mul2(kb, sub2(u0[h], half2of(um4, h)))));
                     }
                     if (rowok && j0 < L.nxp) {
-                        const float o[4] = {out[0].x, out[0].y, out[1].x, out[1].y};
-                        store4(a.uout + so + fidx3(L, i, k0, j0), j0, L.nxp, o);
+                        if (a.uout != nullptr) {
+                            const float o[4] = {out[0].x, out[0].y, out[1].x, out[1].y};
+                            store4(a.uout + so + fidx3(L, i, k0, j0), j0, L.nxp, o);
+                        }
+                        if (a.qout != nullptr) { // for the backward step's imaging
+                            const float qv[4] = {q[0].x, q[0].y, q[1].x, q[1].y};
+                            store4(a.qout + so + fidx3(L, i, k0, j0), j0, L.nxp, qv);
+                        }
                     }
                     if (a.illum_utt && a.acc_illum != nullptr) {
                         // (u^{n+1} - 2u^n + u^{n-1})^2 replaces u^2
@@ -310,8 +316,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
 }
 
 // ----------------------------------------------------------- backward step
-// stage: [halo u(i)] [halo psi(i)] [u(i+4)] [psi(i+4)] [psi_b(i)] [c2(i)] [damp(i)]
-constexpr int BWD3_STAGE_F = 2 * HALO3 + 5 * PT3;
+// The imaging factor q^{m-1} = Lhat u^{m-1} + f delta_s / dx is the one the
+// re-propagation's forward step m-1 computed (and kept): read as a point
+// tile, bitwise the value a Laplacian here would give.
+// stage: [halo psi(i)] [psi(i+4)] [psi_b(i)] [c2(i)] [damp(i)] [q(i)]
+constexpr int BWD3_STAGE_F = HALO3 + 5 * PT3;
 
 template <int STAGES, int MINB>
 __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd3Args a)
@@ -365,26 +374,23 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
         float *sg = ring + st * BWD3_STAGE_F;
         const uint32_t bar = smem_u32(&bars[st]);
         fence_proxy_async_smem();
-        mbar_expect_tx(bar, (2 * HALO3 + 5 * PT3) * 4);
-        tma_load_4d(smem_u32(sg + 2 * HALO3), &a.tm_upt, GXL + bj, bk + GY, i + RADIUS + GZ, iss.s, bar);
-        tma_load_4d(smem_u32(sg + 2 * HALO3 + PT3), &a.tm_ppt, GXL + bj, bk + GY, i + RADIUS + GZ, iss.s, bar);
-        tma_load_4d(smem_u32(sg), &a.tm_u, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
-        tma_load_4d(smem_u32(sg + HALO3), &a.tm_p, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
-        tma_load_4d(smem_u32(sg + 2 * HALO3 + 2 * PT3), &a.tm_pb, GXL + bj, bk + GY, i + GZ, iss.s, bar);
-        tma_load_4d(smem_u32(sg + 2 * HALO3 + 3 * PT3), &a.tm_c2, GXL + bj, bk + GY, i + GZ, 0, bar);
-        tma_load_4d(smem_u32(sg + 2 * HALO3 + 4 * PT3), &a.tm_damp, GXL + bj, bk + GY, i + GZ, 0, bar);
+        mbar_expect_tx(bar, (HALO3 + 5 * PT3) * 4);
+        tma_load_4d(smem_u32(sg + HALO3), &a.tm_ppt, GXL + bj, bk + GY, i + RADIUS + GZ, iss.s, bar);
+        tma_load_4d(smem_u32(sg), &a.tm_p, GXL + bj - RADIUS, bk + GY - RADIUS, i + GZ, iss.s, bar);
+        tma_load_4d(smem_u32(sg + HALO3 + PT3), &a.tm_pb, GXL + bj, bk + GY, i + GZ, iss.s, bar);
+        tma_load_4d(smem_u32(sg + HALO3 + 2 * PT3), &a.tm_c2, GXL + bj, bk + GY, i + GZ, 0, bar);
+        tma_load_4d(smem_u32(sg + HALO3 + 3 * PT3), &a.tm_damp, GXL + bj, bk + GY, i + GZ, 0, bar);
+        tma_load_4d(smem_u32(sg + HALO3 + 4 * PT3), &a.tm_q, GXL + bj, bk + GY, i + GZ, iss.s, bar);
     };
     if (threadIdx.x == 0)
         for (int t = 0; t < D; ++t) issue(t);
     __syncthreads();
 
-    float4 zu[9], zp[9];
+    float4 zp[9];
     int slot = 0, zi = 0, zend = 0; // plane zi of the item of slot `slot`
     Item3 it{-1, 0, 0, 0};
     int k0 = 0, j0 = 0, my_e = 0, re = 0, my_plane = 0x7fffffff;
     int2 zr = make_int2(1, 0);
-    int4 src = make_int4(-1, -1, -1, 0);
-    float amp = 0.f;
     bool rowok = false;
     for (int t = 0;; ++t) {
         if (threadIdx.x == 0) issue(t + D);
@@ -397,10 +403,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
             k0 = bk + ty;
             j0 = bj + 4 * tx;
             rowok = k0 < L.nyp;
-            load_window(zu, a.uin + (long long)it.s * L.fstride, L, it.z0, k0, j0);
             load_window(zp, a.pin + (long long)it.s * L.fstride, L, it.z0, k0, j0);
-            src = c.src[it.s];
-            amp = c.wav[(long long)it.s * c.nt + (m - 1)] * c.src_scale;
             re = 0;
             my_plane = 0x7fffffff;
             zr = make_int2(1, 0);
@@ -432,19 +435,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
         const bool ok = stage_ready<STAGES>(bars, t, &s_abort);
         if (ok) {
             const float *sg = ring + st * BWD3_STAGE_F;
-            zu[8] = lds4(&sg[2 * HALO3 + ty * TX + 4 * tx]);
-            zp[8] = lds4(&sg[2 * HALO3 + PT3 + ty * TX + 4 * tx]);
+            zp[8] = lds4(&sg[HALO3 + ty * TX + 4 * tx]);
             {
-                float2 qu[2], qp[2];
-                lap3_4(qu, sg, zu, tx, ty);
-                lap3_4(qp, sg + HALO3, zp, tx, ty);
-                if (i == src.x && k0 == src.y) {
-                    const int d = src.z - j0;
-                    if (d == 0) qu[0].x += amp;
-                    if (d == 1) qu[0].y += amp;
-                    if (d == 2) qu[1].x += amp;
-                    if (d == 3) qu[1].y += amp;
-                }
+                float2 qp[2];
+                lap3_4(qp, sg, zp, tx, ty);
                 if (inj) {
                     // each thread reads and clears its own four entries; the
                     // end-of-iteration barrier orders the clear before the
@@ -456,9 +450,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
                     qp[1] = add2(qp[1], hi2(s4));
                 }
                 const float4 p1 = zp[4];
-                const float4 pb4 = lds4(&sg[2 * HALO3 + 2 * PT3 + ty * TX + 4 * tx]);
-                const float4 c24 = lds4(&sg[2 * HALO3 + 3 * PT3 + ty * TX + 4 * tx]);
-                const float4 ia4 = lds4(&sg[2 * HALO3 + 4 * PT3 + ty * TX + 4 * tx]);
+                const float4 pb4 = lds4(&sg[HALO3 + PT3 + ty * TX + 4 * tx]);
+                const float4 c24 = lds4(&sg[HALO3 + 2 * PT3 + ty * TX + 4 * tx]);
+                const float4 ia4 = lds4(&sg[HALO3 + 3 * PT3 + ty * TX + 4 * tx]);
+                const float4 q4 = lds4(&sg[HALO3 + 4 * PT3 + ty * TX + 4 * tx]);
                 float2 pn[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -472,7 +467,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
                     const float o[4] = {pn[0].x, pn[0].y, pn[1].x, pn[1].y};
                     store4(a.pb + so + fidx3(L, i, k0, j0), j0, L.nxp, o);
                     // imaging: G += psi^m (Lhat u^{m-1} + f delta_s / dx), padded grid
-                    const float g[4] = {pn[0].x * qu[0].x, pn[0].y * qu[0].y, pn[1].x * qu[1].x, pn[1].y * qu[1].y};
+                    const float g[4] = {pn[0].x * q4.x, pn[0].y * q4.y, pn[1].x * q4.z, pn[1].y * q4.w};
                     const long long rowb = ((long long)i * L.nyp + k0) * L.nxp;
                     if ((L.nxp & 3) == 0 && j0 + 3 < L.nxp) {
                         red_add4(a.acc_grad + rowb + j0, g[0], g[1], g[2], g[3]);
@@ -485,10 +480,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
             }
         }
 #pragma unroll
-        for (int z = 0; z < 8; ++z) {
-            zu[z] = zu[z + 1];
-            zp[z] = zp[z + 1];
-        }
+        for (int z = 0; z < 8; ++z) zp[z] = zp[z + 1];
         __syncthreads();
         if (s_abort) {
             if (threadIdx.x == 0) {
@@ -514,7 +506,7 @@ struct Variant3 {
 #define V3F(ST, MINB) {256 + (ST) * FWD3_STAGE_F * 4, (const void *)k_fwd3d<ST, MINB>, 0}
 #define V3B(ST, MINB) {256 + (ST) * BWD3_STAGE_F * 4, (const void *)k_bwd3d<ST, MINB>, 0}
 Variant3 g_var3f[] = {V3F(3, 4), V3F(3, 5), V3F(2, 5)};
-Variant3 g_var3b[] = {V3B(3, 3), V3B(2, 4)};
+Variant3 g_var3b[] = {V3B(3, 3), V3B(2, 4), V3B(3, 4), V3B(2, 5)};
 constexpr int NV3F = (int)(sizeof g_var3f / sizeof g_var3f[0]);
 constexpr int NV3B = (int)(sizeof g_var3b / sizeof g_var3b[0]);
 

@@ -385,7 +385,7 @@ def test_3d_workspace_and_options(lib):
 
 def test_3d_autotune_set_checks_the_variants(lib):
     """fwi_autotune_set on a 3-D problem accepts the compiled variants (3
-    forward, 2 backward) and z-segment counts >= 0 and refuses others, before
+    forward, 4 backward) and z-segment counts >= 0 and refuses others, before
     any device work; fwi_autotune_reset forgets the choice."""
     from paper_1406_1864_gb300 import _lib as L
     g = L.FwiGrid(3, 20, 24, 28, 10.0, 1e-3, 100, 8, 3000.0, 0.05)
@@ -394,7 +394,7 @@ def test_3d_autotune_set_checks_the_variants(lib):
     ge = L.FwiGeometry(1, 2, src.ctypes.data, rec.ctypes.data, 1)
     o = L.FwiOptions(0, 0, -1, 1, 1e-3)
     o.ckpt = L.FWI_CKPT_SNAPSHOT
-    for fv, bv, ok in ((0, 0, True), (2, 1, True), (3, 0, False), (0, 2, False), (-1, 0, False)):
+    for fv, bv, ok in ((0, 0, True), (2, 3, True), (3, 0, False), (0, 4, False), (-1, 0, False)):
         ch = (ctypes.c_int * 4)(fv, 1, bv, 1)
         st = lib.fwi_autotune_set(ctypes.byref(g), ctypes.byref(ge), ctypes.byref(o), ch)
         assert (st == L.FWI_OK) == ok, (fv, bv, st)
