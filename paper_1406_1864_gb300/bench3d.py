@@ -7,8 +7,9 @@ point-step per shot) and one snapshot-checkpointed gradient per snapshot
 precision, with CUDA events on the library's stream, after fwi_autotune has
 picked the step variants (``--no-autotune``: the defaults), and from the
 gradient's phase times an upper bound of the backward step per level (20 B
-of fields per padded point-step per shot: psi^{m+1}, psi^{m+2}, psi^m,
-u^{m-1}, c2). Prints one JSON line.
+of fields per padded point-step per shot: psi^{m+1}, psi^{m+2}, psi^m, the
+imaging factor q^{m-1} kept by the re-propagation, c2). Prints one JSON
+line.
 Defaults: the 200 x 400 x 400, 8-shot, nt 3000 workload in shot groups of 4.
 """
 from __future__ import annotations

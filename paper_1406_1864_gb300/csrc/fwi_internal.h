@@ -4,6 +4,7 @@
 #pragma once
 
 #include "fwi_args.h"
+#include "fwi_args3d.h"
 
 namespace fwi {
 // 3-D steps: compiled variants of the forward (backward = false) or backward
