@@ -127,7 +127,9 @@ __device__ __forceinline__ void load_window(float4 (&zw)[9], const float *f, con
 // stage: [halo u(i)] [u(i+4)] [u_prev(i)] [c2(i)] [damp(i)]
 constexpr int FWD3_STAGE_F = HALO3 + 4 * PT3;
 
-template <int STAGES, int MINB>
+// QOUT: also store q^n (a.qout) and skip u^{n+1} where a.uout is null (the
+// segments' re-propagation); otherwise neither test is compiled
+template <int STAGES, int MINB, bool QOUT = false>
 __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd3Args a)
 {
     constexpr int D = STAGES - 1;
@@ -253,11 +255,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd3d(const __grid_constant__ Fwd
                                                   mul2(kb, sub2(u0[h], half2of(um4, h)))));
                     }
                     if (rowok && j0 < L.nxp) {
-                        if (a.uout != nullptr) {
+                        if (!QOUT || a.uout != nullptr) {
                             const float o[4] = {out[0].x, out[0].y, out[1].x, out[1].y};
                             store4(a.uout + so + fidx3(L, i, k0, j0), j0, L.nxp, o);
                         }
-                        if (a.qout != nullptr) { // for the backward step's imaging
+                        if (QOUT) { // for the backward step's imaging
                             const float qv[4] = {q[0].x, q[0].y, q[1].x, q[1].y};
                             store4(a.qout + so + fidx3(L, i, k0, j0), j0, L.nxp, qv);
                         }
@@ -501,10 +503,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd3d(const __grid_constant__ Bwd
 struct Variant3 {
     int smem;
     const void *fn;
-    int occ; // resident CTAs per SM (occupancy calculator)
+    int occ;          // resident CTAs per SM (occupancy calculator)
+    const void *fn_q; // forward step: the instance that also stores q^n
 };
-#define V3F(ST, MINB) {256 + (ST) * FWD3_STAGE_F * 4, (const void *)k_fwd3d<ST, MINB>, 0}
-#define V3B(ST, MINB) {256 + (ST) * BWD3_STAGE_F * 4, (const void *)k_bwd3d<ST, MINB>, 0}
+#define V3F(ST, MINB) \
+    {256 + (ST) * FWD3_STAGE_F * 4, (const void *)k_fwd3d<ST, MINB, false>, 0, (const void *)k_fwd3d<ST, MINB, true>}
+#define V3B(ST, MINB) {256 + (ST) * BWD3_STAGE_F * 4, (const void *)k_bwd3d<ST, MINB>, 0, nullptr}
 Variant3 g_var3f[] = {V3F(3, 4), V3F(3, 5), V3F(2, 5)};
 Variant3 g_var3b[] = {V3B(3, 3), V3B(2, 4), V3B(3, 4), V3B(2, 5)};
 constexpr int NV3F = (int)(sizeof g_var3f / sizeof g_var3f[0]);
@@ -525,6 +529,7 @@ void prepare_kernels3()
                 int occ = 0;
                 if (have_dev) {
                     cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem);
+                    if (v.fn_q) cudaFuncSetAttribute(v.fn_q, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem);
                     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, TPB, v.smem) != cudaSuccess)
                         occ = 0;
                 }
@@ -631,24 +636,28 @@ Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward, int variant, int nse
 }
 
 namespace {
-template <class A> cudaError_t launch3(const Variant3 &v, const A &a, const Tiling3 &t, cudaStream_t st)
+template <class A>
+cudaError_t launch3(const void *fn, const Variant3 &v, const A &a, const Tiling3 &t, cudaStream_t st)
 {
     if (t.ctas <= 0) return cudaSuccess;
     void *args[] = {const_cast<A *>(&a)};
-    return cudaLaunchKernel(v.fn, dim3(t.ctas), dim3(TPB), args, v.smem, st);
+    return cudaLaunchKernel(fn, dim3(t.ctas), dim3(TPB), args, v.smem, st);
 }
 } // namespace
 
 cudaError_t launch_fwd3d(const Fwd3Args &a, const Tiling3 &t, int variant, cudaStream_t st)
 {
     if (variant < 0 || variant >= NV3F) return cudaErrorInvalidValue;
-    return launch3(g_var3f[variant], a, t, st);
+    if (a.uout == nullptr && a.qout == nullptr) return cudaErrorInvalidValue;
+    const Variant3 &v = g_var3f[variant];
+    return launch3(a.qout != nullptr ? v.fn_q : v.fn, v, a, t, st);
 }
 
 cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, int variant, cudaStream_t st)
 {
     if (variant < 0 || variant >= NV3B) return cudaErrorInvalidValue;
-    return launch3(g_var3b[variant], a, t, st);
+    const Variant3 &v = g_var3b[variant];
+    return launch3(v.fn, v, a, t, st);
 }
 
 bool encode_field_map3(CUtensorMap *map, const float *base, const Lay3D &L, int nfields, int bx, int by)
