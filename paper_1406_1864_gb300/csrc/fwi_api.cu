@@ -638,10 +638,14 @@ fwi_status run_forward(const Plan &pl, const fwi_geometry *ge, void *ws, float *
 
 // Backward loop with snapshot checkpoints. For segment j = nck-1..0 (levels
 // n_j = jK .. e_j = min(jK+K-1, nt-2)): restore (u^{n_j}, u^{n_j-1}) from
-// snapshot j, re-run forward steps n_j..e_j-1 into one slot per level, then
-// run adjoint steps m = e_j+1 .. n_j+1, each reading u^{m-1} from its slot.
-// The re-run is the same plain forward step as the forward loop (no traces,
-// no accumulators), so with F32 snapshots u^{m-1} is the forward's own value.
+// snapshot j, re-run forward steps n_j..e_j into one slot per level, then
+// run adjoint steps m = e_j+1 .. n_j+1. The re-run is the same plain forward
+// step as the forward loop (no traces, no accumulators), so with F32
+// snapshots it reproduces the forward's own fields; its step n also keeps
+// the imaging factor q^n = Lhat u^n + f delta_s, in place of u^{n-1} (read
+// only by the thread that then writes q^n there), and adjoint step m reads
+// q^{m-1} instead of computing it from u^{m-1}. Step e_j computes q^{e_j}
+// only.
 fwi_status run_backward_segments(const Plan &pl, const fwi_geometry *ge, void *ws, BwdArgs &a, float *const U[2],
                                  float *const Pp[2], const CUtensorMap ph[2], const CUtensorMap pp[2], cudaStream_t st)
 {
@@ -660,26 +664,29 @@ fwi_status run_backward_segments(const Plan &pl, const fwi_geometry *ge, void *w
     int fhx, fhy, fpx, fpy, bhx, bhy, bpx, bpy;
     step_boxes(STEP_FWD, pl.tr, fhx, fhy, fpx, fpy);
     step_boxes(STEP_BWD, pl.tb, bhx, bhy, bpx, bpy);
-    std::vector<CUtensorMap> fh(K + 1), fp(K + 1), bh(K + 1);
+    std::vector<CUtensorMap> fh(K + 1), fp(K + 1), bq(K + 1);
     for (int i = 0; i <= K; ++i)
         if (!encode_field_map(&fh[i], S[i], pl.L, pl.ns, fhx, fhy, pl.tr.spi) ||
             !encode_field_map(&fp[i], S[i], pl.L, pl.ns, fpx, fpy, pl.tr.spi) ||
-            !encode_field_map(&bh[i], S[i], pl.L, pl.ns, bhx, bhy))
+            !encode_field_map(&bq[i], S[i], pl.L, pl.ns, bpx, bpy))
             return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed for the segment buffers");
+    auto qbuf = [&](int i) { return i == 0 ? K : i - 1; }; // slot of q^{n_j + i}
     FwdArgs f{};
     f.c = make_common(pl, ge, ws, pl.tr);
     f.hmax = -1;
+    a.qin = 1;
     for (int j = pl.nck - 1; j >= 0; --j) {
         const int n0 = j * K, n1 = std::min(n0 + K - 1, pl.nt - 2);
         fwi_status sr = restore_snapshot(pl, ws, j, S[0], S[K], st);
         if (sr != FWI_OK) return sr;
-        for (int n = n0; n < n1; ++n) {
+        for (int n = n0; n <= n1; ++n) {
             const int i = n - n0;
             f.n = n;
             f.last = 0;
             f.tm_cur = fh[i];
-            f.tm_prev = fp[i == 0 ? K : i - 1];
-            f.uout = S[i + 1];
+            f.tm_prev = fp[qbuf(i)];
+            f.uout = n < n1 ? S[i + 1] : nullptr;
+            f.qout = S[qbuf(i)];
             f.c.sched = at<int>(ws, pl.sched) + 2 * pl.nt + n;
             if ((e = launch_fwd_step(f, pl.tr, false, st)) != cudaSuccess) return cuda_fail(e, "segment step");
             t_launch[1]++;
@@ -687,7 +694,7 @@ fwi_status run_backward_segments(const Plan &pl, const fwi_geometry *ge, void *w
         for (int m = n1 + 1; m >= n0 + 1; --m) {
             a.m = m;
             a.c.sched = at<int>(ws, pl.sched) + pl.nt + m;
-            a.tm_ub = bh[m - 1 - n0];
+            a.tm_ub = bq[qbuf(m - 1 - n0)];
             a.tm_pa = ph[(m + 1) & 1];
             a.tm_ua = pp[m & 1]; // not read without reconstruction
             a.tm_pb = pp[m & 1];

@@ -101,6 +101,8 @@ struct FwdArgs {
     StepCommon c;
     float *uout;           // u^{n+1} is written here (the u^{n-1} buffer, or a
                            // segment slot when re-propagating from a snapshot)
+    float *qout;           // re-propagation: q^n = Lhat u^n + f delta_s (in place of
+                           // u^{n-1}) for the backward step's imaging, else null
     float *band;           // [ns][nt][nbandp] checkpoints (u^{n+1} stored) or null
     float *seis;           // [ns][nt][nrec] traces or null
     float *acc_illum;      // [nz][nx] or null (red.add)
@@ -113,7 +115,7 @@ struct FwdArgs {
 };
 
 struct BwdArgs {
-    CUtensorMap tm_ub;     // u^{m-1}, halo box
+    CUtensorMap tm_ub;     // u^{m-1}, halo box (qin: q^{m-1}, point box)
     CUtensorMap tm_pa;     // psi^{m+1}, halo box
     CUtensorMap tm_ua;     // u^m, point box
     CUtensorMap tm_pb;     // psi^{m+2}, point box
@@ -131,6 +133,8 @@ struct BwdArgs {
     int m;
     int recon;             // 1: rebuild u^{m-2} (model) / restore it (sponge);
                            // 0: u^{m-1} comes from a re-propagated segment
+    int qin;               // 1: the imaging factor q^{m-1} = Lhat u^{m-1} + f delta_s
+                           // is read (tm_ub), kept by the segment's re-propagation
 };
 
 // The work of one step launch: the (tile, shot) pairs of one model, or of up

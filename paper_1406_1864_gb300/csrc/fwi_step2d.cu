@@ -323,9 +323,13 @@ using FwdRing = Ring<8 * RZ, HX, SPI, SPI, STAGES, 2 * 8 * RZ * TX * 4>; // + c2
 
 // NHC: offsets h = 0 .. NHC-1 of the offset Hessian are accumulated (any
 // hmax <= NHC-1; offsets above hmax are computed and not stored)
-template <int RZ, int HX, bool WITH_H, int STAGES, int MINB, int NM, int SPI = 1, int NHC = HMAX_LIMIT + 1>
+// QOUT (segments re-propagated from snapshots): also store q^n = Lhat u^n +
+// f delta_s at a.qout, and u^{n+1} only where a.uout is not null
+template <int RZ, int HX, bool WITH_H, int STAGES, int MINB, int NM, int SPI = 1, int NHC = HMAX_LIMIT + 1,
+          bool QOUT = false>
 __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ Batch<FwdArgs, NM> B)
 {
+    static_assert(!QOUT || (!WITH_H && NM == 1), "q output: plain forward step of one model");
     using R = FwdRing<RZ, HX, WITH_H, STAGES, SPI>;
     static_assert(SPI == 1 || R::HALO_B == R::HALO * 4, "contiguous shot tiles");
     constexpr int TZ = 8 * RZ;
@@ -540,12 +544,20 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                     const float4 um4 = lds4(&pm[(ty * RZ + r) * TX + 4 * tx]);
                     const float4 c24 = lds4(&c2s[(ty * RZ + r) * TX + 4 * tx]);
                     float2 out[2];
+                    if constexpr (QOUT) {
+                        // in place of u^{n-1}: this thread read its points' u^{n-1} (um4) above
+                        const int i = i0 + r;
+                        const float qv[4] = {q[0].x, q[0].y, q[1].x, q[1].y};
+                        if (colok && i < L.nzp)
+                            store4(a.qout + (long long)ss * L.fstride + fidx(L, i, j0), j0, L.nxp, qv);
+                    }
                     if (!tile_sponge) {
 #pragma unroll
                         for (int h = 0; h < 2; ++h)
                             out[h] = add2(u0[h], fma2(half2of(c24, h), q[h], sub2(u0[h], half2of(um4, h))));
-                        *reinterpret_cast<float4 *>(up + fidx(L, i0 + r, j0)) =
-                            make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+                        if (!QOUT || a.uout != nullptr)
+                            *reinterpret_cast<float4 *>(up + fidx(L, i0 + r, j0)) =
+                                make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
                     } else {
                         // damped update; identical to the plain one where eta = 0
                         const int i = i0 + r;
@@ -558,7 +570,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_fwd_step(const __grid_constant__ 
                                                       mul2(kb, sub2(u0[h], half2of(um4, h)))));
                         }
                         const float o[4] = {out[0].x, out[0].y, out[1].x, out[1].y};
-                        if (colok && i < L.nzp) store4(up + fidx(L, i, j0), j0, L.nxp, o);
+                        if ((!QOUT || a.uout != nullptr) && colok && i < L.nzp) store4(up + fidx(L, i, j0), j0, L.nxp, o);
                         if (a.band != nullptr && sg.brow[r] != -1) {
                             float *bb = a.band + ((long long)ss * c.nt + a.n + 1) * L.nbandp;
                             if (sg.brow[r] >= 0) {
@@ -733,9 +745,12 @@ template <int RZ, int STAGES, int HE>
 using BwdRingE = Ring<8 * RZ, RADIUS + 2 * HE, 2, 2, STAGES,
                       3 * 8 * RZ * TX * 4 + (HE > 0 ? 8 * RZ * (TX + 4 * HE) * 4 : 0)>;
 
-template <int RZ, int STAGES, int MINB, int NM, int HE = 0>
+// QIN: q^{m-1} is read as a point tile (into the first halo slot) instead of
+// computed from a u^{m-1} halo tile (snapshot checkpoints, one model)
+template <int RZ, int STAGES, int MINB, int NM, int HE = 0, bool QIN = false>
 __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ Batch<BwdArgs, NM> B)
 {
+    static_assert(!QIN || (HE == 0 && NM == 1), "q input: plain backward step of one model");
     static_assert(HE == 0 || (HE % 2 == 0 && NM == 1), "extended imaging: even HE, one model");
     using R = BwdRingE<RZ, STAGES, HE>;
     constexpr int TZ = 8 * RZ;
@@ -783,10 +798,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
         const int bi = bz * TZ, bj = bx * TX;
         const int st = k % STAGES;
         const uint32_t bar = smem_u32(&bars[st]);
-        const bool need_ua = recon && m >= 2;
+        const bool need_ua = !QIN && recon && m >= 2;
         fence_proxy_async_smem();
-        mbar_expect_tx(bar, (2 * R::HALO + (need_ua ? 2 : 1) * R::PT) * 4);
-        tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_ub, GXL + bj - HX, bi, d.s, bar);
+        mbar_expect_tx(bar, ((QIN ? 1 : 2) * R::HALO + (need_ua ? 2 : 1) * R::PT + (QIN ? R::PT : 0)) * 4);
+        if constexpr (QIN)
+            tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_ub, GXL + bj, bi + GZ, d.s, bar);
+        else
+            tma_load_3d(smem_u32(R::halo(smem, st, 0)), &a.tm_ub, GXL + bj - HX, bi, d.s, bar);
         tma_load_3d(smem_u32(R::halo(smem, st, 1)), &a.tm_pa, GXL + bj - HX, bi, d.s, bar);
         tma_load_3d(smem_u32(R::point(smem, st, 1)), &a.tm_pb, GXL + bj, bi + GZ, d.s, bar);
         if (need_ua) tma_load_3d(smem_u32(R::point(smem, st, 0)), &a.tm_ua, GXL + bj, bi + GZ, d.s, bar);
@@ -983,7 +1001,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
             // step m-1; done above with the extended image), then Lhat psi^{m+1};
             // one column window live at a time
 #pragma unroll
-            for (int fld = HE > 0 ? 1 : 0; fld < 2; ++fld) {
+            for (int fld = (HE > 0 || QIN) ? 1 : 0; fld < 2; ++fld) {
                 const float *sf = fld == 0 ? su : sp;
                 float4 zc[RZ + 2 * RADIUS];
 #pragma unroll
@@ -1003,7 +1021,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
 #pragma unroll
             for (int r = 0; r < RZ; ++r) {
                 const float amp = now.amp * c.src_scale;
-                if (HE == 0 && src_tile) {
+                if constexpr (QIN) { // the kept q^{m-1}, its source term included
+                    const float4 q4 = lds4(&su[(ty * RZ + r) * TX + 4 * tx]);
+                    qu[r][0] = lo2(q4);
+                    qu[r][1] = hi2(q4);
+                } else if (HE == 0 && src_tile) {
                     if (sslot == r * 4 + 0) qu[r][0].x += amp;
                     if (sslot == r * 4 + 1) qu[r][0].y += amp;
                     if (sslot == r * 4 + 2) qu[r][1].x += amp;
@@ -1015,7 +1037,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bwd_step(const __grid_constant__ 
                     qp[r][1] = add2(qp[r][1], hi2(inj));
                 }
                 const int sr = ty * RZ + r + RADIUS;
-                const float4 uc = lds4(&su[sr * TXS + HX + 4 * tx]);
+                const float4 uc = QIN ? make_float4(0.f, 0.f, 0.f, 0.f) : lds4(&su[sr * TXS + HX + 4 * tx]); // (QIN: no rebuild)
                 const float4 pc = lds4(&sp[sr * TXS + HX + 4 * tx]);
                 const float2 p1[2] = {lo2(pc), hi2(pc)};
                 const float2 u1[2] = {lo2(uc), hi2(uc)};
@@ -1366,23 +1388,27 @@ namespace {
 struct Variant {
     int rz, spi, smem; // tile rows / 8, shots per item, dynamic shared memory
     int nh;            // offsets of the offset Hessian it accumulates (valid for hmax <= nh - 1)
-    const void *fn[2]; // one model per launch, batch of up to BATCH_MAX models
+    const void *fn[3]; // one model per launch, batch of up to BATCH_MAX models, and (plain
+                       // forward and backward steps) the one-model instance that keeps (forward)
+                       // or reads (backward) the imaging factor q of a re-propagated segment
     int occ[2];        // resident CTAs per SM (from the occupancy calculator)
 };
 
 #define FWD_VARIANT(RZ, ST, MINB, SPI)                                                     \
     {RZ, SPI, FwdRing<RZ, RADIUS, false, ST, SPI>::SMEM, 0,                                \
      {(const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, 1, SPI>,                       \
-      (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, BATCH_MAX, SPI>},              \
+      (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, BATCH_MAX, SPI>,               \
+      (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, 1, SPI, HMAX_LIMIT + 1, true>}, \
      {0, 0}}
 #define FWDH_VARIANT(ST, MINB, SPI, NHC)                                                   \
     {1, SPI, FwdRing<1, HMAX_LIMIT, true, ST, SPI>::SMEM, NHC,                             \
      {(const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, 1, SPI, NHC>,                \
-      (const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, BATCH_MAX, SPI, NHC>},       \
+      (const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, BATCH_MAX, SPI, NHC>, nullptr}, \
      {0, 0}}
 #define BWD_VARIANT(RZ, ST, MINB)                                                          \
     {RZ, 1, BwdRing<RZ, ST>::SMEM, 0,                                                      \
-     {(const void *)k_bwd_step<RZ, ST, MINB, 1>, (const void *)k_bwd_step<RZ, ST, MINB, BATCH_MAX>}, \
+     {(const void *)k_bwd_step<RZ, ST, MINB, 1>, (const void *)k_bwd_step<RZ, ST, MINB, BATCH_MAX>, \
+      (const void *)k_bwd_step<RZ, ST, MINB, 1, 0, true>},                                \
      {0, 0}}
 
 // forward: 64 x 16 tiles (3 stages, 4 CTAs/SM), 64 x 32 (2 stages), 64 x 8
@@ -1436,6 +1462,9 @@ void prepare_kernels()
                     }
                     v[i].occ[b] = occ > 0 ? occ : 2;
                 }
+            for (int i = 0; i < n; ++i)
+                if (have_dev && v[i].fn[2])
+                    cudaFuncSetAttribute(v[i].fn[2], cudaFuncAttributeMaxDynamicSharedMemorySize, v[i].smem);
         }
         cudaGetLastError();
     });
@@ -1597,16 +1626,19 @@ cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, c
 {
     int n = 0;
     const Variant &v = variants(with_offh ? STEP_FWD_OFFH : STEP_FWD, n)[t.variant];
+    if (a.qout != nullptr && (with_offh || !v.fn[2])) return cudaErrorInvalidValue;
+    if (a.qout == nullptr && a.uout == nullptr) return cudaErrorInvalidValue;
     Batch<FwdArgs, 1> b;
-    return launch_variant(v, 0, b, batch_fill(b, &a, &t, 1, v.occ[0]), st);
+    return launch_variant(v, a.qout != nullptr ? 2 : 0, b, batch_fill(b, &a, &t, 1, v.occ[0]), st);
 }
 
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st)
 {
     int n = 0;
     const Variant &v = variants(STEP_BWD, n)[t.variant];
+    if (a.qin && (a.recon || !v.fn[2])) return cudaErrorInvalidValue;
     Batch<BwdArgs, 1> b;
-    return launch_variant(v, 0, b, batch_fill(b, &a, &t, 1, v.occ[0]), st);
+    return launch_variant(v, a.qin ? 2 : 0, b, batch_fill(b, &a, &t, 1, v.occ[0]), st);
 }
 
 cudaError_t launch_fwd_batch(const FwdArgs *a, const Tiling *t, int nm, bool with_offh, cudaStream_t st)
