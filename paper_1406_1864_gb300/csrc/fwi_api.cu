@@ -613,11 +613,12 @@ fwi_status run_forward_models(int nm, const Plan *pl, const fwi_geometry *const 
             a[k].tm_cur = mh[k][n & 1];
             a[k].tm_prev = mp[k][(n + 1) & 1];
             a[k].c.sched = at<int>(ws[0], pl[0].sched) + n;
+            a[k].uin = U[k][n & 1];
             a[k].uout = U[k][(n + 1) & 1];
         }
         e = nm == 1 ? launch_fwd_step(a[0], til[0], offh, st) : launch_fwd_batch(a.data(), til.data(), nm, offh, st);
         if (e != cudaSuccess) return cuda_fail(e, "forward step");
-        t_launch[0]++;
+        t_launch[0] += fwd_split(til[0], offh) ? 1 + nm : 1; // (split: one offset-Hessian sum per model)
     }
     if (ev1) cudaEventRecord(ev1, st);
     for (int k = 0; k < nm; ++k)

@@ -99,6 +99,8 @@ struct FwdArgs {
     CUtensorMap tm_cur;    // u^n, halo box
     CUtensorMap tm_prev;   // u^{n-1}, point box
     StepCommon c;
+    const float *uin;      // u^n (the buffer of tm_cur): the offset-Hessian sums of the
+                           // split variants read it
     float *uout;           // u^{n+1} is written here (the u^{n-1} buffer, or a
                            // segment slot when re-propagating from a snapshot)
     float *qout;           // re-propagation: q^n = Lhat u^n + f delta_s (in place of

@@ -51,6 +51,8 @@ void step_tuned_clear();
 bool encode_field_map(CUtensorMap *map, const float *base, const Lay2D &L, int nfields, int bx, int by,
                       int bz = 1);
 cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st);
+// with the offset Hessian: does the tiling's variant launch k_offh_level after the plain step
+bool fwd_split(const Tiling &t, bool with_offh);
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st);
 // one launch over the (tile, shot) pairs of nm <= BATCH_MAX models at the
 // same time level (per-model arguments and tilings of the same kind)

@@ -40,6 +40,7 @@
 
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -1380,6 +1381,144 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
     }
 }
 
+// ------------------------------------ offset Hessian beside the plain step
+// The offset-Hessian diagonal of one time level as a kernel of its own
+// (Sec. 3): acc_offh[h][x] += sum_s u_s^n(x + h e_x) u_s^n(x - h e_x),
+// h = 0..hmax, at the physical points (u = 0 outside the padded grid: the
+// ghost columns), launched after the plain forward step of the level (the
+// split offset-Hessian variants). A CTA takes one 64 x 8 tile of the physical
+// region and a chunk of shots; the tile's rows with 12 columns on each side
+// come through a shared-memory ring of cp.async copies, two shots per stage;
+// each thread sums the products of its 4 points of one row in registers
+// across the chunk and adds them with one vector reduction per offset.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+template <int NHC, int NST>
+__global__ void __launch_bounds__(TPB, 4) k_offh_level(const float *__restrict__ u, const Lay2D L, int ns,
+                                                       int chunk, int hmax, float *acc_offh)
+{
+    constexpr int WL = HMAX_LIMIT, NW = (2 * WL + 4) / 4;
+    constexpr int RW = TX + 2 * WL;   // a staged row: physical columns ixb - WL .. ixb + TX + WL - 1
+    constexpr int NCH = 8 * (RW / 4); // 16-byte pieces of one shot's rows
+    static_assert(NCH <= 2 * TPB, "two pieces per thread");
+    __shared__ __align__(16) float sm[NST][2][8 * RW];
+    const int ntz = (L.nz + 7) / 8, ntx = (L.nx + TX - 1) / TX, ntiles = ntz * ntx;
+    const int c = blockIdx.x / ntiles, tile = blockIdx.x - c * ntiles;
+    const int bz = tile / ntx, bx = tile - bz * ntx;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int iz0 = bz * 8, ixb = bx * TX;
+    const int iz = iz0 + ty, ix0 = ixb + 4 * tx;
+    const int s0 = c * chunk, s1 = min(ns, s0 + chunk), nsh = max(0, s1 - s0);
+    // Pieces of rows below the model or of columns past nx + WL are not
+    // copied: only points outside the model (never stored) read them. With
+    // the sponge width a multiple of 4 the pieces start on 16-byte
+    // boundaries (this thread's two: fixed offsets, precomputed); otherwise
+    // they are copied 4 bytes at a time.
+    const bool al = (L.P & 3) == 0;
+    long long g0 = -1, g1 = -1;
+    int d0 = 0, d1 = 0;
+    {
+        int r = threadIdx.x / (RW / 4), c4 = threadIdx.x - r * (RW / 4), col = ixb - WL + 4 * c4;
+        if (iz0 + r < L.nz && col < L.nx + WL) {
+            g0 = fidx(L, iz0 + r + L.P, col + L.P);
+            d0 = r * RW + 4 * c4;
+        }
+        const int e1 = threadIdx.x + TPB;
+        if (e1 < NCH) {
+            r = e1 / (RW / 4);
+            c4 = e1 - r * (RW / 4);
+            col = ixb - WL + 4 * c4;
+            if (iz0 + r < L.nz && col < L.nx + WL) {
+                g1 = fidx(L, iz0 + r + L.P, col + L.P);
+                d1 = r * RW + 4 * c4;
+            }
+        }
+    }
+    // shots 2k and 2k + 1 of the chunk into stage b (one commit group)
+    auto stage = [&](int k, int b) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int s = s0 + 2 * k + q;
+            if (s >= s1) break;
+            const float *src = u + (long long)s * L.fstride;
+            if (al) {
+                if (g0 >= 0) cp_async16(&sm[b][q][d0], src + g0);
+                if (g1 >= 0) cp_async16(&sm[b][q][d1], src + g1);
+            } else {
+                for (int e = threadIdx.x; e < 8 * RW; e += TPB) {
+                    const int r = e / RW, cc = e - r * RW, col = ixb - WL + cc;
+                    if (iz0 + r < L.nz && col < L.nx + WL)
+                        cp_async4(&sm[b][q][r * RW + cc], src + fidx(L, iz0 + r + L.P, col + L.P));
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    float2 acc[NHC][2];
+#pragma unroll
+    for (int h = 0; h < NHC; ++h) acc[h][0] = acc[h][1] = make_float2(0.f, 0.f);
+    const int npair = (nsh + 1) / 2;
+#pragma unroll
+    for (int k = 0; k < NST - 1; ++k) {
+        if (k < npair) stage(k, k);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+#pragma unroll 1
+    for (int k = 0; k < npair; ++k) {
+        // the group of pair k is complete when at most NST - 2 younger ones are pending
+        asm volatile("cp.async.wait_group %0;" ::"n"(NST - 2) : "memory");
+        __syncthreads(); // pair k visible to all; pair k - 1's stage free for reuse
+        if (k + NST - 1 < npair) stage(k + NST - 1, (k + NST - 1) % NST);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        const int nq = min(2, nsh - 2 * k);
+#pragma unroll 1
+        for (int q = 0; q < nq; ++q) {
+            const float *row = &sm[k % NST][q][ty * RW + 4 * tx];
+            float w[4 * NW];
+#pragma unroll
+            for (int kk = 0; kk < NW; ++kk) {
+                const float4 t = lds4(row + 4 * kk);
+                w[4 * kk] = t.x; w[4 * kk + 1] = t.y; w[4 * kk + 2] = t.z; w[4 * kk + 3] = t.w;
+            }
+            // u(x+h) u(x-h); even h: points (0, 1) and (2, 3) on lane pairs;
+            // odd h: (1, 2) paired, 0 and 3 scalar (as in the fused step)
+#pragma unroll
+            for (int h = 0; h < NHC; ++h) {
+                if ((h & 1) == 0) {
+#pragma unroll
+                    for (int qq = 0; qq < 2; ++qq)
+                        acc[h][qq] = fma2(f2(w[WL + 2 * qq + h], w[WL + 2 * qq + 1 + h]),
+                                          f2(w[WL + 2 * qq - h], w[WL + 2 * qq + 1 - h]), acc[h][qq]);
+                } else {
+                    acc[h][0] = fma2(f2(w[WL + 1 + h], w[WL + 2 + h]), f2(w[WL + 1 - h], w[WL + 2 - h]), acc[h][0]);
+                    acc[h][1].x = fmaf(w[WL + h], w[WL - h], acc[h][1].x);
+                    acc[h][1].y = fmaf(w[WL + 3 + h], w[WL + 3 - h], acc[h][1].y);
+                }
+            }
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (iz >= L.nz || ix0 >= L.nx) return;
+    const long long nphys = (long long)L.nz * L.nx, o = (long long)iz * L.nx + ix0;
+    const bool vec = ((L.P | L.nx) & 3) == 0 && ix0 + 3 < L.nx;
+#pragma unroll
+    for (int h = 0; h < NHC; ++h) {
+        if (h > hmax) continue;
+        const float v[4] = {(h & 1) ? acc[h][1].x : acc[h][0].x, (h & 1) ? acc[h][0].x : acc[h][0].y,
+                            (h & 1) ? acc[h][0].y : acc[h][1].x, acc[h][1].y};
+        if (vec) {
+            red_add4(acc_offh + h * nphys + o, v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+                if (ix0 + p < L.nx) atomicAdd(acc_offh + h * nphys + o + p, v[p]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 namespace {
 // Compiled tile variants of each kind of step (index 0 is the default; the
@@ -1388,6 +1527,7 @@ namespace {
 struct Variant {
     int rz, spi, smem; // tile rows / 8, shots per item, dynamic shared memory
     int nh;            // offsets of the offset Hessian it accumulates (valid for hmax <= nh - 1)
+    int split;         // offset Hessian: 1 = the plain step, then k_offh_level
     const void *fn[3]; // one model per launch, batch of up to BATCH_MAX models, and (plain
                        // forward and backward steps) the one-model instance that keeps (forward)
                        // or reads (backward) the imaging factor q of a re-propagated segment
@@ -1395,18 +1535,24 @@ struct Variant {
 };
 
 #define FWD_VARIANT(RZ, ST, MINB, SPI)                                                     \
-    {RZ, SPI, FwdRing<RZ, RADIUS, false, ST, SPI>::SMEM, 0,                                \
+    {RZ, SPI, FwdRing<RZ, RADIUS, false, ST, SPI>::SMEM, 0, 0,                             \
      {(const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, 1, SPI>,                       \
       (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, BATCH_MAX, SPI>,               \
       (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, 1, SPI, HMAX_LIMIT + 1, true>}, \
      {0, 0}}
 #define FWDH_VARIANT(ST, MINB, SPI, NHC)                                                   \
-    {1, SPI, FwdRing<1, HMAX_LIMIT, true, ST, SPI>::SMEM, NHC,                             \
+    {1, SPI, FwdRing<1, HMAX_LIMIT, true, ST, SPI>::SMEM, NHC, 0,                          \
      {(const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, 1, SPI, NHC>,                \
       (const void *)k_fwd_step<1, HMAX_LIMIT, true, ST, MINB, BATCH_MAX, SPI, NHC>, nullptr}, \
      {0, 0}}
+// the plain step with the offset Hessian summed by k_offh_level after it
+#define FWDS_VARIANT(RZ, ST, MINB, SPI)                                                    \
+    {RZ, SPI, FwdRing<RZ, RADIUS, false, ST, SPI>::SMEM, HMAX_LIMIT + 1, 1,               \
+     {(const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, 1, SPI>,                       \
+      (const void *)k_fwd_step<RZ, RADIUS, false, ST, MINB, BATCH_MAX, SPI>, nullptr},     \
+     {0, 0}}
 #define BWD_VARIANT(RZ, ST, MINB)                                                          \
-    {RZ, 1, BwdRing<RZ, ST>::SMEM, 0,                                                      \
+    {RZ, 1, BwdRing<RZ, ST>::SMEM, 0, 0,                                                   \
      {(const void *)k_bwd_step<RZ, ST, MINB, 1>, (const void *)k_bwd_step<RZ, ST, MINB, BATCH_MAX>, \
       (const void *)k_bwd_step<RZ, ST, MINB, 1, 0, true>},                                \
      {0, 0}}
@@ -1415,11 +1561,13 @@ struct Variant {
 // (6 CTAs/SM), 64 x 16 with two shots per item (2 stages)
 Variant g_var_f[] = {FWD_VARIANT(2, 3, 4, 1), FWD_VARIANT(4, 2, 4, 1), FWD_VARIANT(1, 3, 6, 1),
                      FWD_VARIANT(2, 2, 4, 2)};
-// forward with the offset Hessian: 64 x 8 tiles, halo 12 (its 44 register
-// accumulators rule out taller tiles), one or two shots per item (the
-// accumulators serve both shots of an item)
-// and the offset count compiled for hmax <= 12 or <= 10
-Variant g_var_h[] = {FWDH_VARIANT(3, 4, 1, 13), FWDH_VARIANT(3, 4, 2, 13), FWDH_VARIANT(3, 4, 2, 11)};
+// forward with the offset Hessian: fused, 64 x 8 tiles, halo 12 (its 44
+// register accumulators rule out taller tiles), one or two shots per item
+// (the accumulators serve both shots of an item) and the offset count
+// compiled for hmax <= 12 or <= 10; split, the plain step (64 x 16 tiles, one
+// or two shots per item) and k_offh_level
+Variant g_var_h[] = {FWDH_VARIANT(3, 4, 1, 13), FWDH_VARIANT(3, 4, 2, 13), FWDH_VARIANT(3, 4, 2, 11),
+                     FWDS_VARIANT(2, 3, 4, 1), FWDS_VARIANT(2, 2, 4, 2)};
 // backward: 64 x 16 tiles (2 stages, 4 CTAs/SM), 64 x 8 (5 CTAs/SM)
 Variant g_var_b[] = {BWD_VARIANT(2, 2, 4), BWD_VARIANT(1, 2, 5)};
 
@@ -1569,7 +1717,9 @@ void step_tuned_clear()
 
 void step_boxes(StepKind kind, const Tiling &t, int &hx, int &hy, int &px, int &py)
 {
-    const int halo = kind == STEP_FWD_OFFH ? HMAX_LIMIT : RADIUS;
+    int n = 0;
+    const bool fused_h = kind == STEP_FWD_OFFH && !variants(kind, n)[t.variant].split;
+    const int halo = fused_h ? HMAX_LIMIT : RADIUS;
     hx = TX + 2 * halo;
     hy = t.tz + 2 * RADIUS;
     px = TX;
@@ -1622,6 +1772,39 @@ Tiling make_tiling(const Lay2D &L, int ns, StepKind kind, int variant, int chunk
     return t;
 }
 
+namespace {
+// k_offh_level for one model's level (split variants): a chunk of shots per
+// tile such that the tiles x chunks fill the resident CTAs about once
+cudaError_t launch_offh_sums(const FwdArgs &a, cudaStream_t st)
+{
+    if (a.acc_offh == nullptr || a.uin == nullptr) return a.acc_offh == nullptr ? cudaSuccess : cudaErrorInvalidValue;
+    static int occ = 0;
+    if (occ == 0) {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_offh_level<13, 4>, TPB, 0) != cudaSuccess || o <= 0) o = 4;
+        cudaGetLastError();
+        occ = o;
+    }
+    const Lay2D &L = a.c.L;
+    const int ns = a.c.ns;
+    const int ntiles = ((L.nz + 7) / 8) * ((L.nx + TX - 1) / TX);
+    const int nch = std::max(1, std::min(ns, sm_count_dev() * occ / std::max(1, ntiles)));
+    const int chunk = ((ns + nch - 1) / nch + 1) & ~1;
+    const int grid = ntiles * ((ns + chunk - 1) / chunk);
+    if (a.hmax <= 10)
+        k_offh_level<11, 4><<<grid, TPB, 0, st>>>(a.uin, L, ns, chunk, a.hmax, a.acc_offh);
+    else
+        k_offh_level<13, 4><<<grid, TPB, 0, st>>>(a.uin, L, ns, chunk, a.hmax, a.acc_offh);
+    return cudaGetLastError();
+}
+} // namespace
+
+bool fwd_split(const Tiling &t, bool with_offh)
+{
+    int n = 0;
+    return with_offh && variants(STEP_FWD_OFFH, n)[t.variant].split != 0;
+}
+
 cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, cudaStream_t st)
 {
     int n = 0;
@@ -1629,7 +1812,9 @@ cudaError_t launch_fwd_step(const FwdArgs &a, const Tiling &t, bool with_offh, c
     if (a.qout != nullptr && (with_offh || !v.fn[2])) return cudaErrorInvalidValue;
     if (a.qout == nullptr && a.uout == nullptr) return cudaErrorInvalidValue;
     Batch<FwdArgs, 1> b;
-    return launch_variant(v, a.qout != nullptr ? 2 : 0, b, batch_fill(b, &a, &t, 1, v.occ[0]), st);
+    cudaError_t e = launch_variant(v, a.qout != nullptr ? 2 : 0, b, batch_fill(b, &a, &t, 1, v.occ[0]), st);
+    if (e == cudaSuccess && with_offh && v.split) e = launch_offh_sums(a, st);
+    return e;
 }
 
 cudaError_t launch_bwd_step(const BwdArgs &a, const Tiling &t, cudaStream_t st)
@@ -1647,7 +1832,9 @@ cudaError_t launch_fwd_batch(const FwdArgs *a, const Tiling *t, int nm, bool wit
     int n = 0;
     const Variant &v = variants(with_offh ? STEP_FWD_OFFH : STEP_FWD, n)[t[0].variant];
     Batch<FwdArgs, BATCH_MAX> b;
-    return launch_variant(v, 1, b, batch_fill(b, a, t, nm, v.occ[1]), st);
+    cudaError_t e = launch_variant(v, 1, b, batch_fill(b, a, t, nm, v.occ[1]), st);
+    for (int k = 0; k < nm && e == cudaSuccess && with_offh && v.split; ++k) e = launch_offh_sums(a[k], st);
+    return e;
 }
 
 cudaError_t launch_bwd_batch(const BwdArgs *a, const Tiling *t, int nm, cudaStream_t st)

@@ -97,6 +97,8 @@ def test_traffic_tool_reads_ncu_csv(tmp_path):
         "k_fwd_step<offset Hessian>"
     assert traffic.key_of("void k_fwd_step<2, 4, 0, 2, 4, 1, 2, 13>(Batch<FwdArgs, T6>)") == "k_fwd_step"
     assert traffic.key_of("void k_bwd_step<2, 2, 4, 1, 0>(Batch<BwdArgs, T4>)") == "k_bwd_step"
+    assert traffic.key_of("void k_offh_level<11, 4>(const float *, Lay2D, int, int, int, float *)") == \
+        "k_offh_level"
     assert traffic.key_of("k_prep_c2(...)") is None
     hdr = '"ID","Kernel Name","Metric Name","Metric Value"\n'
     rows = []

@@ -14,7 +14,7 @@ from paper_1406_1864_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-N_FWD, N_FWDH, N_BWD = 4, 3, 2  # compiled variants of each kind
+N_FWD, N_FWDH, N_BWD = 4, 5, 2  # compiled variants of each kind (offset Hessian: 3 fused, 2 split)
 
 
 @pytest.fixture(scope="module")

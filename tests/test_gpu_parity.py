@@ -131,6 +131,29 @@ def test_offset_hessian(torch_cuda, oracle_mod, hmax):
     assert rel(out["offh"][0], out["illum"]) <= 1e-6
 
 
+@pytest.mark.parametrize("hmax", [0, 3, 12])
+def test_offset_hessian_split_variants(torch_cuda, oracle_mod, hmax):
+    """The split offset-Hessian variants (the plain step, then k_offh_level
+    per level), pinned with fwi_autotune_set on the ragged grid (sponge 7:
+    the rows are copied 4 bytes at a time) and on a grid with an 8-cell
+    sponge (16-byte copies), against the oracle: gradient, illumination,
+    every offset slice, offset-preconditioned gradient (1e-4)."""
+    from paper_1406_1864_gb300 import fwi
+    N_FWD_FUSED = 3  # split variants follow the fused ones
+    for p in (ragged_problem(nt=250, ns=3),
+              W.dipping(nz=41, nx=131, dx=10.0, dt=1e-3, nt=240, ns=5, nrec=30, rec_step=4, f0=15.0, seed=4,
+                        sponge=8)):
+        grid, geom = fwi.from_problem(p)
+        opts = fwi.Options(hmax=hmax, precond="offset")
+        try:
+            for fv in (N_FWD_FUSED, N_FWD_FUSED + 1):
+                fwi.autotune_set(grid, geom, opts, {"forward_variant": fv, "forward_chunk": 3,
+                                                     "backward_variant": 0, "backward_chunk": 8})
+                check_gradient(torch_cuda, oracle_mod, p, hmax=hmax, precond="offset")
+        finally:
+            fwi.autotune_reset()
+
+
 def test_offset_hessian_entry_point(torch_cuda, oracle_mod):
     torch = torch_cuda
     p = W.dipping(nz=50, nx=140, nt=400, ns=4, nrec=70, f0=12.0, seed=5, sponge=10)
