@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default tile variants (no fwi_autotune)")
+    ap.add_argument("--tiles", default="", help="F,FC,B,BC: pin the forward / backward tile variants and shot "
+                    "chunks (fwi_autotune_set) instead of autotuning")
     ap.add_argument("--profile-region", action="store_true",
                     help="cudaProfilerStart/Stop around the timed steps (ncu --profile-from-start off)")
     ap.add_argument("--no-graph", action="store_true",
@@ -269,7 +271,11 @@ def run_ours(args):
     graph = None
     phase_box = []
     tiles = None
-    if not args.no_autotune:  # tile variants timed on this problem (not timed)
+    if args.tiles:
+        fv, fc, bv, bc = (int(x) for x in args.tiles.split(","))
+        tiles = {"forward_variant": fv, "forward_chunk": fc, "backward_variant": bv, "backward_chunk": bc}
+        fwi.autotune_set(grid, geom, opts, tiles)
+    elif not args.no_autotune:  # tile variants timed on this problem (not timed)
         tiles = fwi.autotune(grid, geom, v, opts, ws=ws)
 
     if world > 1:

@@ -4,15 +4,18 @@ The benchmark times the full preconditioned gradient of the 300 x 1000-cell
 dipping model with all 96 shots: the time-integral misfit of Eq. 2, the
 offset-Hessian diagonal for |h| <= 10 (Sec. 3), the shot illumination of
 Eq. 1 and offset preconditioning (Sec. 3.1). Its launches cover the whole
-padded grid with every shot: two-shot items, shot chunks of 16 (forward) and
-8 (backward) per tile, more tile chunks than resident CTAs (so CTAs take a
-second chunk), items that span chunk boundaries. Here the same grid, shots,
+padded grid with every shot: the plain forward step in two-shot items and
+the offset-Hessian sums of all 96 shots per tile after it (the split
+variant), shot chunks of 8 per tile, more tile chunks than resident CTAs (so
+CTAs take a second chunk), items that span chunk boundaries. Here the same grid, shots,
 receivers and options run with nt cut to 300, so that the FP64 oracle can
 compute every output point by point (about 0.85 GB of wavefield history per
 shot and thread), and the outputs are compared element by element:
 
-  - with the benchmark's tile choice pinned (forward variant 2, chunk 16;
-    backward variant 0, chunk 8), called directly, sponge checkpoints;
+  - with the benchmark's tile choice pinned (forward variant 4, the split
+    one, chunk 8; backward variant 0, chunk 8), called directly, sponge
+    checkpoints; and with the fused offset-Hessian step (forward variant 2,
+    chunk 16);
   - with the autotuner's own choice, through the recorded CUDA graph the
     benchmark replays, sponge checkpoints;
   - with F32 snapshot checkpoints (the forward field re-propagated bit for
@@ -44,7 +47,8 @@ HMAX = 10
 TOL_GRAD = 1e-4
 TOL_MISFIT = 1e-5
 TOL_DIV = 1e-5  # FP32 division against FP64 of the same inputs
-BENCH_TILES = {"forward_variant": 2, "forward_chunk": 16, "backward_variant": 0, "backward_chunk": 8}
+BENCH_TILES = {"forward_variant": 4, "forward_chunk": 8, "backward_variant": 0, "backward_chunk": 8}
+FUSED_TILES = {"forward_variant": 2, "forward_chunk": 16, "backward_variant": 0, "backward_chunk": 8}
 
 
 def rel(a, b):
@@ -97,7 +101,8 @@ def compare(res, ref, pre_vs_oracle):
     return errs
 
 
-def test_bench_tiles_direct_call(case):
+@pytest.mark.parametrize("tiles", [BENCH_TILES, FUSED_TILES], ids=["split", "fused"])
+def test_bench_tiles_direct_call(case, tiles):
     import torch
     from paper_1406_1864_gb300 import fwi
     p, d_obs, ref = case
@@ -105,7 +110,7 @@ def test_bench_tiles_direct_call(case):
     v = torch.as_tensor(p.v_init, device="cuda")
     d = torch.as_tensor(d_obs, device="cuda")
     try:
-        fwi.autotune_set(grid, geom, opts(), BENCH_TILES)
+        fwi.autotune_set(grid, geom, opts(), tiles)
         res = fwi.adjoint_gradient(grid, geom, v, d, opts())
         torch.cuda.synchronize()
     finally:
