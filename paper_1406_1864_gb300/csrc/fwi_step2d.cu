@@ -6,9 +6,11 @@
 // leapfrog discretisation of the constant-density acoustic equation of Sec. 2
 // with an absorbing sponge u_tt + 2 eta u_t. Fused into the same pass over the
 // tile: receiver extraction d^n = R u^n [Sec. 2], the shot illumination of
-// Eq. 1 (sum u^2, or the u_tt^2 form), the offset-Hessian diagonal of Sec. 3
-// (sum u(x+h) u(x-h)) and the sponge checkpoint of u^{n+1} used by the
-// adjoint pass.
+// Eq. 1 (sum u^2, or the u_tt^2 form), the sponge checkpoint of u^{n+1} used
+// by the adjoint pass and, in the fused offset-Hessian variants, the
+// offset-Hessian diagonal of Sec. 3 (sum u(x+h) u(x-h)); the split variants
+// leave that sum to k_offh_level, launched after the plain step of each level
+// (the autotuner keeps whichever is faster for the problem).
 //
 // Backward step (one launch per m = nt-1 .. 1, all shots), fused:
 //   - adjoint of the discrete forward map (the back-propagated residual of
