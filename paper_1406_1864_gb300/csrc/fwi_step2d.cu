@@ -1390,15 +1390,17 @@ __global__ void __launch_bounds__(TPB, MINB) k_born_step(const __grid_constant__
 // ghost columns), launched after the plain forward step of the level (the
 // split offset-Hessian variants). A CTA takes one 64 x 8 tile of the physical
 // region and a chunk of shots; the tile's rows with 12 columns on each side
-// come through a shared-memory ring of cp.async copies, two shots per stage;
-// each thread sums the products of its 4 points of one row in registers
-// across the chunk and adds them with one vector reduction per offset.
+// come through a shared-memory ring of cp.async copies, SPS shots per stage
+// (one barrier per stage); each thread sums the products of its 4 points of
+// one row in registers across the chunk, two shots at a time (both windows
+// read before the products), and adds them with one vector reduction per
+// offset.
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-template <int NHC, int NST>
+template <int NHC, int NST, int SPS>
 __global__ void __launch_bounds__(TPB, 4) k_offh_level(const float *__restrict__ u, const Lay2D L, int ns,
                                                        int chunk, int hmax, float *acc_offh)
 {
@@ -1406,7 +1408,7 @@ __global__ void __launch_bounds__(TPB, 4) k_offh_level(const float *__restrict__
     constexpr int RW = TX + 2 * WL;   // a staged row: physical columns ixb - WL .. ixb + TX + WL - 1
     constexpr int NCH = 8 * (RW / 4); // 16-byte pieces of one shot's rows
     static_assert(NCH <= 2 * TPB, "two pieces per thread");
-    __shared__ __align__(16) float sm[NST][2][8 * RW];
+    __shared__ __align__(16) float sm[NST][SPS][8 * RW];
     const int ntz = (L.nz + 7) / 8, ntx = (L.nx + TX - 1) / TX, ntiles = ntz * ntx;
     const int c = blockIdx.x / ntiles, tile = blockIdx.x - c * ntiles;
     const int bz = tile / ntx, bx = tile - bz * ntx;
@@ -1439,11 +1441,11 @@ __global__ void __launch_bounds__(TPB, 4) k_offh_level(const float *__restrict__
             }
         }
     }
-    // shots 2k and 2k + 1 of the chunk into stage b (one commit group)
+    // shots SPS k .. SPS k + SPS - 1 of the chunk into stage b (one commit group)
     auto stage = [&](int k, int b) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int s = s0 + 2 * k + q;
+        for (int q = 0; q < SPS; ++q) {
+            const int s = s0 + SPS * k + q;
             if (s >= s1) break;
             const float *src = u + (long long)s * L.fstride;
             if (al) {
@@ -1462,43 +1464,56 @@ __global__ void __launch_bounds__(TPB, 4) k_offh_level(const float *__restrict__
     float2 acc[NHC][2];
 #pragma unroll
     for (int h = 0; h < NHC; ++h) acc[h][0] = acc[h][1] = make_float2(0.f, 0.f);
-    const int npair = (nsh + 1) / 2;
+    auto window = [&](const float *row, float (&w)[4 * NW]) {
+#pragma unroll
+        for (int kk = 0; kk < NW; ++kk) {
+            const float4 t = lds4(row + 4 * kk);
+            w[4 * kk] = t.x; w[4 * kk + 1] = t.y; w[4 * kk + 2] = t.z; w[4 * kk + 3] = t.w;
+        }
+    };
+    // u(x+h) u(x-h); even h: points (0, 1) and (2, 3) on lane pairs; odd h:
+    // (1, 2) paired, 0 and 3 scalar (as in the fused step)
+    auto products = [&](const float (&w)[4 * NW]) {
+#pragma unroll
+        for (int h = 0; h < NHC; ++h) {
+            if ((h & 1) == 0) {
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq)
+                    acc[h][qq] = fma2(f2(w[WL + 2 * qq + h], w[WL + 2 * qq + 1 + h]),
+                                      f2(w[WL + 2 * qq - h], w[WL + 2 * qq + 1 - h]), acc[h][qq]);
+            } else {
+                acc[h][0] = fma2(f2(w[WL + 1 + h], w[WL + 2 + h]), f2(w[WL + 1 - h], w[WL + 2 - h]), acc[h][0]);
+                acc[h][1].x = fmaf(w[WL + h], w[WL - h], acc[h][1].x);
+                acc[h][1].y = fmaf(w[WL + 3 + h], w[WL + 3 - h], acc[h][1].y);
+            }
+        }
+    };
+    const int nstage = (nsh + SPS - 1) / SPS;
 #pragma unroll
     for (int k = 0; k < NST - 1; ++k) {
-        if (k < npair) stage(k, k);
+        if (k < nstage) stage(k, k);
         else asm volatile("cp.async.commit_group;" ::: "memory");
     }
 #pragma unroll 1
-    for (int k = 0; k < npair; ++k) {
-        // the group of pair k is complete when at most NST - 2 younger ones are pending
+    for (int k = 0; k < nstage; ++k) {
+        // the group of stage k is complete when at most NST - 2 younger ones are pending
         asm volatile("cp.async.wait_group %0;" ::"n"(NST - 2) : "memory");
-        __syncthreads(); // pair k visible to all; pair k - 1's stage free for reuse
-        if (k + NST - 1 < npair) stage(k + NST - 1, (k + NST - 1) % NST);
+        __syncthreads(); // stage k visible to all; stage k - 1's slot free for reuse
+        if (k + NST - 1 < nstage) stage(k + NST - 1, (k + NST - 1) % NST);
         else asm volatile("cp.async.commit_group;" ::: "memory");
-        const int nq = min(2, nsh - 2 * k);
+        const int nq = min(SPS, nsh - SPS * k);
+        const int b = k % NST;
 #pragma unroll 1
-        for (int q = 0; q < nq; ++q) {
-            const float *row = &sm[k % NST][q][ty * RW + 4 * tx];
-            float w[4 * NW];
-#pragma unroll
-            for (int kk = 0; kk < NW; ++kk) {
-                const float4 t = lds4(row + 4 * kk);
-                w[4 * kk] = t.x; w[4 * kk + 1] = t.y; w[4 * kk + 2] = t.z; w[4 * kk + 3] = t.w;
-            }
-            // u(x+h) u(x-h); even h: points (0, 1) and (2, 3) on lane pairs;
-            // odd h: (1, 2) paired, 0 and 3 scalar (as in the fused step)
-#pragma unroll
-            for (int h = 0; h < NHC; ++h) {
-                if ((h & 1) == 0) {
-#pragma unroll
-                    for (int qq = 0; qq < 2; ++qq)
-                        acc[h][qq] = fma2(f2(w[WL + 2 * qq + h], w[WL + 2 * qq + 1 + h]),
-                                          f2(w[WL + 2 * qq - h], w[WL + 2 * qq + 1 - h]), acc[h][qq]);
-                } else {
-                    acc[h][0] = fma2(f2(w[WL + 1 + h], w[WL + 2 + h]), f2(w[WL + 1 - h], w[WL + 2 - h]), acc[h][0]);
-                    acc[h][1].x = fmaf(w[WL + h], w[WL - h], acc[h][1].x);
-                    acc[h][1].y = fmaf(w[WL + 3 + h], w[WL + 3 - h], acc[h][1].y);
-                }
+        for (int q = 0; q < nq; q += 2) {
+            float w0[4 * NW];
+            window(&sm[b][q][ty * RW + 4 * tx], w0);
+            if (q + 1 < nq) { // shots in order: q, then q + 1
+                float w1[4 * NW];
+                window(&sm[b][q + 1][ty * RW + 4 * tx], w1);
+                products(w0);
+                products(w1);
+            } else {
+                products(w0);
             }
         }
     }
@@ -1783,7 +1798,7 @@ cudaError_t launch_offh_sums(const FwdArgs &a, cudaStream_t st)
     static int occ = 0;
     if (occ == 0) {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_offh_level<13, 4>, TPB, 0) != cudaSuccess || o <= 0) o = 4;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_offh_level<13, 3, 4>, TPB, 0) != cudaSuccess || o <= 0) o = 4;
         cudaGetLastError();
         occ = o;
     }
@@ -1794,9 +1809,9 @@ cudaError_t launch_offh_sums(const FwdArgs &a, cudaStream_t st)
     const int chunk = ((ns + nch - 1) / nch + 1) & ~1;
     const int grid = ntiles * ((ns + chunk - 1) / chunk);
     if (a.hmax <= 10)
-        k_offh_level<11, 4><<<grid, TPB, 0, st>>>(a.uin, L, ns, chunk, a.hmax, a.acc_offh);
+        k_offh_level<11, 3, 4><<<grid, TPB, 0, st>>>(a.uin, L, ns, chunk, a.hmax, a.acc_offh);
     else
-        k_offh_level<13, 4><<<grid, TPB, 0, st>>>(a.uin, L, ns, chunk, a.hmax, a.acc_offh);
+        k_offh_level<13, 3, 4><<<grid, TPB, 0, st>>>(a.uin, L, ns, chunk, a.hmax, a.acc_offh);
     return cudaGetLastError();
 }
 } // namespace
