@@ -46,9 +46,11 @@
  *     (ndim = 3; 25-point Laplacian, source f / dx^3) are taken by
  *     fwi_workspace_bytes, fwi_forward (save = 1 with ckpt =
  *     FWI_CKPT_SNAPSHOT and all shots in one group), fwi_adjoint_apply,
- *     fwi_adjoint_gradient (ckpt = FWI_CKPT_SNAPSHOT, hmax = -1),
- *     fwi_illumination and fwi_autotune*; the other entry points return
- *     FWI_ERR_INVALID_ARG for them.
+ *     fwi_adjoint_gradient (ckpt = FWI_CKPT_SNAPSHOT), fwi_illumination,
+ *     fwi_offset_hessian_diag, fwi_precondition and fwi_autotune*, with
+ *     [nz][ny][nx] model arrays and [hmax+1][nz][ny][nx] offset Hessians
+ *     (offsets along x); the other entry points return FWI_ERR_INVALID_ARG
+ *     for them.
  */
 #ifndef FWI_H
 #define FWI_H
@@ -396,7 +398,9 @@ fwi_status fwi_illumination(const fwi_grid *grid, const fwi_geometry *geom,
 /* Diagonal of the localized subsurface-offset Hessian [Sec. 3], source side,
    horizontal offsets h = 0..opts->hmax (opts->hmax >= 0):
    offh DEVICE [hmax+1][nz][nx] = sum_s sum_n u_s^n(x + h e_x) u_s^n(x - h e_x) dt,
-   u = 0 outside the padded grid. offh[0] equals the illumination. */
+   u = 0 outside the padded grid. offh[0] equals the illumination. 3-D grids:
+   offh [hmax+1][nz][ny][nx], offsets along x, shots in groups of
+   opts->shot_group. Workspace of FWI_OP_OFFSET_HESSIAN. */
 fwi_status fwi_offset_hessian_diag(const fwi_grid *grid, const fwi_geometry *geom,
                                    const fwi_options *opts, const float *v, float *offh,
                                    void *ws, size_t ws_bytes, void *stream);
@@ -404,7 +408,9 @@ fwi_status fwi_offset_hessian_diag(const fwi_grid *grid, const fwi_geometry *geo
 /* Diagonal preconditioning [Sec. 3.1, Fig. 5]: out = grad / (P + eps max P),
    P = scale[0] (kind FWI_PRECOND_ILLUM: scale is an illumination [nz][nx]) or
    P = |scale[0]| + 2 sum_{h=1..hmax} |scale[h]| (FWI_PRECOND_OFFSET: scale is an
-   offset Hessian [hmax+1][nz][nx]). All DEVICE; ws of FWI_OP_PRECONDITION. */
+   offset Hessian [hmax+1][nz][nx]); on 3-D grids [nz][ny][nx] and
+   [hmax+1][nz][ny][nx]. All DEVICE; ws of FWI_OP_PRECONDITION (geometry and
+   options not needed). */
 fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float *scale, int kind,
                             int hmax, float eps, float *out, void *ws, size_t ws_bytes,
                             void *stream);

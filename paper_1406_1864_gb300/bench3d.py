@@ -8,8 +8,11 @@ precision, with CUDA events on the library's stream, after fwi_autotune has
 picked the step variants (``--no-autotune``: the defaults), and from the
 gradient's phase times an upper bound of the backward step per level (20 B
 of fields per padded point-step per shot: psi^{m+1}, psi^{m+2}, psi^m, the
-imaging factor q^{m-1} kept by the re-propagation, c2). Prints one JSON
-line.
+imaging factor q^{m-1} kept by the re-propagation, c2). With ``--hmax H``
+also the offset-Hessian diagonal (offsets 0..H): its forward phase against
+that of the illumination pass (the same steps without the sums) gives the
+sums' time per level (4 B per physical point-step per shot: u^n read once
+more). Prints one JSON line.
 Defaults: the 200 x 400 x 400, 8-shot, nt 3000 workload in shot groups of 4.
 """
 from __future__ import annotations
@@ -36,6 +39,7 @@ def main():
                     "(fwi_autotune_set) instead of autotuning")
     ap.add_argument("--segments", default="0,0", help="F,B: z-segments per column with --variants "
                     "(0: chosen from the items and resident CTAs)")
+    ap.add_argument("--hmax", type=int, default=-1, help=">= 0: also time the offset-Hessian diagonal")
     args = ap.parse_args()
     p = W.dipping3d(nz=args.nz, ny=args.ny, nx=args.nx, nt=args.nt, ns=args.shots)
     grid, geom = fwi.from_problem(p)
@@ -84,6 +88,22 @@ def main():
             bus = (1e3 * ph["forward_ms"] - (ph["forward_launches"] + n_rep) * us) / n_bwd
             out["gradients"][snap]["backward_us_per_level_est"] = bus
             out["gradients"][snap]["backward_alg_GBps_est"] = 20 * npad * g / (bus * 1e-6) / 1e9
+    if args.hmax >= 0:
+        runs = {"illumination": lambda: fwi.illumination(grid, geom, v, grp, ws=ws),
+                "offset_hessian": lambda: fwi.offset_hessian_diag(
+                    grid, geom, v, fwi.Options(hmax=args.hmax, shot_group=args.shot_group), ws=ws)}
+        ms = {}
+        for name, run in runs.items():
+            for _ in range(2):  # the first call warms up
+                run()
+                torch.cuda.synchronize()
+            ms[name] = fwi.last_phase_times()["forward_ms"]
+        levels = max(1, (p.nt - 1) * -(-p.nshots // g))
+        ous = 1e3 * (ms["offset_hessian"] - ms["illumination"]) / levels
+        out["offset_hessian"] = {"hmax": args.hmax, "forward_phase_ms": ms["offset_hessian"],
+                                 "illumination_forward_phase_ms": ms["illumination"],
+                                 "sums_us_per_level_est": ous,
+                                 "sums_alg_GBps_est": 4 * p.phys_points * g / (ous * 1e-6) / 1e9 if ous > 0 else None}
     fwi.profile(False)
     print(json.dumps(out), flush=True)
 

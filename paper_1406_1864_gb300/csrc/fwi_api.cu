@@ -1018,10 +1018,11 @@ Lay3D make_layout3(const fwi_grid *g)
 struct Plan3 {
     Lay3D L;
     int ns_all = 0, G = 0, nt = 0, nrec = 0, op = 0;
+    int hmax = -1; // offsets of the offset Hessian (gradient, offset-Hessian diagonal), -1: none
     bool need_bwd = false;
     Tiling3 tf{}, tb{};
     int vf = 0, vb = 0; // step variants (autotuned per shape, else the defaults)
-    Part scal, sched, c2, damp, u[2], p[2], syn, acc_i, acc_g, tab, snaps, snap_max, seg;
+    Part scal, sched, c2, damp, u[2], p[2], syn, acc_i, acc_h, acc_g, tab, snaps, snap_max, seg;
     size_t tab_src = 0, tab_ptr = 0, tab_ent = 0, tab_zr = 0;
     int snap_prec = FWI_SNAP_F32, K = 0, nck = 0;
     size_t total = 0;
@@ -1034,10 +1035,12 @@ fwi_status make_plan3(const fwi_grid *g, const fwi_geometry *ge, const fwi_optio
     if ((st = check_grid3(g)) != FWI_OK) return st;
     if ((st = check_geom3(g, ge, coords)) != FWI_OK) return st;
     if ((st = check_opts(o, op)) != FWI_OK) return st;
-    if (op != FWI_OP_FORWARD && op != FWI_OP_FORWARD_SAVE && op != FWI_OP_GRADIENT && op != FWI_OP_ILLUMINATION)
+    if (op != FWI_OP_FORWARD && op != FWI_OP_FORWARD_SAVE && op != FWI_OP_GRADIENT && op != FWI_OP_ILLUMINATION &&
+        op != FWI_OP_OFFSET_HESSIAN)
         return fail(FWI_ERR_INVALID_ARG, "3-D grids support forward modelling (with or without checkpoints for "
-                                         "fwi_adjoint_apply), gradients and illumination");
-    if (o && o->hmax >= 0) return fail(FWI_ERR_INVALID_ARG, "the offset Hessian is 2-D only (hmax must be -1)");
+                                         "fwi_adjoint_apply), gradients, illumination and the offset Hessian");
+    if (op == FWI_OP_OFFSET_HESSIAN && o->hmax < 0)
+        return fail(FWI_ERR_INVALID_ARG, "the offset-Hessian diagonal needs hmax >= 0");
     const bool ckpts = op == FWI_OP_GRADIENT || op == FWI_OP_FORWARD_SAVE;
     if (ckpts && (!o || o->ckpt != FWI_CKPT_SNAPSHOT))
         return fail(FWI_ERR_INVALID_ARG, "3-D gradients and fwi_forward(save = 1) need ckpt = FWI_CKPT_SNAPSHOT "
@@ -1045,9 +1048,8 @@ fwi_status make_plan3(const fwi_grid *g, const fwi_geometry *ge, const fwi_optio
     if (op == FWI_OP_FORWARD_SAVE && o->shot_group > 0 && o->shot_group < ge->nshots)
         return fail(FWI_ERR_INVALID_ARG, "3-D fwi_forward(save = 1) keeps the snapshots of every shot for "
                                          "fwi_adjoint_apply: shot_group must be 0 or >= nshots");
-    if (op == FWI_OP_GRADIENT && o->precond == FWI_PRECOND_OFFSET)
-        return fail(FWI_ERR_INVALID_ARG, "precond=OFFSET needs the offset Hessian (2-D only)");
     pl.L = make_layout3(g);
+    pl.hmax = (op == FWI_OP_GRADIENT || op == FWI_OP_OFFSET_HESSIAN) ? o->hmax : -1;
     pl.op = op;
     pl.nt = g->nt;
     pl.ns_all = ge->nshots;
@@ -1074,6 +1076,7 @@ fwi_status make_plan3(const fwi_grid *g, const fwi_geometry *ge, const fwi_optio
     take(pl.u[0], fbytes * pl.G);
     take(pl.u[1], fbytes * pl.G);
     if (op != FWI_OP_FORWARD) take(pl.acc_i, nphys * sizeof(float));
+    if (pl.hmax >= 0) take(pl.acc_h, (size_t)(pl.hmax + 1) * nphys * sizeof(float));
     if (pl.need_bwd) {
         take(pl.p[0], fbytes * pl.G);
         take(pl.p[1], fbytes * pl.G);
@@ -1226,12 +1229,13 @@ fwi_status snap3_restore(const Plan3 &pl, void *ws, int g, int j, float *u, floa
 }
 
 // forward time loop of one shot group [s0, s0 + g): traces into seis (the
-// group's rows) or null, illumination into acc_i or null, snapshots if `save`;
-// levels [n_begin, n_end) (n_end < 0: to nt), events ea / eb (if given)
-// recorded around the step launches
+// group's rows) or null, illumination into acc_i or null, the offset-Hessian
+// sums of offsets 0..pl.hmax into acc_h or null, snapshots if `save`; levels
+// [n_begin, n_end) (n_end < 0: to nt), events ea / eb (if given) recorded
+// around the step launches
 fwi_status run_forward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, void *ws, float *seis,
-                        float *acc_i, int illum_utt, bool save, cudaStream_t st, int n_begin = 0, int n_end = -1,
-                        cudaEvent_t ea = nullptr, cudaEvent_t eb = nullptr)
+                        float *acc_i, float *acc_h, int illum_utt, bool save, cudaStream_t st, int n_begin = 0,
+                        int n_end = -1, cudaEvent_t ea = nullptr, cudaEvent_t eb = nullptr)
 {
     cudaError_t e;
     for (int b = 0; b < 2; ++b)
@@ -1268,6 +1272,12 @@ fwi_status run_forward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, 
         a.c.sched = at<int>(ws, pl.sched) + n;
         if ((e = launch_fwd3d(a, pl.tf, pl.vf, st)) != cudaSuccess) return cuda_fail(e, "3-D forward step");
         t_launch[0]++;
+        // u^n stays in U[n & 1] until step n + 1 overwrites it (u^0 = 0 adds nothing)
+        if (acc_h && n > 0) {
+            if ((e = launch_offh3d(U[n & 1], pl.L, g, pl.hmax, acc_h, st)) != cudaSuccess)
+                return cuda_fail(e, "3-D offset-Hessian sums");
+            t_launch[0]++;
+        }
     }
     if (eb && (e = cudaEventRecord(eb, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     for (int b = 0; b < 2; ++b) {
@@ -1415,6 +1425,8 @@ fwi_status setup3(const Plan3 &pl, const float *v, void *ws, cudaStream_t st)
     t_launch[2]++;
     if (pl.acc_i.bytes && (e = cudaMemsetAsync(at<char>(ws, pl.acc_i), 0, pl.acc_i.bytes, st)) != cudaSuccess)
         return cuda_fail(e, "memset");
+    if (pl.acc_h.bytes && (e = cudaMemsetAsync(at<char>(ws, pl.acc_h), 0, pl.acc_h.bytes, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
     if (pl.acc_g.bytes && (e = cudaMemsetAsync(at<char>(ws, pl.acc_g), 0, pl.acc_g.bytes, st)) != cudaSuccess)
         return cuda_fail(e, "memset");
     return FWI_OK;
@@ -1448,9 +1460,11 @@ fwi_status finish3(const Plan3 &pl, void *ws, cudaStream_t st)
 
 fwi_status check_ws3(const Plan3 &pl, void *ws, size_t ws_bytes) { return check_ws_bytes(ws, ws_bytes, pl.total); }
 
-// forward modelling (seis) and / or illumination (illum) of all shots
+// forward modelling (seis), illumination (illum) and / or the offset-Hessian
+// diagonal (offh, op FWI_OP_OFFSET_HESSIAN) of all shots
 fwi_status forward3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, int op,
-                    const float *v, float *seis, float *illum, void *ws, size_t ws_bytes, cudaStream_t st)
+                    const float *v, float *seis, float *illum, float *offh, void *ws, size_t ws_bytes,
+                    cudaStream_t st)
 {
     Plan3 pl;
     fwi_status s = make_plan3(grid, geom, opts, op, true, pl);
@@ -1459,12 +1473,13 @@ fwi_status forward3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_op
     begin_call(st);
     if ((s = setup3(pl, v, ws, st)) != FWI_OK) return s;
     float *acc_i = illum ? at<float>(ws, pl.acc_i) : nullptr;
+    float *acc_h = offh && pl.hmax >= 0 ? at<float>(ws, pl.acc_h) : nullptr;
     const int utt = opts ? opts->illum_mode : 0;
     for (int s0 = 0; s0 < pl.ns_all; s0 += pl.G) {
         const int g = std::min(pl.G, pl.ns_all - s0);
         if ((s = upload_tables3(pl, geom, s0, g, ws, st)) != FWI_OK) return s;
         float *sg = seis ? seis + (size_t)s0 * pl.nt * pl.nrec : nullptr;
-        if ((s = run_forward3(pl, geom, s0, g, ws, sg, acc_i, utt, op == FWI_OP_FORWARD_SAVE, st)) != FWI_OK)
+        if ((s = run_forward3(pl, geom, s0, g, ws, sg, acc_i, acc_h, utt, op == FWI_OP_FORWARD_SAVE, st)) != FWI_OK)
             return s;
     }
     prof_record(1, st);
@@ -1476,28 +1491,37 @@ fwi_status forward3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_op
         if (e != cudaSuccess) return cuda_fail(e, "illumination output");
         t_launch[2]++;
     }
+    if (acc_h) {
+        cudaError_t e = launch_finish_accum_n((long long)pl.L.nz * pl.L.ny * pl.L.nx, acc_h, 1, pl.hmax + 1,
+                                              pl.L.dt, offh, st, opts->hess_v6 ? v : nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "offset-Hessian output");
+        t_launch[2]++;
+    }
     prof_record(3, st);
     return finish3(pl, ws, st);
 }
 
 fwi_status gradient3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
-                     const float *d_obs, float *grad, float *grad_pre, double *misfit, float *illum, void *ws,
-                     size_t ws_bytes, cudaStream_t st)
+                     const float *d_obs, float *grad, float *grad_pre, double *misfit, float *illum, float *offh,
+                     void *ws, size_t ws_bytes, cudaStream_t st)
 {
     Plan3 pl;
     fwi_status s = make_plan3(grid, geom, opts, FWI_OP_GRADIENT, true, pl);
     if (s != FWI_OK) return s;
     if (!v || !grad || (!d_obs && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v, d_obs or grad is NULL");
+    if (offh && opts->hmax < 0) return fail(FWI_ERR_INVALID_ARG, "offh requested with hmax < 0");
     if ((s = check_ws3(pl, ws, ws_bytes)) != FWI_OK) return s;
     cudaError_t e;
     begin_call(st);
     if ((s = setup3(pl, v, ws, st)) != FWI_OK) return s;
     float *acc_i = at<float>(ws, pl.acc_i), *syn = at<float>(ws, pl.syn);
+    float *acc_h = pl.hmax >= 0 ? at<float>(ws, pl.acc_h) : nullptr;
     double *J = at<double>(ws, pl.scal, 0);
     for (int s0 = 0; s0 < pl.ns_all; s0 += pl.G) {
         const int g = std::min(pl.G, pl.ns_all - s0);
         if ((s = upload_tables3(pl, geom, s0, g, ws, st)) != FWI_OK) return s;
-        if ((s = run_forward3(pl, geom, s0, g, ws, syn, acc_i, opts->illum_mode, true, st)) != FWI_OK) return s;
+        if ((s = run_forward3(pl, geom, s0, g, ws, syn, acc_i, acc_h, opts->illum_mode, true, st)) != FWI_OK)
+            return s;
         const long long nsamp = (long long)g * pl.nt * pl.nrec;
         if (nsamp > 0) {
             const float *dg = d_obs + (size_t)s0 * pl.nt * pl.nrec;
@@ -1520,19 +1544,27 @@ fwi_status gradient3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_o
     t_launch[2]++;
     const long long nphys = (long long)pl.L.nz * pl.L.ny * pl.L.nx;
     const float iscale = opts->illum_mode == FWI_ILLUM_U2 ? pl.L.dt : 1.0f / (pl.L.dt * pl.L.dt * pl.L.dt);
-    float *ill_out = illum ? illum : acc_i;
-    if ((e = launch_finish_accum_n(nphys, acc_i, 1, 1, iscale, ill_out, st, opts->hess_v6 ? v : nullptr)) !=
-        cudaSuccess)
+    float *ill_out = illum ? illum : acc_i; // in place when not requested
+    const float *v6 = opts->hess_v6 ? v : nullptr;
+    if ((e = launch_finish_accum_n(nphys, acc_i, 1, 1, iscale, ill_out, st, v6)) != cudaSuccess)
         return cuda_fail(e, "illumination output");
     t_launch[2]++;
+    float *off_out = nullptr;
+    if (acc_h) {
+        off_out = offh ? offh : acc_h;
+        if ((e = launch_finish_accum_n(nphys, acc_h, 1, pl.hmax + 1, pl.L.dt, off_out, st, v6)) != cudaSuccess)
+            return cuda_fail(e, "offset-Hessian output");
+        t_launch[2]++;
+    }
     if (grad_pre) {
         if (opts->precond == FWI_PRECOND_NONE) {
             if ((e = cudaMemcpyAsync(grad_pre, grad, nphys * sizeof(float), cudaMemcpyDeviceToDevice, st)) !=
                 cudaSuccess)
                 return cuda_fail(e, "copy");
         } else {
-            if ((e = launch_precond_n(nphys, grad, ill_out, 1, 0, opts->eps, grad_pre, at<unsigned>(ws, pl.scal, 12),
-                                      st)) != cudaSuccess)
+            const bool ill = opts->precond == FWI_PRECOND_ILLUM;
+            if ((e = launch_precond_n(nphys, grad, ill ? ill_out : off_out, ill ? 1 : 2, pl.hmax, opts->eps, grad_pre,
+                                      at<unsigned>(ws, pl.scal, 12), st)) != cudaSuccess)
                 return cuda_fail(e, "precondition kernel");
             t_launch[2] += 2;
         }
@@ -1707,6 +1739,13 @@ fwi_status fwi_workspace_bytes(const fwi_grid *grid, const fwi_geometry *geom, c
         t_err.clear();
         return FWI_OK;
     }
+    if (grid && grid->ndim == 3 && op == FWI_OP_PRECONDITION) {
+        fwi_status s3 = check_grid3(grid);
+        if (s3 != FWI_OK) return s3;
+        *bytes = ALIGN; // the status word and the maximum (as fwi_precondition uses them)
+        t_err.clear();
+        return FWI_OK;
+    }
     if (grid && grid->ndim == 3) {
         Plan3 p3;
         fwi_status s3 = make_plan3(grid, geom, opts, op, false, p3);
@@ -1737,7 +1776,7 @@ fwi_status fwi_forward(const fwi_grid *grid, const fwi_geometry *geom, const fwi
     Trace trace_("fwi_forward");
     if (grid && grid->ndim == 3) {
         if (!v || (!seis && geom && geom->nrec > 0)) return fail(FWI_ERR_INVALID_ARG, "v or seis is NULL");
-        return forward3(grid, geom, opts, save ? FWI_OP_FORWARD_SAVE : FWI_OP_FORWARD, v, seis, nullptr, ws,
+        return forward3(grid, geom, opts, save ? FWI_OP_FORWARD_SAVE : FWI_OP_FORWARD, v, seis, nullptr, nullptr, ws,
                         ws_bytes, static_cast<cudaStream_t>(stream));
     }
     Plan pl;
@@ -1788,11 +1827,9 @@ fwi_status fwi_adjoint_gradient(const fwi_grid *grid, const fwi_geometry *geom, 
                                 float *illum, float *offh, void *ws, size_t ws_bytes, void *stream)
 {
     Trace trace_("fwi_adjoint_gradient");
-    if (grid && grid->ndim == 3) {
-        if (offh) return fail(FWI_ERR_INVALID_ARG, "the offset Hessian is 2-D only");
-        return gradient3(grid, geom, opts, v, d_obs, grad, grad_pre, misfit, illum, ws, ws_bytes,
+    if (grid && grid->ndim == 3)
+        return gradient3(grid, geom, opts, v, d_obs, grad, grad_pre, misfit, illum, offh, ws, ws_bytes,
                          static_cast<cudaStream_t>(stream));
-    }
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_GRADIENT, true, pl);
     if (s != FWI_OK) return s;
@@ -1811,7 +1848,7 @@ fwi_status fwi_illumination(const fwi_grid *grid, const fwi_geometry *geom, cons
     Trace trace_("fwi_illumination");
     if (grid && grid->ndim == 3) {
         if (!v || !illum) return fail(FWI_ERR_INVALID_ARG, "v or illum is NULL");
-        return forward3(grid, geom, opts, FWI_OP_ILLUMINATION, v, nullptr, illum, ws, ws_bytes,
+        return forward3(grid, geom, opts, FWI_OP_ILLUMINATION, v, nullptr, illum, nullptr, ws, ws_bytes,
                         static_cast<cudaStream_t>(stream));
     }
     Plan pl;
@@ -1839,6 +1876,11 @@ fwi_status fwi_offset_hessian_diag(const fwi_grid *grid, const fwi_geometry *geo
                                    const float *v, float *offh, void *ws, size_t ws_bytes, void *stream)
 {
     Trace trace_("fwi_offset_hessian_diag");
+    if (grid && grid->ndim == 3) {
+        if (!v || !offh) return fail(FWI_ERR_INVALID_ARG, "v or offh is NULL");
+        return forward3(grid, geom, opts, FWI_OP_OFFSET_HESSIAN, v, nullptr, nullptr, offh, ws, ws_bytes,
+                        static_cast<cudaStream_t>(stream));
+    }
     Plan pl;
     fwi_status s = make_plan(grid, geom, opts, FWI_OP_OFFSET_HESSIAN, true, pl);
     if (s != FWI_OK) return s;
@@ -1864,26 +1906,36 @@ fwi_status fwi_precondition(const fwi_grid *grid, const float *grad, const float
                             float eps, float *out, void *ws, size_t ws_bytes, void *stream)
 {
     Trace trace_("fwi_precondition");
+    // elementwise over the physical grid: in 3-D only the status word and
+    // the maximum live in the workspace
+    const bool three = grid && grid->ndim == 3;
     Plan pl;
-    fwi_status s = make_plan(grid, nullptr, nullptr, FWI_OP_PRECONDITION, false, pl);
+    Plan3 p3;
+    fwi_status s = three ? check_grid3(grid) : make_plan(grid, nullptr, nullptr, FWI_OP_PRECONDITION, false, pl);
     if (s != FWI_OK) return s;
+    if (three) {
+        p3.scal = Part{0, ALIGN};
+        p3.total = ALIGN;
+    }
     if (!grad || !scale || !out) return fail(FWI_ERR_INVALID_ARG, "grad, scale or out is NULL");
     if (kind != FWI_PRECOND_ILLUM && kind != FWI_PRECOND_OFFSET) return fail(FWI_ERR_INVALID_ARG, "kind=%d", kind);
     if (kind == FWI_PRECOND_OFFSET && (hmax < 0 || hmax > FWI_HMAX_LIMIT))
         return fail(FWI_ERR_INVALID_ARG, "hmax=%d outside 0..%d", hmax, FWI_HMAX_LIMIT);
     if (!(eps > 0.f)) return fail(FWI_ERR_INVALID_ARG, "eps must be > 0");
-    if ((s = check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
+    if ((s = three ? check_ws3(p3, ws, ws_bytes) : check_ws(pl, ws, ws_bytes)) != FWI_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     begin_call(st);
     prof_record(1, st);
     prof_record(2, st);
+    const Part &scal = three ? p3.scal : pl.scal;
+    const long long nphys = three ? (long long)grid->nz * grid->ny * grid->nx : (long long)pl.L.nz * pl.L.nx;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(at<char>(ws, pl.scal), 0, pl.scal.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
-    if ((e = launch_precond(pl.L, grad, scale, kind, hmax, eps, out, at<unsigned>(ws, pl.scal, 12), st)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(at<char>(ws, scal), 0, scal.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_precond_n(nphys, grad, scale, kind, hmax, eps, out, at<unsigned>(ws, scal, 12), st)) != cudaSuccess)
         return cuda_fail(e, "precondition kernel");
     t_launch[2] += 2;
     prof_record(3, st);
-    return finish(pl, ws, st);
+    return three ? finish3(p3, ws, st) : finish(pl, ws, st);
 }
 
 fwi_status fwi_misfit(const fwi_grid *grid, const fwi_geometry *geom, const fwi_options *opts, const float *v,
@@ -2252,8 +2304,8 @@ fwi_status autotune3(const fwi_grid *grid, const fwi_geometry *geom, const fwi_o
             }
             float ms = 0.f;
             for (int rep = 0; rep < 2 && s == FWI_OK; ++rep) { // first pass warms up
-                s = b == 0 ? run_forward3(p, geom, 0, p.G, ws, nullptr, nullptr, 0, false, st, 1, 1 + nlev, ev.a,
-                                          ev.b)
+                s = b == 0 ? run_forward3(p, geom, 0, p.G, ws, nullptr, nullptr, nullptr, 0, false, st, 1,
+                                          1 + nlev, ev.a, ev.b)
                            : time_backward3(p, geom, ws, nlev, st, ev.a, ev.b);
                 if (s == FWI_OK && (e = cudaEventSynchronize(ev.b)) != cudaSuccess) s = cuda_fail(e, "sync");
                 if (s == FWI_OK) cudaEventElapsedTime(&ms, ev.a, ev.b);

@@ -506,6 +506,75 @@ struct Variant3 {
     int occ;          // resident CTAs per SM (occupancy calculator)
     const void *fn_q; // forward step: the instance that also stores q^n
 };
+
+// --------------------------------------------------------- offset Hessian
+// The offset-Hessian diagonal of one 3-D time level (Sec. 3, horizontal
+// offsets along x): acc[h][i][k][j] += sum_s u_s^n(x + h e_x) u_s^n(x - h e_x),
+// h = 0..hmax, at the physical points; u = 0 outside the padded grid (the
+// ghost columns, at least 16 on each side, are never written). Launched
+// after the forward step of each level, which leaves u^n in place. One
+// thread per 4 consecutive x points of one (z, y) row; it walks the shots of
+// the group with its NHC x 4 sums in registers and reads each shot's x window
+// (its 4 points and W0 columns on each side) from global memory: in 16-byte
+// pieces when the window starts on a 16-byte boundary (AL: sponge width a
+// multiple of 4), else one float at a time. Neighbouring threads' windows
+// overlap, so the re-reads hit L1; the field itself is read once per level.
+template <int NHC, bool AL>
+__global__ void __launch_bounds__(TPB) k_offh3d_level(const float *__restrict__ u, const Lay3D L, int ns, int hmax,
+                                                      float *__restrict__ acc)
+{
+    constexpr int W0 = AL ? (NHC - 1 + 3) / 4 * 4 : NHC - 1; // window columns left of the 4 points
+    constexpr int NWIN = 4 + 2 * W0;
+    const int nxq = (L.nx + 3) / 4;
+    const long long nrow = (long long)L.nz * L.ny;
+    const long long t = (long long)blockIdx.x * TPB + threadIdx.x;
+    if (t >= nrow * nxq) return;
+    const long long row = t / nxq;
+    const int j0 = 4 * (int)(t - row * nxq);
+    const int i = (int)(row / L.ny), k = (int)(row - (long long)i * L.ny);
+    const float *base = u + fidx3(L, i + L.P, k + L.P, j0 + L.P - W0);
+    float s4[NHC][4];
+#pragma unroll
+    for (int h = 0; h < NHC; ++h)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) s4[h][p] = 0.f;
+#pragma unroll 1
+    for (int s = 0; s < ns; ++s) {
+        const float *w0 = base + (long long)s * L.fstride;
+        float w[NWIN];
+        if (AL) {
+#pragma unroll
+            for (int q = 0; q < NWIN / 4; ++q) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(w0) + q);
+                w[4 * q] = v.x;
+                w[4 * q + 1] = v.y;
+                w[4 * q + 2] = v.z;
+                w[4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < NWIN; ++e) w[e] = __ldg(w0 + e);
+        }
+#pragma unroll
+        for (int h = 0; h < NHC; ++h)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) s4[h][p] = fmaf(w[W0 + p + h], w[W0 + p - h], s4[h][p]);
+    }
+    const long long nphys = nrow * L.nx, o = row * L.nx + j0;
+    const bool vec = (L.nx & 3) == 0;
+#pragma unroll
+    for (int h = 0; h < NHC; ++h) {
+        if (h > hmax) break;
+        float *d = acc + h * nphys + o;
+        if (vec) {
+            red_add4(d, s4[h][0], s4[h][1], s4[h][2], s4[h][3]);
+        } else {
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+                if (j0 + p < L.nx) atomicAdd(d + p, s4[h][p]);
+        }
+    }
+}
 #define V3F(ST, MINB) \
     {256 + (ST) * FWD3_STAGE_F * 4, (const void *)k_fwd3d<ST, MINB, false>, 0, (const void *)k_fwd3d<ST, MINB, true>}
 #define V3B(ST, MINB) {256 + (ST) * BWD3_STAGE_F * 4, (const void *)k_bwd3d<ST, MINB>, 0, nullptr}
@@ -658,6 +727,36 @@ cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, int variant, cudaS
     if (variant < 0 || variant >= NV3B) return cudaErrorInvalidValue;
     const Variant3 &v = g_var3b[variant];
     return launch3(v.fn, v, a, t, st);
+}
+
+namespace {
+template <int NHC>
+void offh3_instance(bool al, unsigned blocks, const float *u, const Lay3D &L, int ns, int hmax, float *acc,
+                    cudaStream_t st)
+{
+    if (al)
+        k_offh3d_level<NHC, true><<<blocks, TPB, 0, st>>>(u, L, ns, hmax, acc);
+    else
+        k_offh3d_level<NHC, false><<<blocks, TPB, 0, st>>>(u, L, ns, hmax, acc);
+}
+} // namespace
+
+cudaError_t launch_offh3d(const float *u, const Lay3D &L, int ns, int hmax, float *acc, cudaStream_t st)
+{
+    if (hmax < 0 || hmax > HMAX_LIMIT || ns < 0 || !u || !acc) return cudaErrorInvalidValue;
+    const long long n = (long long)L.nz * L.ny * ((L.nx + 3) / 4);
+    if (n == 0 || ns == 0) return cudaSuccess;
+    const long long blocks = (n + TPB - 1) / TPB;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const bool al = (L.P & 3) == 0;
+    // compiled offset counts: 4 (hmax <= 3), 11 (<= 10), 13 (<= 12)
+    if (hmax <= 3)
+        offh3_instance<4>(al, (unsigned)blocks, u, L, ns, hmax, acc, st);
+    else if (hmax <= 10)
+        offh3_instance<11>(al, (unsigned)blocks, u, L, ns, hmax, acc, st);
+    else
+        offh3_instance<13>(al, (unsigned)blocks, u, L, ns, hmax, acc, st);
+    return cudaGetLastError();
 }
 
 bool encode_field_map3(CUtensorMap *map, const float *base, const Lay3D &L, int nfields, int bx, int by)

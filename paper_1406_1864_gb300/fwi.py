@@ -430,7 +430,8 @@ def gauss_newton_hvp(grid: Grid, geom: Geometry, v: torch.Tensor, dv: torch.Tens
 
 def offset_hessian_diag(grid: Grid, geom: Geometry, v: torch.Tensor, opts: Options, *, ws=None,
                         stream=None) -> torch.Tensor:
-    """fwi_offset_hessian_diag: [hmax+1, nz, nx] source-side offset-Hessian diagonal."""
+    """fwi_offset_hessian_diag: [hmax+1, nz, nx] (3-D: [hmax+1, nz, ny, nx]) source-side
+    offset-Hessian diagonal, offsets along x."""
     _dev(v, "v", grid.shape)
     out = torch.empty((opts.hmax + 1,) + grid.shape, dtype=torch.float32, device=v.device)
     buf, nb = _ws(ws, workspace_bytes(grid, geom, opts, "offset_hessian"))

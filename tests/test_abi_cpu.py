@@ -339,9 +339,10 @@ def test_batch_workspace_and_errors(lib):
 
 def test_3d_workspace_and_options(lib):
     """3-D plans: snapshot checkpoints required for gradients and for forward
-    modelling that keeps checkpoints (all shots in one group), no offset
-    Hessian; shot groups bound the workspace (one group's fields and
-    snapshots); forward modelling needs no checkpoints."""
+    modelling that keeps checkpoints (all shots in one group); the offset
+    Hessian (gradients, its diagonal) adds its hmax + 1 sums of the physical
+    grid and needs hmax >= 0; shot groups bound the workspace (one group's
+    fields and snapshots); forward modelling needs no checkpoints."""
     from paper_1406_1864_gb300 import _lib as L
     g = L.FwiGrid(3, 20, 24, 28, 10.0, 1e-3, 100, 8, 3000.0, 0.05)
     ns, nrec = 4, 6
@@ -365,7 +366,13 @@ def test_3d_workspace_and_options(lib):
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[1] < one
     st, fw = ws_bytes(lib, g, ge, o, L.FWI_OP_FORWARD)
     assert st == L.FWI_OK and fw < one
+    st, plain = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
+    nphys = 20 * 24 * 28
     o.hmax = 2
+    st, with_h = ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)
+    assert st == L.FWI_OK, lib.fwi_last_error()
+    assert with_h - plain == -(-3 * nphys * 4 // 256) * 256
+    o.hmax = 13
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[0] == L.FWI_ERR_INVALID_ARG
     o.hmax, o.precond = -1, L.FWI_PRECOND_OFFSET
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[0] == L.FWI_ERR_INVALID_ARG
@@ -379,6 +386,21 @@ def test_3d_workspace_and_options(lib):
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_FORWARD_SAVE)[0] == L.FWI_ERR_INVALID_ARG
     o.ckpt = L.FWI_CKPT_SNAPSHOT
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_OFFSET_HESSIAN)[0] == L.FWI_ERR_INVALID_ARG
+    assert b"hmax >= 0" in lib.fwi_last_error()
+    o.hmax = 3
+    st, oh = ws_bytes(lib, g, ge, o, L.FWI_OP_OFFSET_HESSIAN)
+    assert st == L.FWI_OK, lib.fwi_last_error()
+    assert oh < fs  # no snapshots
+    o.hmax = -1
+    # the elementwise division: status word and maximum only
+    assert ws_bytes(lib, g, None, None, L.FWI_OP_PRECONDITION) == (L.FWI_OK, 256)
+    one_f = ctypes.c_void_p(256)
+    st = lib.fwi_precondition(ctypes.byref(g), None, one_f, L.FWI_PRECOND_OFFSET, 2, ctypes.c_float(1e-3), one_f,
+                              None, 0, None)
+    assert st == L.FWI_ERR_INVALID_ARG and b"NULL" in lib.fwi_last_error()
+    st = lib.fwi_precondition(ctypes.byref(g), one_f, one_f, L.FWI_PRECOND_OFFSET, 13, ctypes.c_float(1e-3), one_f,
+                              None, 0, None)
+    assert st == L.FWI_ERR_INVALID_ARG and b"hmax" in lib.fwi_last_error()
     o.shot_group = -1
     assert ws_bytes(lib, g, ge, o, L.FWI_OP_GRADIENT)[0] == L.FWI_ERR_INVALID_ARG
 

@@ -104,8 +104,10 @@ def test_3d_errors(torch_cuda, case):
     p, g, grid, geom, v, d, d_true, ref = case
     with pytest.raises(_lib.FwiError):  # sponge checkpoints are 2-D only
         fwi.adjoint_gradient(grid, geom, v, d, fwi.Options())
-    with pytest.raises(_lib.FwiError):  # the offset Hessian is 2-D only
-        fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot", hmax=2, precond="illum"))
+    with pytest.raises(_lib.FwiError):  # offsets 0..12 only
+        fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot", hmax=13, precond="illum"))
+    with pytest.raises(_lib.FwiError):  # the offset-Hessian diagonal needs hmax >= 0
+        fwi.offset_hessian_diag(grid, geom, v, fwi.Options(hmax=-1))
     fast = v.clone()
     fast[3, 4, 5] = 9000.0
     with pytest.raises(_lib.FwiError) as e:
@@ -113,6 +115,78 @@ def test_3d_errors(torch_cuda, case):
     assert e.value.status == _lib.FWI_ERR_CFL
     again = fwi.adjoint_gradient(grid, geom, v, d, fwi.Options(ckpt="snapshot"))
     assert np.isfinite(again["grad"].cpu().numpy()).all()
+
+
+def problem3h(sponge, nx):
+    """The ragged grid with another sponge width and nx: sponge 8 and nx 24
+    put every offset-Hessian window on a 16-byte boundary and every row of
+    sums on one (the vector paths), sponge 6 and nx 26 neither."""
+    p = W.dipping3d(nz=18, ny=21, nx=nx, dx=10.0, dt=8e-4, nt=150, ns=3, rec_step=3, f0=15.0, seed=3,
+                    sponge=sponge)
+    src = p.src.copy()
+    src[-1] = [17, 20, nx - 1]  # a source in the bottom corner
+    p.src = src
+    return p
+
+
+@pytest.fixture(scope="module", params=[(6, 26), (8, 24)], ids=["unaligned", "aligned"])
+def case_h(request, torch_cuda, oracle_mod):
+    """Oracle gradient with the offset Hessian at hmax 12 and both
+    preconditioners, on the grid of problem3h."""
+    torch = torch_cuda
+    from paper_1406_1864_gb300 import fwi
+    p = problem3h(*request.param)
+    g = oracle_mod.Grid.of(p)
+    w64 = p.wavelet.astype(np.float64)
+    d_true = oracle_mod.forward(g, p.v_true, p.src, p.rec, w64)["seis"]
+    ref = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w64, d_true.astype(np.float32).astype(np.float64),
+                                  hmax=12)
+    grid, geom = fwi.from_problem(p)
+    v = torch.as_tensor(np.ascontiguousarray(p.v_init), device="cuda")
+    d = torch.as_tensor(d_true.astype(np.float32), device="cuda")
+    return p, grid, geom, v, d, ref
+
+
+@pytest.mark.parametrize("hmax", [0, 3, 7, 12])
+def test_3d_offset_hessian_entry_point(torch_cuda, case_h, hmax):
+    """fwi_offset_hessian_diag on 3-D grids (Sec. 3, offsets along x): every
+    offset against the oracle (1e-4) for each compiled offset count (4, 11,
+    13), H(x, 0) against the oracle's illumination, in shot groups of 2."""
+    from paper_1406_1864_gb300 import fwi
+    p, grid, geom, v, d, ref = case_h
+    H = fwi.offset_hessian_diag(grid, geom, v, fwi.Options(hmax=hmax, shot_group=2)).cpu().numpy()
+    assert H.shape == (hmax + 1, p.nz, p.ny, p.nx)
+    for h in range(hmax + 1):
+        assert rel(H[h], ref["offh"][h]) <= 1e-4, h
+    assert rel(H[0], ref["illum"]) <= 1e-4
+
+
+def test_3d_gradient_offset_preconditioned(torch_cuda, case_h):
+    """fwi_adjoint_gradient on a 3-D grid with the offset Hessian (hmax 12)
+    and the offset preconditioner (Sec. 3.1): gradient, every offset of H
+    and the preconditioned gradient against the oracle (1e-4), F32
+    snapshots; without the offh output (the sums finished in place) the
+    preconditioned gradient is the same; hess_v6 scales H by 4 / v^6."""
+    import torch
+    from paper_1406_1864_gb300 import fwi
+    p, grid, geom, v, d, ref = case_h
+    o = fwi.Options(ckpt="snapshot", snap="f32", hmax=12, precond="offset", shot_group=2)
+    r = fwi.adjoint_gradient(grid, geom, v, d, o)
+    assert rel(r["grad"].cpu(), ref["grad"]) <= 1e-4
+    for h in range(13):
+        assert rel(r["offh"][h].cpu(), ref["offh"][h]) <= 1e-4, h
+    assert rel(r["grad_pre"].cpu(), ref["grad_pre_offset"]) <= 1e-4
+    r2 = fwi.adjoint_gradient(grid, geom, v, d, o, want_offh=False)
+    assert "offh" not in r2
+    assert rel(r2["grad_pre"].cpu(), r["grad_pre"].cpu()) <= 1e-6
+    pre = fwi.precondition(grid, r["grad"], r["offh"], "offset")  # the entry point on a 3-D grid
+    assert rel(pre.cpu(), r["grad_pre"].cpu()) <= 1e-6
+    o6 = fwi.Options(hmax=3, shot_group=2, hess_v6=True)
+    H6 = fwi.offset_hessian_diag(grid, geom, v, o6)
+    w6 = 4.0 / v.double() ** 6
+    H1 = fwi.offset_hessian_diag(grid, geom, v, fwi.Options(hmax=3, shot_group=2))
+    assert rel(H6.cpu().double(), (H1.double() * w6).cpu()) <= 1e-5
+    assert torch.isfinite(H6).all()
 
 
 N3_FWD, N3_BWD = 3, 4  # compiled 3-D step variants

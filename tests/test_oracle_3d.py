@@ -6,7 +6,8 @@ reference of the 3-D GPU tests:
 * gradient of the OLS and time-integral misfits against central finite
   differences of the misfit along smooth directions and an edge direction
   that reaches the sponge (1e-6);
-* illumination (Eq. 1) against the brute-force sum over the dumped field.
+* illumination (Eq. 1) and the offset-Hessian diagonal (Sec. 3) against
+  brute-force sums over the dumped field.
 A planted mistake (a wrong sign of the adjoint source) fails the FD check.
 """
 import numpy as np
@@ -98,3 +99,31 @@ def test_3d_illumination_brute_force(oracle_mod):
     u = out["dump"]                                   # [nt, nzp, nyp, nxp]
     I = np.sum(u[:, P:P + p.nz, P:P + p.ny, P:P + p.nx] ** 2, axis=0) * p.dt
     assert np.allclose(out["illum"], I, rtol=1e-12, atol=0)
+
+
+def test_3d_offset_hessian_brute_force(oracle_mod):
+    """Sec. 3's offset-Hessian diagonal in 3-D, H(x, h) = sum_n u(x + h e_x)
+    u(x - h e_x) dt, against explicit shifts of the dumped field with zeros
+    outside the padded grid (hmax 6 reaches past the 4-cell sponge); H(x, 0)
+    is the illumination of Eq. 1; the same products shifted along y instead
+    of x do not match (the offset axis is pinned)."""
+    p = tiny3d(ns=1)
+    g = oracle_mod.Grid.of(p)
+    P, hmax = p.sponge, 6
+    out = oracle_mod.forward(g, p.v_init, p.src, p.rec, p.wavelet, illum=True, hmax=hmax, dump_shot=0)
+    u = out["dump"]                                   # [nt, nzp, nyp, nxp]
+    Z = hmax
+    up = np.pad(u, ((0, 0), (0, 0), (Z, Z), (Z, Z)))  # zero outside the padded grid along y and x
+    zs = slice(P, P + p.nz)
+
+    def at(dy, dx):
+        return up[:, zs, P + Z + dy:P + Z + dy + p.ny, P + Z + dx:P + Z + dx + p.nx]
+
+    H = out["offh"]
+    assert H.shape == (hmax + 1, p.nz, p.ny, p.nx)
+    for h in range(hmax + 1):
+        ref = np.sum(at(0, h) * at(0, -h), axis=0) * p.dt
+        assert np.allclose(H[h], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max()), h
+    assert np.allclose(H[0], out["illum"], rtol=1e-12, atol=0)
+    wrong = np.sum(at(2, 0) * at(-2, 0), axis=0) * p.dt
+    assert np.abs(wrong - H[2]).max() > 1e-2 * np.abs(H[2]).max()
