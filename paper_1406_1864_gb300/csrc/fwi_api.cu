@@ -1258,6 +1258,7 @@ fwi_status run_forward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, 
     if ((s = maps3(pl, at<float>(ws, pl.c2), 1, nullptr, &a.tm_c2)) != FWI_OK) return s;
     if ((s = maps3(pl, at<float>(ws, pl.damp), 1, nullptr, &a.tm_damp)) != FWI_OK) return s;
     if (n_end < 0) n_end = pl.nt;
+    if (acc_h && (n_begin != 0 || n_end != pl.nt)) return fail(FWI_ERR_INVALID_ARG, "offset-Hessian sums need every level");
     if (ea && (e = cudaEventRecord(ea, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     for (int n = n_begin; n < n_end; ++n) {
         if (save && n % pl.K == 0 && n <= pl.nt - 2)
@@ -1272,9 +1273,12 @@ fwi_status run_forward3(const Plan3 &pl, const fwi_geometry *ge, int s0, int g, 
         a.c.sched = at<int>(ws, pl.sched) + n;
         if ((e = launch_fwd3d(a, pl.tf, pl.vf, st)) != cudaSuccess) return cuda_fail(e, "3-D forward step");
         t_launch[0]++;
-        // u^n stays in U[n & 1] until step n + 1 overwrites it (u^0 = 0 adds nothing)
-        if (acc_h && n > 0) {
-            if ((e = launch_offh3d(U[n & 1], pl.L, g, pl.hmax, acc_h, st)) != cudaSuccess)
+        // after an even step n the buffers hold u^n (overwritten by step n + 1)
+        // and u^{n+1} (written by step n when n <= nt - 2): both levels are
+        // summed in one launch; u^0 = 0 adds nothing
+        if (acc_h && n % 2 == 0) {
+            const float *lo = n > 0 ? U[n & 1] : nullptr, *hi = n + 1 <= pl.nt - 1 ? U[(n + 1) & 1] : nullptr;
+            if ((e = launch_offh3d(lo, hi, pl.L, g, pl.hmax, acc_h, st)) != cudaSuccess)
                 return cuda_fail(e, "3-D offset-Hessian sums");
             t_launch[0]++;
         }

@@ -21,8 +21,10 @@ Tiling3 make_tiling3(const Lay3D &L, int ns, bool backward, int variant, int nse
 bool encode_field_map3(CUtensorMap *map, const float *base, const Lay3D &L, int nfields, int bx, int by);
 cudaError_t launch_fwd3d(const Fwd3Args &a, const Tiling3 &t, int variant, cudaStream_t st);
 cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, int variant, cudaStream_t st);
-// offset-Hessian sums of one 3-D level: acc[h][x] += sum_s u_s(x + h e_x) u_s(x - h e_x), h <= hmax
-cudaError_t launch_offh3d(const float *u, const Lay3D &L, int ns, int hmax, float *acc, cudaStream_t st);
+// offset-Hessian sums of up to two 3-D levels (u0, u1; null: skipped):
+// acc[h][x] += sum_levels sum_s u_s(x + h e_x) u_s(x - h e_x), h <= hmax
+cudaError_t launch_offh3d(const float *u0, const float *u1, const Lay3D &L, int ns, int hmax, float *acc,
+                          cudaStream_t st);
 cudaError_t launch_prep3d(const Lay3D &L, const float *v, float *c2, float *damp, float cfl_limit, int *status,
                           cudaStream_t st);
 cudaError_t launch_fold_grad3d(const Lay3D &L, const float *acc, const float *v, float *grad, cudaStream_t st);

@@ -511,67 +511,126 @@ struct Variant3 {
 // The offset-Hessian diagonal of one 3-D time level (Sec. 3, horizontal
 // offsets along x): acc[h][i][k][j] += sum_s u_s^n(x + h e_x) u_s^n(x - h e_x),
 // h = 0..hmax, at the physical points; u = 0 outside the padded grid (the
-// ghost columns, at least 16 on each side, are never written). Launched
-// after the forward step of each level, which leaves u^n in place. One
-// thread per 4 consecutive x points of one (z, y) row; it walks the shots of
-// the group with its NHC x 4 sums in registers and reads each shot's x window
-// (its 4 points and W0 columns on each side) from global memory: in 16-byte
-// pieces when the window starts on a 16-byte boundary (AL: sponge width a
-// multiple of 4), else one float at a time. Neighbouring threads' windows
-// overlap, so the re-reads hit L1; the field itself is read once per level.
-template <int NHC, bool AL>
-__global__ void __launch_bounds__(TPB) k_offh3d_level(const float *__restrict__ u, const Lay3D L, int ns, int hmax,
-                                                      float *__restrict__ acc)
+// ghost columns, at least 16 on each side, are never written). One launch
+// sums up to two levels (u0, u1; a null pointer is skipped): the forward
+// step of an even level n leaves u^n and u^{n+1} in its two buffers, so the
+// sums of both go out in one pass over the accumulators, whose read and
+// write per launch (hmax + 1 planes of the model) would otherwise outweigh
+// the fields of a few shots.
+// The physical grid is taken as nz ny rows of nx points. A CTA owns 8
+// consecutive rows x 64 columns: it copies the rows of SPS shots, with 12
+// columns on each side, into shared memory by cp.async (16-byte pieces when
+// the sponge width is a multiple of 4, else 4-byte ones), all shots' copies
+// in flight together, then each thread forms the products of its 4 points of
+// one row from its x window, with its NHC x 4 sums in registers across the
+// shots, and adds them with one reduction per offset (a vector one when the
+// row of 4 starts on a 16-byte boundary).
+constexpr int OH3_W = HMAX_LIMIT;          // staged columns on each side of the tile
+constexpr int OH3_RW = TX + 2 * OH3_W;     // floats of one staged row
+constexpr int OH3_NP = 8 * (OH3_RW / 4);   // 16-byte pieces of one shot's 8 rows
+constexpr int OH3_SPS = 4;                 // shots staged per pass
+
+__device__ __forceinline__ void oh3_cp16(void *dst, const void *src)
 {
-    constexpr int W0 = AL ? (NHC - 1 + 3) / 4 * 4 : NHC - 1; // window columns left of the 4 points
-    constexpr int NWIN = 4 + 2 * W0;
-    const int nxq = (L.nx + 3) / 4;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void oh3_cp4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+template <int NHC>
+__global__ void __launch_bounds__(TPB) k_offh3d_level(const float *__restrict__ u0, const float *__restrict__ u1,
+                                                      const Lay3D L, int ns, int hmax, float *__restrict__ acc)
+{
+    static_assert(NHC - 1 <= OH3_W, "window wider than the staged columns");
+    static_assert(OH3_NP <= 2 * TPB, "two pieces per thread and shot");
+    __shared__ __align__(16) float sm[OH3_SPS][8 * OH3_RW];
     const long long nrow = (long long)L.nz * L.ny;
-    const long long t = (long long)blockIdx.x * TPB + threadIdx.x;
-    if (t >= nrow * nxq) return;
-    const long long row = t / nxq;
-    const int j0 = 4 * (int)(t - row * nxq);
-    const int i = (int)(row / L.ny), k = (int)(row - (long long)i * L.ny);
-    const float *base = u + fidx3(L, i + L.P, k + L.P, j0 + L.P - W0);
+    const int ntx = (L.nx + TX - 1) / TX;
+    const long long r0 = (long long)(blockIdx.x / ntx) * 8;
+    const int x0 = (int)(blockIdx.x % ntx) * TX;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const bool al = (L.P & 3) == 0;
+    // this thread's two pieces: row r of the tile, columns x0 - W + 4 c4 ..;
+    // pieces of rows past the grid or wholly right of nx + W are not copied
+    // (only points outside the model, never stored, read them)
+    long long g[2] = {-1, -1};
+    int d[2] = {0, 0};
+#pragma unroll
+    for (int e2 = 0; e2 < 2; ++e2) {
+        const int e = threadIdx.x + e2 * TPB;
+        if (e >= OH3_NP) break;
+        const int r = e / (OH3_RW / 4), c4 = e - r * (OH3_RW / 4), col = x0 - OH3_W + 4 * c4;
+        if (r0 + r < nrow && col < L.nx + OH3_W) {
+            const int i = (int)((r0 + r) / L.ny), k = (int)(r0 + r - (long long)i * L.ny);
+            g[e2] = fidx3(L, i + L.P, k + L.P, col + L.P);
+            d[e2] = r * OH3_RW + 4 * c4;
+        }
+    }
     float s4[NHC][4];
 #pragma unroll
     for (int h = 0; h < NHC; ++h)
 #pragma unroll
         for (int p = 0; p < 4; ++p) s4[h][p] = 0.f;
+    const int nsb = (ns + OH3_SPS - 1) / OH3_SPS;
 #pragma unroll 1
-    for (int s = 0; s < ns; ++s) {
-        const float *w0 = base + (long long)s * L.fstride;
-        float w[NWIN];
-        if (AL) {
+    for (int pass = 0; pass < 2 * nsb; ++pass) {
+        // passes over (level, block of OH3_SPS shots): level 0's, then level 1's
+        const int l = pass >= nsb, sb = (pass - l * nsb) * OH3_SPS;
+        const float *u = l ? u1 : u0;
+        if (u == nullptr) continue; // uniform across the CTA
+        const int nq = min(OH3_SPS, ns - sb);
+        for (int q = 0; q < nq; ++q) {
+            const float *src = u + (long long)(sb + q) * L.fstride;
 #pragma unroll
-            for (int q = 0; q < NWIN / 4; ++q) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(w0) + q);
-                w[4 * q] = v.x;
-                w[4 * q + 1] = v.y;
-                w[4 * q + 2] = v.z;
-                w[4 * q + 3] = v.w;
+            for (int e2 = 0; e2 < 2; ++e2) {
+                if (g[e2] < 0) continue;
+                if (al) {
+                    oh3_cp16(&sm[q][d[e2]], src + g[e2]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) oh3_cp4(&sm[q][d[e2] + c], src + g[e2] + c);
+                }
             }
-        } else {
-#pragma unroll
-            for (int e = 0; e < NWIN; ++e) w[e] = __ldg(w0 + e);
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        for (int q = 0; q < nq; ++q) {
+            const float *row = &sm[q][ty * OH3_RW + 4 * tx]; // columns x - W .. x + 3 + W
+            float w[4 + 2 * OH3_W];
 #pragma unroll
-        for (int h = 0; h < NHC; ++h)
+            for (int c = 0; c < (4 + 2 * OH3_W) / 4; ++c) {
+                const float4 t4 = lds4(row + 4 * c);
+                w[4 * c] = t4.x;
+                w[4 * c + 1] = t4.y;
+                w[4 * c + 2] = t4.z;
+                w[4 * c + 3] = t4.w;
+            }
 #pragma unroll
-            for (int p = 0; p < 4; ++p) s4[h][p] = fmaf(w[W0 + p + h], w[W0 + p - h], s4[h][p]);
+            for (int h = 0; h < NHC; ++h)
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+                    s4[h][p] = fmaf(w[OH3_W + p + h], w[OH3_W + p - h], s4[h][p]);
+        }
+        __syncthreads(); // the next pass overwrites the rows
     }
+    const long long row = r0 + ty;
+    const int j0 = x0 + 4 * tx;
+    if (row >= nrow || j0 >= L.nx) return;
     const long long nphys = nrow * L.nx, o = row * L.nx + j0;
     const bool vec = (L.nx & 3) == 0;
 #pragma unroll
     for (int h = 0; h < NHC; ++h) {
         if (h > hmax) break;
-        float *d = acc + h * nphys + o;
+        float *dst = acc + h * nphys + o;
         if (vec) {
-            red_add4(d, s4[h][0], s4[h][1], s4[h][2], s4[h][3]);
+            red_add4(dst, s4[h][0], s4[h][1], s4[h][2], s4[h][3]);
         } else {
 #pragma unroll
             for (int p = 0; p < 4; ++p)
-                if (j0 + p < L.nx) atomicAdd(d + p, s4[h][p]);
+                if (j0 + p < L.nx) atomicAdd(dst + p, s4[h][p]);
         }
     }
 }
@@ -729,33 +788,21 @@ cudaError_t launch_bwd3d(const Bwd3Args &a, const Tiling3 &t, int variant, cudaS
     return launch3(v.fn, v, a, t, st);
 }
 
-namespace {
-template <int NHC>
-void offh3_instance(bool al, unsigned blocks, const float *u, const Lay3D &L, int ns, int hmax, float *acc,
-                    cudaStream_t st)
+cudaError_t launch_offh3d(const float *u0, const float *u1, const Lay3D &L, int ns, int hmax, float *acc,
+                          cudaStream_t st)
 {
-    if (al)
-        k_offh3d_level<NHC, true><<<blocks, TPB, 0, st>>>(u, L, ns, hmax, acc);
-    else
-        k_offh3d_level<NHC, false><<<blocks, TPB, 0, st>>>(u, L, ns, hmax, acc);
-}
-} // namespace
-
-cudaError_t launch_offh3d(const float *u, const Lay3D &L, int ns, int hmax, float *acc, cudaStream_t st)
-{
-    if (hmax < 0 || hmax > HMAX_LIMIT || ns < 0 || !u || !acc) return cudaErrorInvalidValue;
-    const long long n = (long long)L.nz * L.ny * ((L.nx + 3) / 4);
-    if (n == 0 || ns == 0) return cudaSuccess;
-    const long long blocks = (n + TPB - 1) / TPB;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    const bool al = (L.P & 3) == 0;
+    if (hmax < 0 || hmax > HMAX_LIMIT || ns < 0 || !acc) return cudaErrorInvalidValue;
+    const long long tiles = ((long long)L.nz * L.ny + 7) / 8 * ((L.nx + TX - 1) / TX);
+    if (tiles == 0 || ns == 0 || (!u0 && !u1)) return cudaSuccess;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)tiles;
     // compiled offset counts: 4 (hmax <= 3), 11 (<= 10), 13 (<= 12)
     if (hmax <= 3)
-        offh3_instance<4>(al, (unsigned)blocks, u, L, ns, hmax, acc, st);
+        k_offh3d_level<4><<<blocks, TPB, 0, st>>>(u0, u1, L, ns, hmax, acc);
     else if (hmax <= 10)
-        offh3_instance<11>(al, (unsigned)blocks, u, L, ns, hmax, acc, st);
+        k_offh3d_level<11><<<blocks, TPB, 0, st>>>(u0, u1, L, ns, hmax, acc);
     else
-        offh3_instance<13>(al, (unsigned)blocks, u, L, ns, hmax, acc, st);
+        k_offh3d_level<13><<<blocks, TPB, 0, st>>>(u0, u1, L, ns, hmax, acc);
     return cudaGetLastError();
 }
 
