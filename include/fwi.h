@@ -104,9 +104,9 @@ enum {
 
 /* Grid and time axis. */
 typedef struct {
-    int ndim;     /* 2                                                        */
+    int ndim;     /* 2, or 3 for the entry points that take 3-D grids        */
     int nz;       /* model rows (depth)                                       */
-    int ny;       /* 1 in 2-D                                                 */
+    int ny;       /* 1 in 2-D; model rows across in 3-D                       */
     int nx;       /* model columns                                            */
     float dx;     /* grid spacing (m), the same on every axis                 */
     float dt;     /* time step (s)                                            */
