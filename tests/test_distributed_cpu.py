@@ -7,7 +7,9 @@ partial sums come from the FP64 oracle for its own shots (no GPU in these
 tests), and the result on every rank must equal the oracle's gradient of all
 shots at once -- the sums over shots of Sec. 2, Eq. 1 and Sec. 3 -- up to the
 order of the FP64 additions. Worlds of 2 ranks with 3 shots (uneven split)
-and of 3 ranks with 2 shots (one rank without shots).
+and of 3 ranks with 2 shots (one rank without shots), and a 3-D model over
+3 ranks with 2 shots and the offset preconditioner ([hmax+1, nz, ny, nx]
+offset Hessians; the rank without shots contributes zeros of that shape).
 """
 import socket
 
@@ -37,12 +39,20 @@ class HostGeometry:
         return HostGeometry(self.src[s0:s1], self.rec[s0:s1], self.wav[s0:s1])
 
 
-def problem(ns):
+def problem(ns, ndim=2):
+    if ndim == 3:
+        return W.dipping3d(nz=8, ny=7, nx=9, dx=10.0, dt=5e-4, nt=70, ns=ns, rec_step=3, f0=20.0, seed=2,
+                           sponge=4)
     return W.dipping(nz=18, nx=26, dx=10.0, dt=1e-3, nt=90, ns=ns, nrec=13, rec_step=2, f0=20.0,
                      seed=4, sponge=5)
 
 
-def worker(rank, world, port, ns, hmax, precond, queue):
+def flat(a, ndim, lead=0):
+    """The oracle's [.., nz, ny, nx] arrays as the library's shapes (2-D: ny dropped)."""
+    return a if ndim == 3 else np.take(a, 0, axis=lead + 1)
+
+
+def worker(rank, world, port, ns, hmax, precond, ndim, queue):
     import torch
     import torch.distributed as dist
 
@@ -53,7 +63,7 @@ def worker(rank, world, port, ns, hmax, precond, queue):
     dist.init_process_group("gloo", rank=rank, world_size=world,
                             init_method=f"tcp://127.0.0.1:{port}")
     try:
-        p = problem(ns)
+        p = problem(ns, ndim)
         g = oracle.Grid.of(p)
         w64 = p.wavelet.astype(np.float64)
         d_all = oracle.forward(g, p.v_true, p.src, p.rec, w64)["seis"]
@@ -64,11 +74,11 @@ def worker(rank, world, port, ns, hmax, precond, queue):
         def compute(grid, sub, v, d_obs, o):
             r = oracle.fwi_gradient(g, v, sub.src, sub.rec, sub.wav, d_obs.numpy(),
                                     hmax=None if o.hmax < 0 else o.hmax)
-            out = {"grad": torch.from_numpy(r["grad"][:, 0, :].copy()),
-                   "illum": torch.from_numpy(r["illum"][:, 0, :].copy()),
+            out = {"grad": torch.from_numpy(flat(r["grad"], ndim).copy()),
+                   "illum": torch.from_numpy(flat(r["illum"], ndim).copy()),
                    "misfit": torch.tensor(r["J"], dtype=torch.float64)}
             if o.hmax >= 0:
-                out["offh"] = torch.from_numpy(r["offh"][:, :, 0, :].copy())
+                out["offh"] = torch.from_numpy(flat(r["offh"], ndim, lead=1).copy())
             return out
 
         def precondition(grid, grad, scale, kind, eps):
@@ -76,7 +86,7 @@ def worker(rank, world, port, ns, hmax, precond, queue):
             return torch.from_numpy(oracle.precondition(grad.numpy(), P, eps))
 
         class G:  # grid stand-in: shape only
-            shape = (p.nz, p.nx)
+            shape = (p.nz, p.ny, p.nx) if ndim == 3 else (p.nz, p.nx)
 
         v = torch.from_numpy(np.ascontiguousarray(p.v_init, dtype=np.float64))
         res = D.sharded_gradient(G(), geom, v, torch.from_numpy(d_all[s0:s1].copy()), opts, rank=rank,
@@ -87,12 +97,12 @@ def worker(rank, world, port, ns, hmax, precond, queue):
         dist.destroy_process_group()
 
 
-def run_world(world, ns, hmax, precond):
+def run_world(world, ns, hmax, precond, ndim=2):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = free_port()
-    procs = [ctx.Process(target=worker, args=(r, world, port, ns, hmax, precond, q)) for r in range(world)]
+    procs = [ctx.Process(target=worker, args=(r, world, port, ns, hmax, precond, ndim, q)) for r in range(world)]
     for pr in procs:
         pr.start()
     out = {}
@@ -126,24 +136,26 @@ def test_shot_range_partitions():
         shot_range(4, 2, 2)
 
 
-@pytest.mark.parametrize("world,ns,hmax,precond", [(2, 3, 2, "offset"), (3, 2, -1, "illum")])
-def test_sharded_gradient_equals_all_shots(oracle_mod, world, ns, hmax, precond):
+@pytest.mark.parametrize("world,ns,hmax,precond,ndim", [(2, 3, 2, "offset", 2), (3, 2, -1, "illum", 2),
+                                                     (3, 2, 3, "offset", 3)])
+def test_sharded_gradient_equals_all_shots(oracle_mod, world, ns, hmax, precond, ndim):
     from paper_1406_1864_gb300.distributed import shot_range
-    out = run_world(world, ns, hmax, precond)
+    out = run_world(world, ns, hmax, precond, ndim)
     for rank, (n, _) in out.items():
         s0, s1 = shot_range(ns, rank, world)
         assert n == s1 - s0
-    p = problem(ns)
+    p = problem(ns, ndim)
     g = oracle_mod.Grid.of(p)
     w64 = p.wavelet.astype(np.float64)
     d_all = oracle_mod.forward(g, p.v_true, p.src, p.rec, w64)["seis"]
     ref = oracle_mod.fwi_gradient(g, p.v_init, p.src, p.rec, w64, d_all,
                                   hmax=None if hmax < 0 else hmax)
     for rank, (_, res) in out.items():
-        assert rel(res["grad"], ref["grad"][:, 0, :]) <= 1e-12, rank
-        assert rel(res["illum"], ref["illum"][:, 0, :]) <= 1e-12, rank
+        assert rel(res["grad"], flat(ref["grad"], ndim)) <= 1e-12, rank
+        assert rel(res["illum"], flat(ref["illum"], ndim)) <= 1e-12, rank
         assert abs(float(res["misfit"]) - ref["J"]) <= 1e-12 * ref["J"], rank
         key = "grad_pre_illum" if precond == "illum" else "grad_pre_offset"
-        assert rel(res["grad_pre"], ref[key][:, 0, :]) <= 1e-12, rank
+        assert rel(res["grad_pre"], flat(ref[key], ndim)) <= 1e-12, rank
         if hmax >= 0:
-            assert rel(res["offh"], ref["offh"][:, :, 0, :]) <= 1e-12, rank
+            assert res["offh"].shape == (hmax + 1,) + flat(ref["grad"], ndim).shape
+            assert rel(res["offh"], flat(ref["offh"], ndim, lead=1)) <= 1e-12, rank
