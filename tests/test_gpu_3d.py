@@ -5,7 +5,10 @@ Small ragged grid (padded 30 x 33 x 38: not a multiple of the 64 x 8
 columns), receivers on the surface grid plus some at depth, on edges and in
 corners. Tolerances as in 2-D: traces 1e-5, gradient / illumination /
 preconditioned gradient 1e-4 with F32 snapshots, 1e-2 with bfloat16 ones;
-shot groups (opts.shot_group) give the all-at-once result.
+shot groups (opts.shot_group) give the all-at-once result. The offset-Hessian
+diagonal (Sec. 3, offsets along x) and the offset-preconditioned gradient
+1e-4, on grids whose sponge width makes the sums' copies 16-byte (sponge 8)
+or 4-byte (sponge 6).
 """
 import numpy as np
 import pytest
